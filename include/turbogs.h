@@ -1,0 +1,240 @@
+/*
+ * turbogs.h -- C ABI of the B300 (sm_103a) hot path of Turbo-GS fitting:
+ * a differentiable tile-based 3D Gaussian splatting rasterizer with dilated
+ * rendering (arXiv 2412.13547, Sec. 3.1), the per-Gaussian densification
+ * statistics it feeds (Sec. 3.3) and a fused Adam step (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named d_* or documented as "device" are CUDA device pointers; the
+ *   caller owns all of them. The library never allocates device memory (scratch
+ *   is passed in, sized by the *_workspace_size queries). GsCamera, GsDilation,
+ *   bg[3] and GsAdamTensor arrays are read on the host at call time.
+ * - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *   default stream) and returns a status: GS_OK, GS_ERR_ARG for a bad argument
+ *   (nothing is launched), GS_ERR_CUDA when a launch failed (gs_last_error()
+ *   gives the CUDA error string of the calling thread).
+ * - Arrays are contiguous, row-major, FP32 unless stated. Per-Gaussian arrays
+ *   have n rows; images are height x width x 3 (HWC).
+ * - Image geometry: an hr image of width x height pixels with pixel centres at
+ *   integer coordinates. A dilation (d, ox, oy) renders the lattice of hr pixels
+ *   (d*u + ox, d*v + oy) as a w_ds x h_ds image, w_ds = ceil((width - ox)/d),
+ *   h_ds = ceil((height - oy)/d), tiled by tile x tile downsampled pixels
+ *   (tiles_x = ceil(w_ds/tile), tiles_y = ceil(h_ds/tile)); tile ids are
+ *   row-major, ty * tiles_x + tx.
+ */
+#ifndef TURBOGS_H
+#define TURBOGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* gs_stream_t; /* cudaStream_t */
+
+enum {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,
+    GS_ERR_CAPACITY = 2,
+    GS_ERR_CUDA = 3,
+    GS_ERR_TIMEOUT = 4
+};
+
+/* Storage type of the SH coefficients (and of Adam's optional shadow copy). */
+enum { GS_DTYPE_F32 = 0, GS_DTYPE_BF16 = 1, GS_DTYPE_F16 = 2 };
+
+/* Pinhole camera (Sec. 3.1 projects with the original, hr focal length).
+ * A world point m maps to camera space t = R m + T (R row-major; x right,
+ * y down, z forward) and to the hr pixel (fx t_x/t_z + cx, fy t_y/t_z + cy).
+ * Gaussians with t_z <= z_near are culled. */
+typedef struct {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float z_near;
+} GsCamera;
+
+/* Dilated rendering (Sec. 3.1): stride d >= 1, offsets 0 <= ox, oy < d.
+ * center_mode 0 bins a Gaussian around the downsampled centre (p - o)/d, the
+ * lattice the offset renders; 1 uses (p - (d-1)/2)/d, Eq. 3 combined with the
+ * pixel map of Eq. 5. Eq. 4: the downsampled radius is r/d. tile is the tile
+ * edge in downsampled pixels (Sec. 3.1 fixes 16; 8 and 32 are accepted). */
+typedef struct {
+    int32_t d, ox, oy, center_mode, tile;
+} GsDilation;
+
+/* Width of the per-Gaussian records below, in floats. */
+#define GS_SPLAT_FLOATS 12
+#define GS_GRAD2D_FLOATS 12
+
+/* Splat record written by gs_project (48 bytes per Gaussian):
+ *   [0] x_hi  [1] y_hi  [2] conic A  [3] conic B
+ *   [4] conic C  [5] opacity  [6] r  [7] g
+ *   [8] b  [9] depth t_z  [10] x_lo  [11] y_lo
+ * The hr image-plane centre is (x_hi + x_lo, y_hi + y_lo), kept as an unevaluated
+ * float-float sum so that pixel offsets at 4K stay accurate. The conic is the
+ * inverse 2D covariance: G = exp(-(A dx^2 + C dy^2)/2 - B dx dy) (Sec. 3, Eq. 1).
+ *
+ * 2D gradient record accumulated by gs_render_bwd (48 bytes per Gaussian):
+ *   [0] dL/dx  [1] dL/dy  [2] dL/dA  [3] dL/dB
+ *   [4] dL/dC  [5] dL/dopacity  [6] dL/dr  [7] dL/dg
+ *   [8] dL/db  [9..11] zero padding                                       */
+
+/* Library version (major*10000 + minor*100 + patch) and the per-thread error. */
+int32_t gs_version(void);
+const char* gs_last_error(void);
+
+/* Size of the downsampled image and of its tile grid (host arithmetic only). */
+int32_t gs_grid(const GsCamera* cam, const GsDilation* dil,
+                int32_t* w_ds, int32_t* h_ds, int32_t* tiles_x, int32_t* tiles_y);
+
+/* ---------------------------------------------------------------------------
+ * gs_project -- Sec. 3 (Sigma = R S S^T R^T, opacity, SH colour) and Sec. 3.1
+ * (EWA projection Sigma' = J W Sigma W^T J^T with the hr focal length plus a
+ * 0.3 px^2 low-pass term, 3-sigma radius r = ceil(3 sqrt(lambda_max)) in hr
+ * pixels, downsampled centre and radius r/d of Eq. 3-4, and the rectangle of
+ * downsampled tiles it touches).
+ *   means (n x 3), log_scales (n x 3, scale = exp), quats (n x 4, (w,x,y,z),
+ *   any norm > 0), opacity_logits (n, opacity = sigmoid), sh (n x K x 3 with
+ *   K = (sh_degree+1)^2, sh_degree <= 3, of type sh_dtype): device inputs.
+ *   Colour = max(0, sum_k Y_k(dir) sh_k + 0.5), dir = unit(mean - camera centre),
+ *   real SH with Condon-Shortley phase, index l*l + l + m.
+ * Outputs (device): splats (n x 12, layout above), radii (n, 0 = culled),
+ *   rects (n x 4: x0, y0, x1, y1 inclusive tile indices; culled: 0, 0, -1, -1),
+ *   tiles_touched (n).
+ * Errors: GS_ERR_ARG for n < 0, a null pointer with n > 0, sh_degree outside
+ *   0..3, a bad dtype, d < 1 or d > 64, offsets outside [0, d), tile not in
+ *   {8, 16, 32}, or a non-positive image size or focal length. */
+int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
+                   const float* means, const float* log_scales, const float* quats,
+                   const float* opacity_logits, const void* sh,
+                   const GsCamera* cam, const GsDilation* dil,
+                   float* splats, int32_t* radii, int32_t* rects, int32_t* tiles_touched,
+                   gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_bin_sort -- the tile-Gaussian pairs of the tile-based rasterizer (Sec. 3,
+ * and the "duplicateWithKeys"/"sortPairs" stages profiled in Sec. 3.1): for
+ * every tile of every Gaussian's rect, the pair (key = tile_id << 32 |
+ * float32 bits of the depth, value = Gaussian index), sorted ascending by
+ * (key, value), and per-tile [start, end) ranges into the sorted values.
+ * Inputs (device): rects, tiles_touched (from gs_project), splats (depth = [9]).
+ * Outputs (device): sorted_ids (capacity entries; the first num_pairs hold the
+ *   Gaussian ids tile by tile, front to back), ranges (tiles_x*tiles_y x 2,
+ *   uint32 start/end), num_pairs (one int64: the pair count K).
+ * No host synchronisation: K is computed and consumed on the device. When
+ *   K > capacity, *num_pairs still receives K, no pair is written beyond
+ *   capacity, every range is set empty (the render then sees no Gaussian) and
+ *   the caller must grow the buffers and call again; K <= 2^31 - 1.
+ * workspace: device scratch of gs_bin_sort_workspace_size(n, capacity,
+ *   tiles_x*tiles_y) bytes, 256-byte aligned; its contents need no init.
+ * Errors: GS_ERR_ARG for bad sizes, null pointers or a short workspace. */
+size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles);
+int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
+                    const float* splats, int32_t tiles_x, int32_t tiles_y,
+                    void* workspace, size_t workspace_bytes, int64_t capacity,
+                    uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
+                    gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_render_fwd -- front-to-back alpha blending (Sec. 3, Eq. 2) of the lattice
+ * pixels of the dilated image (Sec. 3.1: tile lists from the downsampled grid,
+ * Gaussian evaluated at the hr pixel (d*u + ox, d*v + oy), Eq. 5).
+ * Per pixel, walking its tile's list: alpha = min(0.99, opacity * G); entries
+ * with alpha < 1/255 (or a positive exponent) are skipped; the walk stops
+ * before an entry that would take the transmittance below 1e-4; finally
+ * C += T * bg.
+ * Inputs (device): splats, sorted_ids, ranges (from gs_bin_sort). bg: host
+ *   float[3].
+ * Outputs (device): img (h_ds x w_ds x 3), t_final (h_ds x w_ds), last
+ *   (h_ds x w_ds: list position + 1 of the last blended entry, 0 if none),
+ *   counts (nullable, 2 x uint64 accumulated with +=: list entries evaluated
+ *   and entries blended; the caller zeroes it). */
+int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
+                      const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
+                      const float* bg, float* img, float* t_final, uint32_t* last,
+                      unsigned long long* counts, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_loss_l1 -- L1 photometric loss of the rendered lattice pixels against the
+ * hr target sampled at the same pixels (supervision with "corresponding
+ * high-resolution pixels", Sec. 3.1): L = mean |img - target| over h_ds*w_ds*3
+ * values, dL/dimg = sign(img - target) / (3 * h_ds * w_ds) (sign(0) = 0).
+ * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3).
+ * Outputs (device): dl_dimg (h_ds x w_ds x 3), loss (one float, overwritten). */
+int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
+                   const float* target, float* dl_dimg, float* loss, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_render_bwd -- backward of gs_render_fwd. The per-pixel blend state is not
+ * stored: each pixel replays its list back to front from t_final and last,
+ * recovering T_i = T_{i+1} / (1 - alpha_i), and the per-Gaussian gradients of
+ * the pixels of a tile are reduced in registers/shared memory before one set
+ * of atomics per (tile, Gaussian).
+ * Inputs (device): as gs_render_fwd plus t_final, last and dl_dimg.
+ * Output (device): grad2d (n x 12, layout above), accumulated with +=; with
+ *   zero_grad2d != 0 the library first zeroes it on the stream. */
+int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
+                      const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
+                      const float* bg, const float* t_final, const uint32_t* last,
+                      const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
+                      gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_project_bwd -- chain rule of gs_project: from grad2d to the parameter
+ * gradients (overwritten, FP32, same shapes as the parameters; d_sh is
+ * n x K x 3 FP32 whatever sh_dtype is). Culled Gaussians get zero gradients.
+ * With pos_acc, col_acc and count non-null it also performs gs_densify_stats.
+ * Inputs (device): the gs_project inputs, tiles_touched, grad2d. */
+int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
+                       const float* means, const float* log_scales, const float* quats,
+                       const float* opacity_logits, const void* sh,
+                       const GsCamera* cam, const GsDilation* dil,
+                       const int32_t* tiles_touched, const float* grad2d,
+                       float* d_means, float* d_log_scales, float* d_quats,
+                       float* d_opacity_logits, float* d_sh,
+                       float* pos_acc, float* col_acc, int32_t* count,
+                       gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_densify_stats -- position-appearance densification scores (Sec. 3.3): for
+ * every Gaussian with tiles_touched > 0, pos_acc += |(dL/dx, dL/dy)|_2 (hr
+ * pixel units), col_acc += |(dL/dr, dL/dg, dL/db)|_2, count += 1 (device). */
+int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* grad2d,
+                         float* pos_acc, float* col_acc, int32_t* count, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_adam -- one fused Adam step (Kingma & Ba, bias-corrected; Sec. 4.1 trains
+ * with Adam) over up to GS_ADAM_MAX_TENSORS tensors in a single launch:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Each tensor has numel elements in rows of row_width (one row per Gaussian);
+ * with row_mask (device, one byte per row, shared by all tensors) non-null,
+ * rows whose byte is 0 are left untouched ("sparse" Adam over visible
+ * Gaussians). shadow (nullable) receives the updated parameter converted to
+ * shadow_dtype (e.g. the BF16 SH storage the projection reads).
+ * The GsAdamTensor array is read on the host; all its pointers are device. */
+#define GS_ADAM_MAX_TENSORS 8
+typedef struct {
+    float* param;
+    const float* grad;
+    float* m;
+    float* v;
+    void* shadow;
+    int64_t numel;
+    int32_t row_width;
+    int32_t shadow_dtype;
+    float lr;
+    float pad_;
+} GsAdamTensor;
+int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float beta2,
+                float eps, int32_t step, const uint8_t* row_mask, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TURBOGS_H */

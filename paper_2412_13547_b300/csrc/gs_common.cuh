@@ -1,0 +1,238 @@
+// gs_common.cuh -- device-side helpers shared by the turbogs kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/turbogs.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// Constants of the method (Sec. 3 Eq. 2 early-stop rule; Sec. 3.1 low-pass).
+// ---------------------------------------------------------------------------
+constexpr float kLowPass = 0.3f;          // px^2 added to the 2D covariance diagonal
+constexpr float kDiscFloor = 0.1f;        // floor of the eigenvalue discriminant
+constexpr float kAlphaMax = 0.99f;        // alpha clamp
+constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha skip threshold
+constexpr float kTStop = 1e-4f;           // stop before transmittance drops below
+constexpr float kClampFov = 1.3f;         // Jacobian clamp, x the half field of view
+
+// Device copies of the camera and dilation, passed by value to kernels.
+struct Cam {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int width, height;
+    float z_near;
+    float lim_x, lim_y;   // clamp of t_x/t_z, t_y/t_z in the Jacobian
+    float ccx, ccy, ccz;  // camera centre in world space, -R^T T
+};
+
+struct Dil {
+    int d, ox, oy, mode, tile;
+    int w_ds, h_ds, tiles_x, tiles_y;
+};
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (error-free transformations with FMA). Used to carry
+// the hr image-plane centre with ~1e-6 px error at 4K, where plain FP32 loses
+// ~1e-3 px and the steep edge of a small splat turns that into a visible error.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, lo);
+}
+
+// sum_k a_k * b_k + c, accumulated in float-float
+__device__ __forceinline__ ff ff_dot3_add(float a0, float b0, float a1, float b1, float a2, float b2,
+                                          float c)
+{
+    ff acc = two_prod(a0, b0);
+    acc = ff_add(acc, two_prod(a1, b1));
+    acc = ff_add(acc, two_prod(a2, b2));
+    acc = ff_add(acc, ff{c, 0.0f});
+    return acc;
+}
+
+// (a.hi + a.lo) / (b.hi + b.lo) as float-float
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    float q = __fdiv_rn(a.hi, b.hi);
+    float r = __fmaf_rn(-q, b.hi, a.hi);  // exact remainder of the leading term
+    r = __fadd_rn(r, __fsub_rn(a.lo, __fmul_rn(q, b.lo)));
+    float q2 = __fdiv_rn(r, b.hi);
+    return fast_two_sum(q, q2);
+}
+
+// f * (u.hi + u.lo) + c as float-float (f, c exact floats)
+__device__ __forceinline__ ff ff_affine(float f, ff u, float c)
+{
+    ff p = two_prod(f, u.hi);
+    ff s = two_sum(p.hi, c);
+    float lo = __fadd_rn(__fadd_rn(s.lo, p.lo), __fmul_rn(f, u.lo));
+    return two_sum(s.hi, lo);
+}
+
+// Accurate a*d - b*c (Kahan's algorithm with FMA).
+__device__ __forceinline__ float det2(float a, float b, float c, float d)
+{
+    float w = __fmul_rn(b, c);
+    float e = __fmaf_rn(-b, c, w);
+    float f = __fmaf_rn(a, d, -w);
+    return __fadd_rn(f, e);
+}
+
+// ---------------------------------------------------------------------------
+// The per-entry blend arithmetic, with rounding pinned by intrinsics so the
+// forward pass and the backward replay take identical skip/clamp decisions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float splat_power(float dx, float dy, float A, float B, float C)
+{
+    // -(A dx^2 + C dy^2)/2 - B dx dy
+    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+}
+
+__device__ __forceinline__ float splat_alpha_raw(float power, float opacity)
+{
+    return __fmul_rn(opacity, __expf(power));
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics up to degree 3 (Condon-Shortley phase, index
+// l*l + l + m), written as Cartesian polynomials of the unit direction. The
+// normalisation constants follow from sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!).
+// ---------------------------------------------------------------------------
+constexpr float kPi = 3.14159265358979323846f;
+
+struct ShConst {
+    float k0, k1, k2a, k2b, k2c, k3a, k3b, k3c, k3d, k3e;
+};
+
+__device__ __forceinline__ ShConst sh_const()
+{
+    ShConst c;
+    c.k0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+    c.k1 = 0.4886025119029199f;    // sqrt(3/(4 pi))
+    c.k2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+    c.k2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+    c.k2c = 0.5462742152960396f;   // sqrt(15/pi)/4
+    c.k3a = 0.5900435899266435f;   // sqrt(35/(2 pi))/4
+    c.k3b = 2.890611442640554f;    // sqrt(105/pi)/2
+    c.k3c = 0.4570457994644658f;   // sqrt(21/(2 pi))/4
+    c.k3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+    c.k3e = 1.445305721320277f;    // sqrt(105/pi)/4
+    return c;
+}
+
+// Basis values Y[0..(deg+1)^2) at the unit direction (x, y, z).
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y)
+{
+    const ShConst c = sh_const();
+    Y[0] = c.k0;
+    if (deg < 1) return;
+    Y[1] = -c.k1 * y;
+    Y[2] = c.k1 * z;
+    Y[3] = -c.k1 * x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = c.k2a * x * y;
+    Y[5] = -c.k2a * y * z;
+    Y[6] = c.k2b * (2.0f * zz - xx - yy);
+    Y[7] = -c.k2a * x * z;
+    Y[8] = c.k2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -c.k3a * y * (3.0f * xx - yy);
+    Y[10] = c.k3b * x * y * z;
+    Y[11] = -c.k3c * y * (4.0f * zz - xx - yy);
+    Y[12] = c.k3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -c.k3c * x * (4.0f * zz - xx - yy);
+    Y[14] = c.k3e * z * (xx - yy);
+    Y[15] = -c.k3a * x * (xx - 3.0f * yy);
+}
+
+// Gradient of sum_k w_k Y_k(x, y, z) with respect to (x, y, z), for weights w.
+__device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z, const float* w,
+                                             float& gx, float& gy, float& gz)
+{
+    const ShConst c = sh_const();
+    gx = gy = gz = 0.0f;
+    if (deg < 1) return;
+    gx += -c.k1 * w[3];
+    gy += -c.k1 * w[1];
+    gz += c.k1 * w[2];
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    gx += c.k2a * y * w[4] - 2.0f * c.k2b * x * w[6] - c.k2a * z * w[7] + 2.0f * c.k2c * x * w[8];
+    gy += c.k2a * x * w[4] - c.k2a * z * w[5] - 2.0f * c.k2b * y * w[6] - 2.0f * c.k2c * y * w[8];
+    gz += -c.k2a * y * w[5] + 4.0f * c.k2b * z * w[6] - c.k2a * x * w[7];
+    if (deg < 3) return;
+    gx += -6.0f * c.k3a * x * y * w[9] + c.k3b * y * z * w[10] + 2.0f * c.k3c * x * y * w[11]
+          - 6.0f * c.k3d * x * z * w[12] - c.k3c * (4.0f * zz - 3.0f * xx - yy) * w[13]
+          + 2.0f * c.k3e * x * z * w[14] - 3.0f * c.k3a * (xx - yy) * w[15];
+    gy += -3.0f * c.k3a * (xx - yy) * w[9] + c.k3b * x * z * w[10]
+          - c.k3c * (4.0f * zz - xx - 3.0f * yy) * w[11] - 6.0f * c.k3d * y * z * w[12]
+          + 2.0f * c.k3c * x * y * w[13] - 2.0f * c.k3e * y * z * w[14] + 6.0f * c.k3a * x * y * w[15];
+    gz += c.k3b * x * y * w[10] - 8.0f * c.k3c * y * z * w[11]
+          + c.k3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12] - 8.0f * c.k3c * x * z * w[13]
+          + c.k3e * (xx - yy) * w[14];
+}
+
+// SH storage conversions
+__device__ __forceinline__ float load_sh_elem(const void* base, int64_t idx, int dtype)
+{
+    if (dtype == GS_DTYPE_F32) return reinterpret_cast<const float*>(base)[idx];
+    if (dtype == GS_DTYPE_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[idx]);
+    return __half2float(reinterpret_cast<const __half*>(base)[idx]);
+}
+
+// Unit quaternion (w, x, y, z) -> row-major rotation matrix.
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float* R)
+{
+    float xx = x * x, yy = y * y, zz = z * z;
+    float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+    R[0] = 1.0f - 2.0f * (yy + zz); R[1] = 2.0f * (xy - wz);        R[2] = 2.0f * (xz + wy);
+    R[3] = 2.0f * (xy + wz);        R[4] = 1.0f - 2.0f * (xx + zz); R[5] = 2.0f * (yz - wx);
+    R[6] = 2.0f * (xz - wy);        R[7] = 2.0f * (yz + wx);        R[8] = 1.0f - 2.0f * (xx + yy);
+}
+
+}  // namespace gs
+
+// Host-side helpers shared by the API translation units.
+namespace gs_host {
+void set_error(const char* msg);
+int32_t check_launch(const char* what);
+bool make_cam(const GsCamera* in, gs::Cam* out);
+bool make_dil(const GsCamera* cam, const GsDilation* in, gs::Dil* out);
+}  // namespace gs_host

@@ -1,0 +1,595 @@
+// gs_project.cu -- projection forward (Sec. 3, Sec. 3.1 EWA + dilated binning
+// geometry), its backward, and the densification statistics (Sec. 3.3).
+//
+// One thread per Gaussian, 4 warps per block. Each warp first copies the rows
+// of its 32 Gaussians (means, log-scales and the SH block, which is 192 of the
+// 236 bytes per Gaussian at degree 3) from global memory with coalesced 16-byte
+// loads into shared memory, padded to an odd row stride so the per-lane reads
+// that follow are free of bank conflicts.
+#include <cmath>
+
+#include "gs_common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kThreads = 32 * kWarps;
+
+template <int W>
+struct RowStride {
+    static constexpr int value = (W % 2 == 0) ? W + 1 : W;
+};
+
+// Copy rows [g0, g0+32) of a row-major array of W 32-bit words per row into
+// shared memory with row stride S. Full warps use 16-byte loads.
+template <int W, int S>
+__device__ __forceinline__ void warp_stage(const uint32_t* __restrict__ src, int n, int g0,
+                                           uint32_t* __restrict__ dst, int lane)
+{
+    const int rows = min(32, n - g0);
+    const uint32_t* base = src + (int64_t)g0 * W;
+    if (rows == 32 && (W % 4 == 0 || ((reinterpret_cast<uintptr_t>(base) & 15) == 0))) {
+        const uint4* b4 = reinterpret_cast<const uint4*>(base);
+#pragma unroll 4
+        for (int q = lane; q < 8 * W; q += 32) {
+            uint4 v = __ldg(b4 + q);
+            int w0 = 4 * q;
+            dst[((w0 + 0) / W) * S + (w0 + 0) % W] = v.x;
+            dst[((w0 + 1) / W) * S + (w0 + 1) % W] = v.y;
+            dst[((w0 + 2) / W) * S + (w0 + 2) % W] = v.z;
+            dst[((w0 + 3) / W) * S + (w0 + 3) % W] = v.w;
+        }
+    } else {
+        for (int w = lane; w < rows * W; w += 32) dst[(w / W) * S + w % W] = __ldg(base + w);
+    }
+    __syncwarp();
+}
+
+template <int DEG, int DT>
+struct ShLayout {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+    static constexpr int BYTES = K * 3 * (DT == GS_DTYPE_F32 ? 4 : 2);
+    static constexpr bool STAGE = (BYTES % 4) == 0;
+    static constexpr int W = STAGE ? BYTES / 4 : 1;
+    static constexpr int S = RowStride<W>::value;
+    static constexpr int WARP_WORDS = 32 * (3 + 3) + (STAGE ? 32 * S : 0);
+};
+
+template <int DEG, int DT>
+__device__ __forceinline__ void read_sh(const uint32_t* s_sh, const void* sh, int g, int lane,
+                                        float (&c)[16][3])
+{
+    using L = ShLayout<DEG, DT>;
+    if constexpr (L::STAGE) {
+        const uint32_t* row = s_sh + lane * L::S;
+        if constexpr (DT == GS_DTYPE_F32) {
+#pragma unroll
+            for (int k = 0; k < L::K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) c[k][ch] = __uint_as_float(row[3 * k + ch]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < L::K * 3; ++e) {
+                uint32_t wv = row[e >> 1];
+                uint16_t hv = (e & 1) ? (uint16_t)(wv >> 16) : (uint16_t)(wv & 0xffffu);
+                float f;
+                if constexpr (DT == GS_DTYPE_BF16) f = __bfloat162float(__ushort_as_bfloat16(hv));
+                else f = __half2float(__ushort_as_half(hv));
+                c[e / 3][e % 3] = f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < L::K * 3; ++e) c[e / 3][e % 3] = load_sh_elem(sh, (int64_t)g * L::K * 3 + e, DT);
+    }
+}
+
+// Everything the forward projection of one Gaussian computes; the backward
+// recomputes it instead of storing it.
+struct Proj {
+    bool culled;
+    float s[3], qn[4], inv_qnorm, R[9], M[9];
+    float tz, u, v, uc, vc;
+    bool clamp_x, clamp_y;
+    float Tm[6], N[6];
+    float a, b, c, det, A, B, C;
+    int radius;
+    ff px, py;
+    float dir[3], inv_vlen;
+    float rgb_raw[3];
+    float opacity;
+    int4 rect;
+    int tiles;
+};
+
+template <int DEG>
+__device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, const float* mean,
+                                            const float* log_scale, float4 q, float logit,
+                                            const float (&sh)[16][3], Proj& P)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    P.culled = true;
+    P.rect = make_int4(0, 0, -1, -1);
+    P.tiles = 0;
+    P.radius = 0;
+    P.opacity = 1.0f / (1.0f + expf(-logit));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P.s[j] = expf(log_scale[j]);
+    float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    if (!(qn2 > 0.0f)) return;
+    P.inv_qnorm = 1.0f / sqrtf(qn2);
+    P.qn[0] = q.x * P.inv_qnorm; P.qn[1] = q.y * P.inv_qnorm;
+    P.qn[2] = q.z * P.inv_qnorm; P.qn[3] = q.w * P.inv_qnorm;
+    quat_rot(P.qn[0], P.qn[1], P.qn[2], P.qn[3], P.R);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P.M[3 * i + j] = P.R[3 * i + j] * P.s[j];
+
+    // camera space, float-float
+    ff tx = ff_dot3_add(cam.R[0], mean[0], cam.R[1], mean[1], cam.R[2], mean[2], cam.T[0]);
+    ff ty = ff_dot3_add(cam.R[3], mean[0], cam.R[4], mean[1], cam.R[5], mean[2], cam.T[1]);
+    ff tz = ff_dot3_add(cam.R[6], mean[0], cam.R[7], mean[1], cam.R[8], mean[2], cam.T[2]);
+    P.tz = tz.hi;
+    if (!(P.tz > cam.z_near)) return;
+    ff u = ff_div(tx, tz), v = ff_div(ty, tz);
+    P.u = u.hi;
+    P.v = v.hi;
+    P.clamp_x = fabsf(P.u) > cam.lim_x;
+    P.clamp_y = fabsf(P.v) > cam.lim_y;
+    P.uc = P.clamp_x ? copysignf(cam.lim_x, P.u) : P.u;
+    P.vc = P.clamp_y ? copysignf(cam.lim_y, P.v) : P.v;
+
+    // Tm = J W with J = [[fx/tz, 0, -fx uc/tz], [0, fy/tz, -fy vc/tz]]
+    float j00 = cam.fx / P.tz, j02 = -cam.fx * P.uc / P.tz;
+    float j11 = cam.fy / P.tz, j12 = -cam.fy * P.vc / P.tz;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        P.Tm[j] = j00 * cam.R[j] + j02 * cam.R[6 + j];
+        P.Tm[3 + j] = j11 * cam.R[3 + j] + j12 * cam.R[6 + j];
+    }
+    // N = Tm M, Sigma' = N N^T + low-pass
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            P.N[3 * i + k] = P.Tm[3 * i] * P.M[k] + P.Tm[3 * i + 1] * P.M[3 + k] + P.Tm[3 * i + 2] * P.M[6 + k];
+    float a0 = P.N[0] * P.N[0] + P.N[1] * P.N[1] + P.N[2] * P.N[2];
+    float b0 = P.N[0] * P.N[3] + P.N[1] * P.N[4] + P.N[2] * P.N[5];
+    float c0 = P.N[3] * P.N[3] + P.N[4] * P.N[4] + P.N[5] * P.N[5];
+    // det(N N^T) as the sum of squared 2x2 minors (Cauchy-Binet): no cancellation
+    float m01 = det2(P.N[0], P.N[1], P.N[3], P.N[4]);
+    float m02 = det2(P.N[0], P.N[2], P.N[3], P.N[5]);
+    float m12 = det2(P.N[1], P.N[2], P.N[4], P.N[5]);
+    float det0 = m01 * m01 + m02 * m02 + m12 * m12;
+    P.a = a0 + kLowPass;
+    P.b = b0;
+    P.c = c0 + kLowPass;
+    P.det = det0 + kLowPass * (a0 + c0) + kLowPass * kLowPass;
+    if (!(P.det > 0.0f)) return;
+    float inv_det = 1.0f / P.det;
+    P.A = P.c * inv_det;
+    P.B = -P.b * inv_det;
+    P.C = P.a * inv_det;
+    float hd = 0.5f * (P.a - P.c);
+    float disc = hd * hd + P.b * P.b;  // = mid^2 - det, without cancellation
+    float lam = 0.5f * (P.a + P.c) + sqrtf(fmaxf(disc, kDiscFloor));
+    P.radius = (int)ceilf(3.0f * sqrtf(lam));
+
+    P.px = ff_affine(cam.fx, u, cam.cx);
+    P.py = ff_affine(cam.fy, v, cam.cy);
+
+    // downsampled centre (Eq. 3 with the lattice of the offset, or Eq. 3+5 literal)
+    float shx = dil.mode == 0 ? (float)dil.ox : 0.5f * (float)(dil.d - 1);
+    float shy = dil.mode == 0 ? (float)dil.oy : 0.5f * (float)(dil.d - 1);
+    float pdx = __fdiv_rn(__fadd_rn(__fsub_rn(P.px.hi, shx), P.px.lo), (float)dil.d);
+    float pdy = __fdiv_rn(__fadd_rn(__fsub_rn(P.py.hi, shy), P.py.lo), (float)dil.d);
+    float rds = __fdiv_rn((float)P.radius, (float)dil.d);  // Eq. 4
+    float inv_tile = 1.0f / (float)dil.tile;               // exact (power of two)
+    int x0 = (int)floorf(__fmul_rn(__fsub_rn(pdx, rds), inv_tile));
+    int x1 = (int)floorf(__fmul_rn(__fadd_rn(pdx, rds), inv_tile));
+    int y0 = (int)floorf(__fmul_rn(__fsub_rn(pdy, rds), inv_tile));
+    int y1 = (int)floorf(__fmul_rn(__fadd_rn(pdy, rds), inv_tile));
+    x0 = max(x0, 0);
+    y0 = max(y0, 0);
+    x1 = min(x1, dil.tiles_x - 1);
+    y1 = min(y1, dil.tiles_y - 1);
+    if (P.radius <= 0 || x0 > x1 || y0 > y1) return;
+    P.rect = make_int4(x0, y0, x1, y1);
+    P.tiles = (x1 - x0 + 1) * (y1 - y0 + 1);
+    P.culled = false;
+
+    // view-dependent colour
+    float vx = mean[0] - cam.ccx, vy = mean[1] - cam.ccy, vz = mean[2] - cam.ccz;
+    P.inv_vlen = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+    P.dir[0] = vx * P.inv_vlen; P.dir[1] = vy * P.inv_vlen; P.dir[2] = vz * P.inv_vlen;
+    float Y[16];
+    sh_basis(DEG, P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
+        P.rgb_raw[ch] = acc + 0.5f;
+    }
+}
+
+template <int DEG, int DT>
+__global__ void __launch_bounds__(kThreads)
+k_project(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+          const float4* __restrict__ quats, const float* __restrict__ logits, const void* __restrict__ sh,
+          Cam cam, Dil dil, float4* __restrict__ splats, int* __restrict__ radii,
+          int4* __restrict__ rects, int* __restrict__ tiles_touched)
+{
+    using L = ShLayout<DEG, DT>;
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * kWarps + warp) * 32;
+    if (g0 >= n) return;
+    uint32_t* s_mean = smem + warp * L::WARP_WORDS;
+    uint32_t* s_scale = s_mean + 32 * 3;
+    uint32_t* s_sh = s_scale + 32 * 3;
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(means), n, g0, s_mean, lane);
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(log_scales), n, g0, s_scale, lane);
+    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh), n, g0, s_sh, lane);
+    const int g = g0 + lane;
+    if (g >= n) return;
+
+    float mean[3], ls[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
+        ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
+    }
+    float c[16][3];
+    read_sh<DEG, DT>(s_sh, sh, g, lane, c);
+    Proj P;
+    project_one<DEG>(cam, dil, mean, ls, quats[g], logits[g], c, P);
+
+    float4* out = splats + 3 * (int64_t)g;
+    if (P.culled) {
+        out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
+        radii[g] = 0;
+        rects[g] = make_int4(0, 0, -1, -1);
+        tiles_touched[g] = 0;
+        return;
+    }
+    out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
+    out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
+    out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
+    radii[g] = P.radius;
+    rects[g] = P.rect;
+    tiles_touched[g] = P.tiles;
+}
+
+// ---------------------------------------------------------------------------
+// Backward of the projection (chain rule through conic, Sigma' = N N^T + lp,
+// N = J W M, M = R(q) S, the image-plane centre and the SH direction).
+// ---------------------------------------------------------------------------
+template <int DEG, int DT>
+__global__ void __launch_bounds__(kThreads)
+k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+              const float4* __restrict__ quats, const float* __restrict__ logits,
+              const void* __restrict__ sh, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
+              const float4* __restrict__ grad2d, float* __restrict__ d_means,
+              float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
+              float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pos_acc,
+              float* __restrict__ col_acc, int* __restrict__ count)
+{
+    using L = ShLayout<DEG, DT>;
+    constexpr int K = L::K;
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * kWarps + warp) * 32;
+    if (g0 >= n) return;
+    uint32_t* s_mean = smem + warp * L::WARP_WORDS;
+    uint32_t* s_scale = s_mean + 32 * 3;
+    uint32_t* s_sh = s_scale + 32 * 3;
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(means), n, g0, s_mean, lane);
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(log_scales), n, g0, s_scale, lane);
+    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh), n, g0, s_sh, lane);
+    const int g = g0 + lane;
+    if (g >= n) return;
+
+    float mean[3], ls[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
+        ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
+    }
+    float c[16][3];
+    read_sh<DEG, DT>(s_sh, sh, g, lane, c);
+    Proj P;
+    project_one<DEG>(cam, dil, mean, ls, quats[g], logits[g], c, P);
+
+    float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f};
+    float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float glogit = 0.0f;
+    float* gsh = d_sh + (int64_t)g * K * 3;
+    if (P.culled) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            d_means[3 * (int64_t)g + j] = 0.f;
+            d_log_scales[3 * (int64_t)g + j] = 0.f;
+        }
+        d_quats[g] = gq;
+        d_logits[g] = 0.f;
+#pragma unroll
+        for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
+        return;
+    }
+    const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
+    const float gpx = G0.x, gpy = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y;
+    float grgb[3] = {G1.z, G1.w, G2.x};
+
+    // densification statistics (Sec. 3.3)
+    if (pos_acc != nullptr && tiles_touched[g] > 0) {
+        pos_acc[g] += sqrtf(gpx * gpx + gpy * gpy);
+        col_acc[g] += sqrtf(grgb[0] * grgb[0] + grgb[1] * grgb[1] + grgb[2] * grgb[2]);
+        count[g] += 1;
+    }
+
+    // opacity = sigmoid(logit)
+    glogit = gop * P.opacity * (1.0f - P.opacity);
+
+    // colour: SH coefficients and the view direction
+    float Y[16];
+    sh_basis(DEG, P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        if (!(P.rgb_raw[ch] > 0.0f)) grgb[ch] = 0.0f;
+    float wsh[16];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        wsh[k] = grgb[0] * c[k][0] + grgb[1] * c[k][1] + grgb[2] * c[k][2];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = Y[k] * grgb[ch];
+    }
+    float gdx, gdy, gdz;
+    sh_basis_vjp(DEG, P.dir[0], P.dir[1], P.dir[2], wsh, gdx, gdy, gdz);
+    float dd = gdx * P.dir[0] + gdy * P.dir[1] + gdz * P.dir[2];
+    gm[0] += (gdx - P.dir[0] * dd) * P.inv_vlen;
+    gm[1] += (gdy - P.dir[1] * dd) * P.inv_vlen;
+    gm[2] += (gdz - P.dir[2] * dd) * P.inv_vlen;
+
+    // conic = inverse of Sigma': dL/dSigma' = -K Gk K, Gk = [[gA, gB/2], [gB/2, gC]]
+    float k00 = P.A * gA + P.B * 0.5f * gB, k01 = P.A * 0.5f * gB + P.B * gC;
+    float k10 = P.B * gA + P.C * 0.5f * gB, k11 = P.B * 0.5f * gB + P.C * gC;
+    float s00 = -(k00 * P.A + k01 * P.B);
+    float s01 = -(k00 * P.B + k01 * P.C);
+    float s11 = -(k10 * P.B + k11 * P.C);
+    // Sigma' = N N^T + lp: dL/dN = 2 S N
+    float dN[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dN[k] = 2.0f * (s00 * P.N[k] + s01 * P.N[3 + k]);
+        dN[3 + k] = 2.0f * (s01 * P.N[k] + s11 * P.N[3 + k]);
+    }
+    // N = Tm M: dTm = dN M^T, dM = Tm^T dN
+    float dTm[6], dM[9];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dTm[3 * i + j] = dN[3 * i] * P.M[3 * j] + dN[3 * i + 1] * P.M[3 * j + 1] + dN[3 * i + 2] * P.M[3 * j + 2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dM[3 * j + k] = P.Tm[j] * dN[k] + P.Tm[3 + j] * dN[3 + k];
+    // Tm = J W: dJ_il = sum_j dTm_ij W_lj (only J00, J02, J11, J12 vary)
+    float dJ00 = dTm[0] * cam.R[0] + dTm[1] * cam.R[1] + dTm[2] * cam.R[2];
+    float dJ02 = dTm[0] * cam.R[6] + dTm[1] * cam.R[7] + dTm[2] * cam.R[8];
+    float dJ11 = dTm[3] * cam.R[3] + dTm[4] * cam.R[4] + dTm[5] * cam.R[5];
+    float dJ12 = dTm[3] * cam.R[6] + dTm[4] * cam.R[7] + dTm[5] * cam.R[8];
+    const float tz = P.tz, itz = 1.0f / tz, itz2 = itz * itz;
+    float dt0 = 0.f, dt1 = 0.f, dt2 = 0.f;
+    dt2 += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz2;
+    if (P.clamp_x) {
+        dt2 += dJ02 * cam.fx * P.uc * itz2;
+    } else {
+        dt0 += -dJ02 * cam.fx * itz2;
+        dt2 += 2.0f * dJ02 * cam.fx * P.u * itz2;
+    }
+    if (P.clamp_y) {
+        dt2 += dJ12 * cam.fy * P.vc * itz2;
+    } else {
+        dt1 += -dJ12 * cam.fy * itz2;
+        dt2 += 2.0f * dJ12 * cam.fy * P.v * itz2;
+    }
+    // image-plane centre p = (fx tx/tz + cx, fy ty/tz + cy)
+    dt0 += gpx * cam.fx * itz;
+    dt1 += gpy * cam.fy * itz;
+    dt2 += -(gpx * cam.fx * P.u + gpy * cam.fy * P.v) * itz;
+    // t = W mean + T
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gm[j] += cam.R[j] * dt0 + cam.R[3 + j] * dt1 + cam.R[6 + j] * dt2;
+
+    // M = R diag(s)
+    float dR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            acc += dM[3 * j + k] * P.R[3 * j + k];
+            dR[3 * j + k] = dM[3 * j + k] * P.s[k];
+        }
+        gls[k] = acc * P.s[k];
+    }
+    // R(w, x, y, z)
+    const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+    float gw = 2.0f * (z * (dR[3] - dR[1]) + y * (dR[2] - dR[6]) + x * (dR[7] - dR[5]));
+    float gx = 2.0f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5]) - 2.0f * x * (dR[4] + dR[8]));
+    float gy = 2.0f * (x * (dR[1] + dR[3]) + z * (dR[5] + dR[7]) + w * (dR[2] - dR[6]) - 2.0f * y * (dR[0] + dR[8]));
+    float gz = 2.0f * (x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) + w * (dR[3] - dR[1]) - 2.0f * z * (dR[0] + dR[4]));
+    float qd = gw * w + gx * x + gy * y + gz * z;
+    gq = make_float4((gw - w * qd) * P.inv_qnorm, (gx - x * qd) * P.inv_qnorm,
+                     (gy - y * qd) * P.inv_qnorm, (gz - z * qd) * P.inv_qnorm);
+
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        d_means[3 * (int64_t)g + j] = gm[j];
+        d_log_scales[3 * (int64_t)g + j] = gls[j];
+    }
+    d_quats[g] = gq;
+    d_logits[g] = glogit;
+}
+
+__global__ void k_densify(int n, const int* __restrict__ tiles_touched, const float4* __restrict__ grad2d,
+                          float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n || tiles_touched[g] <= 0) return;
+    float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
+    pos_acc[g] += sqrtf(G0.x * G0.x + G0.y * G0.y);
+    col_acc[g] += sqrtf(G1.z * G1.z + G1.w * G1.w + G2.x * G2.x);
+    count[g] += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch over (degree, dtype)
+// ---------------------------------------------------------------------------
+template <int DEG, int DT>
+int32_t launch_project(int n, const float* means, const float* log_scales, const float* quats,
+                       const float* logits, const void* sh, const Cam& cam, const Dil& dil, float* splats,
+                       int* radii, int* rects, int* tiles, cudaStream_t st)
+{
+    using L = ShLayout<DEG, DT>;
+    size_t smem = sizeof(uint32_t) * L::WARP_WORDS * kWarps;
+    auto kern = k_project<DEG, DT>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = (n + kThreads - 1) / kThreads;
+    kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,
+                                         cam, dil, reinterpret_cast<float4*>(splats), radii,
+                                         reinterpret_cast<int4*>(rects), tiles);
+    return gs_host::check_launch("gs_project");
+}
+
+template <int DEG, int DT>
+int32_t launch_project_bwd(int n, const float* means, const float* log_scales, const float* quats,
+                           const float* logits, const void* sh, const Cam& cam, const Dil& dil,
+                           const int* tiles, const float* grad2d, float* d_means, float* d_ls, float* d_q,
+                           float* d_logits, float* d_sh, float* pos, float* col, int* cnt, cudaStream_t st)
+{
+    using L = ShLayout<DEG, DT>;
+    size_t smem = sizeof(uint32_t) * L::WARP_WORDS * kWarps;
+    auto kern = k_project_bwd<DEG, DT>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = (n + kThreads - 1) / kThreads;
+    kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,
+                                         cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
+                                         reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
+    return gs_host::check_launch("gs_project_bwd");
+}
+
+#define GS_DISPATCH_DEG_DT(deg, dt, FN, ...)                                                          \
+    switch ((deg) * 3 + (dt)) {                                                                       \
+        case 0: return FN<0, GS_DTYPE_F32>(__VA_ARGS__);                                              \
+        case 1: return FN<0, GS_DTYPE_BF16>(__VA_ARGS__);                                             \
+        case 2: return FN<0, GS_DTYPE_F16>(__VA_ARGS__);                                              \
+        case 3: return FN<1, GS_DTYPE_F32>(__VA_ARGS__);                                              \
+        case 4: return FN<1, GS_DTYPE_BF16>(__VA_ARGS__);                                             \
+        case 5: return FN<1, GS_DTYPE_F16>(__VA_ARGS__);                                              \
+        case 6: return FN<2, GS_DTYPE_F32>(__VA_ARGS__);                                              \
+        case 7: return FN<2, GS_DTYPE_BF16>(__VA_ARGS__);                                             \
+        case 8: return FN<2, GS_DTYPE_F16>(__VA_ARGS__);                                              \
+        case 9: return FN<3, GS_DTYPE_F32>(__VA_ARGS__);                                              \
+        case 10: return FN<3, GS_DTYPE_BF16>(__VA_ARGS__);                                            \
+        default: return FN<3, GS_DTYPE_F16>(__VA_ARGS__);                                             \
+    }
+
+bool check_params(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* a, const void* b, const void* c,
+                  const void* d, const void* e)
+{
+    if (n < 0) { gs_host::set_error("n must be >= 0"); return false; }
+    if (sh_degree < 0 || sh_degree > 3) { gs_host::set_error("sh_degree must be in 0..3"); return false; }
+    if (sh_dtype < GS_DTYPE_F32 || sh_dtype > GS_DTYPE_F16) { gs_host::set_error("bad sh_dtype"); return false; }
+    if (n > 0 && (!a || !b || !c || !d || !e)) { gs_host::set_error("null parameter pointer"); return false; }
+    if (n > 0 && ((reinterpret_cast<uintptr_t>(c) & 15) != 0)) {
+        gs_host::set_error("quats must be 16-byte aligned");
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" {
+
+int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* means, const float* log_scales,
+                   const float* quats, const float* opacity_logits, const void* sh, const GsCamera* cam,
+                   const GsDilation* dil, float* splats, int32_t* radii, int32_t* rects, int32_t* tiles_touched,
+                   gs_stream_t stream)
+{
+    using namespace gs;
+    if (!check_params(n, sh_degree, sh_dtype, means, log_scales, quats, opacity_logits, sh)) return GS_ERR_ARG;
+    Cam c;
+    Dil d;
+    if (!gs_host::make_cam(cam, &c) || !gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
+    if (n > 0 && (!splats || !radii || !rects || !tiles_touched)) {
+        gs_host::set_error("gs_project: null output pointer");
+        return GS_ERR_ARG;
+    }
+    if (n > 0 && (((reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(rects)) & 15) != 0)) {
+        gs_host::set_error("gs_project: splats and rects must be 16-byte aligned");
+        return GS_ERR_ARG;
+    }
+    if (n == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project, n, means, log_scales, quats, opacity_logits, sh, c, d,
+                       splats, radii, rects, tiles_touched, st);
+}
+
+int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* means, const float* log_scales,
+                       const float* quats, const float* opacity_logits, const void* sh, const GsCamera* cam,
+                       const GsDilation* dil, const int32_t* tiles_touched, const float* grad2d, float* d_means,
+                       float* d_log_scales, float* d_quats, float* d_opacity_logits, float* d_sh, float* pos_acc,
+                       float* col_acc, int32_t* count, gs_stream_t stream)
+{
+    using namespace gs;
+    if (!check_params(n, sh_degree, sh_dtype, means, log_scales, quats, opacity_logits, sh)) return GS_ERR_ARG;
+    Cam c;
+    Dil d;
+    if (!gs_host::make_cam(cam, &c) || !gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
+    if (n > 0 && (!tiles_touched || !grad2d || !d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)) {
+        gs_host::set_error("gs_project_bwd: null pointer");
+        return GS_ERR_ARG;
+    }
+    if ((pos_acc == nullptr) != (col_acc == nullptr) || (pos_acc == nullptr) != (count == nullptr)) {
+        gs_host::set_error("gs_project_bwd: pos_acc, col_acc and count must be all null or all set");
+        return GS_ERR_ARG;
+    }
+    if (n > 0 && (((reinterpret_cast<uintptr_t>(grad2d) | reinterpret_cast<uintptr_t>(d_quats)) & 15) != 0)) {
+        gs_host::set_error("gs_project_bwd: grad2d and d_quats must be 16-byte aligned");
+        return GS_ERR_ARG;
+    }
+    if (n == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd, n, means, log_scales, quats, opacity_logits, sh, c,
+                       d, tiles_touched, grad2d, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, pos_acc,
+                       col_acc, count, st);
+}
+
+int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* grad2d, float* pos_acc,
+                         float* col_acc, int32_t* count, gs_stream_t stream)
+{
+    if (n < 0) { gs_host::set_error("n must be >= 0"); return GS_ERR_ARG; }
+    if (n > 0 && (!tiles_touched || !grad2d || !pos_acc || !col_acc || !count)) {
+        gs_host::set_error("gs_densify_stats: null pointer");
+        return GS_ERR_ARG;
+    }
+    if (n > 0 && (reinterpret_cast<uintptr_t>(grad2d) & 15) != 0) {
+        gs_host::set_error("gs_densify_stats: grad2d must be 16-byte aligned");
+        return GS_ERR_ARG;
+    }
+    if (n == 0) return GS_OK;
+    gs::k_densify<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        n, tiles_touched, reinterpret_cast<const float4*>(grad2d), pos_acc, col_acc, count);
+    return gs_host::check_launch("gs_densify_stats");
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""The hot path of Turbo-GS fitting on the device: buffers, the autograd
+wrapper and one full training step (project -> bin/sort -> blend -> L1 ->
+blend backward -> projection backward + densification statistics -> Adam).
+
+Every stage is one call into ``libturbogs.so`` through ``raster``; this module
+only owns device memory and orders the calls on the current CUDA stream.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import raster as R
+from .raster import Dilation
+
+
+def _dev(x, device, dtype=torch.float32):
+    return torch.as_tensor(x, dtype=dtype).to(device).contiguous()
+
+
+@dataclass
+class GaussianParams:
+    """Device tensors of the Gaussians (Sec. 3): means, log-scales, quaternions
+    (w,x,y,z), opacity logits and SH coefficients (n x K x 3). ``sh_store`` is the
+    tensor the projection reads: ``sh`` itself, or a BF16/FP16 copy kept in sync
+    by Adam (mixed-precision storage; blending and accumulation stay FP32)."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_store: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @classmethod
+    def from_arrays(cls, arrays: dict, device="cuda", sh_dtype=torch.float32):
+        p = {k: _dev(arrays[k], device) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        p["opacity_logits"] = p["opacity_logits"].reshape(-1)
+        store = p["sh"] if sh_dtype == torch.float32 else p["sh"].to(sh_dtype).contiguous()
+        return cls(sh_store=store, **p)
+
+    def tensors(self):
+        return [self.means, self.log_scales, self.quats, self.opacity_logits, self.sh]
+
+
+class Rasterizer:
+    """Scratch of the hot path for up to ``n`` Gaussians, a pair capacity and a
+    tile grid. Nothing here synchronises with the host except ``num_pairs()``
+    and ``ensure_capacity``."""
+
+    def __init__(self, n: int, capacity: int = 1 << 20, max_tiles: int = 1, device="cuda"):
+        self.device = torch.device(device)
+        self.n = int(n)
+        self.splats = torch.zeros(self.n, R.SPLAT_FLOATS, device=self.device)
+        self.radii = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        self.rects = torch.zeros(self.n, 4, dtype=torch.int32, device=self.device)
+        self.tiles_touched = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        self.grad2d = torch.zeros(self.n, R.GRAD2D_FLOATS, device=self.device)
+        self.num_pairs_dev = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.capacity = 0
+        self.max_tiles = 0
+        self.ensure_tiles(max_tiles)
+        self._alloc_pairs(int(capacity))
+
+    def _alloc_pairs(self, capacity: int):
+        capacity = max(1, int(capacity))
+        self.sorted_ids = torch.empty(capacity, dtype=torch.int32, device=self.device)
+        ws = R.gs_bin_sort_workspace_size(self.n, capacity, max(1, self.max_tiles))
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.capacity = capacity
+
+    def ensure_tiles(self, num_tiles: int):
+        if num_tiles > self.max_tiles:
+            self.max_tiles = int(num_tiles)
+            self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
+
+    def ensure_capacity(self, k: int, headroom: float = 1.25):
+        if k > self.capacity:
+            self._alloc_pairs(int(math.ceil(k * headroom)) + 1024)
+
+    def num_pairs(self) -> int:
+        return int(self.num_pairs_dev.item())
+
+    # -- stages ---------------------------------------------------------------
+    def project(self, p: GaussianParams, cam, dil: Dilation):
+        R.gs_project(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, self.splats,
+                     self.radii, self.rects, self.tiles_touched)
+
+    def bin(self, cam, dil: Dilation):
+        w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+        self.ensure_tiles(tx * ty)
+        R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, tx, ty, self.workspace, self.capacity,
+                      self.sorted_ids, self.ranges, self.num_pairs_dev)
+        return w_ds, h_ds, tx, ty
+
+    def bin_checked(self, cam, dil: Dilation):
+        """bin(), then read K (host sync) and redo it with grown buffers on overflow."""
+        grid = self.bin(cam, dil)
+        k = self.num_pairs()
+        if k > self.capacity:
+            self.ensure_capacity(k)
+            grid = self.bin(cam, dil)
+        return grid
+
+    def render(self, cam, dil: Dilation, bg, img, t_final, last, counts=None):
+        R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts)
+
+    def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg):
+        R.gs_render_bwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, t_final, last, dl_dimg,
+                        self.grad2d, zero_grad2d=True)
+
+
+def image_buffers(h_ds: int, w_ds: int, device="cuda"):
+    return (torch.empty(h_ds, w_ds, 3, device=device), torch.empty(h_ds, w_ds, device=device),
+            torch.empty(h_ds, w_ds, dtype=torch.int32, device=device))
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+class _RasterizeFn(torch.autograd.Function):
+    """Differentiable dilated render of one view. Only (t_final, last) and the
+    binned lists are kept for backward; the per-pixel blend state is replayed."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, cam, dil, bg, cap_hint):
+        n = means.shape[0]
+        p = GaussianParams(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                           opacity_logits.contiguous(), sh.contiguous(), sh.contiguous())
+        w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+        rast = Rasterizer(n, capacity=cap_hint[0], max_tiles=tx * ty, device=means.device)
+        rast.project(p, cam, dil)
+        rast.bin_checked(cam, dil)
+        cap_hint[0] = max(cap_hint[0], rast.capacity)
+        img, t_final, last = image_buffers(h_ds, w_ds, means.device)
+        rast.render(cam, dil, bg, img, t_final, last)
+        ctx.rast, ctx.cam, ctx.dil, ctx.bg, ctx.p = rast, cam, dil, bg, p
+        ctx.save_for_backward(t_final, last)
+        ctx.mark_non_differentiable(t_final, last)
+        return img, t_final, last
+
+    @staticmethod
+    def backward(ctx, dl_dimg, _g_t, _g_last):
+        t_final, last = ctx.saved_tensors
+        rast, p = ctx.rast, ctx.p
+        rast.render_bwd(ctx.cam, ctx.dil, ctx.bg, t_final, last, dl_dimg.contiguous())
+        g = [torch.empty_like(t) for t in (p.means, p.log_scales, p.quats, p.opacity_logits)]
+        d_sh = torch.empty(p.sh.shape, dtype=torch.float32, device=p.sh.device)
+        R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh, ctx.cam, ctx.dil,
+                         rast.tiles_touched, rast.grad2d, g[0], g[1], g[2], g[3], d_sh)
+        ctx.rast = None
+        return g[0], g[1], g[2], g[3], d_sh.to(p.sh.dtype), None, None, None, None
+
+
+_CAP_HINT = [1 << 16]
+
+
+def rasterize(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation = Dilation(), bg=(0.0, 0.0, 0.0)):
+    """Render the dilated lattice of one view; differentiable in the five
+    parameter tensors. Returns (img h_ds x w_ds x 3, t_final, last)."""
+    return _RasterizeFn.apply(means, log_scales, quats, opacity_logits, sh, cam, dil, tuple(bg), _CAP_HINT)
+
+
+# ---------------------------------------------------------------------------
+# One full training step of the hot path
+# ---------------------------------------------------------------------------
+
+@dataclass
+class AdamConfig:
+    lr_means: float = 1.6e-4
+    lr_log_scales: float = 5e-3
+    lr_quats: float = 1e-3
+    lr_opacity: float = 5e-2
+    lr_sh: float = 2.5e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+
+class TrainStep:
+    """project -> bin/sort -> blend -> L1 -> blend bwd -> projection bwd with
+    densification statistics -> fused Adam, all on the current stream with no
+    host synchronisation (the pair capacity is fixed up front)."""
+
+    def __init__(self, params: GaussianParams, rast: Rasterizer, adam: AdamConfig = AdamConfig(),
+                 max_pixels: int = 1, bg=(0.0, 0.0, 0.0), densify: bool = True):
+        dev = params.means.device
+        self.p, self.rast, self.adam, self.bg = params, rast, adam, tuple(bg)
+        self.grads = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.step_count = 0
+        self.img = torch.empty(max_pixels * 3, device=dev)
+        self.t_final = torch.empty(max_pixels, device=dev)
+        self.last = torch.empty(max_pixels, dtype=torch.int32, device=dev)
+        self.dl = torch.empty(max_pixels * 3, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        n = params.n
+        self.densify = densify
+        self.pos_acc = torch.zeros(n, device=dev)
+        self.col_acc = torch.zeros(n, device=dev)
+        self.vis_count = torch.zeros(n, dtype=torch.int32, device=dev)
+
+    def __call__(self, cam, dil: Dilation, target: torch.Tensor, counts: bool = False):
+        p, rast = self.p, self.rast
+        rast.project(p, cam, dil)
+        w_ds, h_ds, tx, ty = rast.bin(cam, dil)
+        P = w_ds * h_ds
+        img = self.img[:3 * P].view(h_ds, w_ds, 3)
+        t_final = self.t_final[:P].view(h_ds, w_ds)
+        last = self.last[:P].view(h_ds, w_ds)
+        dl = self.dl[:3 * P].view(h_ds, w_ds, 3)
+        rast.render(cam, dil, self.bg, img, t_final, last, self.counts if counts else None)
+        R.gs_loss_l1(cam, dil, img, target, dl, self.loss)
+        rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
+        g = self.grads
+        R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, rast.tiles_touched,
+                         rast.grad2d, g[0], g[1], g[2], g[3], g[4],
+                         self.pos_acc if self.densify else None, self.col_acc if self.densify else None,
+                         self.vis_count if self.densify else None)
+        self.step_count += 1
+        a = self.adam
+        lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
+        entries = []
+        for i, t in enumerate(p.tensors()):
+            e = dict(param=t, grad=g[i], m=self.m[i], v=self.v[i], lr=lrs[i], row_width=max(1, t[0].numel()))
+            if i == 4 and p.sh_store.data_ptr() != p.sh.data_ptr():
+                e["shadow"] = p.sh_store
+            entries.append(e)
+        R.gs_adam(entries, a.beta1, a.beta2, a.eps, self.step_count)
+        return self.loss
+
+    # kernels launched per step (project, bin_sort internals, render, loss, bwd, proj bwd, adam)
+    def launches_per_step(self, n_tiles: int, capacity: int) -> int:
+        bits = max(1, math.ceil(math.log2(max(2, n_tiles))))
+        tile_passes = (bits + 7) // 8
+        # gs_bin_sort: depth keys + 4 depth passes x 3 + scan 3 + emit + tile passes x 3 + ranges
+        binsort = 1 + 4 * 3 + 3 + 1 + tile_passes * 3 + 1
+        return 1 + binsort + 1 + 1 + 1 + 1 + 1

@@ -1,0 +1,236 @@
+"""Thin Python binding of ``libturbogs.so`` (C ABI in ``include/turbogs.h``).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch CUDA tensors become device pointers, the current
+torch stream becomes the ``cudaStream_t``. All arithmetic runs in the CUDA
+kernels. A missing library raises ``RuntimeError`` (no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libturbogs.so")
+
+GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT = 0, 1, 2, 3, 4
+GS_DTYPE_F32, GS_DTYPE_BF16, GS_DTYPE_F16 = 0, 1, 2
+SPLAT_FLOATS = 12
+GRAD2D_FLOATS = 12
+ADAM_MAX_TENSORS = 8
+
+SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
+           "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd", "gs_densify_stats", "gs_adam")
+
+
+class GsError(RuntimeError):
+    pass
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("T", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("z_near", ctypes.c_float)]
+
+
+class GsDilation(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("ox", ctypes.c_int32), ("oy", ctypes.c_int32),
+                ("center_mode", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+class GsAdamTensor(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("shadow", ctypes.c_void_p), ("numel", ctypes.c_int64),
+                ("row_width", ctypes.c_int32), ("shadow_dtype", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("pad_", ctypes.c_float)]
+
+
+@dataclass(frozen=True)
+class Dilation:
+    """Sec. 3.1: render the lattice (d*u + ox, d*v + oy) of the hr image."""
+    d: int = 1
+    ox: int = 0
+    oy: int = 0
+    center_mode: int = 0
+    tile: int = 16
+
+    def c(self) -> GsDilation:
+        return GsDilation(self.d, self.ox, self.oy, self.center_mode, self.tile)
+
+
+def camera(cam) -> GsCamera:
+    """GsCamera from any object with R (3x3), T (3), fx, fy, cx, cy, width, height[, z_near]."""
+    c = GsCamera()
+    R = [float(x) for row in cam.R for x in row] if not hasattr(cam.R, "reshape") else \
+        [float(x) for x in cam.R.reshape(9)]
+    c.R[:] = R
+    c.T[:] = [float(x) for x in (cam.T.reshape(3) if hasattr(cam.T, "reshape") else cam.T)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.z_near = float(getattr(cam, "z_near", 0.2))
+    return c
+
+
+_lib = None
+
+
+def load():
+    """Load libturbogs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libturbogs.so is missing: build it with `python -m paper_2412_13547_b300.build_native`"
+                           " (there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    cam_p, dil_p = ctypes.POINTER(GsCamera), ctypes.POINTER(GsDilation)
+    lib.gs_version.restype = i32
+    lib.gs_last_error.restype = ctypes.c_char_p
+    lib.gs_grid.argtypes = [cam_p, dil_p, P, P, P, P]
+    lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P]
+    lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32]
+    lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
+    lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
+    lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, P]
+    lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
+    lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P]
+    lib.gs_project_bwd.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P, P, P, P, P, P]
+    lib.gs_densify_stats.argtypes = [i32, P, P, P, P, P, P]
+    lib.gs_adam.argtypes = [ctypes.POINTER(GsAdamTensor), i32, f32, f32, f32, i32, P, P]
+    for name in SYMBOLS:
+        if name not in ("gs_last_error", "gs_bin_sort_workspace_size"):
+            getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, name: str):
+    if rc != GS_OK:
+        msg = load().gs_last_error().decode(errors="replace")
+        raise GsError(f"{name} failed ({rc}): {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_SH_DTYPE = {torch.float32: GS_DTYPE_F32, torch.bfloat16: GS_DTYPE_BF16, torch.float16: GS_DTYPE_F16}
+
+
+def sh_degree_of(sh: torch.Tensor) -> int:
+    k = sh.shape[1]
+    deg = int(round(k ** 0.5)) - 1
+    if (deg + 1) ** 2 != k or sh.shape[2] != 3:
+        raise ValueError("sh must be n x (deg+1)^2 x 3")
+    return deg
+
+
+def gs_version() -> int:
+    return int(load().gs_version())
+
+
+def gs_grid(cam, dil: Dilation):
+    out = [ctypes.c_int32() for _ in range(4)]
+    _check(load().gs_grid(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), *[ctypes.byref(o) for o in out]),
+           "gs_grid")
+    return tuple(int(o.value) for o in out)
+
+
+def gs_project(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, splats, radii, rects,
+               tiles_touched, stream=None):
+    n = means.shape[0]
+    deg = sh_degree_of(sh)
+    _check(load().gs_project(n, deg, _SH_DTYPE[sh.dtype], _ptr(means), _ptr(log_scales), _ptr(quats),
+                             _ptr(opacity_logits), _ptr(sh), ctypes.byref(camera(cam)), ctypes.byref(dil.c()),
+                             _ptr(splats), _ptr(radii), _ptr(rects), _ptr(tiles_touched), _stream(stream)),
+           "gs_project")
+
+
+def gs_bin_sort_workspace_size(n: int, capacity: int, num_tiles: int) -> int:
+    return int(load().gs_bin_sort_workspace_size(int(n), int(capacity), int(num_tiles)))
+
+
+def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, capacity, sorted_ids, ranges,
+                num_pairs, stream=None):
+    _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x), int(tiles_y),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(), int(capacity),
+                              _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)), "gs_bin_sort")
+
+
+def _bg(bg):
+    arr = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    return arr
+
+
+def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, counts=None,
+                  stream=None):
+    _check(load().gs_render_fwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
+                                ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last), _ptr(counts),
+                                _stream(stream)), "gs_render_fwd")
+
+
+def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
+    _check(load().gs_loss_l1(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
+                             _ptr(dl_dimg), _ptr(loss), _stream(stream)), "gs_loss_l1")
+
+
+def gs_render_bwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, t_final, last, dl_dimg, grad2d,
+                  zero_grad2d=True, stream=None):
+    _check(load().gs_render_bwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
+                                ctypes.byref(dil.c()), _bg(bg), _ptr(t_final), _ptr(last), _ptr(dl_dimg),
+                                _ptr(grad2d), int(bool(zero_grad2d)), _stream(stream)), "gs_render_bwd")
+
+
+def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, tiles_touched, grad2d,
+                   d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, pos_acc=None, col_acc=None, count=None,
+                   stream=None):
+    n = means.shape[0]
+    deg = sh_degree_of(sh)
+    _check(load().gs_project_bwd(n, deg, _SH_DTYPE[sh.dtype], _ptr(means), _ptr(log_scales), _ptr(quats),
+                                 _ptr(opacity_logits), _ptr(sh), ctypes.byref(camera(cam)), ctypes.byref(dil.c()),
+                                 _ptr(tiles_touched), _ptr(grad2d), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
+                                 _ptr(d_opacity_logits), _ptr(d_sh), _ptr(pos_acc), _ptr(col_acc), _ptr(count),
+                                 _stream(stream)), "gs_project_bwd")
+
+
+def gs_densify_stats(n, tiles_touched, grad2d, pos_acc, col_acc, count, stream=None):
+    _check(load().gs_densify_stats(int(n), _ptr(tiles_touched), _ptr(grad2d), _ptr(pos_acc), _ptr(col_acc),
+                                   _ptr(count), _stream(stream)), "gs_densify_stats")
+
+
+def gs_adam(entries, beta1, beta2, eps, step, row_mask=None, stream=None):
+    """entries: list of dicts with param, grad, m, v (float32 CUDA tensors), lr,
+    and optional shadow (bf16/fp16/fp32 tensor of the same shape) and row_width."""
+    arr = (GsAdamTensor * max(1, len(entries)))()
+    for i, e in enumerate(entries):
+        p = e["param"]
+        for k in ("grad", "m", "v"):
+            if e[k].shape != p.shape or e[k].dtype != torch.float32:
+                raise ValueError(f"adam entry {i}: {k} must match param (float32)")
+        sh = e.get("shadow")
+        arr[i].param = p.data_ptr()
+        arr[i].grad = e["grad"].data_ptr()
+        arr[i].m = e["m"].data_ptr()
+        arr[i].v = e["v"].data_ptr()
+        arr[i].shadow = sh.data_ptr() if sh is not None else None
+        arr[i].numel = p.numel()
+        arr[i].row_width = int(e.get("row_width", p[0].numel() if p.dim() > 1 and p.shape[0] > 0 else 1))
+        arr[i].shadow_dtype = _SH_DTYPE[sh.dtype] if sh is not None else GS_DTYPE_F32
+        arr[i].lr = float(e["lr"])
+    _check(load().gs_adam(arr, len(entries), float(beta1), float(beta2), float(eps), int(step), _ptr(row_mask),
+                          _stream(stream)), "gs_adam")

@@ -1,0 +1,75 @@
+"""C-ABI library checks that need no GPU: it loads, exports every entry point
+declared in include/turbogs.h, and rejects bad arguments before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2412_13547_b300 import build_native, raster as R
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "turbogs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    build_native.build()
+    lib = R.load()
+    names = declared_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(R.SYMBOLS)
+
+
+def test_host_only_calls():
+    assert R.gs_version() >= 100
+    cam = type("C", (), dict(R=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], T=[0, 0, 0], fx=100.0, fy=100.0, cx=63.5,
+                             cy=47.5, width=130, height=97))()
+    assert R.gs_grid(cam, R.Dilation(1, 0, 0)) == (130, 97, 9, 7)
+    assert R.gs_grid(cam, R.Dilation(2, 1, 0)) == (65, 49, 5, 4)
+    assert R.gs_grid(cam, R.Dilation(3, 2, 2, tile=8)) == (43, 32, 6, 4)
+    assert R.gs_bin_sort_workspace_size(1000, 5000, 64) > 0
+    with pytest.raises(R.GsError):
+        R.gs_grid(cam, R.Dilation(2, 2, 0))       # offset >= d
+    with pytest.raises(R.GsError):
+        R.gs_grid(cam, R.Dilation(2, 0, 0, tile=12))
+
+
+def test_bad_arguments_are_rejected_before_launch():
+    lib = R.load()
+    cam = R.GsCamera()
+    cam.width, cam.height, cam.fx, cam.fy = 64, 64, 50.0, 50.0
+    dil = R.GsDilation(1, 0, 0, 0, 16)
+    P = ctypes.c_void_p
+    # n < 0
+    assert lib.gs_project(-1, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    # sh degree 4
+    assert lib.gs_project(0, 4, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    # null pointers with n > 0
+    assert lib.gs_project(5, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    assert "null" in lib.gs_last_error().decode()
+    # bad dilation
+    bad = R.GsDilation(0, 0, 0, 0, 16)
+    assert lib.gs_render_fwd(0, None, None, P(16), ctypes.byref(cam), ctypes.byref(bad), None, None, None, None,
+                             None, None) == R.GS_ERR_ARG
+    # capacity >= 2^31
+    assert lib.gs_bin_sort(0, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None) == R.GS_ERR_ARG
+    # adam: too many tensors, bad step
+    arr = (R.GsAdamTensor * 9)()
+    assert lib.gs_adam(arr, 9, 0.9, 0.999, 1e-8, 1, None, None) == R.GS_ERR_ARG
+    assert lib.gs_adam(arr, 1, 0.9, 0.999, 1e-8, 0, None, None) == R.GS_ERR_ARG
+    # empty inputs are a no-op success
+    assert lib.gs_project(0, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_OK
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        R.load()

@@ -1,0 +1,533 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Staged as the method is: projection (continuous values within FP32 rounding,
+integer radius/rect/tile counts exact except where the oracle flags a decision
+within rounding distance of its threshold), binning (bit-exact: the oracle's
+binning of the GPU's own FP32 rects and depth bits), blending (image within
+1e-4 abs), backward (gradients within 1e-3 of the per-tensor maximum), and
+the full step. Tolerances follow the spec bar: images 1e-4 max abs,
+gradients 1e-3 relative, keys/sort order/ranges bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_2412_13547_b300 import raster as R
+from paper_2412_13547_b300 import scenes
+from paper_2412_13547_b300.pipeline import GaussianParams, Rasterizer, TrainStep, AdamConfig, image_buffers
+
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def scene_small():
+    s, cam, tgt = scenes.workload_small()
+    return U.params_np(s), cam, tgt
+
+
+def scene_sh3(w=160, h=120):
+    s = scenes.small_scene(3000, index=11, sh_degree=3, log_scale_mean=-2.6)
+    s.sh[:, 1:, :] = np.random.default_rng(5).normal(0, 0.1, s.sh[:, 1:, :].shape)
+    cam = scenes.look_at(scenes.orbit_eye(3.0, 60.0, 25.0), width=w, height=h)
+    return U.params_np(s), cam, scenes.target_image(w, h, 11)
+
+
+def scene_clusters(n=40000, w=1280, h=720, index=5):
+    s = scenes.cluster_scene(n, index=index, log_scale_mean=-3.6)
+    cam = scenes.look_at(scenes.orbit_eye(2.6, 30.0, 20.0), width=w, height=h)
+    return U.params_np(s), cam, scenes.target_image(w, h, index)
+
+
+DILATIONS = [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0), R.Dilation(2, 0, 1, 1), R.Dilation(4, 3, 3),
+             R.Dilation(1, 0, 0, tile=8), R.Dilation(2, 1, 1, tile=32), R.Dilation(3, 2, 0)]
+
+
+def _dil_id(d):
+    return f"d{d.d}o{d.ox}{d.oy}m{d.center_mode}t{d.tile}"
+
+
+# ---------------------------------------------------------------------------
+# Projection
+# ---------------------------------------------------------------------------
+
+def check_projection(p32, cam, dil, out, sh_f64=None):
+    p64 = U.params_f64(p32)
+    if sh_f64 is not None:
+        p64["sh"] = sh_f64
+    o = orc.project(p64, orc.as_camera(cam), orc.as_dilation(dil))
+    flagged = (o["flags"] & orc.FLAG_AMBIGUOUS) != 0
+    ok = ~flagged
+    assert flagged.mean() < 0.02, flagged.mean()
+    np.testing.assert_array_equal(out["radii"][ok], o["radius"][ok])
+    np.testing.assert_array_equal(out["rects"][ok], o["rect"][ok])
+    np.testing.assert_array_equal(out["tiles_touched"][ok], o["tiles_touched"][ok])
+    vis = ok & (o["tiles_touched"] > 0)
+    g = U.gpu_proj_as_oracle(out)
+    assert np.abs(g["xy"][vis] - o["xy"][vis]).max(initial=0) < 1e-4
+    cmax = np.abs(o["conic"][vis]).max(1, initial=0)[:, None]
+    assert (np.abs(g["conic"][vis] - o["conic"][vis]) <= 2e-5 * cmax + 1e-12).all()
+    assert np.abs(g["opacity"][vis] - o["opacity"][vis]).max(initial=0) < 1e-6
+    assert np.abs(g["rgb"][vis] - o["rgb"][vis]).max(initial=0) < 2e-5
+    assert (np.abs(g["depth"][vis] - o["depth"][vis]) <= 1e-6 * o["depth"][vis]).all()
+    return o
+
+
+@pytest.mark.parametrize("dil", DILATIONS, ids=_dil_id)
+def test_projection_parity_small(dil):
+    p32, cam, _ = scene_small()
+    out, *_ = U.run_forward(p32, cam, dil)
+    check_projection(p32, cam, dil, out)
+
+
+@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_projection_parity_sh3_storage(sh_dtype):
+    p32, cam, _ = scene_sh3()
+    dil = R.Dilation(2, 1, 0)
+    out, _, p, _ = U.run_forward(p32, cam, dil, sh_dtype=sh_dtype)
+    # the oracle sees exactly the stored (rounded) coefficients
+    sh_f64 = p.sh_store.float().cpu().numpy().astype(np.float64)
+    check_projection(p32, cam, dil, out, sh_f64=sh_f64)
+
+
+# ---------------------------------------------------------------------------
+# Binning: bit-exact
+# ---------------------------------------------------------------------------
+
+def check_binning(out):
+    w_ds, h_ds, tx, ty = out["grid"]
+    keys, vals, ranges = orc.bin_sort(out["rects"], out["tiles_touched"].astype(np.int64), U.gpu_depth_bits(out),
+                                      tx, ty)
+    assert out["k"] == len(vals) == int(out["tiles_touched"].astype(np.int64).sum())
+    np.testing.assert_array_equal(out["sorted_ids"], vals)
+    np.testing.assert_array_equal(out["ranges"], ranges)
+    np.testing.assert_array_equal(U.gpu_keys(out), keys)
+
+
+@pytest.mark.parametrize("dil", DILATIONS, ids=_dil_id)
+def test_binning_bitexact_small(dil):
+    p32, cam, _ = scene_small()
+    out, *_ = U.run_forward(p32, cam, dil)
+    check_binning(out)
+
+
+@pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1), R.Dilation(1, 0, 0, tile=8)], ids=_dil_id)
+def test_binning_bitexact_many_pairs(dil):
+    """Millions of pairs, thousands of tiles: several sort blocks, two tile passes."""
+    p32, cam, _ = scene_clusters()
+    out, *_ = U.run_forward(p32, cam, dil)
+    assert out["k"] > 1_000_000 or dil.d > 1
+    check_binning(out)
+
+
+def test_binning_equal_depths_keep_index_order():
+    """Gaussians with identical depth bits: ties ordered by index."""
+    n = 64
+    rng = np.random.default_rng(3)
+    p = dict(means=np.c_[rng.uniform(-0.3, 0.3, (n, 2)), np.zeros(n)].astype(np.float32),
+             log_scales=np.full((n, 3), -2.0, np.float32),
+             quats=np.tile([1, 0, 0, 0], (n, 1)).astype(np.float32),
+             opacity_logits=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32))
+    cam = scenes.Cam(R=np.eye(3), T=np.array([0.0, 0.0, 3.0]), fx=60.0, fy=60.0, cx=47.5, cy=31.5, width=96,
+                     height=64)
+    out, *_ = U.run_forward(p, cam, R.Dilation())
+    assert len(np.unique(out["splats"][:, 9])) == 1
+    check_binning(out)
+
+
+# ---------------------------------------------------------------------------
+# Blend forward / backward on the same lists
+# ---------------------------------------------------------------------------
+
+def render_case(p32, cam, dil, bg=(0.1, 0.2, 0.3)):
+    out, rast, p, bufs = U.run_forward(p32, cam, dil, bg)
+    o = orc.project(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil))
+    # Gaussians the two sides cull differently get no exact comparison: their tiles are excluded
+    cull_diff = (o["tiles_touched"] > 0) != (out["tiles_touched"] > 0)
+    of = orc.render_fwd(o, out["sorted_ids"], out["ranges"], orc.as_camera(cam), orc.as_dilation(dil), bg)
+    w_ds, h_ds, tx, ty = out["grid"]
+    bad_tiles = np.zeros(tx * ty, bool)
+    for g in np.nonzero(cull_diff)[0]:
+        rc = out["rects"][g] if out["tiles_touched"][g] > 0 else o["rect"][g]
+        for yy in range(rc[1], rc[3] + 1):
+            bad_tiles[yy * tx + rc[0]: yy * tx + rc[2] + 1] = True
+    excl = of["ambiguous"] | U.tile_pixel_mask(bad_tiles, w_ds, h_ds, tx, dil.tile)
+    return out, rast, p, bufs, o, of, excl
+
+
+@pytest.mark.parametrize("dil", DILATIONS, ids=_dil_id)
+def test_render_fwd_parity(dil):
+    p32, cam, _ = scene_small()
+    out, rast, p, bufs, o, of, excl = render_case(p32, cam, dil)
+    # pixels where a gate value (alpha vs 1/255 or 0.99, transmittance vs 1e-4) lies within the
+    # oracle's margin of its threshold may legitimately branch the other way in FP32
+    assert excl.mean() < 5e-3
+    keep = ~excl
+    assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
+    assert np.abs(out["t_final"] - of["t_final"])[keep].max() < 1e-5
+    np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
+    assert out["counts"][0] == of["n_eval"] or excl.any()
+    assert out["counts"][1] == of["n_blend"] or excl.any()
+
+
+def test_render_fwd_parity_sh3_ragged():
+    p32, cam, _ = scene_sh3(131, 97)
+    for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1), R.Dilation(3, 0, 2, tile=8)]:
+        out, rast, p, bufs, o, of, excl = render_case(p32, cam, dil)
+        keep = ~excl
+        assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
+        np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
+
+
+def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
+    out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg)
+    rng = np.random.default_rng(seed)
+    dl = rng.standard_normal(out["img"].shape) * 1e-3
+    dl[excl] = 0.0
+    dl_t = torch.tensor(dl, dtype=torch.float32, device=U.DEV)
+    rast.render_bwd(cam, dil, bg, t_final, last, dl_t)
+    torch.cuda.synchronize()
+    g2d = rast.grad2d.cpu().numpy()
+    og = orc.render_bwd(o, out["sorted_ids"], out["ranges"], orc.as_camera(cam), orc.as_dilation(dil),
+                        dl.astype(np.float32).astype(np.float64), bg)
+    return out, rast, p, o, og, g2d, excl
+
+
+@pytest.mark.parametrize("dil", DILATIONS, ids=_dil_id)
+def test_render_bwd_parity(dil):
+    p32, cam, _ = scene_small()
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil)
+    gg = U.split_grad2d(g2d)
+    for k in ("dxy", "dconic", "dopacity", "drgb"):
+        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
+    assert np.all(g2d[:, 9:] == 0.0)
+
+
+def test_render_bwd_parity_sh3():
+    p32, cam, _ = scene_sh3()
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 0, 1))
+    gg = U.split_grad2d(g2d)
+    for k in ("dxy", "dconic", "dopacity", "drgb"):
+        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, k
+
+
+@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.bfloat16])
+def test_project_bwd_parity(sh_dtype):
+    p32, cam, _ = scene_sh3()
+    dil = R.Dilation(2, 1, 0)
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil)
+    flagged = (o["flags"] & orc.FLAG_AMBIGUOUS) != 0
+    g2d[flagged] = 0.0
+    rast.grad2d.copy_(torch.tensor(g2d, device=U.DEV))
+    pp = U.gpu_params(p32, sh_dtype)
+    grads = [torch.empty_like(t) for t in pp.tensors()]
+    R.gs_project_bwd(pp.means, pp.log_scales, pp.quats, pp.opacity_logits, pp.sh_store, cam, dil, rast.tiles_touched,
+                     rast.grad2d, *grads)
+    torch.cuda.synchronize()
+    p64 = U.params_f64(p32)
+    p64["sh"] = pp.sh_store.float().cpu().numpy().astype(np.float64)
+    ref = orc.project_bwd(p64, orc.as_camera(cam), orc.as_dilation(dil), U.split_grad2d(g2d))
+    for name, g in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads):
+        assert U.max_rel(g.cpu().numpy(), ref[name]) < GRAD_TOL, (name, U.max_rel(g.cpu().numpy(), ref[name]))
+
+
+# ---------------------------------------------------------------------------
+# Loss, densification statistics, Adam
+# ---------------------------------------------------------------------------
+
+def test_loss_l1_parity():
+    _, cam, tgt = scene_small()
+    for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0), R.Dilation(3, 2, 1)]:
+        w_ds, h_ds, _, _ = R.gs_grid(cam, dil)
+        img = np.random.default_rng(1).uniform(0, 1, (h_ds, w_ds, 3)).astype(np.float32)
+        t_img = torch.tensor(img, device=U.DEV)
+        t_tgt = torch.tensor(tgt, device=U.DEV)
+        dl = torch.empty_like(t_img)
+        loss = torch.zeros(1, device=U.DEV)
+        R.gs_loss_l1(cam, dil, t_img, t_tgt, dl, loss)
+        L, g = orc.loss_l1(img, tgt, orc.as_camera(cam), orc.as_dilation(dil))
+        assert abs(loss.item() - L) < 1e-6 * max(1.0, L)
+        np.testing.assert_allclose(dl.cpu().numpy(), g, rtol=1e-6, atol=1e-12)
+
+
+def test_densify_stats_parity():
+    p32, cam, _ = scene_small()
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 1, 1))
+    n = p.n
+    pos = torch.zeros(n, device=U.DEV)
+    col = torch.zeros(n, device=U.DEV)
+    cnt = torch.zeros(n, dtype=torch.int32, device=U.DEV)
+    for _ in range(2):
+        R.gs_densify_stats(n, rast.tiles_touched, rast.grad2d, pos, col, cnt)
+    # fused path of the projection backward gives the same accumulation
+    pos2, col2, cnt2 = torch.zeros_like(pos), torch.zeros_like(col), torch.zeros_like(cnt)
+    grads = [torch.empty_like(t) for t in p.tensors()]
+    R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, R.Dilation(2, 1, 1),
+                     rast.tiles_touched, rast.grad2d, *grads, pos2, col2, cnt2)
+    torch.cuda.synchronize()
+    rp, rc, rn = np.zeros(n), np.zeros(n), np.zeros(n, np.int32)
+    gg = U.split_grad2d(g2d)
+    for _ in range(2):
+        orc.densify_stats(out["tiles_touched"], gg, rp, rc, rn)
+    np.testing.assert_allclose(pos.cpu().numpy(), rp, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(col.cpu().numpy(), rc, rtol=1e-6, atol=1e-12)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), rn)
+    np.testing.assert_allclose(pos2.cpu().numpy() * 2, rp, rtol=1e-6, atol=1e-12)
+    np.testing.assert_array_equal(cnt2.cpu().numpy() * 2, rn)
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_adam_parity(masked):
+    rng = np.random.default_rng(7)
+    shapes = [(1001, 3), (1001, 4), (1001,), (1001, 16, 3)]
+    params = [rng.standard_normal(s).astype(np.float32) for s in shapes]
+    mask = (rng.uniform(size=1001) < 0.6).astype(np.uint8) if masked else None
+    dev = [dict(param=torch.tensor(x, device=U.DEV), grad=torch.zeros(x.shape, device=U.DEV),
+                m=torch.zeros(x.shape, device=U.DEV), v=torch.zeros(x.shape, device=U.DEV), lr=1e-2 * (i + 1))
+           for i, x in enumerate(params)]
+    # the shadow mirrors the parameter; rows the mask skips keep their old copy
+    shadow = dev[3]["param"].to(torch.bfloat16)
+    dev[3]["shadow"] = shadow
+    ref = [dict(p=x.astype(np.float64), m=np.zeros(x.shape), v=np.zeros(x.shape)) for x in params]
+    mask_t = None if mask is None else torch.tensor(mask, device=U.DEV)
+    for step in range(1, 4):
+        for i, x in enumerate(params):
+            g = rng.standard_normal(x.shape).astype(np.float32)
+            dev[i]["grad"].copy_(torch.tensor(g))
+            orc.adam(ref[i]["p"], g.astype(np.float64), ref[i]["m"], ref[i]["v"], 1e-2 * (i + 1), 0.9, 0.999, 1e-8,
+                     step, row_mask=mask)
+        R.gs_adam(dev, 0.9, 0.999, 1e-8, step, row_mask=mask_t)
+    torch.cuda.synchronize()
+    for i in range(len(params)):
+        np.testing.assert_allclose(dev[i]["param"].cpu().numpy(), ref[i]["p"], rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(dev[i]["m"].cpu().numpy(), ref[i]["m"], rtol=1e-5, atol=1e-7)
+    np.testing.assert_array_equal(shadow.float().cpu().numpy(),
+                                  dev[3]["param"].to(torch.bfloat16).float().cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# The full step against the oracle's own pipeline
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0)], ids=_dil_id)
+def test_full_step_parity(dil):
+    p32, cam, tgt = scene_small()
+    bg = (0.0, 0.0, 0.0)
+    ref = orc.forward_backward(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil), tgt, bg)
+    p = U.gpu_params(p32)
+    w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+    rast = Rasterizer(p.n, capacity=len(ref["vals"]) + 1000, max_tiles=tx * ty)
+    step = TrainStep(p, rast, AdamConfig(), max_pixels=w_ds * h_ds, bg=bg)
+    before = [t.clone() for t in p.tensors()]
+    loss = step(cam, dil, torch.tensor(tgt, device=U.DEV))
+    torch.cuda.synchronize()
+    assert abs(loss.item() - ref["loss"]) < 1e-5
+    img = step.img[:3 * w_ds * h_ds].view(h_ds, w_ds, 3).cpu().numpy()
+    diff = np.abs(img - ref["fwd"]["img"]).max(-1)
+    assert (diff > IMG_TOL).mean() < 1e-3
+    assert rast.num_pairs() == len(ref["vals"])
+    for name, g in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), step.grads):
+        assert U.max_rel(g.cpu().numpy(), ref["grads"][name]) < GRAD_TOL, name
+    # Adam moved every visible Gaussian's parameters
+    moved = (p.means != before[0]).any(1).cpu().numpy()
+    assert moved[ref["proj"]["tiles_touched"] > 0].mean() > 0.5
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_and_all_culled():
+    _, cam, _ = scene_small()
+    bg = (0.25, 0.5, 0.75)
+    for n, z in [(0, 0.0), (50, 10.0)]:
+        rng = np.random.default_rng(0)
+        # camera at radius 4 looking at the origin: push everything behind it
+        eye = np.array(scenes.orbit_eye(4.0, 30.0, 20.0))
+        p = dict(means=(eye * 1.5 + rng.uniform(-0.1, 0.1, (n, 3))).astype(np.float32),
+                 log_scales=np.full((n, 3), -2.0, np.float32), quats=rng.standard_normal((n, 4)).astype(np.float32),
+                 opacity_logits=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32))
+        if n == 0:
+            p = {k: v[:0] for k, v in p.items()}
+            p["sh"] = np.zeros((0, 1, 3), np.float32)
+            out = dict()
+            w_ds, h_ds, tx, ty = R.gs_grid(cam, R.Dilation())
+            rast = Rasterizer(1, capacity=16, max_tiles=tx * ty)
+            rast.n = 0
+            R.gs_bin_sort(0, rast.rects, rast.tiles_touched, rast.splats, tx, ty, rast.workspace, 16,
+                          rast.sorted_ids, rast.ranges, rast.num_pairs_dev)
+            img, tf, last = image_buffers(h_ds, w_ds)
+            R.gs_render_fwd(0, rast.splats, rast.sorted_ids, rast.ranges, cam, R.Dilation(), bg, img, tf, last)
+            torch.cuda.synchronize()
+            assert rast.num_pairs() == 0
+            np.testing.assert_allclose(img.cpu().numpy(), np.broadcast_to(bg, img.shape), atol=0)
+            continue
+        out, *_ = U.run_forward(p, cam, R.Dilation(), bg)
+        assert out["k"] == 0 and (out["radii"] == 0).all()
+        np.testing.assert_allclose(out["img"], np.broadcast_to(bg, out["img"].shape), atol=1e-7)
+        assert (out["t_final"] == 1.0).all() and (out["last"] == 0).all()
+
+
+def test_one_gaussian_covering_every_tile():
+    p = dict(means=np.zeros((1, 3), np.float32), log_scales=np.full((1, 3), 0.5, np.float32),
+             quats=np.array([[1, 0, 0, 0]], np.float32), opacity_logits=np.array([2.0], np.float32),
+             sh=np.full((1, 1, 3), 0.3, np.float32))
+    cam = scenes.look_at(scenes.orbit_eye(4.0, 0.0, 0.0), width=200, height=150)
+    for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1)]:
+        out, rast, p_, bufs, o, of, excl = render_case(p, cam, dil)
+        w_ds, h_ds, tx, ty = out["grid"]
+        assert out["k"] == tx * ty
+        check_binning(out)
+        assert np.abs(out["img"] - of["img"])[~excl].max() < IMG_TOL
+
+
+def test_capacity_overflow_then_regrow():
+    p32, cam, _ = scene_small()
+    dil = R.Dilation()
+    out_ok, *_ = U.run_forward(p32, cam, dil)
+    k = out_ok["k"]
+    out, rast, p, bufs = U.run_forward(p32, cam, dil, bg=(0.5, 0.5, 0.5), capacity=k // 2)
+    assert out["k"] == k and rast.capacity < k
+    assert (out["ranges"] == 0).all()
+    np.testing.assert_allclose(out["img"], 0.5, atol=1e-7)
+    rast.ensure_capacity(k)
+    rast.bin(cam, dil)
+    torch.cuda.synchronize()
+    assert (rast.ranges[: out["ranges"].shape[0]].cpu().numpy().view(np.uint32) == out_ok["ranges"]).all()
+
+
+def test_deterministic_forward():
+    p32, cam, _ = scene_sh3()
+    a, *_ = U.run_forward(p32, cam, R.Dilation(2, 1, 0))
+    b, *_ = U.run_forward(p32, cam, R.Dilation(2, 1, 0))
+    for k in ("splats", "sorted_ids", "ranges", "img", "t_final", "last"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+# ---------------------------------------------------------------------------
+# autograd.Function
+# ---------------------------------------------------------------------------
+
+def test_autograd_matches_oracle_gradient():
+    from paper_2412_13547_b300.pipeline import rasterize
+    p32, cam, _ = scene_sh3(96, 80)
+    dil = R.Dilation(2, 1, 0)
+    p = U.gpu_params(p32)
+    ts = [t.clone().requires_grad_(True) for t in p.tensors()]
+    rng = np.random.default_rng(0)
+    w_ds, h_ds, _, _ = R.gs_grid(cam, dil)
+    wts = torch.tensor(rng.standard_normal((h_ds, w_ds, 3)), dtype=torch.float32, device=U.DEV)
+    img, _, _ = rasterize(*ts, cam, dil)
+    (img * wts).sum().backward()
+    o = orc.project(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil))
+    out, *_ = U.run_forward(p32, cam, dil)
+    np.testing.assert_allclose(img.detach().cpu().numpy(), out["img"], atol=0)
+    og = orc.render_bwd(o, out["sorted_ids"], out["ranges"], orc.as_camera(cam), orc.as_dilation(dil),
+                        wts.cpu().numpy().astype(np.float64))
+    ref = orc.project_bwd(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil), og)
+    for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), ts):
+        assert U.max_rel(t.grad.cpu().numpy(), ref[name]) < GRAD_TOL, name
+
+
+def test_autograd_finite_differences_hd_64_params():
+    """1920x1080, 1M Gaussians, d=2: the autograd.Function gradient of a random
+    linear loss against FP64 central differences (the oracle's forward with the
+    lists held fixed) on 64 sampled parameters."""
+    from paper_2412_13547_b300.pipeline import rasterize
+    scene, cam, _ = scenes.workload_hd()
+    p32 = U.params_np(scene)
+    dil = R.Dilation(2, 1, 0)
+    ocam, odil = orc.as_camera(cam), orc.as_dilation(dil)
+    out, *_ = U.run_forward(p32, cam, dil)
+    w_ds, h_ds, tx, ty = out["grid"]
+    p64 = U.params_f64(p32)
+    o = orc.project(p64, ocam, odil)
+    of = orc.render_fwd(o, out["sorted_ids"], out["ranges"], ocam, odil)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((h_ds, w_ds, 3))
+    w[of["ambiguous"]] = 0.0
+    p = U.gpu_params(p32)
+    ts = [t.clone().requires_grad_(True) for t in p.tensors()]
+    img, _, _ = rasterize(*ts, cam, dil)
+    (img * torch.tensor(w, dtype=torch.float32, device=U.DEV)).sum().backward()
+    grads = {name: t.grad.cpu().numpy() for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), ts)}
+    ok = (out["tiles_touched"] > 0) & ((o["flags"] & orc.FLAG_AMBIGUOUS) == 0) & (out["tiles_touched"] < 400)
+    names = ["means"] * 3 + ["log_scales"] * 3 + ["quats"] * 4 + ["opacity_logits"] + ["sh"] * 48
+    picks = rng.choice(np.nonzero(ok)[0], 64, replace=False)
+    fd, an, grp = [], [], []
+    for g in picks:
+        k = int(rng.integers(len(names)))
+        name = names[k]
+        elem = k - names.index(name)
+        rc = out["rects"][g]
+        tiles = np.array([yy * tx + xx for yy in range(rc[1], rc[3] + 1) for xx in range(rc[0], rc[2] + 1)], np.int32)
+        sub_v = np.concatenate([out["sorted_ids"][out["ranges"][t, 0]:out["ranges"][t, 1]] for t in tiles])
+        lens = np.array([out["ranges"][t, 1] - out["ranges"][t, 0] for t in tiles], np.int64)
+        sub_r = np.c_[np.r_[0, np.cumsum(lens)[:-1]], np.cumsum(lens)].astype(np.uint32)
+        pm = U.tile_pixel_mask(np.isin(np.arange(tx * ty), tiles), w_ds, h_ds, tx, dil.tile)
+        vals = []
+        for sgn in (1.0, -1.0):
+            one = {kk: vv[g:g + 1].copy() for kk, vv in p64.items()}
+            flat = one[name].reshape(-1)
+            h = 1e-6 * max(1.0, abs(flat[elem]))
+            flat[elem] += sgn * h
+            po = orc.project(one, ocam, odil)
+            pr = {kk: o[kk].copy() for kk in ("xy", "conic", "opacity", "rgb", "depth")}
+            for kk in pr:
+                pr[kk][g] = po[kk][0]
+            im = orc.render_fwd(pr, sub_v, sub_r, ocam, odil, tile_ids=tiles)["img"]
+            vals.append(float(np.sum((w * im)[pm])))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+        an.append(float(grads[name].reshape(len(p32["means"]), -1)[g, elem]))
+        grp.append(name)
+    fd, an, grp = np.array(fd), np.array(an), np.array(grp)
+    for name in set(grp):
+        sel = grp == name
+        scale = np.abs(fd[sel]).max()
+        assert np.abs(an[sel] - fd[sel]).max() <= GRAD_TOL * scale + 1e-9, (name, an[sel], fd[sel])
+
+
+# ---------------------------------------------------------------------------
+# Full size: 3840x2160, 3M Gaussians, in the launch configuration of the bench
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,ox,oy", [(2, 1, 0), (4, 3, 1)])
+def test_uhd_sampled_tiles_parity(d, ox, oy):
+    scene, cam, tgt = scenes.workload_uhd()
+    p32 = U.params_np(scene)
+    dil = R.Dilation(d, ox, oy)
+    out, rast, p, (img, t_final, last) = U.run_forward(p32, cam, dil)
+    w_ds, h_ds, tx, ty = out["grid"]
+    rng = np.random.default_rng(d)
+    # tiles with content, sampled uniformly
+    nonempty = np.nonzero(out["ranges"][:, 1] > out["ranges"][:, 0])[0]
+    tiles = np.sort(rng.choice(nonempty, 12, replace=False)).astype(np.int32)
+    # binning of those tiles, bit-exact against the oracle's per-tile lists of the GPU rects
+    sv, sr = orc.bin_tiles(out["rects"], U.gpu_depth_bits(out), tx, tiles)
+    for k, t in enumerate(tiles):
+        np.testing.assert_array_equal(out["sorted_ids"][out["ranges"][t, 0]:out["ranges"][t, 1]],
+                                      sv[sr[k, 0]:sr[k, 1]])
+    # projection of every Gaussian
+    o = check_projection(p32, cam, dil, out)
+    # blend of the sampled tiles
+    of = orc.render_fwd(o, sv, sr, orc.as_camera(cam), orc.as_dilation(dil), (0.0, 0.0, 0.0), tile_ids=tiles)
+    mask = np.zeros(tx * ty, bool)
+    mask[tiles] = True
+    pm = U.tile_pixel_mask(mask, w_ds, h_ds, tx, dil.tile) & ~of["ambiguous"]
+    assert np.abs(out["img"] - of["img"])[pm].max() < IMG_TOL
+    np.testing.assert_array_equal(out["last"][pm], of["last"][pm])
+    # backward restricted to the sampled tiles (dL/dimg zero elsewhere)
+    dl = rng.standard_normal(out["img"].shape) * 1e-3
+    dl[~pm] = 0.0
+    rast.render_bwd(cam, dil, (0.0, 0.0, 0.0), t_final, last, torch.tensor(dl, dtype=torch.float32, device=U.DEV))
+    torch.cuda.synchronize()
+    og = orc.render_bwd(o, sv, sr, orc.as_camera(cam), orc.as_dilation(dil), dl.astype(np.float32), tile_ids=tiles)
+    gg = U.split_grad2d(rast.grad2d.cpu().numpy())
+    for k in ("dxy", "dconic", "dopacity", "drgb"):
+        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, k
