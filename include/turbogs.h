@@ -141,6 +141,31 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
                     gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_bin_sort_static -- gs_bin_sort for callers that cannot allocate device
+ * memory: a renderer plugin or embedded host that only hands over its own input
+ * and output buffers, or a serving process whose device memory budget is fixed
+ * once at start-up and forbids cudaMalloc afterwards. The paper has no
+ * counterpart; it exists for those callers only.
+ * Same arguments, results and errors as gs_bin_sort, minus the workspace: the
+ * scratch lives in one array of GS_BIN_SORT_STATIC_SCRATCH_BYTES (32 MiB)
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits. Calls whose gs_bin_sort_workspace_size(n, capacity,
+ * tiles_x*tiles_y) exceeds that size return GS_ERR_ARG (nothing launched) with
+ * the required size in gs_last_error(); for example n = 256K Gaussians with
+ * capacity = 1.5M pairs fits. The call allocates nothing and calls no
+ * allocating routine.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's
+ * contents: calls that may overlap on the GPU (different streams, or
+ * different host threads on one device) race on it, so serialise them. */
+#define GS_BIN_SORT_STATIC_SCRATCH_BYTES (32u << 20)
+int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
+                           const float* splats, int32_t tiles_x, int32_t tiles_y, int64_t capacity,
+                           uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
+                           gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * gs_render_fwd -- front-to-back alpha blending (Sec. 3, Eq. 2) of the lattice
  * pixels of the dilated image (Sec. 3.1: tile lists from the downsampled grid,
  * Gaussian evaluated at the hr pixel (d*u + ox, d*v + oy), Eq. 5).

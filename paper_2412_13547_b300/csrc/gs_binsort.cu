@@ -13,8 +13,14 @@
 // Per-tile ranges are read off the sorted tile keys. The pair count K stays on
 // the device; every kernel clamps to the caller's capacity.
 #include <cstdio>
+#include <mutex>
 
 #include "gs_common.cuh"
+
+// Scratch of gs_bin_sort_static: one array per device, held while the library
+// is loaded. Only device code may name it directly; host code must use the
+// address returned by cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_bin_sort_scratch[GS_BIN_SORT_STATIC_SCRATCH_BYTES];
 
 namespace gs {
 namespace {
@@ -538,6 +544,59 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         k_ranges<<<148 * 8, 256, 0, st>>>(kfinal, num_pairs, capacity, reinterpret_cast<uint2*>(ranges));
     }
     return gs_host::check_launch("gs_bin_sort");
+}
+
+// Device address of g_bin_sort_scratch, looked up once per device with that
+// device current.
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
+                           int32_t tiles_x, int32_t tiles_y, int64_t capacity, uint32_t* sorted_ids,
+                           uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
+{
+    if (n < 0 || capacity < 0 || tiles_x <= 0 || tiles_y <= 0) {
+        gs_host::set_error("gs_bin_sort_static: bad sizes (n >= 0, capacity >= 0, tiles > 0)");
+        return GS_ERR_ARG;
+    }
+    const size_t need = gs_bin_sort_workspace_size(n, capacity, tiles_x * tiles_y);
+    if (need > (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg),
+                      "gs_bin_sort_static: n=%d, capacity=%lld need %zu bytes of scratch; the static array holds "
+                      "%u (use gs_bin_sort with a caller workspace)",
+                      n, (long long)capacity, need, (unsigned)GS_BIN_SORT_STATIC_SCRATCH_BYTES);
+        gs_host::set_error(msg);
+        return GS_ERR_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        gs_host::set_error(e != cudaSuccess ? cudaGetErrorString(e) : "gs_bin_sort_static: device index too large");
+        return GS_ERR_CUDA;
+    }
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (g_static_ptr[dev] == nullptr) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_bin_sort_scratch);
+            if (e != cudaSuccess || p == nullptr) {
+                char msg[256];
+                std::snprintf(msg, sizeof(msg), "gs_bin_sort_static: cudaGetSymbolAddress failed: %s",
+                              cudaGetErrorString(e));
+                gs_host::set_error(msg);
+                return GS_ERR_CUDA;
+            }
+            g_static_ptr[dev] = p;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    return gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, scratch,
+                       (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES, capacity, sorted_ids, ranges, num_pairs, stream);
 }
 
 }  // extern "C"

@@ -23,7 +23,7 @@ GRAD2D_FLOATS = 12
 ADAM_MAX_TENSORS = 8
 
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
-           "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd", "gs_densify_stats", "gs_adam")
+           "gs_bin_sort_static", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd", "gs_densify_stats", "gs_adam")
 
 
 class GsError(RuntimeError):
@@ -95,6 +95,7 @@ def load():
     lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32]
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
     lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
+    lib.gs_bin_sort_static.argtypes = [i32, P, P, P, i32, i32, i64, P, P, P, P]
     lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, P]
     lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
     lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P]
@@ -170,6 +171,17 @@ def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, ca
     _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x), int(tiles_y),
                               _ptr(workspace), workspace.numel() * workspace.element_size(), int(capacity),
                               _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)), "gs_bin_sort")
+
+
+BIN_SORT_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def gs_bin_sort_static(n, rects, tiles_touched, splats, tiles_x, tiles_y, capacity, sorted_ids, ranges, num_pairs,
+                       stream=None):
+    """gs_bin_sort without a workspace argument: for callers that cannot allocate device memory."""
+    _check(load().gs_bin_sort_static(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x),
+                                     int(tiles_y), int(capacity), _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs),
+                                     _stream(stream)), "gs_bin_sort_static")
 
 
 def _bg(bg):
