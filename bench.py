@@ -427,6 +427,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stages-json", default="")
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -453,7 +454,7 @@ def main():
     if args.workload != "uhd":
         args.no_cpu_baseline = True
     w0, h0, tx0, ty0 = R.gs_grid(cam, R.Dilation(1, 0, 0))
-    rast = Rasterizer(params.n, capacity=1 << 20, max_tiles=tx0 * ty0, device=device)
+    rast = Rasterizer(params.n, capacity=1 << 20, max_tiles=tx0 * ty0, device=device, pixels_per_thread=args.ppt)
     kmax = 0
     for d in (1, 2, 4):
         for ox in range(d):

@@ -178,11 +178,17 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
  * Outputs (device): img (h_ds x w_ds x 3), t_final (h_ds x w_ds), last
  *   (h_ds x w_ds: list position + 1 of the last blended entry, 0 if none),
  *   counts (nullable, 2 x uint64 accumulated with +=: list entries evaluated
- *   and entries blended; the caller zeroes it). */
+ *   and entries blended; the caller zeroes it).
+ * pixels_per_thread: launch shape, not semantics -- each thread of the
+ *   tile's CTA handles this many pixels: 0 = the library default, else 1 or 2
+ *   for tile 8, 1, 2 or 4 for tile 16, 2 or 4 for tile 32 (whole warps, at
+ *   most 512 threads; others give GS_ERR_ARG). Results are identical for
+ *   every value. */
 int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
                       const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
                       const float* bg, float* img, float* t_final, uint32_t* last,
-                      unsigned long long* counts, gs_stream_t stream);
+                      unsigned long long* counts, int32_t pixels_per_thread,
+                      gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_loss_l1 -- L1 photometric loss of the rendered lattice pixels against the
@@ -202,12 +208,14 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
  * of atomics per (tile, Gaussian).
  * Inputs (device): as gs_render_fwd plus t_final, last and dl_dimg.
  * Output (device): grad2d (n x 12, layout above), accumulated with +=; with
- *   zero_grad2d != 0 the library first zeroes it on the stream. */
+ *   zero_grad2d != 0 the library first zeroes it on the stream.
+ * pixels_per_thread: as for gs_render_fwd (results equal up to the order of
+ *   the floating-point atomic additions). */
 int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
                       const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
                       const float* bg, const float* t_final, const uint32_t* last,
                       const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
-                      gs_stream_t stream);
+                      int32_t pixels_per_thread, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_project_bwd -- chain rule of gs_project: from grad2d to the parameter

@@ -10,12 +10,6 @@
 namespace gs {
 namespace {
 
-struct SplatStage {
-    float2 p;   // centre relative to the tile's hr origin
-    float4 co;  // conic A, B, C, opacity
-    float4 rgb;
-};
-
 __device__ __forceinline__ void load_stage(const float4* __restrict__ splats, uint32_t g, float X0, float Y0,
                                            float2& p, float4& co, float4& rgb)
 {
@@ -28,76 +22,151 @@ __device__ __forceinline__ void load_stage(const float4* __restrict__ splats, ui
     rgb = make_float4(v1.z, v1.w, v2.x, 0.0f);
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(TILE * TILE)
+// Bounding box (x0, x1, y0, y1; tile-relative hr pixels) of the region where a
+// splat can pass the alpha gate: o exp(-q/2) >= 1/255 <=> q = d^T K d <= tau =
+// 2 ln(255 o), an ellipse whose half-extents are sqrt(tau Sigma_xx),
+// sqrt(tau Sigma_yy) with Sigma = K^-1. tau and the extents are padded well
+// beyond the FP32 error of the gate itself, so every pixel outside the box
+// fails the gate in the kernel's own arithmetic: skipping it changes nothing.
+__device__ __forceinline__ float4 gate_box(float2 p, float4 co)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (!(co.w * 255.0f >= 1.0f)) return make_float4(inf, -inf, inf, -inf);  // never passes
+    const float detK = det2(co.x, co.y, co.y, co.z);  // A C - B^2, FMA-exact
+    const float tau = fmaxf(2.0f * logf(255.0f * co.w), 0.0f) * 1.001f + 1e-3f;
+    const float ex = sqrtf(tau * co.z / detK) * 1.001f + 0.01f;
+    const float ey = sqrtf(tau * co.x / detK) * 1.001f + 0.01f;
+    if (!(detK > 0.0f) || !(ex < 1e30f) || !(ey < 1e30f)) return make_float4(-inf, inf, -inf, inf);
+    return make_float4(p.x - ex, p.x + ex, p.y - ey, p.y + ey);
+}
+
+// Pixels of a CTA: each warp owns a compact 8-column block of 4*PPT rows and
+// each lane one column and PPT consecutive rows of it. Several pixels per
+// thread share one shared-memory read of each staged record and, in the
+// backward, one warp reduction per list entry.
+template <int TILE, int PPT>
+struct TileGeom {
+    static constexpr int PIXELS = TILE * TILE;
+    static constexpr int THREADS = PIXELS / PPT;
+    static constexpr int BATCH = PIXELS < 256 ? PIXELS : 256;
+    static constexpr int WROWS = 4 * PPT;        // rows of a warp's block
+    static constexpr int WCOLS = TILE / 8;       // warp blocks across the tile
+};
+
+template <int TILE, int PPT>
+struct WarpBlock {
+    int lx, ly0;           // this thread's column and first row in the tile
+    float wx0, wx1, wy0, wy1;  // the warp's pixel block, tile-relative hr pixels
+    __device__ __forceinline__ WarpBlock(int tid, int d)
+    {
+        using Geo = TileGeom<TILE, PPT>;
+        const int warp = tid >> 5, lane = tid & 31;
+        const int bx = warp % Geo::WCOLS, by = warp / Geo::WCOLS;
+        lx = bx * 8 + (lane & 7);
+        ly0 = by * Geo::WROWS + (lane >> 3) * PPT;
+        wx0 = (float)(d * bx * 8);
+        wx1 = (float)(d * (bx * 8 + 7));
+        wy0 = (float)(d * by * Geo::WROWS);
+        wy1 = (float)(d * (by * Geo::WROWS + Geo::WROWS - 1));
+    }
+    __device__ __forceinline__ bool misses(float4 box) const
+    {
+        return box.x > wx1 || box.y < wx0 || box.z > wy1 || box.w < wy0;
+    }
+};
+
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
              Dil dil, float3 bg, float* __restrict__ img, float* __restrict__ t_final, uint32_t* __restrict__ last,
              unsigned long long* __restrict__ counts)
 {
-    constexpr int BLOCK = TILE * TILE;
-    constexpr int BATCH = BLOCK < 256 ? BLOCK : 256;
+    using Geo = TileGeom<TILE, PPT>;
+    constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
     __shared__ float2 s_p[BATCH];
+    __shared__ float4 s_box[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
     __shared__ unsigned long long s_cnt[2];
 
     const int tile = blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
-    const int u = tx * TILE + lx, v = ty * TILE + ly;
-    const bool inside = u < dil.w_ds && v < dil.h_ds;
-    // hr origin of the tile and this pixel's hr offset from it (small exact floats)
+    const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
+    const int u = tx * TILE + wb.lx;
+    // hr origin of the tile and this thread's hr offsets from it (small exact floats)
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
-    const float xr = (float)(dil.d * lx), yr = (float)(dil.d * ly);
+    const float xr = (float)(dil.d * wb.lx);
 
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0ull;
     const uint2 rg = ranges[tile];
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last_pos = 0, n_eval = 0, n_blend = 0;
-    bool done = !inside;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], yr[PPT];
+    uint32_t last_pos[PPT];
+    bool done[PPT];
+    int n_live = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.0f; C0[k] = C1[k] = C2[k] = 0.0f; last_pos[k] = 0;
+        yr[k] = (float)(dil.d * (wb.ly0 + k));
+        done[k] = !(u < dil.w_ds && ty * TILE + wb.ly0 + k < dil.h_ds);
+        n_live += done[k] ? 0 : 1;
+    }
+    uint32_t n_eval = 0, n_blend = 0;
 
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(done) == BLOCK) break;
-        const uint32_t idx = start + threadIdx.x;
-        if ((int)threadIdx.x < BATCH && idx < rg.y) {
+        if (__syncthreads_count(n_live == 0) == NT) break;
+        const int cnt = (int)((rg.y - start) < (uint32_t)BATCH ? (rg.y - start) : (uint32_t)BATCH);
+        for (int i = threadIdx.x; i < cnt; i += NT) {
             float2 p; float4 co, rgb;
-            load_stage(splats, __ldg(ids + idx), X0, Y0, p, co, rgb);
-            s_p[threadIdx.x] = p;
-            s_co[threadIdx.x] = co;
-            s_rgb[threadIdx.x] = rgb;
+            load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
+            s_p[i] = p;
+            s_box[i] = gate_box(p, co);
+            s_co[i] = co;
+            s_rgb[i] = rgb;
         }
         __syncthreads();
-        if (!done) {
-            const int cnt = (int)((rg.y - start) < (uint32_t)BATCH ? (rg.y - start) : (uint32_t)BATCH);
+        if (n_live > 0) {
             for (int j = 0; j < cnt; ++j) {
-                ++n_eval;
+                // every live pixel visits the entry (the blend count of the method);
+                // a warp whose block lies outside the entry's gate box skips the arithmetic
+                if (wb.misses(s_box[j])) { n_eval += n_live; continue; }
                 const float2 p = s_p[j];
                 const float4 co = s_co[j];
-                const float dx = __fsub_rn(xr, p.x), dy = __fsub_rn(yr, p.y);
-                const float power = splat_power(dx, dy, co.x, co.y, co.z);
-                if (power > 0.0f) continue;
-                const float alpha = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < kTStop) { done = true; break; }
-                const float4 c = s_rgb[j];
-                const float w = alpha * T;
-                C0 = fmaf(c.x, w, C0);
-                C1 = fmaf(c.y, w, C1);
-                C2 = fmaf(c.z, w, C2);
-                T = Tn;
-                last_pos = start + j - rg.x + 1;
-                ++n_blend;
+                const float dx = __fsub_rn(xr, p.x);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (done[k]) continue;
+                    ++n_eval;
+                    const float dy = __fsub_rn(yr[k], p.y);
+                    const float power = splat_power(dx, dy, co.x, co.y, co.z);
+                    if (power > 0.0f) continue;
+                    const float alpha = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
+                    if (alpha < kAlphaMin) continue;
+                    const float Tn = T[k] * (1.0f - alpha);
+                    if (Tn < kTStop) { done[k] = true; --n_live; continue; }
+                    const float4 c = s_rgb[j];
+                    const float w = alpha * T[k];
+                    C0[k] = fmaf(c.x, w, C0[k]);
+                    C1[k] = fmaf(c.y, w, C1[k]);
+                    C2[k] = fmaf(c.z, w, C2[k]);
+                    T[k] = Tn;
+                    last_pos[k] = start + j - rg.x + 1;
+                    ++n_blend;
+                }
+                if (n_live == 0) break;
             }
         }
     }
-    if (inside) {
-        const int64_t pix = (int64_t)v * dil.w_ds + u;
-        img[3 * pix] = fmaf(T, bg.x, C0);
-        img[3 * pix + 1] = fmaf(T, bg.y, C1);
-        img[3 * pix + 2] = fmaf(T, bg.z, C2);
-        t_final[pix] = T;
-        last[pix] = last_pos;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int v = ty * TILE + wb.ly0 + k;
+        if (u < dil.w_ds && v < dil.h_ds) {
+            const int64_t pix = (int64_t)v * dil.w_ds + u;
+            img[3 * pix] = fmaf(T[k], bg.x, C0[k]);
+            img[3 * pix + 1] = fmaf(T[k], bg.y, C1[k]);
+            img[3 * pix + 2] = fmaf(T[k], bg.z, C2[k]);
+            t_final[pix] = T[k];
+            last[pix] = last_pos[k];
+        }
     }
     if (counts != nullptr) {
         unsigned long long e = n_eval, b = n_blend;
@@ -119,21 +188,65 @@ k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     }
 }
 
+// Sum of 9 per-lane values over a warp by recursive halving: at each step a
+// lane keeps one half of its live slots and sends the other half to its xor
+// partner (5 + 3 + 2 + 1 + 1 = 12 shuffles instead of 9 x 5). On return lane L
+// holds the warp total of component comp (or comp = -1); lanes L and L^1 hold
+// the same component, and components 0..8 each sit on one such pair.
+__device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& comp)
+{
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+    float w[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float hi = i < 4 ? v[5 + i] : 0.0f;
+        const float keep = h16 ? hi : v[i];
+        const float send = h16 ? v[i] : hi;
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float hi = i < 2 ? w[3 + i] : 0.0f;
+        const float keep = h8 ? hi : w[i];
+        const float send = h8 ? w[i] : hi;
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float hi = i < 1 ? x[2] : 0.0f;
+        const float keep = h4 ? hi : x[i];
+        const float send = h4 ? x[i] : hi;
+        y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float z = (h2 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, h2 ? y[0] : y[1], 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    // slot bookkeeping: y slot -> x slot -> w slot -> component
+    int ys = h2 ? 1 : 0;
+    int xs = h4 ? (ys == 0 ? 2 : -1) : ys;
+    int ws = xs < 0 ? -1 : (h8 ? (xs < 2 ? 3 + xs : -1) : xs);
+    comp = ws < 0 ? -1 : (h16 ? (ws < 4 ? 5 + ws : -1) : ws);
+    return z;
+}
+
 // Backward: replay each pixel's list back to front from (t_final, last),
-// recovering T_i = T_{i+1} / (1 - alpha_i). Per list entry the 32 lanes of a
-// warp evaluate the same Gaussian; their 9 partial gradients are summed with
-// xor shuffles, folded into a per-batch shared-memory accumulator (9 lanes,
-// one component each), and flushed with one set of vector atomics per
-// (tile, Gaussian) at the end of the batch.
-template <int TILE>
-__global__ void __launch_bounds__(TILE * TILE)
+// recovering T_i = T_{i+1} / (1 - alpha_i). A warp skips entries past the last
+// contributor of all its pixels and entries whose gate box misses its block.
+// Per remaining entry a thread sums the 9 partial gradients of its pixels, the
+// warp sums them (warp_sum9), one lane per component adds the total into a
+// per-batch shared-memory accumulator, and at the end of the batch each
+// (tile, Gaussian) gets one set of vector atomics.
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
              Dil dil, float3 bg, const float* __restrict__ t_final, const uint32_t* __restrict__ last,
              const float* __restrict__ dl_dimg, float* __restrict__ grad2d)
 {
-    constexpr int BLOCK = TILE * TILE;
-    constexpr int BATCH = BLOCK < 256 ? BLOCK : 256;
+    using Geo = TileGeom<TILE, PPT>;
+    constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
     __shared__ float2 s_p[BATCH];
+    __shared__ float4 s_box[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_id[BATCH];
@@ -142,28 +255,36 @@ k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
 
     const int tile = blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
     const int lane = threadIdx.x & 31;
-    const int u = tx * TILE + lx, v = ty * TILE + ly;
-    const bool inside = u < dil.w_ds && v < dil.h_ds;
+    const int u = tx * TILE + wb.lx;
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
-    const float xr = (float)(dil.d * lx), yr = (float)(dil.d * ly);
+    const float xr = (float)(dil.d * wb.lx);
     const uint2 rg = ranges[tile];
 
-    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    uint32_t n_last = 0;
-    if (inside) {
-        const int64_t pix = (int64_t)v * dil.w_ds + u;
-        T = t_final[pix];
-        n_last = last[pix];
-        g0 = dl_dimg[3 * pix];
-        g1 = dl_dimg[3 * pix + 1];
-        g2 = dl_dimg[3 * pix + 2];
+    float T[PPT], S0[PPT], S1[PPT], S2[PPT], g0[PPT], g1[PPT], g2[PPT], yr[PPT];
+    uint32_t n_last[PPT];
+    uint32_t my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int v = ty * TILE + wb.ly0 + k;
+        yr[k] = (float)(dil.d * (wb.ly0 + k));
+        T[k] = 1.0f; g0[k] = g1[k] = g2[k] = 0.0f; n_last[k] = 0;
+        if (u < dil.w_ds && v < dil.h_ds) {
+            const int64_t pix = (int64_t)v * dil.w_ds + u;
+            T[k] = t_final[pix];
+            n_last[k] = last[pix];
+            g0[k] = dl_dimg[3 * pix];
+            g1[k] = dl_dimg[3 * pix + 1];
+            g2[k] = dl_dimg[3 * pix + 2];
+        }
+        S0[k] = T[k] * bg.x; S1[k] = T[k] * bg.y; S2[k] = T[k] * bg.z;
+        my_max = max(my_max, n_last[k]);
     }
-    float S0 = T * bg.x, S1 = T * bg.y, S2 = T * bg.z;
+    const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
-    if (n_last > 0) atomicMax(&s_max_last, n_last);
+    if (lane == 0 && warp_max > 0) atomicMax(&s_max_last, warp_max);
     __syncthreads();
     const uint32_t n_proc = s_max_last;
     if (n_proc == 0) return;
@@ -172,82 +293,79 @@ k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
         const uint32_t bstart = (uint32_t)b * BATCH;
         const int cnt = (int)((n_proc - bstart) < (uint32_t)BATCH ? (n_proc - bstart) : (uint32_t)BATCH);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t g = __ldg(ids + rg.x + bstart + threadIdx.x);
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            const uint32_t g = __ldg(ids + rg.x + bstart + i);
             float2 p; float4 co, rgb;
             load_stage(splats, g, X0, Y0, p, co, rgb);
-            s_p[threadIdx.x] = p;
-            s_co[threadIdx.x] = co;
-            s_rgb[threadIdx.x] = rgb;
-            s_id[threadIdx.x] = g;
+            s_p[i] = p;
+            s_box[i] = gate_box(p, co);
+            s_co[i] = co;
+            s_rgb[i] = rgb;
+            s_id[i] = g;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_acc[threadIdx.x][k] = 0.0f;
+            for (int k = 0; k < 9; ++k) s_acc[i][k] = 0.0f;
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
+        const int j_top = warp_max > bstart ? (int)min((uint32_t)cnt, warp_max - bstart) - 1 : -1;
+        for (int j = j_top; j >= 0; --j) {
+            if (wb.misses(s_box[j])) continue;
             const uint32_t pos = bstart + (uint32_t)j;
             float r[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) r[k] = 0.0f;
             bool contrib = false;
-            if (pos < n_last) {
-                const float2 p = s_p[j];
-                const float4 co = s_co[j];
-                const float dx = __fsub_rn(xr, p.x), dy = __fsub_rn(yr, p.y);
+            const float2 p = s_p[j];
+            const float4 co = s_co[j];
+            const float4 c = s_rgb[j];
+            const float dx = __fsub_rn(xr, p.x);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pos >= n_last[k]) continue;
+                const float dy = __fsub_rn(yr[k], p.y);
                 const float power = splat_power(dx, dy, co.x, co.y, co.z);
-                if (power <= 0.0f) {
-                    const float G = __expf(power);
-                    const float a_raw = __fmul_rn(co.w, G);  // as splat_alpha_raw
-                    const float alpha = fminf(kAlphaMax, a_raw);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float4 c = s_rgb[j];
-                        const float one_m = 1.0f - alpha;
-                        const float Ti = T / one_m;
-                        const float w = alpha * Ti;
-                        r[6] = w * g0;
-                        r[7] = w * g1;
-                        r[8] = w * g2;
-                        const float inv = 1.0f / one_m;
-                        const float dalpha = g0 * (Ti * c.x - S0 * inv) + g1 * (Ti * c.y - S1 * inv) +
-                                             g2 * (Ti * c.z - S2 * inv);
-                        S0 = fmaf(c.x, w, S0);
-                        S1 = fmaf(c.y, w, S1);
-                        S2 = fmaf(c.z, w, S2);
-                        T = Ti;
-                        if (a_raw < kAlphaMax) {
-                            const float dpower = a_raw * dalpha;
-                            r[5] = G * dalpha;
-                            r[2] = -0.5f * dx * dx * dpower;
-                            r[3] = -dx * dy * dpower;
-                            r[4] = -0.5f * dy * dy * dpower;
-                            r[0] = dpower * (co.x * dx + co.y * dy);
-                            r[1] = dpower * (co.z * dy + co.y * dx);
-                        }
-                    }
+                if (power > 0.0f) continue;
+                const float G = __expf(power);
+                const float a_raw = __fmul_rn(co.w, G);  // as splat_alpha_raw
+                const float alpha = fminf(kAlphaMax, a_raw);
+                if (alpha < kAlphaMin) continue;
+                contrib = true;
+                const float one_m = 1.0f - alpha;
+                const float Ti = T[k] / one_m;
+                const float w = alpha * Ti;
+                r[6] = fmaf(w, g0[k], r[6]);
+                r[7] = fmaf(w, g1[k], r[7]);
+                r[8] = fmaf(w, g2[k], r[8]);
+                const float inv = 1.0f / one_m;
+                const float dalpha = g0[k] * (Ti * c.x - S0[k] * inv) + g1[k] * (Ti * c.y - S1[k] * inv) +
+                                     g2[k] * (Ti * c.z - S2[k] * inv);
+                S0[k] = fmaf(c.x, w, S0[k]);
+                S1[k] = fmaf(c.y, w, S1[k]);
+                S2[k] = fmaf(c.z, w, S2[k]);
+                T[k] = Ti;
+                if (a_raw < kAlphaMax) {
+                    const float dpower = a_raw * dalpha;
+                    r[5] = fmaf(G, dalpha, r[5]);
+                    r[2] = fmaf(-0.5f * dx * dx, dpower, r[2]);
+                    r[3] = fmaf(-dx * dy, dpower, r[3]);
+                    r[4] = fmaf(-0.5f * dy * dy, dpower, r[4]);
+                    r[0] = fmaf(dpower, co.x * dx + co.y * dy, r[0]);
+                    r[1] = fmaf(dpower, co.z * dy + co.y * dx, r[1]);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
-                }
-                float mine = r[0];
-#pragma unroll
-                for (int k = 1; k < 9; ++k)
-                    if (lane == k) mine = r[k];
-                if (lane < 9) atomicAdd(&s_acc[j][lane], mine);
+                int comp;
+                const float z = warp_sum9(r, lane, comp);
+                if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], z);
             }
         }
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const float* a = s_acc[threadIdx.x];
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            const float* a = s_acc[i];
             bool any = false;
 #pragma unroll
             for (int k = 0; k < 9; ++k) any |= (a[k] != 0.0f);
             if (any) {
-                float* dst = grad2d + (int64_t)GS_GRAD2D_FLOATS * s_id[threadIdx.x];
+                float* dst = grad2d + (int64_t)GS_GRAD2D_FLOATS * s_id[i];
                 atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a[0], a[1], a[2], a[3]));
                 atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(a[4], a[5], a[6], a[7]));
                 atomicAdd(dst + 8, a[8]);
@@ -284,6 +402,21 @@ __global__ void k_loss_l1(Dil dil, int width, const float* __restrict__ img, con
     }
 }
 
+// Pixels per thread: 0 picks the default; otherwise 1, 2 or 4 such that the
+// CTA is whole warps and at most 512 threads (tile 8: 1 or 2; tile 32: 2 or 4).
+// The kernels use full-warp shuffles and votes, so a partial warp is refused.
+int resolve_ppt(int tile, int ppt)
+{
+    if (ppt == 0) return tile == 8 ? 1 : 2;
+    const int threads = (ppt == 1 || ppt == 2 || ppt == 4) ? tile * tile / ppt : 0;
+    if (threads < 32 || threads > 512 || threads % 32 != 0) {
+        gs_host::set_error("pixels_per_thread must be 0 (default), 1, 2 or 4, giving 32..512 threads per tile "
+                           "(tile 8: 1 or 2; tile 16: 1, 2 or 4; tile 32: 2 or 4)");
+        return -1;
+    }
+    return ppt;
+}
+
 bool check_render_args(int32_t n, const float* splats, const uint32_t* ids, const uint32_t* ranges)
 {
     if (n < 0) { gs_host::set_error("n must be >= 0"); return false; }
@@ -302,30 +435,38 @@ extern "C" {
 
 int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids, const uint32_t* ranges,
                       const GsCamera* cam, const GsDilation* dil, const float* bg, float* img, float* t_final,
-                      uint32_t* last, unsigned long long* counts, gs_stream_t stream)
+                      uint32_t* last, unsigned long long* counts, int32_t pixels_per_thread, gs_stream_t stream)
 {
     using namespace gs;
     Dil d;
     if (!gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
     if (!check_render_args(n, splats, sorted_ids, ranges)) return GS_ERR_ARG;
     if (!bg || !img || !t_final || !last) { gs_host::set_error("gs_render_fwd: null pointer"); return GS_ERR_ARG; }
+    const int ppt = resolve_ppt(d.tile, pixels_per_thread);
+    if (ppt < 0) return GS_ERR_ARG;
     const float3 b = make_float3(bg[0], bg[1], bg[2]);
     const int tiles = d.tiles_x * d.tiles_y;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float4* sp = reinterpret_cast<const float4*>(splats);
     const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-    switch (d.tile) {
-        case 8: k_render_fwd<8><<<tiles, 64, 0, st>>>(sp, sorted_ids, rg, d, b, img, t_final, last, counts); break;
-        case 16: k_render_fwd<16><<<tiles, 256, 0, st>>>(sp, sorted_ids, rg, d, b, img, t_final, last, counts); break;
-        default: k_render_fwd<32><<<tiles, 1024, 0, st>>>(sp, sorted_ids, rg, d, b, img, t_final, last, counts); break;
+#define GS_FWD(T_, P_) k_render_fwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, d, b, img, t_final, last, counts)
+    switch (d.tile * 8 + ppt) {
+        case 8 * 8 + 1: GS_FWD(8, 1); break;
+        case 8 * 8 + 2: GS_FWD(8, 2); break;
+        case 16 * 8 + 1: GS_FWD(16, 1); break;
+        case 16 * 8 + 2: GS_FWD(16, 2); break;
+        case 16 * 8 + 4: GS_FWD(16, 4); break;
+        case 32 * 8 + 2: GS_FWD(32, 2); break;
+        default: GS_FWD(32, 4); break;
     }
+#undef GS_FWD
     return gs_host::check_launch("gs_render_fwd");
 }
 
 int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids, const uint32_t* ranges,
                       const GsCamera* cam, const GsDilation* dil, const float* bg, const float* t_final,
                       const uint32_t* last, const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
-                      gs_stream_t stream)
+                      int32_t pixels_per_thread, gs_stream_t stream)
 {
     using namespace gs;
     Dil d;
@@ -339,17 +480,25 @@ int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids
         gs_host::set_error("gs_render_bwd: grad2d must be 16-byte aligned");
         return GS_ERR_ARG;
     }
+    const int ppt = resolve_ppt(d.tile, pixels_per_thread);
+    if (ppt < 0) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (zero_grad2d && n > 0) cudaMemsetAsync(grad2d, 0, (size_t)n * GS_GRAD2D_FLOATS * sizeof(float), st);
     const float3 b = make_float3(bg[0], bg[1], bg[2]);
     const int tiles = d.tiles_x * d.tiles_y;
     const float4* sp = reinterpret_cast<const float4*>(splats);
     const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-    switch (d.tile) {
-        case 8: k_render_bwd<8><<<tiles, 64, 0, st>>>(sp, sorted_ids, rg, d, b, t_final, last, dl_dimg, grad2d); break;
-        case 16: k_render_bwd<16><<<tiles, 256, 0, st>>>(sp, sorted_ids, rg, d, b, t_final, last, dl_dimg, grad2d); break;
-        default: k_render_bwd<32><<<tiles, 1024, 0, st>>>(sp, sorted_ids, rg, d, b, t_final, last, dl_dimg, grad2d); break;
+#define GS_BWD(T_, P_) k_render_bwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, d, b, t_final, last, dl_dimg, grad2d)
+    switch (d.tile * 8 + ppt) {
+        case 8 * 8 + 1: GS_BWD(8, 1); break;
+        case 8 * 8 + 2: GS_BWD(8, 2); break;
+        case 16 * 8 + 1: GS_BWD(16, 1); break;
+        case 16 * 8 + 2: GS_BWD(16, 2); break;
+        case 16 * 8 + 4: GS_BWD(16, 4); break;
+        case 32 * 8 + 2: GS_BWD(32, 2); break;
+        default: GS_BWD(32, 4); break;
     }
+#undef GS_BWD
     return gs_host::check_launch("gs_render_bwd");
 }
 

@@ -53,8 +53,10 @@ class Rasterizer:
     tile grid. Nothing here synchronises with the host except ``num_pairs()``
     and ``ensure_capacity``."""
 
-    def __init__(self, n: int, capacity: int = 1 << 20, max_tiles: int = 1, device="cuda"):
+    def __init__(self, n: int, capacity: int = 1 << 20, max_tiles: int = 1, device="cuda",
+                 pixels_per_thread: int = 0):
         self.device = torch.device(device)
+        self.ppt = int(pixels_per_thread)
         self.n = int(n)
         self.splats = torch.zeros(self.n, R.SPLAT_FLOATS, device=self.device)
         self.radii = torch.zeros(self.n, dtype=torch.int32, device=self.device)
@@ -108,11 +110,12 @@ class Rasterizer:
         return grid
 
     def render(self, cam, dil: Dilation, bg, img, t_final, last, counts=None):
-        R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts)
+        R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts,
+                        pixels_per_thread=self.ppt)
 
     def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg):
         R.gs_render_bwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, t_final, last, dl_dimg,
-                        self.grad2d, zero_grad2d=True)
+                        self.grad2d, zero_grad2d=True, pixels_per_thread=self.ppt)
 
 
 def image_buffers(h_ds: int, w_ds: int, device="cuda"):

@@ -96,9 +96,9 @@ def load():
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
     lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
     lib.gs_bin_sort_static.argtypes = [i32, P, P, P, i32, i32, i64, P, P, P, P]
-    lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, P]
+    lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P]
     lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
-    lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P]
+    lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, i32, P]
     lib.gs_project_bwd.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P, P, P, P, P, P]
     lib.gs_densify_stats.argtypes = [i32, P, P, P, P, P, P]
     lib.gs_adam.argtypes = [ctypes.POINTER(GsAdamTensor), i32, f32, f32, f32, i32, P, P]
@@ -190,10 +190,10 @@ def _bg(bg):
 
 
 def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, counts=None,
-                  stream=None):
+                  pixels_per_thread=0, stream=None):
     _check(load().gs_render_fwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last), _ptr(counts),
-                                _stream(stream)), "gs_render_fwd")
+                                int(pixels_per_thread), _stream(stream)), "gs_render_fwd")
 
 
 def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
@@ -202,10 +202,11 @@ def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
 
 
 def gs_render_bwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, t_final, last, dl_dimg, grad2d,
-                  zero_grad2d=True, stream=None):
+                  zero_grad2d=True, pixels_per_thread=0, stream=None):
     _check(load().gs_render_bwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(t_final), _ptr(last), _ptr(dl_dimg),
-                                _ptr(grad2d), int(bool(zero_grad2d)), _stream(stream)), "gs_render_bwd")
+                                _ptr(grad2d), int(bool(zero_grad2d)), int(pixels_per_thread), _stream(stream)),
+           "gs_render_bwd")
 
 
 def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, tiles_touched, grad2d,

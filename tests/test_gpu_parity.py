@@ -185,6 +185,34 @@ def test_render_fwd_parity_sh3_ragged():
         np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
 
 
+@pytest.mark.parametrize("tile,ppts", [(8, (1, 2)), (16, (1, 2, 4)), (32, (2, 4))])
+def test_launch_shape_does_not_change_results(tile, ppts):
+    """pixels_per_thread is a launch shape: the forward is bit-identical across it
+    and the backward differs only by the order of floating-point atomics."""
+    p32, cam, _ = scene_sh3(131, 97)
+    dil = R.Dilation(2, 1, 0, tile=tile)
+    p = U.gpu_params(p32)
+    w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+    outs = []
+    for ppt in ppts:
+        rast = Rasterizer(p.n, capacity=1 << 16, max_tiles=tx * ty, pixels_per_thread=ppt)
+        rast.project(p, cam, dil)
+        rast.bin_checked(cam, dil)
+        img, tf, last = image_buffers(h_ds, w_ds)
+        counts = torch.zeros(2, dtype=torch.int64, device=U.DEV)
+        rast.render(cam, dil, (0.1, 0.2, 0.3), img, tf, last, counts)
+        dl = torch.tensor(np.random.default_rng(0).standard_normal((h_ds, w_ds, 3)) * 1e-3, dtype=torch.float32,
+                          device=U.DEV)
+        rast.render_bwd(cam, dil, (0.1, 0.2, 0.3), tf, last, dl)
+        torch.cuda.synchronize()
+        outs.append([img.cpu().numpy(), tf.cpu().numpy(), last.cpu().numpy(), counts.cpu().numpy(),
+                     rast.grad2d.cpu().numpy()])
+    for o in outs[1:]:
+        for a, b in zip(o[:4], outs[0][:4]):
+            np.testing.assert_array_equal(a, b)
+        assert U.max_rel(o[4], outs[0][4]) < 1e-5
+
+
 def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
     out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg)
     rng = np.random.default_rng(seed)
