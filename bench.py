@@ -107,7 +107,7 @@ class ClockSampler:
 # Our arm
 # ---------------------------------------------------------------------------
 
-STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam")
+STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
 
 
 def setup(args, device):
@@ -163,24 +163,10 @@ class TimedStep:
         mark("render_bwd", 0)
         rast.render_bwd(cam, dil, st.bg, t_final, last, dl)
         mark("render_bwd", 1)
-        g = st.grads
-        mark("project_bwd", 0)
-        R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil,
-                         rast.tiles_touched, rast.grad2d, g[0], g[1], g[2], g[3], g[4], st.pos_acc, st.col_acc,
-                         st.vis_count)
-        mark("project_bwd", 1)
         st.step_count += 1
-        a = st.adam
-        lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
-        entries = []
-        for j, t in enumerate(p.tensors()):
-            e = dict(param=t, grad=g[j], m=st.m[j], v=st.v[j], lr=lrs[j], row_width=max(1, t[0].numel()))
-            if j == 4 and p.sh_store.data_ptr() != p.sh.data_ptr():
-                e["shadow"] = p.sh_store
-            entries.append(e)
-        mark("adam", 0)
-        R.gs_adam(entries, a.beta1, a.beta2, a.eps, st.step_count)
-        mark("adam", 1)
+        mark("project_bwd_adam", 0)
+        st.optimize(cam, dil)
+        mark("project_bwd_adam", 1)
         return st.loss
 
     def stage_ms(self, steps):
@@ -268,10 +254,9 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     rows["loss"] = ("hbm", 36.0 * step_pixels)
     # blend backward: ~45 FP32 flops per replayed (pixel, entry)
     rows["render_bwd"] = ("alu", 45.0 * res["replayed_per_step"])
-    # projection backward: parameters + 2D grads in, parameter grads + densify stats out
-    rows["project_bwd"] = ("hbm", params_b + n * 48 + n * 4 * (3 + 3 + 4 + 1 + 48) + n * 24)
-    # Adam: p, g, m, v read, p, m, v written (FP32) for 59 floats per Gaussian
-    rows["adam"] = ("hbm", n * 59 * 4 * 7)
+    # projection backward + densification statistics + Adam, fused: parameters, moments and the
+    # 2D record read, parameters and moments written, statistics read-modify-written
+    rows["project_bwd_adam"] = ("hbm", 3 * params_b + n * 48 + 3 * n * 59 * 4 + n * (24 + 4))
     out = {}
     for s, (bound, work) in rows.items():
         ms = res["stage_ms"][s]

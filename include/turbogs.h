@@ -234,6 +234,37 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
                        gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_project_bwd_adam -- gs_project_bwd, gs_densify_stats and gs_adam fused
+ * into one pass over the Gaussians (the gradient of each Gaussian goes from
+ * its 2D record straight into its Adam update, never through HBM). Results
+ * equal gs_project_bwd followed by gs_adam with the same settings bit for bit.
+ * adam->param[0..4] are the FP32 parameters (means, log_scales, quats,
+ * opacity_logits, sh), updated in place; m, v their moments; lr per tensor.
+ * sh_store (device) is the SH storage the forward projection read: adam->param[4]
+ * itself (sh_dtype FP32) or its BF16/FP16 copy, which is then refreshed from the
+ * updated FP32 values when adam->sh_shadow points at it. With adam->sparse != 0
+ * Gaussians with tiles_touched == 0 are left untouched (no moment decay).
+ * grads_out (nullable host array of 5 device pointers, each nullable) receives
+ * the gradients as gs_project_bwd would write them. pos_acc/col_acc/count:
+ * as in gs_project_bwd. */
+typedef struct {
+    float* param[5];
+    float* m[5];
+    float* v[5];
+    float lr[5];
+    float beta1, beta2, eps;
+    int32_t step;
+    int32_t sparse;
+    void* sh_shadow;
+    int32_t sh_shadow_dtype;
+} GsAdamParams;
+int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                            const GsCamera* cam, const GsDilation* dil,
+                            const int32_t* tiles_touched, const float* grad2d,
+                            const GsAdamParams* adam, float* pos_acc, float* col_acc,
+                            int32_t* count, float* const* grads_out, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * gs_densify_stats -- position-appearance densification scores (Sec. 3.3): for
  * every Gaussian with tiles_touched > 0, pos_acc += |(dL/dx, dL/dy)|_2 (hr
  * pixel units), col_acc += |(dL/dr, dL/dg, dL/db)|_2, count += 1 (device). */

@@ -30,18 +30,12 @@ struct AdamArgs {
 
 __device__ __forceinline__ void adam_elem(float& p, float g, float& m, float& v, const AdamArgs& a, float lr)
 {
-    m = fmaf(a.b1, m, (1.0f - a.b1) * g);
-    v = fmaf(a.b2, v, (1.0f - a.b2) * g * g);
-    const float mhat = m * a.inv_bc1;
-    const float vhat = v * a.inv_bc2;
-    p -= lr * mhat / (sqrtf(vhat) + a.eps);
+    adam_step(p, g, m, v, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, lr);
 }
 
 __device__ __forceinline__ void store_shadow(void* shadow, int dtype, int64_t e, float val)
 {
-    if (dtype == GS_DTYPE_BF16) reinterpret_cast<__nv_bfloat16*>(shadow)[e] = __float2bfloat16_rn(val);
-    else if (dtype == GS_DTYPE_F16) reinterpret_cast<__half*>(shadow)[e] = __float2half_rn(val);
-    else reinterpret_cast<float*>(shadow)[e] = val;
+    store_as(shadow, dtype, e, val);
 }
 
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a)

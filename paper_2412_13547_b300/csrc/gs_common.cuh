@@ -209,6 +209,26 @@ __device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z,
           + c.k3e * (xx - yy) * w[14];
 }
 
+// One Adam update (Kingma & Ba, bias-corrected; inv_bc = 1 / (1 - beta^step)),
+// rounding pinned with intrinsics so every kernel that applies it agrees bit
+// for bit.
+__device__ __forceinline__ void adam_step(float& p, float g, float& m, float& v, float b1, float b2, float eps,
+                                          float inv_bc1, float inv_bc2, float lr)
+{
+    m = __fmaf_rn(b1, m, __fmul_rn(1.0f - b1, g));
+    v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.0f - b2, g), g));
+    const float mhat = __fmul_rn(m, inv_bc1);
+    const float vhat = __fmul_rn(v, inv_bc2);
+    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), eps)));
+}
+
+__device__ __forceinline__ void store_as(void* dst, int dtype, int64_t e, float val)
+{
+    if (dtype == GS_DTYPE_BF16) reinterpret_cast<__nv_bfloat16*>(dst)[e] = __float2bfloat16_rn(val);
+    else if (dtype == GS_DTYPE_F16) reinterpret_cast<__half*>(dst)[e] = __float2half_rn(val);
+    else reinterpret_cast<float*>(dst)[e] = val;
+}
+
 // SH storage conversions
 __device__ __forceinline__ float load_sh_elem(const void* base, int64_t idx, int dtype)
 {

@@ -269,71 +269,25 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
 // Backward of the projection (chain rule through conic, Sigma' = N N^T + lp,
 // N = J W M, M = R(q) S, the image-plane centre and the SH direction).
 // ---------------------------------------------------------------------------
-template <int DEG, int DT>
-__global__ void __launch_bounds__(kThreads)
-k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
-              const float4* __restrict__ quats, const float* __restrict__ logits,
-              const void* __restrict__ sh, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
-              const float4* __restrict__ grad2d, float* __restrict__ d_means,
-              float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
-              float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pos_acc,
-              float* __restrict__ col_acc, int* __restrict__ count)
+struct ParamGrad {
+    float gm[3], gls[3];
+    float4 gq;
+    float glogit;
+    float gsh[16][3];
+};
+
+// Gradients of one visible Gaussian from its 2D gradient record (G0, G1, G2).
+template <int DEG>
+__device__ __forceinline__ void project_bwd_one(const Cam& cam, const Proj& P, const float (&c)[16][3],
+                                                float4 G0, float4 G1, float4 G2, ParamGrad& R)
 {
-    using L = ShLayout<DEG, DT>;
-    constexpr int K = L::K;
-    extern __shared__ uint32_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g0 = (blockIdx.x * kWarps + warp) * 32;
-    if (g0 >= n) return;
-    uint32_t* s_mean = smem + warp * L::WARP_WORDS;
-    uint32_t* s_scale = s_mean + 32 * 3;
-    uint32_t* s_sh = s_scale + 32 * 3;
-    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(means), n, g0, s_mean, lane);
-    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(log_scales), n, g0, s_scale, lane);
-    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh), n, g0, s_sh, lane);
-    const int g = g0 + lane;
-    if (g >= n) return;
-
-    float mean[3], ls[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
-        ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
-    }
-    float c[16][3];
-    read_sh<DEG, DT>(s_sh, sh, g, lane, c);
-    Proj P;
-    project_one<DEG>(cam, dil, mean, ls, quats[g], logits[g], c, P);
-
-    float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f};
-    float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
-    float glogit = 0.0f;
-    float* gsh = d_sh + (int64_t)g * K * 3;
-    if (P.culled) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            d_means[3 * (int64_t)g + j] = 0.f;
-            d_log_scales[3 * (int64_t)g + j] = 0.f;
-        }
-        d_quats[g] = gq;
-        d_logits[g] = 0.f;
-#pragma unroll
-        for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
-        return;
-    }
-    const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
+    constexpr int K = (DEG + 1) * (DEG + 1);
     const float gpx = G0.x, gpy = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y;
     float grgb[3] = {G1.z, G1.w, G2.x};
-
-    // densification statistics (Sec. 3.3)
-    if (pos_acc != nullptr && tiles_touched[g] > 0) {
-        pos_acc[g] += sqrtf(gpx * gpx + gpy * gpy);
-        col_acc[g] += sqrtf(grgb[0] * grgb[0] + grgb[1] * grgb[1] + grgb[2] * grgb[2]);
-        count[g] += 1;
-    }
-
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R.gm[j] = 0.0f;
     // opacity = sigmoid(logit)
-    glogit = gop * P.opacity * (1.0f - P.opacity);
+    R.glogit = gop * P.opacity * (1.0f - P.opacity);
 
     // colour: SH coefficients and the view direction
     float Y[16];
@@ -346,14 +300,14 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
     for (int k = 0; k < K; ++k) {
         wsh[k] = grgb[0] * c[k][0] + grgb[1] * c[k][1] + grgb[2] * c[k][2];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = Y[k] * grgb[ch];
+        for (int ch = 0; ch < 3; ++ch) R.gsh[k][ch] = Y[k] * grgb[ch];
     }
     float gdx, gdy, gdz;
     sh_basis_vjp(DEG, P.dir[0], P.dir[1], P.dir[2], wsh, gdx, gdy, gdz);
     float dd = gdx * P.dir[0] + gdy * P.dir[1] + gdz * P.dir[2];
-    gm[0] += (gdx - P.dir[0] * dd) * P.inv_vlen;
-    gm[1] += (gdy - P.dir[1] * dd) * P.inv_vlen;
-    gm[2] += (gdz - P.dir[2] * dd) * P.inv_vlen;
+    R.gm[0] += (gdx - P.dir[0] * dd) * P.inv_vlen;
+    R.gm[1] += (gdy - P.dir[1] * dd) * P.inv_vlen;
+    R.gm[2] += (gdz - P.dir[2] * dd) * P.inv_vlen;
 
     // conic = inverse of Sigma': dL/dSigma' = -K Gk K, Gk = [[gA, gB/2], [gB/2, gC]]
     float k00 = P.A * gA + P.B * 0.5f * gB, k01 = P.A * 0.5f * gB + P.B * gC;
@@ -405,7 +359,7 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
     dt2 += -(gpx * cam.fx * P.u + gpy * cam.fy * P.v) * itz;
     // t = W mean + T
 #pragma unroll
-    for (int j = 0; j < 3; ++j) gm[j] += cam.R[j] * dt0 + cam.R[3 + j] * dt1 + cam.R[6 + j] * dt2;
+    for (int j = 0; j < 3; ++j) R.gm[j] += cam.R[j] * dt0 + cam.R[3 + j] * dt1 + cam.R[6 + j] * dt2;
 
     // M = R diag(s)
     float dR[9];
@@ -417,7 +371,7 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
             acc += dM[3 * j + k] * P.R[3 * j + k];
             dR[3 * j + k] = dM[3 * j + k] * P.s[k];
         }
-        gls[k] = acc * P.s[k];
+        R.gls[k] = acc * P.s[k];
     }
     // R(w, x, y, z)
     const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
@@ -426,16 +380,255 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
     float gy = 2.0f * (x * (dR[1] + dR[3]) + z * (dR[5] + dR[7]) + w * (dR[2] - dR[6]) - 2.0f * y * (dR[0] + dR[8]));
     float gz = 2.0f * (x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) + w * (dR[3] - dR[1]) - 2.0f * z * (dR[0] + dR[4]));
     float qd = gw * w + gx * x + gy * y + gz * z;
-    gq = make_float4((gw - w * qd) * P.inv_qnorm, (gx - x * qd) * P.inv_qnorm,
+    R.gq = make_float4((gw - w * qd) * P.inv_qnorm, (gx - x * qd) * P.inv_qnorm,
                      (gy - y * qd) * P.inv_qnorm, (gz - z * qd) * P.inv_qnorm);
 
+}
+
+__device__ __forceinline__ void densify_one(int g, const int* tiles_touched, float4 G0, float4 G1, float4 G2,
+                                            float* pos_acc, float* col_acc, int* count)
+{
+    if (pos_acc != nullptr && tiles_touched[g] > 0) {
+        pos_acc[g] += sqrtf(G0.x * G0.x + G0.y * G0.y);
+        col_acc[g] += sqrtf(G1.z * G1.z + G1.w * G1.w + G2.x * G2.x);
+        count[g] += 1;
+    }
+}
+
+template <int DEG, int DT>
+__global__ void __launch_bounds__(kThreads)
+k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+              const float4* __restrict__ quats, const float* __restrict__ logits,
+              const void* __restrict__ sh, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
+              const float4* __restrict__ grad2d, float* __restrict__ d_means,
+              float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
+              float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pos_acc,
+              float* __restrict__ col_acc, int* __restrict__ count)
+{
+    using L = ShLayout<DEG, DT>;
+    constexpr int K = L::K;
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * kWarps + warp) * 32;
+    if (g0 >= n) return;
+    uint32_t* s_mean = smem + warp * L::WARP_WORDS;
+    uint32_t* s_scale = s_mean + 32 * 3;
+    uint32_t* s_sh = s_scale + 32 * 3;
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(means), n, g0, s_mean, lane);
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(log_scales), n, g0, s_scale, lane);
+    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh), n, g0, s_sh, lane);
+    const int g = g0 + lane;
+    if (g >= n) return;
+
+    float mean[3], ls[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        d_means[3 * (int64_t)g + j] = gm[j];
-        d_log_scales[3 * (int64_t)g + j] = gls[j];
+        mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
+        ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
     }
-    d_quats[g] = gq;
-    d_logits[g] = glogit;
+    float c[16][3];
+    read_sh<DEG, DT>(s_sh, sh, g, lane, c);
+    Proj P;
+    project_one<DEG>(cam, dil, mean, ls, quats[g], logits[g], c, P);
+    float* gsh = d_sh + (int64_t)g * K * 3;
+    if (P.culled) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            d_means[3 * (int64_t)g + j] = 0.f;
+            d_log_scales[3 * (int64_t)g + j] = 0.f;
+        }
+        d_quats[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d_logits[g] = 0.f;
+#pragma unroll
+        for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
+        return;
+    }
+    const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
+    densify_one(g, tiles_touched, G0, G1, G2, pos_acc, col_acc, count);
+    ParamGrad R;
+    project_bwd_one<DEG>(cam, P, c, G0, G1, G2, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        d_means[3 * (int64_t)g + j] = R.gm[j];
+        d_log_scales[3 * (int64_t)g + j] = R.gls[j];
+    }
+    d_quats[g] = R.gq;
+    d_logits[g] = R.glogit;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = R.gsh[k][ch];
+}
+
+// ---------------------------------------------------------------------------
+// Projection backward + densification statistics + Adam in one pass: each
+// warp takes 32 Gaussians, computes their gradients into shared memory and
+// then updates the parameter rows and their moments with coalesced accesses
+// over the warp's contiguous segment of every tensor.
+// ---------------------------------------------------------------------------
+struct AdamDev {
+    float* p[5];
+    float* m[5];
+    float* v[5];
+    float lr[5];
+    float b1, b2, eps, inv_bc1, inv_bc2;
+    int sparse;
+    void* shadow;
+    int shadow_dtype;
+    float* gout[5];
+};
+
+template <int DEG, int DT>
+struct FusedLayout {
+    using L = ShLayout<DEG, DT>;
+    static constexpr int KW = L::K * 3;                   // SH floats per Gaussian
+    static constexpr int GS = KW % 2 == 0 ? KW + 1 : KW;  // odd stride of the SH gradient rows
+    static constexpr int WARP_WORDS = L::WARP_WORDS + 32 * 7 + 32 * GS;
+};
+
+// Adam over the warp's contiguous segment [g0*W, (g0+rows)*W) of one tensor,
+// gradients read from shared memory rows of stride GSTRIDE at column offset
+// goff. A full, dense warp moves 16-byte vectors with several in flight per
+// lane; otherwise one element at a time.
+template <int W, int GSTRIDE>
+__device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, int rows, const float* s_grad,
+                                             int goff, const int* tiles_touched, int lane, void* shadow,
+                                             int shadow_dtype)
+{
+    const int64_t base = (int64_t)g0 * W;
+    float* P = a.p[t] + base;
+    float* M = a.m[t] + base;
+    float* V = a.v[t] + base;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) |
+                         reinterpret_cast<uintptr_t>(V);
+    if (rows == 32 && !a.sparse && (al & 15) == 0) {
+        constexpr int Q = 8 * W;  // 16-byte vectors in the segment (32 W floats)
+        float4* P4 = reinterpret_cast<float4*>(P);
+        float4* M4 = reinterpret_cast<float4*>(M);
+        float4* V4 = reinterpret_cast<float4*>(V);
+#pragma unroll 4
+        for (int k = 0; k < (Q + 31) / 32; ++k) {
+            const int q = lane + 32 * k;
+            if (q >= Q) break;
+            float4 p = P4[q], m = M4[q], v = V4[q];
+            float* pp = &p.x;
+            float* mm = &m.x;
+            float* vv = &v.x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = 4 * q + c;
+                const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
+                adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[t]);
+                if (shadow) store_as(shadow, shadow_dtype, base + e, pp[c]);
+                if (a.gout[t]) a.gout[t][base + e] = g;
+            }
+            P4[q] = p;
+            M4[q] = m;
+            V4[q] = v;
+        }
+        return;
+    }
+    for (int e = lane; e < rows * W; e += 32) {
+        const int row = e / W, col = e % W;
+        if (a.sparse && tiles_touched[g0 + row] <= 0) continue;
+        const float g = s_grad[row * GSTRIDE + goff + col];
+        float p = P[e], m = M[e], v = V[e];
+        adam_step(p, g, m, v, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[t]);
+        P[e] = p;
+        M[e] = m;
+        V[e] = v;
+        if (shadow) store_as(shadow, shadow_dtype, base + e, p);
+        if (a.gout[t]) a.gout[t][base + e] = g;
+    }
+}
+
+template <int DEG, int DT>
+__global__ void __launch_bounds__(kThreads)
+k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
+                   const float4* __restrict__ grad2d, AdamDev a, float* __restrict__ pos_acc,
+                   float* __restrict__ col_acc, int* __restrict__ count)
+{
+    using L = ShLayout<DEG, DT>;
+    using F = FusedLayout<DEG, DT>;
+    constexpr int K = L::K;
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * kWarps + warp) * 32;
+    if (g0 >= n) return;
+    const int rows = min(32, n - g0);
+    uint32_t* s_mean = smem + warp * F::WARP_WORDS;
+    uint32_t* s_scale = s_mean + 32 * 3;
+    uint32_t* s_sh = s_scale + 32 * 3;
+    float* s_gms = reinterpret_cast<float*>(smem + warp * F::WARP_WORDS + L::WARP_WORDS);  // 32 x 7
+    float* s_gsh = s_gms + 32 * 7;                                                          // 32 x GS
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[0]), n, g0, s_mean, lane);
+    warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[1]), n, g0, s_scale, lane);
+    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh_store), n, g0, s_sh, lane);
+    const int g = g0 + lane;
+    const bool valid = g < n;
+
+    float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float glogit = 0.0f;
+    float* grow = s_gms + lane * 7;
+    float* gshrow = s_gsh + lane * F::GS;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) grow[j] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
+    if (valid) {
+        float mean[3], ls[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
+            ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
+        }
+        float c[16][3];
+        read_sh<DEG, DT>(s_sh, sh_store, g, lane, c);
+        Proj P;
+        project_one<DEG>(cam, dil, mean, ls, reinterpret_cast<const float4*>(a.p[2])[g], a.p[3][g], c, P);
+        if (!P.culled) {
+            const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
+            densify_one(g, tiles_touched, G0, G1, G2, pos_acc, col_acc, count);
+            ParamGrad R;
+            project_bwd_one<DEG>(cam, P, c, G0, G1, G2, R);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                grow[j] = R.gm[j];
+                grow[3 + j] = R.gls[j];
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) gshrow[3 * k + ch] = R.gsh[k][ch];
+            gq = R.gq;
+            glogit = R.glogit;
+        }
+    }
+    __syncwarp();
+    // coalesced Adam over the warp's rows of means, log-scales and SH
+    adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, tiles_touched, lane, nullptr, 0);
+    adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, tiles_touched, lane, nullptr, 0);
+    adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, tiles_touched, lane, a.shadow, a.shadow_dtype);
+    // quaternions (16-byte rows) and opacity logits, one row per lane
+    if (valid && !(a.sparse && tiles_touched[g] <= 0)) {
+        float4 p = reinterpret_cast<float4*>(a.p[2])[g];
+        float4 m = reinterpret_cast<float4*>(a.m[2])[g];
+        float4 v = reinterpret_cast<float4*>(a.v[2])[g];
+        adam_step(p.x, gq.x, m.x, v.x, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
+        adam_step(p.y, gq.y, m.y, v.y, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
+        adam_step(p.z, gq.z, m.z, v.z, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
+        adam_step(p.w, gq.w, m.w, v.w, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
+        reinterpret_cast<float4*>(a.p[2])[g] = p;
+        reinterpret_cast<float4*>(a.m[2])[g] = m;
+        reinterpret_cast<float4*>(a.v[2])[g] = v;
+        if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
+        float po = a.p[3][g], mo = a.m[3][g], vo = a.v[3][g];
+        adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[3]);
+        a.p[3][g] = po;
+        a.m[3][g] = mo;
+        a.v[3][g] = vo;
+        if (a.gout[3]) a.gout[3][g] = glogit;
+    }
 }
 
 __global__ void k_densify(int n, const int* __restrict__ tiles_touched, const float4* __restrict__ grad2d,
@@ -483,6 +676,21 @@ int32_t launch_project_bwd(int n, const float* means, const float* log_scales, c
                                          cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
                                          reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd");
+}
+
+template <int DEG, int DT>
+int32_t launch_project_bwd_adam(int n, const void* sh_store, const Cam& cam, const Dil& dil, const int* tiles,
+                                const float* grad2d, const AdamDev& a, float* pos, float* col, int* cnt,
+                                cudaStream_t st)
+{
+    using F = FusedLayout<DEG, DT>;
+    size_t smem = sizeof(uint32_t) * F::WARP_WORDS * kWarps;
+    auto kern = k_project_bwd_adam<DEG, DT>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = (n + kThreads - 1) / kThreads;
+    kern<<<blocks, kThreads, smem, st>>>(n, sh_store, cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), a,
+                                         pos, col, cnt);
+    return gs_host::check_launch("gs_project_bwd_adam");
 }
 
 #define GS_DISPATCH_DEG_DT(deg, dt, FN, ...)                                                          \
@@ -572,6 +780,64 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype, const flo
     GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd, n, means, log_scales, quats, opacity_logits, sh, c,
                        d, tiles_touched, grad2d, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, pos_acc,
                        col_acc, count, st);
+}
+
+int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store, const GsCamera* cam,
+                            const GsDilation* dil, const int32_t* tiles_touched, const float* grad2d,
+                            const GsAdamParams* adam, float* pos_acc, float* col_acc, int32_t* count,
+                            float* const* grads_out, gs_stream_t stream)
+{
+    using namespace gs;
+    if (!adam) { gs_host::set_error("gs_project_bwd_adam: adam is null"); return GS_ERR_ARG; }
+    if (!check_params(n, sh_degree, sh_dtype, adam->param[0], adam->param[1], adam->param[2], adam->param[3],
+                      sh_store))
+        return GS_ERR_ARG;
+    Cam c;
+    Dil d;
+    if (!gs_host::make_cam(cam, &c) || !gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
+    if (n > 0) {
+        for (int t = 0; t < 5; ++t)
+            if (!adam->param[t] || !adam->m[t] || !adam->v[t]) {
+                gs_host::set_error("gs_project_bwd_adam: null parameter or moment pointer");
+                return GS_ERR_ARG;
+            }
+        if (!tiles_touched || !grad2d) { gs_host::set_error("gs_project_bwd_adam: null pointer"); return GS_ERR_ARG; }
+        uintptr_t al = reinterpret_cast<uintptr_t>(grad2d) | reinterpret_cast<uintptr_t>(adam->param[2]) |
+                       reinterpret_cast<uintptr_t>(adam->m[2]) | reinterpret_cast<uintptr_t>(adam->v[2]);
+        if (grads_out && grads_out[2]) al |= reinterpret_cast<uintptr_t>(grads_out[2]);
+        if ((al & 15) != 0) {
+            gs_host::set_error("gs_project_bwd_adam: grad2d and the quaternion tensors must be 16-byte aligned");
+            return GS_ERR_ARG;
+        }
+    }
+    if ((pos_acc == nullptr) != (col_acc == nullptr) || (pos_acc == nullptr) != (count == nullptr)) {
+        gs_host::set_error("gs_project_bwd_adam: pos_acc, col_acc and count must be all null or all set");
+        return GS_ERR_ARG;
+    }
+    if (adam->step < 1 || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) || !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) ||
+        !(adam->eps >= 0.0f) ||
+        (adam->sh_shadow && (adam->sh_shadow_dtype < GS_DTYPE_F32 || adam->sh_shadow_dtype > GS_DTYPE_F16))) {
+        gs_host::set_error("gs_project_bwd_adam: need step >= 1, 0 <= beta < 1, eps >= 0, a valid shadow dtype");
+        return GS_ERR_ARG;
+    }
+    if (n == 0) return GS_OK;
+    AdamDev a{};
+    for (int t = 0; t < 5; ++t) {
+        a.p[t] = adam->param[t];
+        a.m[t] = adam->m[t];
+        a.v[t] = adam->v[t];
+        a.lr[t] = adam->lr[t];
+        a.gout[t] = grads_out ? grads_out[t] : nullptr;
+    }
+    a.b1 = adam->beta1; a.b2 = adam->beta2; a.eps = adam->eps;
+    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)adam->step)));
+    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)adam->step)));
+    a.sparse = adam->sparse;
+    a.shadow = adam->sh_shadow;
+    a.shadow_dtype = adam->sh_shadow_dtype;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, c, d, tiles_touched, grad2d, a,
+                       pos_acc, col_acc, count, st);
 }
 
 int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* grad2d, float* pos_acc,

@@ -192,9 +192,11 @@ class TrainStep:
     host synchronisation (the pair capacity is fixed up front)."""
 
     def __init__(self, params: GaussianParams, rast: Rasterizer, adam: AdamConfig = AdamConfig(),
-                 max_pixels: int = 1, bg=(0.0, 0.0, 0.0), densify: bool = True):
+                 max_pixels: int = 1, bg=(0.0, 0.0, 0.0), densify: bool = True, fused: bool = True,
+                 sparse: bool = False):
         dev = params.means.device
         self.p, self.rast, self.adam, self.bg = params, rast, adam, tuple(bg)
+        self.fused, self.sparse = bool(fused), bool(sparse)
         self.grads = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -223,22 +225,33 @@ class TrainStep:
         rast.render(cam, dil, self.bg, img, t_final, last, self.counts if counts else None)
         R.gs_loss_l1(cam, dil, img, target, dl, self.loss)
         rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
-        g = self.grads
-        R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, rast.tiles_touched,
-                         rast.grad2d, g[0], g[1], g[2], g[3], g[4],
-                         self.pos_acc if self.densify else None, self.col_acc if self.densify else None,
-                         self.vis_count if self.densify else None)
         self.step_count += 1
-        a = self.adam
+        self.optimize(cam, dil)
+        return self.loss
+
+    def optimize(self, cam, dil: Dilation):
+        """Projection backward + densification statistics + Adam. The fused
+        path (default) is one kernel; the unfused path writes the parameter
+        gradients to self.grads and runs gs_adam."""
+        p, rast, a, g = self.p, self.rast, self.adam, self.grads
         lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
+        shadow = p.sh_store if p.sh_store.data_ptr() != p.sh.data_ptr() else None
+        stats = (self.pos_acc, self.col_acc, self.vis_count) if self.densify else (None, None, None)
+        if self.fused:
+            R.gs_project_bwd_adam(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,
+                                  p.sh_store, cam, dil, rast.tiles_touched, rast.grad2d, sparse=self.sparse,
+                                  sh_shadow=shadow, pos_acc=stats[0], col_acc=stats[1], count=stats[2])
+            return
+        R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, rast.tiles_touched,
+                         rast.grad2d, g[0], g[1], g[2], g[3], g[4], *stats)
         entries = []
         for i, t in enumerate(p.tensors()):
             e = dict(param=t, grad=g[i], m=self.m[i], v=self.v[i], lr=lrs[i], row_width=max(1, t[0].numel()))
-            if i == 4 and p.sh_store.data_ptr() != p.sh.data_ptr():
-                e["shadow"] = p.sh_store
+            if i == 4 and shadow is not None:
+                e["shadow"] = shadow
             entries.append(e)
-        R.gs_adam(entries, a.beta1, a.beta2, a.eps, self.step_count)
-        return self.loss
+        mask = (rast.tiles_touched > 0).to(torch.uint8) if self.sparse else None
+        R.gs_adam(entries, a.beta1, a.beta2, a.eps, self.step_count, row_mask=mask)
 
     # kernels launched per step (project, bin_sort internals, render, loss, bwd, proj bwd, adam)
     def launches_per_step(self, n_tiles: int, capacity: int) -> int:

@@ -23,7 +23,8 @@ GRAD2D_FLOATS = 12
 ADAM_MAX_TENSORS = 8
 
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
-           "gs_bin_sort_static", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd", "gs_densify_stats", "gs_adam")
+           "gs_bin_sort_static", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
+           "gs_project_bwd_adam", "gs_densify_stats", "gs_adam")
 
 
 class GsError(RuntimeError):
@@ -46,6 +47,13 @@ class GsAdamTensor(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("shadow", ctypes.c_void_p), ("numel", ctypes.c_int64),
                 ("row_width", ctypes.c_int32), ("shadow_dtype", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("pad_", ctypes.c_float)]
+
+
+class GsAdamParams(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p * 5), ("m", ctypes.c_void_p * 5), ("v", ctypes.c_void_p * 5),
+                ("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32), ("sparse", ctypes.c_int32),
+                ("sh_shadow", ctypes.c_void_p), ("sh_shadow_dtype", ctypes.c_int32)]
 
 
 @dataclass(frozen=True)
@@ -101,6 +109,8 @@ def load():
     lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, i32, P]
     lib.gs_project_bwd.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P, P, P, P, P, P]
     lib.gs_densify_stats.argtypes = [i32, P, P, P, P, P, P]
+    lib.gs_project_bwd_adam.argtypes = [i32, i32, i32, P, cam_p, dil_p, P, P, ctypes.POINTER(GsAdamParams), P, P,
+                                        P, P, P]
     lib.gs_adam.argtypes = [ctypes.POINTER(GsAdamTensor), i32, f32, f32, f32, i32, P, P]
     for name in SYMBOLS:
         if name not in ("gs_last_error", "gs_bin_sort_workspace_size"):
@@ -219,6 +229,32 @@ def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilat
                                  _ptr(tiles_touched), _ptr(grad2d), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
                                  _ptr(d_opacity_logits), _ptr(d_sh), _ptr(pos_acc), _ptr(col_acc), _ptr(count),
                                  _stream(stream)), "gs_project_bwd")
+
+
+def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, cam, dil: Dilation, tiles_touched,
+                        grad2d, sparse=False, sh_shadow=None, pos_acc=None, col_acc=None, count=None,
+                        grads_out=None, stream=None):
+    """params, m, v: lists of the 5 FP32 tensors (means, log_scales, quats,
+    opacity_logits, sh), updated in place; lrs: 5 learning rates."""
+    n = params[0].shape[0]
+    deg = sh_degree_of(params[4])
+    a = GsAdamParams()
+    for t in range(5):
+        for arr, src in ((a.param, params), (a.m, m), (a.v, v)):
+            if src[t].dtype != torch.float32 or not src[t].is_contiguous() or not src[t].is_cuda:
+                raise ValueError("parameters and moments must be contiguous FP32 CUDA tensors")
+            arr[t] = src[t].data_ptr()
+        a.lr[t] = float(lrs[t])
+    a.beta1, a.beta2, a.eps, a.step, a.sparse = float(beta1), float(beta2), float(eps), int(step), int(bool(sparse))
+    a.sh_shadow = sh_shadow.data_ptr() if sh_shadow is not None else None
+    a.sh_shadow_dtype = _SH_DTYPE[sh_shadow.dtype] if sh_shadow is not None else GS_DTYPE_F32
+    gout = None
+    if grads_out is not None:
+        gout = (ctypes.c_void_p * 5)(*[g.data_ptr() if g is not None else None for g in grads_out])
+    _check(load().gs_project_bwd_adam(n, deg, _SH_DTYPE[sh_store.dtype], _ptr(sh_store), ctypes.byref(camera(cam)),
+                                      ctypes.byref(dil.c()), _ptr(tiles_touched), _ptr(grad2d), ctypes.byref(a),
+                                      _ptr(pos_acc), _ptr(col_acc), _ptr(count), gout, _stream(stream)),
+           "gs_project_bwd_adam")
 
 
 def gs_densify_stats(n, tiles_touched, grad2d, pos_acc, col_acc, count, stream=None):

@@ -351,7 +351,7 @@ def test_full_step_parity(dil):
     p = U.gpu_params(p32)
     w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
     rast = Rasterizer(p.n, capacity=len(ref["vals"]) + 1000, max_tiles=tx * ty)
-    step = TrainStep(p, rast, AdamConfig(), max_pixels=w_ds * h_ds, bg=bg)
+    step = TrainStep(p, rast, AdamConfig(), max_pixels=w_ds * h_ds, bg=bg, fused=False)
     before = [t.clone() for t in p.tensors()]
     loss = step(cam, dil, torch.tensor(tgt, device=U.DEV))
     torch.cuda.synchronize()
@@ -365,6 +365,50 @@ def test_full_step_parity(dil):
     # Adam moved every visible Gaussian's parameters
     moved = (p.means != before[0]).any(1).cpu().numpy()
     assert moved[ref["proj"]["tiles_touched"] > 0].mean() > 0.5
+
+
+@pytest.mark.parametrize("sh_dtype,sparse", [(torch.float32, False), (torch.bfloat16, False), (torch.float32, True)])
+def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
+    """gs_project_bwd_adam equals gs_project_bwd followed by gs_adam bit for bit
+    (parameters, moments, BF16 shadow, gradients, densification statistics) when
+    both are given the same 2D gradients; three steps in a row."""
+    p32, cam, tgt = scene_sh3()
+    dil = R.Dilation(2, 1, 0)
+    out, rast, p, (img, tf, last) = U.run_forward(p32, cam, dil, sh_dtype=sh_dtype)
+    dl = torch.tensor(np.random.default_rng(2).standard_normal(img.shape) * 1e-3, dtype=torch.float32, device=U.DEV)
+    rast.render_bwd(cam, dil, (0.0, 0.0, 0.0), tf, last, dl)
+    lrs = [1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3]
+    sets = []
+    for _ in range(2):
+        ps = [t.clone() for t in p.tensors()]
+        sets.append(dict(p=ps, m=[torch.zeros_like(t) for t in ps], v=[torch.zeros_like(t) for t in ps],
+                         shadow=p.sh_store.clone() if sh_dtype != torch.float32 else None,
+                         stats=[torch.zeros(p.n, device=U.DEV), torch.zeros(p.n, device=U.DEV),
+                                torch.zeros(p.n, dtype=torch.int32, device=U.DEV)]))
+    mask = (rast.tiles_touched > 0).to(torch.uint8) if sparse else None
+    for step in (1, 2, 3):
+        # unfused: gradients, then the multi-tensor Adam
+        a = sets[0]
+        store = a["shadow"] if a["shadow"] is not None else a["p"][4]
+        g = [torch.empty_like(t) for t in a["p"]]
+        R.gs_project_bwd(*a["p"][:4], store, cam, dil, rast.tiles_touched, rast.grad2d, *g, *a["stats"])
+        ent = [dict(param=a["p"][i], grad=g[i], m=a["m"][i], v=a["v"][i], lr=lrs[i]) for i in range(5)]
+        if a["shadow"] is not None:
+            ent[4]["shadow"] = a["shadow"]
+        R.gs_adam(ent, 0.9, 0.999, 1e-15, step, row_mask=mask)
+        # fused
+        b = sets[1]
+        storeb = b["shadow"] if b["shadow"] is not None else b["p"][4]
+        gout = [torch.full_like(t, 7.0) for t in b["p"]]
+        R.gs_project_bwd_adam(b["p"], b["m"], b["v"], lrs, 0.9, 0.999, 1e-15, step, storeb, cam, dil,
+                              rast.tiles_touched, rast.grad2d, sparse=sparse, sh_shadow=b["shadow"],
+                              pos_acc=b["stats"][0], col_acc=b["stats"][1], count=b["stats"][2], grads_out=gout)
+        torch.cuda.synchronize()
+        for x, y in zip(gout, g):
+            np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+    flat = lambda d: d["p"] + d["m"] + d["v"] + d["stats"] + ([d["shadow"].float()] if d["shadow"] is not None else [])
+    for x, y in zip(flat(sets[0]), flat(sets[1])):
+        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
 
 
 # ---------------------------------------------------------------------------
