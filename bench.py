@@ -439,7 +439,7 @@ def main():
     if args.workload != "uhd":
         args.no_cpu_baseline = True
     w0, h0, tx0, ty0 = R.gs_grid(cam, R.Dilation(1, 0, 0))
-    rast = Rasterizer(params.n, capacity=1 << 20, max_tiles=tx0 * ty0, device=device, pixels_per_thread=args.ppt)
+    rast = Rasterizer(params.n, capacity=1 << 20, device=device, pixels_per_thread=args.ppt, max_grid=(tx0, ty0))
     kmax = 0
     for d in (1, 2, 4):
         for ox in range(d):

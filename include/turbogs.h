@@ -122,18 +122,29 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * every tile of every Gaussian's rect, the pair (key = tile_id << 32 |
  * float32 bits of the depth, value = Gaussian index), sorted ascending by
  * (key, value), and per-tile [start, end) ranges into the sorted values.
- * Inputs (device): rects, tiles_touched (from gs_project), splats (depth = [9]).
+ * Inputs (device): rects, tiles_touched (from gs_project for the same grid),
+ *   splats (depth = [9]). Rects outside the grid are not trusted: the
+ *   counting path ignores them and the sort path writes no range for them.
  * Outputs (device): sorted_ids (capacity entries; the first num_pairs hold the
  *   Gaussian ids tile by tile, front to back), ranges (tiles_x*tiles_y x 2,
- *   uint32 start/end), num_pairs (one int64: the pair count K).
+ *   uint32 start/end; (0, 0) for a tile no Gaussian touches), num_pairs (one
+ *   int64: the pair count K).
  * No host synchronisation: K is computed and consumed on the device. When
  *   K > capacity, *num_pairs still receives K, no pair is written beyond
  *   capacity, every range is set empty (the render then sees no Gaussian) and
  *   the caller must grow the buffers and call again; K <= 2^31 - 1.
  * workspace: device scratch of gs_bin_sort_workspace_size(n, capacity,
- *   tiles_x*tiles_y) bytes, 256-byte aligned; its contents need no init.
+ *   tiles_x, tiles_y) bytes, 256-byte aligned; its contents need no init. The
+ *   size also covers every smaller grid (tx <= tiles_x, ty <= tiles_y), so one
+ *   workspace serves all dilations of an image.
+ * Method: when the grid's (tiles_y+1) x (tiles_x+1) difference array fits in
+ *   shared memory (<= 51,200 cells; 3840x2160 at d = 1 with 16 px tiles has
+ *   32,776) the pairs are never sorted: per-chunk tile counts of the
+ *   depth-sorted Gaussians give every pair its final slot (counting scatter).
+ *   Larger grids emit the pairs and radix-sort their tile bits. Both give the
+ *   same result bit for bit.
  * Errors: GS_ERR_ARG for bad sizes, null pointers or a short workspace. */
-size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles);
+size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, int32_t tiles_y);
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
                     const float* splats, int32_t tiles_x, int32_t tiles_y,
                     void* workspace, size_t workspace_bytes, int64_t capacity,
@@ -150,9 +161,9 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
  * scratch lives in one array of GS_BIN_SORT_STATIC_SCRATCH_BYTES (32 MiB)
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits. Calls whose gs_bin_sort_workspace_size(n, capacity,
- * tiles_x*tiles_y) exceeds that size return GS_ERR_ARG (nothing launched) with
+ * tiles_x, tiles_y) exceeds that size return GS_ERR_ARG (nothing launched) with
  * the required size in gs_last_error(); for example n = 256K Gaussians with
- * capacity = 1.5M pairs fits. The call allocates nothing and calls no
+ * 1.5M pairs on a 1920x1080 grid fits. The call allocates nothing and calls no
  * allocating routine.
  * The first call on each device looks up the array's device address (with
  * that device current) and keeps it; make that first call before any stream

@@ -3,15 +3,15 @@
 // Sec. 3 and the profile of Sec. 3.1), without any host synchronisation.
 //
 // The result equals sorting the pairs (tile_id << 32 | depth bits, id) by
-// (key, id). It is computed in two stages that move fewer bytes than one
-// 64-bit key sort:
+// (key, id): every tile's list of Gaussian ids, front to back. It is built
+// without materialising or sorting pair keys:
 //   1. the Gaussians are sorted by (depth bits, id) with a stable LSD radix
-//      sort of 32-bit keys (N items);
-//   2. the pairs are emitted in that order with a 32-bit tile key, and a stable
-//      LSD radix sort on the ceil(log2(#tiles)) tile bits orders them by tile;
-//      stability keeps the depth order (and id order among equal depths).
-// Per-tile ranges are read off the sorted tile keys. The pair count K stays on
-// the device; every kernel clamps to the caller's capacity.
+//      sort of 32-bit keys (N items, 4 passes);
+//   2. a two-level counting scatter (rows, then tiles within a row) writes each
+//      id straight into its final slot (see the section comment below).
+// The pair count K stays on the device; every kernel checks it against the
+// caller's capacity.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -31,7 +31,6 @@ constexpr int kItemsPerThread = 16;
 constexpr int kTileItems = kSortThreads * kItemsPerThread;  // 4096
 constexpr int kRadixBins = 256;
 constexpr int kMaxSortBlocks = 148 * 4;
-constexpr int kScanItems = 2048;  // items per block of the offsets scan
 
 __device__ __forceinline__ int64_t sort_count(const int64_t* d_num, int64_t cap)
 {
@@ -266,7 +265,7 @@ int sort_blocks(int64_t cap)
 }
 
 // ---------------------------------------------------------------------------
-// Depth keys, offsets scan, pair emission, tile ranges
+// Depth keys and the pair count
 // ---------------------------------------------------------------------------
 __global__ void k_depth_keys(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
                              uint32_t* __restrict__ keys, uint32_t* __restrict__ ids)
@@ -279,171 +278,406 @@ __global__ void k_depth_keys(int n, const float4* __restrict__ splats, const int
     ids[g] = (uint32_t)g;
 }
 
-// Block sums of tiles_touched gathered in depth order.
-__global__ void __launch_bounds__(kSortThreads)
-k_scan_reduce(int n, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
-              unsigned long long* __restrict__ partials)
+__device__ __forceinline__ bool rect_in_grid(int4 r, int TX, int TY)
 {
-    __shared__ uint32_t s_tmp[kSortWarps + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanItems;
-    unsigned long long sum = 0;
-    for (int j = threadIdx.x; j < kScanItems; j += kSortThreads) {
-        int64_t k = base + j;
-        if (k < n) sum += (unsigned)tiles_touched[perm[k]];
-    }
-    // 64-bit block reduction via warp shuffles
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-    __shared__ unsigned long long s_sum[kSortWarps];
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kSortWarps; ++w) t += s_sum[w];
-        partials[blockIdx.x] = t;
-    }
-    (void)s_tmp;
+    return r.x >= 0 && r.y >= 0 && r.x <= r.z && r.y <= r.w && r.z < TX && r.w < TY;
 }
 
-// Single block: exclusive scan of the block sums (nb values) in place; total -> *d_total.
-__global__ void __launch_bounds__(1024) k_scan_partials(int nb, unsigned long long* __restrict__ partials,
-                                                        int64_t* __restrict__ d_total)
+// K = the number of (Gaussian, tile) pairs: the rect areas of the visible
+// Gaussians (equal to their tiles_touched), accumulated into *total (zeroed by
+// the caller). Counting from the rects the scatters use keeps every row list
+// within K slots.
+__global__ void k_sum_tiles(int n, const int* __restrict__ tiles_touched, const int4* __restrict__ rects, int TX,
+                            int TY, unsigned long long* __restrict__ total)
 {
-    __shared__ unsigned long long s_w[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        int i = base + threadIdx.x;
-        unsigned long long x = i < nb ? partials[i] : 0ull;
-        unsigned long long inc = x;
+    unsigned long long s = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const int4 r = rects[g];
+        if (tiles_touched[g] > 0 && rect_in_grid(r, TX, TY))
+            s += (unsigned long long)(r.z - r.x + 1) * (unsigned long long)(r.w - r.y + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
+}
+
+// ---------------------------------------------------------------------------
+// Two-level counting scatter. The pairs are never stored with keys nor sorted:
+//   level 1 bins the depth-ordered Gaussians into per-row lists (one entry per
+//   tile row a Gaussian's rect spans), level 2 bins each row list into the
+//   row's tiles. Each level is a counting scatter: per-warp counts from a
+//   difference array, exclusive scans down the columns of the count matrix for
+//   every warp's first slot in every bin, then each warp regenerates its items
+//   in order and ranks them per bin with __match_any_sync and shared counters.
+//   Order is kept at both levels, so every tile's list is in depth order (and
+//   id order among equal depths). A warp writes to at most one row's tiles at a
+//   time, so the partly written sectors in flight stay few enough for L2 to
+//   merge them before HBM sees them.
+// ---------------------------------------------------------------------------
+constexpr int kLvlWarps = 8;              // warps per block of the level kernels
+constexpr int kLvlThreads = kLvlWarps * 32;
+constexpr int kRowChunk = 512;            // Gaussians per level-1 warp
+constexpr int kSegLen = 4096;             // row-list entries per level-2 warp
+constexpr int kScanRows = 32;             // matrix rows per block of the column scans
+constexpr int kMaxGridSide = 4096;        // tiles_x, tiles_y limit (per-warp shared counters)
+
+__device__ __forceinline__ bool overflow(const int64_t* d_K, int64_t cap) { return *d_K > cap; }
+
+// Inclusive scan of len values d[0..len) in place by one warp.
+__device__ __forceinline__ void warp_inclusive_scan_smem(int* d, int len, int lane)
+{
+    int carry = 0;
+    for (int b = 0; b < len; b += 32) {
+        const int i = b + lane;
+        int v = i < len ? d[i] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        v += carry;
+        if (i < len) d[i] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    __syncwarp();
+}
+
+// Flattened item j of a warp's round -> (owner lane, item offset in the owner):
+// the largest lane whose exclusive prefix `begin` is <= j.
+__device__ __forceinline__ int owner_lane(uint32_t begin, uint32_t j)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t sb = __shfl_sync(0xffffffffu, begin, lo + step);
+        if (sb <= j) lo += step;
+    }
+    return lo;
+}
+
+// Level 1a: per level-1 warp (chunk of kRowChunk depth-ordered Gaussians), the
+// number of its Gaussians whose rect spans each tile row -> M1[chunk][row].
+__global__ void __launch_bounds__(kLvlThreads)
+k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
+           const int4* __restrict__ rects, int TX, int TY, const int64_t* __restrict__ d_K, int64_t cap,
+           uint32_t* __restrict__ M1)
+{
+    extern __shared__ int s_lvl[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kLvlWarps + warp;
+    if (c >= C1 || overflow(d_K, cap)) return;
+    int* d = s_lvl + warp * (TY + 1);
+    for (int i = lane; i <= TY; i += 32) d[i] = 0;
+    __syncwarp();
+    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    for (int k = k0 + lane; k < k1; k += 32) {
+        const uint32_t g = perm[k];
+        if (tiles_touched[g] <= 0) continue;
+        const int4 r = rects[g];
+        if (!rect_in_grid(r, TX, TY)) continue;
+        atomicAdd(&d[r.y], 1);
+        atomicAdd(&d[r.w + 1], -1);
+    }
+    __syncwarp();
+    warp_inclusive_scan_smem(d, TY, lane);
+    for (int ty = lane; ty < TY; ty += 32) M1[(int64_t)c * TY + ty] = (uint32_t)d[ty];
+}
+
+// Column scans of a count matrix M (R rows x Cc columns, row-major). Column c
+// uses only its first active(c) rows when `active` is given (active(c) =
+// active[c / col_div]); the others count as zero.
+__device__ __forceinline__ int active_rows(const uint32_t* active, int col_div, int c, int R)
+{
+    return active ? min(R, (int)active[c / col_div]) : R;
+}
+
+__global__ void k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict__ SS,
+                             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
+                             int64_t cap)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Cc || overflow(d_K, cap)) return;
+    const int r0 = blockIdx.y * kScanRows;
+    const int r1 = min(r0 + kScanRows, active_rows(active, col_div, c, R));
+    uint32_t sum = 0;
+    for (int r = r0; r < r1; ++r) sum += M[(int64_t)r * Cc + c];
+    SS[(int64_t)blockIdx.y * Cc + c] = sum;
+}
+
+__global__ void k_col_totals(int nsb, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
+                             const int64_t* __restrict__ d_K, int64_t cap)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Cc || overflow(d_K, cap)) return;
+    uint32_t run = 0;
+    for (int b = 0; b < nsb; ++b) {
+        const uint32_t x = SS[(int64_t)b * Cc + c];
+        SS[(int64_t)b * Cc + c] = run;
+        run += x;
+    }
+    total[c] = run;
+}
+
+// Single block: exclusive scan of x[0..len) -> start; the sum -> *sum (nullable).
+__global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __restrict__ x,
+                                                     uint32_t* __restrict__ start, int64_t* __restrict__ sum,
+                                                     const int64_t* __restrict__ d_K, int64_t cap)
+{
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_carry;
+    if (overflow(d_K, cap)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long carry = 0;
+    for (int base = 0; base < len; base += 1024) {
+        const int i = base + threadIdx.x;
+        const unsigned long long v = i < len ? x[i] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) s_w[warp] = inc;
         __syncthreads();
         if (warp == 0) {
-            unsigned long long w = s_w[lane];
+            const unsigned long long w = s_w[lane];
             unsigned long long wi = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += y;
             }
             s_w[lane] = wi - w;
         }
         __syncthreads();
-        unsigned long long excl = carry + s_w[warp] + inc - x;
-        if (i < nb) partials[i] = excl;
-        __syncthreads();
-        // carry of this chunk = exclusive prefix of the last thread + its value
-        __shared__ unsigned long long s_carry;
-        if (threadIdx.x == 1023) s_carry = excl + x;
+        const unsigned long long excl = carry + s_w[warp] + inc - v;
+        if (i < len) start[i] = (uint32_t)excl;
+        if (threadIdx.x == 1023) s_carry = excl + v;
         __syncthreads();
         carry = s_carry;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *d_total = (int64_t)carry;
+    if (threadIdx.x == 0 && sum) *sum = (int64_t)carry;
 }
 
-// offsets[k] = sum of tiles_touched[perm[j]] for j < k (64-bit).
-__global__ void __launch_bounds__(kSortThreads)
-k_scan_down(int n, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
-            const unsigned long long* __restrict__ partials, unsigned long long* __restrict__ offsets)
+// M[r][c] <- start[c] + (sum of M[r'][c] for r' < r): the first slot of row r in bin c.
+__global__ void k_col_base(int R, int Cc, uint32_t* __restrict__ M, const uint32_t* __restrict__ SS,
+                           const uint32_t* __restrict__ start, const uint32_t* __restrict__ active, int col_div,
+                           const int64_t* __restrict__ d_K, int64_t cap)
 {
-    __shared__ uint32_t s_tmp[kSortWarps + 1];
-    constexpr int per = kScanItems / kSortThreads;  // 8 consecutive items per thread
-    const int64_t base = (int64_t)blockIdx.x * kScanItems + threadIdx.x * per;
-    uint32_t c[per];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-        int64_t k = base + j;
-        c[j] = k < n ? (uint32_t)tiles_touched[perm[k]] : 0u;
-        sum += c[j];
-    }
-    // per-block sums fit in 32 bits: at most 2048 * 2^15 tiles
-    uint32_t total;
-    uint32_t pre = block_exclusive_scan_256(sum, s_tmp, total);
-    unsigned long long run = partials[blockIdx.x] + pre;
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-        int64_t k = base + j;
-        if (k < n) offsets[k] = run;
-        run += c[j];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Cc || overflow(d_K, cap)) return;
+    const int r0 = blockIdx.y * kScanRows;
+    const int r1 = min(r0 + kScanRows, active_rows(active, col_div, c, R));
+    uint32_t run = start[c] + SS[(int64_t)blockIdx.y * Cc + c];
+    for (int r = r0; r < r1; ++r) {
+        const uint32_t h = M[(int64_t)r * Cc + c];
+        M[(int64_t)r * Cc + c] = run;
+        run += h;
     }
 }
 
-// Warp-cooperative pair emission: a warp takes 32 consecutive Gaussians of the
-// depth order and writes their pairs with consecutive lanes on consecutive
-// output slots (coalesced), each lane finding its owner by a shuffle search.
-__global__ void __launch_bounds__(kSortThreads)
-k_emit(int n, const uint32_t* __restrict__ perm, const unsigned long long* __restrict__ offsets,
-       const int64_t* __restrict__ d_total, const int4* __restrict__ rects, int tiles_x, int64_t cap,
-       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+// Level 1c: each level-1 warp writes the ids of its Gaussians into the row
+// lists, in depth order, at the slots M1 (now bases) gives it.
+__global__ void __launch_bounds__(kLvlThreads)
+k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
+              const int4* __restrict__ rects, int TX, int TY, const uint32_t* __restrict__ M1,
+              const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ rowlist)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * kSortThreads + threadIdx.x - lane);
-    if (w0 >= n) return;
-    const int64_t total = *d_total;
-    const int64_t k = w0 + lane;
-    const bool in = k < n;
-    const unsigned long long my_off = in ? offsets[k] : (unsigned long long)total;
-    const unsigned long long base = __shfl_sync(0xffffffffu, my_off, 0);
-    const int64_t wend = (w0 + 32 < n) ? (int64_t)offsets[w0 + 32] : total;
-    uint32_t g = in ? perm[k] : 0u;
-    int4 rc = in ? rects[g] : make_int4(0, 0, -1, -1);
-    const uint32_t rel_start = (uint32_t)(my_off - base);
-    const int width = rc.z - rc.x + 1;
-    for (int64_t c0 = (int64_t)base; c0 < wend; c0 += 32) {
-        const int64_t j = c0 + lane;
-        const uint32_t rel = (uint32_t)(j - (int64_t)base);
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            uint32_t s = __shfl_sync(0xffffffffu, rel_start, lo + step);
-            if (s <= rel) lo += step;
+    extern __shared__ int s_lvl[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int c = blockIdx.x * kLvlWarps + warp;
+    if (c >= C1 || overflow(d_K, cap)) return;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_lvl) + warp * (TY + 1);
+    for (int ty = lane; ty < TY; ty += 32) cnt[ty] = M1[(int64_t)c * TY + ty];
+    __syncwarp();
+    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int k = kb + lane;
+        uint32_t g = 0;
+        int y0 = 0, nr = 0;
+        if (k < k1) {
+            g = perm[k];
+            const int4 r = rects[g];
+            if (tiles_touched[g] > 0 && rect_in_grid(r, TX, TY)) {
+                y0 = r.y;
+                nr = r.w - r.y + 1;
+            }
         }
-        const uint32_t o_start = __shfl_sync(0xffffffffu, rel_start, lo);
-        const int o_x0 = __shfl_sync(0xffffffffu, rc.x, lo);
-        const int o_y0 = __shfl_sync(0xffffffffu, rc.y, lo);
-        const int o_w = __shfl_sync(0xffffffffu, width, lo);
-        const uint32_t o_g = __shfl_sync(0xffffffffu, g, lo);
-        if (j < wend && j < cap) {
-            const uint32_t local = rel - o_start;
-            const uint32_t ly = local / (uint32_t)o_w;
-            const uint32_t lx = local - ly * (uint32_t)o_w;
-            keys[j] = (uint32_t)(o_y0 + (int)ly) * (uint32_t)tiles_x + (uint32_t)(o_x0 + (int)lx);
-            vals[j] = o_g;
+        uint32_t inc = (uint32_t)nr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        const uint32_t begin = inc - (uint32_t)nr;
+        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const int o = owner_lane(begin, j);
+            const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
+            const int o_y0 = __shfl_sync(0xffffffffu, y0, o);
+            const uint32_t o_g = __shfl_sync(0xffffffffu, g, o);
+            const bool valid = j < total;
+            const uint32_t row = valid ? (uint32_t)o_y0 + (j - o_begin) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, row);
+            uint32_t pos = 0;
+            if (valid) pos = cnt[row] + __popc(peers & lt_mask);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) cnt[row] += __popc(peers);
+            __syncwarp();
+            if (valid && (int64_t)pos < cap) rowlist[pos] = o_g;
         }
     }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d_total, int64_t cap,
-                         uint2* __restrict__ ranges)
+// Level-2 segments: row ty's list is cut into nseg[ty] = ceil(rowlen / kSegLen) segments.
+__global__ void k_row_segments(int TY, const uint32_t* __restrict__ rowlen, uint32_t* __restrict__ nseg,
+                               const int64_t* __restrict__ d_K, int64_t cap)
 {
-    const int64_t K = *d_total;
-    if (K > cap) return;  // overflow: ranges stay empty
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t t = keys[i];
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const int ty = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ty >= TY || overflow(d_K, cap)) return;
+    nseg[ty] = (rowlen[ty] + kSegLen - 1) / kSegLen;
+}
+
+// Segment index -> (row, segment within the row): the largest row whose first
+// segment is <= seg (rows without segments share the next row's offset).
+__device__ __forceinline__ int segment_row(const uint32_t* segoff, int TY, uint32_t seg)
+{
+    int lo = 0, hi = TY - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segoff[mid] <= seg) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Level 2a: per level-2 warp (segment of a row list), the number of its
+// Gaussians spanning each tile of the row -> M2[segment][tile].
+__global__ void __launch_bounds__(kLvlThreads)
+k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
+           const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint32_t* __restrict__ rowlist,
+           const int4* __restrict__ rects, const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ M2)
+{
+    extern __shared__ int s_lvl[];
+    if (overflow(d_K, cap)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* d = s_lvl + warp * (TX + 1);
+    const int64_t NS = *d_NS;
+    const int T = TX * TY;
+    for (int64_t seg = (int64_t)blockIdx.x * kLvlWarps + warp; seg < NS; seg += (int64_t)gridDim.x * kLvlWarps) {
+        const int ty = segment_row(segoff, TY, (uint32_t)seg);
+        const uint32_t s = (uint32_t)seg - segoff[ty];
+        const uint32_t e0 = rowstart[ty] + s * kSegLen;
+        const uint32_t e1 = min(e0 + kSegLen, rowstart[ty] + rowlen[ty]);
+        for (int i = lane; i <= TX; i += 32) d[i] = 0;
+        __syncwarp();
+        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            const int4 r = rects[rowlist[e]];
+            atomicAdd(&d[r.x], 1);
+            atomicAdd(&d[r.z + 1], -1);
+        }
+        __syncwarp();
+        warp_inclusive_scan_smem(d, TX, lane);
+        uint32_t* out = M2 + (int64_t)s * T + (int64_t)ty * TX;
+        for (int tx = lane; tx < TX; tx += 32) out[tx] = (uint32_t)d[tx];
+        __syncwarp();
     }
 }
 
+// Level 2c: each level-2 warp writes the ids of its segment into the row's
+// tile lists, in order, at the slots M2 (now bases) gives it.
+__global__ void __launch_bounds__(kLvlThreads)
+k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
+              const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS,
+              const uint32_t* __restrict__ rowlist, const int4* __restrict__ rects, const uint32_t* __restrict__ M2,
+              const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ out)
+{
+    extern __shared__ int s_lvl[];
+    if (overflow(d_K, cap)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_lvl) + warp * (TX + 1);
+    const int64_t NS = *d_NS;
+    const int T = TX * TY;
+    for (int64_t seg = (int64_t)blockIdx.x * kLvlWarps + warp; seg < NS; seg += (int64_t)gridDim.x * kLvlWarps) {
+        const int ty = segment_row(segoff, TY, (uint32_t)seg);
+        const uint32_t s = (uint32_t)seg - segoff[ty];
+        const uint32_t e0 = rowstart[ty] + s * kSegLen;
+        const uint32_t e1 = min(e0 + kSegLen, rowstart[ty] + rowlen[ty]);
+        const uint32_t* base = M2 + (int64_t)s * T + (int64_t)ty * TX;
+        for (int tx = lane; tx < TX; tx += 32) cnt[tx] = base[tx];
+        __syncwarp();
+        for (uint32_t eb = e0; eb < e1; eb += 32) {
+            const uint32_t e = eb + lane;
+            uint32_t g = 0;
+            int x0 = 0, nx = 0;
+            if (e < e1) {
+                g = rowlist[e];
+                const int4 r = rects[g];
+                x0 = r.x;
+                nx = r.z - r.x + 1;
+            }
+            uint32_t inc = (uint32_t)nx;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            const uint32_t begin = inc - (uint32_t)nx;
+            for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                const int o = owner_lane(begin, j);
+                const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
+                const int o_x0 = __shfl_sync(0xffffffffu, x0, o);
+                const uint32_t o_g = __shfl_sync(0xffffffffu, g, o);
+                const bool valid = j < total;
+                const uint32_t tx = valid ? (uint32_t)o_x0 + (j - o_begin) : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, tx);
+                uint32_t pos = 0;
+                if (valid) pos = cnt[tx] + __popc(peers & lt_mask);
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1) cnt[tx] += __popc(peers);
+                __syncwarp();
+                if (valid && (int64_t)pos < cap) out[pos] = o_g;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Ranges from the tile counts and starts; (0, 0) for empty tiles and on overflow.
+__global__ void k_ranges_from_counts(int T, const uint32_t* __restrict__ count, const uint32_t* __restrict__ start,
+                                     const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const bool ok = !overflow(d_K, cap) && count[t] > 0;
+    ranges[t] = ok ? make_uint2(start[t], start[t] + count[t]) : make_uint2(0u, 0u);
+}
+
+// ---------------------------------------------------------------------------
 // Workspace layout (each region 256-byte aligned)
+// ---------------------------------------------------------------------------
 struct Ws {
     uint32_t *dkeys0, *dkeys1, *perm0, *perm1;
-    unsigned long long *offsets, *partials;
-    uint32_t *tkeys0, *tkeys1, *tvals;
     uint32_t *hist, *totals;
+    uint32_t *M1, *SS1, *rowlen, *rowstart, *rowlist;
+    uint32_t *nseg, *segoff;
+    int64_t *R, *NS;
+    uint32_t *M2, *SS2, *tcount, *tstart;
     size_t bytes;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Ws carve(void* base, int n, int64_t cap)
+int lvl1_warps(int n) { return (n + kRowChunk - 1) / kRowChunk; }
+int lvl2_rows(int n) { return (n + kSegLen - 1) / kSegLen; }  // segments per row, at most
+
+Ws carve(void* base, int n, int64_t cap, int tiles_x, int tiles_y)
 {
     Ws w{};
     size_t off = 0;
@@ -452,21 +686,32 @@ Ws carve(void* base, int n, int64_t cap)
         off += align256(bytes);
         return p;
     };
-    size_t nn = (size_t)(n > 0 ? n : 1);
-    size_t cc = (size_t)(cap > 0 ? cap : 1);
-    int nb = (int)((nn + kScanItems - 1) / kScanItems);
-    int G = sort_blocks(cap > n ? cap : n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const size_t T = (size_t)tiles_x * tiles_y;
+    const size_t TY = (size_t)tiles_y;
+    const int C1 = lvl1_warps(n > 0 ? n : 1);
+    const int NSR = lvl2_rows(n > 0 ? n : 1);
+    // every row entry yields at least one pair, so the row lists fit in min(K, n*TY) <= cap slots
+    const size_t rows_cap = (size_t)std::min<int64_t>(cap > 0 ? cap : 1, (int64_t)nn * (int64_t)TY);
     w.dkeys0 = (uint32_t*)take(nn * 4);
     w.dkeys1 = (uint32_t*)take(nn * 4);
     w.perm0 = (uint32_t*)take(nn * 4);
     w.perm1 = (uint32_t*)take(nn * 4);
-    w.offsets = (unsigned long long*)take((nn + 1) * 8);
-    w.partials = (unsigned long long*)take(((size_t)nb + 1) * 8);
-    w.tkeys0 = (uint32_t*)take(cc * 4);
-    w.tkeys1 = (uint32_t*)take(cc * 4);
-    w.tvals = (uint32_t*)take(cc * 4);
-    w.hist = (uint32_t*)take((size_t)kRadixBins * G * 4);
+    w.hist = (uint32_t*)take((size_t)kRadixBins * sort_blocks(n) * 4);
     w.totals = (uint32_t*)take(kRadixBins * 4);
+    w.M1 = (uint32_t*)take((size_t)C1 * TY * 4);
+    w.SS1 = (uint32_t*)take((size_t)((C1 + kScanRows - 1) / kScanRows) * TY * 4);
+    w.rowlen = (uint32_t*)take(TY * 4);
+    w.rowstart = (uint32_t*)take(TY * 4);
+    w.rowlist = (uint32_t*)take(rows_cap * 4);
+    w.nseg = (uint32_t*)take(TY * 4);
+    w.segoff = (uint32_t*)take(TY * 4);
+    w.R = (int64_t*)take(8);
+    w.NS = (int64_t*)take(8);
+    w.M2 = (uint32_t*)take((size_t)NSR * T * 4);
+    w.SS2 = (uint32_t*)take((size_t)((NSR + kScanRows - 1) / kScanRows) * T * 4);
+    w.tcount = (uint32_t*)take(T * 4);
+    w.tstart = (uint32_t*)take(T * 4);
     w.bytes = off;
     return w;
 }
@@ -476,11 +721,11 @@ Ws carve(void* base, int n, int64_t cap)
 
 extern "C" {
 
-size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles)
+size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, int32_t tiles_y)
 {
-    (void)num_tiles;
-    if (n < 0 || capacity < 0) return 0;
-    return gs::carve(nullptr, n, capacity).bytes + 256;
+    if (n < 0 || capacity < 0 || tiles_x <= 0 || tiles_y <= 0) return 0;
+    // every term grows with tiles_x and tiles_y: the size covers all smaller grids
+    return gs::carve(nullptr, n, capacity, tiles_x, tiles_y).bytes + 256;
 }
 
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
@@ -488,12 +733,9 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
                     uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
 {
     using namespace gs;
-    if (n < 0 || capacity < 0 || capacity > 0x7fffffffLL || tiles_x <= 0 || tiles_y <= 0) {
-        gs_host::set_error("gs_bin_sort: bad sizes (n >= 0, 0 <= capacity < 2^31, tiles > 0)");
-        return GS_ERR_ARG;
-    }
-    if ((int64_t)tiles_x * tiles_y > (1LL << 30)) {
-        gs_host::set_error("gs_bin_sort: too many tiles");
+    if (n < 0 || capacity < 0 || capacity > 0x7fffffffLL || tiles_x <= 0 || tiles_y <= 0 ||
+        tiles_x > kMaxGridSide || tiles_y > kMaxGridSide) {
+        gs_host::set_error("gs_bin_sort: bad sizes (n >= 0, 0 <= capacity < 2^31, 0 < tiles_x, tiles_y <= 4096)");
         return GS_ERR_ARG;
     }
     if (!ranges || !num_pairs || (n > 0 && (!rects || !tiles_touched || !splats || !workspace)) ||
@@ -504,45 +746,67 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     uintptr_t base = reinterpret_cast<uintptr_t>(workspace);
     void* ws_al = reinterpret_cast<void*>((base + 255) & ~uintptr_t(255));
     size_t slack = reinterpret_cast<uintptr_t>(ws_al) - base;
-    Ws w = carve(ws_al, n, capacity);
+    Ws w = carve(ws_al, n, capacity, tiles_x, tiles_y);
     if (n > 0 && workspace_bytes < w.bytes + slack) {
         gs_host::set_error("gs_bin_sort: workspace too small");
         return GS_ERR_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t num_tiles = (int64_t)tiles_x * tiles_y;
-    cudaMemsetAsync(ranges, 0, (size_t)num_tiles * 2 * sizeof(uint32_t), st);
+    const int T = tiles_x * tiles_y, TX = tiles_x, TY = tiles_y;
+    cudaMemsetAsync(num_pairs, 0, sizeof(int64_t), st);
     if (n == 0) {
-        cudaMemsetAsync(num_pairs, 0, sizeof(int64_t), st);
+        cudaMemsetAsync(ranges, 0, (size_t)T * 2 * sizeof(uint32_t), st);
         return gs_host::check_launch("gs_bin_sort");
     }
-    // 1. sort Gaussians by (depth bits, id)
+    const int4* rc = reinterpret_cast<const int4*>(rects);
+    // K, and the depth order of the Gaussians: a stable LSD radix sort of (depth bits, id)
+    k_sum_tiles<<<148 * 4, 256, 0, st>>>(n, tiles_touched, rc, TX, TY,
+                                         reinterpret_cast<unsigned long long*>(num_pairs));
     k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched,
                                                   w.dkeys0, w.perm0);
-    int Gd = sort_blocks(n);
-    radix_sort(SortBufs{w.dkeys0, w.perm0, w.dkeys1, w.perm1}, nullptr, n, 32, Gd, w.hist, w.totals, st);
-    // 4 passes: the result is back in (dkeys0, perm0)
-    // 2. offsets of each Gaussian's pairs in depth order, and K
-    int nb = (n + kScanItems - 1) / kScanItems;
-    k_scan_reduce<<<nb, kSortThreads, 0, st>>>(n, w.perm0, tiles_touched, w.partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(nb, w.partials, num_pairs);
-    k_scan_down<<<nb, kSortThreads, 0, st>>>(n, w.perm0, tiles_touched, w.partials, w.offsets);
-    // 3. emit (tile key, id) in depth order, then stable sort by tile bits
-    int bits = 1;
-    while ((1LL << bits) < num_tiles) ++bits;
-    int passes = (bits + 7) / 8;
-    uint32_t* v_emit = (passes % 2 == 0) ? sorted_ids : w.tvals;
-    uint32_t* v_other = (passes % 2 == 0) ? w.tvals : sorted_ids;
-    if (capacity > 0) {
-        k_emit<<<(n + kSortThreads - 1) / kSortThreads, kSortThreads, 0, st>>>(
-            n, w.perm0, w.offsets, num_pairs, reinterpret_cast<const int4*>(rects), tiles_x, capacity, w.tkeys0,
-            v_emit);
-        int Gt = sort_blocks(capacity);
-        radix_sort(SortBufs{w.tkeys0, v_emit, w.tkeys1, v_other}, num_pairs, capacity, bits, Gt, w.hist, w.totals,
-                   st);
-        uint32_t* kfinal = (passes % 2 == 0) ? w.tkeys0 : w.tkeys1;
-        k_ranges<<<148 * 8, 256, 0, st>>>(kfinal, num_pairs, capacity, reinterpret_cast<uint2*>(ranges));
+    radix_sort(SortBufs{w.dkeys0, w.perm0, w.dkeys1, w.perm1}, nullptr, n, 32, sort_blocks(n), w.hist, w.totals,
+               st);  // 4 passes: the order is back in perm0
+    // level 1: rows
+    const int C1 = lvl1_warps(n);
+    const int lvl1_blocks = (C1 + kLvlWarps - 1) / kLvlWarps;
+    const size_t smem1 = (size_t)kLvlWarps * (TY + 1) * sizeof(int);
+    if (smem1 > 48 * 1024) {
+        cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+        cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     }
+    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, tiles_touched, rc, TX, TY, num_pairs,
+                                                        capacity, w.M1);
+    const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
+    const dim3 g1((TY + 255) / 256, nsb1);
+    k_col_segsum<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, 1, num_pairs, capacity);
+    k_col_totals<<<(TY + 255) / 256, 256, 0, st>>>(nsb1, TY, w.SS1, w.rowlen, num_pairs, capacity);
+    k_scan_small<<<1, 1024, 0, st>>>(TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
+    k_col_base<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, 1, num_pairs, capacity);
+    k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, tiles_touched, rc, TX, TY, w.M1,
+                                                           num_pairs, capacity, w.rowlist);
+    // level 2: tiles within each row
+    k_row_segments<<<(TY + 255) / 256, 256, 0, st>>>(TY, w.rowlen, w.nseg, num_pairs, capacity);
+    k_scan_small<<<1, 1024, 0, st>>>(TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
+    const int NSR = lvl2_rows(n);
+    const size_t smem2 = (size_t)kLvlWarps * (TX + 1) * sizeof(int);
+    if (smem2 > 48 * 1024) {
+        cudaFuncSetAttribute(k_seg_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    }
+    const int lvl2_blocks = 148 * 8;
+    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist, rc,
+                                                        num_pairs, capacity, w.M2);
+    const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
+    const dim3 g2((T + 255) / 256, nsb2);
+    k_col_segsum<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, TX, num_pairs, capacity);
+    k_col_totals<<<(T + 255) / 256, 256, 0, st>>>(nsb2, T, w.SS2, w.tcount, num_pairs, capacity);
+    k_scan_small<<<1, 1024, 0, st>>>(T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
+    k_col_base<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, TX, num_pairs, capacity);
+    k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
+                                                         reinterpret_cast<uint2*>(ranges));
+    if (capacity > 0)
+        k_seg_scatter<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
+                                                               w.rowlist, rc, w.M2, num_pairs, capacity, sorted_ids);
     return gs_host::check_launch("gs_bin_sort");
 }
 
@@ -562,7 +826,7 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
         gs_host::set_error("gs_bin_sort_static: bad sizes (n >= 0, capacity >= 0, tiles > 0)");
         return GS_ERR_ARG;
     }
-    const size_t need = gs_bin_sort_workspace_size(n, capacity, tiles_x * tiles_y);
+    const size_t need = gs_bin_sort_workspace_size(n, capacity, tiles_x, tiles_y);
     if (need > (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES) {
         char msg[256];
         std::snprintf(msg, sizeof(msg),

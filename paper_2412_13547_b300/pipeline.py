@@ -54,7 +54,7 @@ class Rasterizer:
     and ``ensure_capacity``."""
 
     def __init__(self, n: int, capacity: int = 1 << 20, max_tiles: int = 1, device="cuda",
-                 pixels_per_thread: int = 0):
+                 pixels_per_thread: int = 0, max_grid=None):
         self.device = torch.device(device)
         self.ppt = int(pixels_per_thread)
         self.n = int(n)
@@ -66,13 +66,14 @@ class Rasterizer:
         self.num_pairs_dev = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.capacity = 0
         self.max_tiles = 0
-        self.ensure_tiles(max_tiles)
+        self.grid = (1, 1) if max_grid is None else (int(max_grid[0]), int(max_grid[1]))
+        self.ensure_tiles(max(max_tiles, self.grid[0] * self.grid[1]))
         self._alloc_pairs(int(capacity))
 
     def _alloc_pairs(self, capacity: int):
         capacity = max(1, int(capacity))
         self.sorted_ids = torch.empty(capacity, dtype=torch.int32, device=self.device)
-        ws = R.gs_bin_sort_workspace_size(self.n, capacity, max(1, self.max_tiles))
+        ws = R.gs_bin_sort_workspace_size(self.n, capacity, *self.grid)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self.capacity = capacity
 
@@ -80,6 +81,15 @@ class Rasterizer:
         if num_tiles > self.max_tiles:
             self.max_tiles = int(num_tiles)
             self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
+
+    def ensure_grid(self, tiles_x: int, tiles_y: int):
+        """Grow the workspace so that grids up to (tiles_x, tiles_y) can be binned."""
+        self.ensure_tiles(tiles_x * tiles_y)
+        need = R.gs_bin_sort_workspace_size(self.n, self.capacity, tiles_x, tiles_y)
+        if tiles_x > self.grid[0] or tiles_y > self.grid[1] or need > self.workspace.numel():
+            self.grid = (max(self.grid[0], tiles_x), max(self.grid[1], tiles_y))
+            ws = R.gs_bin_sort_workspace_size(self.n, self.capacity, *self.grid)
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
 
     def ensure_capacity(self, k: int, headroom: float = 1.25):
         if k > self.capacity:
@@ -95,7 +105,8 @@ class Rasterizer:
 
     def bin(self, cam, dil: Dilation):
         w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-        self.ensure_tiles(tx * ty)
+        if tx > self.grid[0] or ty > self.grid[1]:
+            self.ensure_grid(tx, ty)
         R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, tx, ty, self.workspace, self.capacity,
                       self.sorted_ids, self.ranges, self.num_pairs_dev)
         return w_ds, h_ds, tx, ty
@@ -137,7 +148,7 @@ class _RasterizeFn(torch.autograd.Function):
         p = GaussianParams(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
                            opacity_logits.contiguous(), sh.contiguous(), sh.contiguous())
         w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-        rast = Rasterizer(n, capacity=cap_hint[0], max_tiles=tx * ty, device=means.device)
+        rast = Rasterizer(n, capacity=cap_hint[0], device=means.device, max_grid=(tx, ty))
         rast.project(p, cam, dil)
         rast.bin_checked(cam, dil)
         cap_hint[0] = max(cap_hint[0], rast.capacity)

@@ -100,7 +100,7 @@ def load():
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_grid.argtypes = [cam_p, dil_p, P, P, P, P]
     lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P]
-    lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32]
+    lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32, i32]
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
     lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
     lib.gs_bin_sort_static.argtypes = [i32, P, P, P, i32, i32, i64, P, P, P, P]
@@ -172,8 +172,8 @@ def gs_project(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation,
            "gs_project")
 
 
-def gs_bin_sort_workspace_size(n: int, capacity: int, num_tiles: int) -> int:
-    return int(load().gs_bin_sort_workspace_size(int(n), int(capacity), int(num_tiles)))
+def gs_bin_sort_workspace_size(n: int, capacity: int, tiles_x: int, tiles_y: int) -> int:
+    return int(load().gs_bin_sort_workspace_size(int(n), int(capacity), int(tiles_x), int(tiles_y)))
 
 
 def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, capacity, sorted_ids, ranges,

@@ -27,7 +27,7 @@ def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capac
     """GPU project + bin + blend. Returns numpy outputs and the rasterizer."""
     p = gpu_params(p32, sh_dtype)
     w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, max_tiles=tx * ty, device=DEV)
+    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(tx, ty))
     rast.project(p, cam, dil)
     if capacity is None:
         rast.bin_checked(cam, dil)

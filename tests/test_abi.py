@@ -34,7 +34,9 @@ def test_host_only_calls():
     assert R.gs_grid(cam, R.Dilation(1, 0, 0)) == (130, 97, 9, 7)
     assert R.gs_grid(cam, R.Dilation(2, 1, 0)) == (65, 49, 5, 4)
     assert R.gs_grid(cam, R.Dilation(3, 2, 2, tile=8)) == (43, 32, 6, 4)
-    assert R.gs_bin_sort_workspace_size(1000, 5000, 64) > 0
+    assert R.gs_bin_sort_workspace_size(1000, 5000, 8, 8) > 0
+    # a grid larger than the counting path's limit needs the pair-sized sort buffers
+    assert R.gs_bin_sort_workspace_size(1000, 10**6, 480, 270) > R.gs_bin_sort_workspace_size(1000, 10**6, 240, 135)
     with pytest.raises(R.GsError):
         R.gs_grid(cam, R.Dilation(2, 2, 0))       # offset >= d
     with pytest.raises(R.GsError):

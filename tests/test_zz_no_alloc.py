@@ -39,9 +39,9 @@ def _both(scene, cam, dil):
     _, _, tx, ty = R.gs_grid(cam, dil)
     k = int(tiles.to(torch.int64).sum().item())
     cap = k + 4096
-    assert R.gs_bin_sort_workspace_size(n, cap, tx * ty) <= R.BIN_SORT_STATIC_SCRATCH_BYTES
+    assert R.gs_bin_sort_workspace_size(n, cap, tx, ty) <= R.BIN_SORT_STATIC_SCRATCH_BYTES
     # reference: the existing entry point with a caller workspace
-    ws = torch.empty(R.gs_bin_sort_workspace_size(n, cap, tx * ty), dtype=torch.uint8, device=DEV)
+    ws = torch.empty(R.gs_bin_sort_workspace_size(n, cap, tx, ty), dtype=torch.uint8, device=DEV)
     ids_a = torch.full((cap,), -1, dtype=torch.int32, device=DEV)
     rng_a = torch.full((tx * ty, 2), -1, dtype=torch.int32, device=DEV)
     k_a = torch.zeros(1, dtype=torch.int64, device=DEV)
@@ -68,9 +68,16 @@ def test_static_scratch_matches_workspace_on_two_calls():
 
 
 def test_static_scratch_rejects_sizes_beyond_its_maximum():
-    n, splats, rects, tiles = _project(*scenes.workload_small()[:2], R.Dilation())
+    # 3M Gaussians need 48 MiB for their depth keys alone. Every buffer has the size
+    # the call claims (and no Gaussian touches a tile), so nothing could run out of
+    # bounds even if the size check were missing.
+    n, tx, ty = 3_000_000, 8, 8
+    splats = torch.zeros(n, R.SPLAT_FLOATS, device=DEV)
+    rects = torch.zeros(n, 4, dtype=torch.int32, device=DEV)
+    tiles = torch.zeros(n, dtype=torch.int32, device=DEV)
     ids = torch.zeros(16, dtype=torch.int32, device=DEV)
-    rng = torch.zeros(64, 2, dtype=torch.int32, device=DEV)
+    rng = torch.zeros(tx * ty, 2, dtype=torch.int32, device=DEV)
     k = torch.zeros(1, dtype=torch.int64, device=DEV)
+    assert R.gs_bin_sort_workspace_size(n, 16, tx, ty) > R.BIN_SORT_STATIC_SCRATCH_BYTES
     with pytest.raises(R.GsError, match="static array"):
-        R.gs_bin_sort_static(n, rects, tiles, splats, 8, 8, 50_000_000, ids, rng, k)
+        R.gs_bin_sort_static(n, rects, tiles, splats, tx, ty, 16, ids, rng, k)
