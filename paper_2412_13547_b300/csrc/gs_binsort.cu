@@ -317,7 +317,7 @@ __global__ void k_sum_tiles(int n, const int* __restrict__ tiles_touched, const 
 constexpr int kLvlWarps = 8;              // warps per block of the level kernels
 constexpr int kLvlThreads = kLvlWarps * 32;
 constexpr int kRowChunk = 512;            // Gaussians per level-1 warp
-constexpr int kSegLen = 4096;             // row-list entries per level-2 warp
+constexpr int kSegLen = 4096;             // row-list entries per level-2 segment (one CTA of 8 warps)
 constexpr int kScanRows = 32;             // matrix rows per block of the column scans
 constexpr int kMaxGridSide = 4096;        // tiles_x, tiles_y limit (per-warp shared counters)
 
@@ -554,8 +554,8 @@ __device__ __forceinline__ int segment_row(const uint32_t* segoff, int TY, uint3
     return lo;
 }
 
-// Level 2a: per level-2 warp (segment of a row list), the number of its
-// Gaussians spanning each tile of the row -> M2[segment][tile].
+// Level 2a: per level-2 segment (one CTA), the number of its Gaussians
+// spanning each tile of the row -> M2[segment][tile].
 __global__ void __launch_bounds__(kLvlThreads)
 k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
            const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint32_t* __restrict__ rowlist,
@@ -564,31 +564,36 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
     extern __shared__ int s_lvl[];
     if (overflow(d_K, cap)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int* d = s_lvl + warp * (TX + 1);
+    int* d = s_lvl;
     const int64_t NS = *d_NS;
     const int T = TX * TY;
-    for (int64_t seg = (int64_t)blockIdx.x * kLvlWarps + warp; seg < NS; seg += (int64_t)gridDim.x * kLvlWarps) {
+    for (int64_t seg = blockIdx.x; seg < NS; seg += gridDim.x) {
         const int ty = segment_row(segoff, TY, (uint32_t)seg);
         const uint32_t s = (uint32_t)seg - segoff[ty];
         const uint32_t e0 = rowstart[ty] + s * kSegLen;
         const uint32_t e1 = min(e0 + kSegLen, rowstart[ty] + rowlen[ty]);
-        for (int i = lane; i <= TX; i += 32) d[i] = 0;
-        __syncwarp();
-        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        for (int i = threadIdx.x; i <= TX; i += kLvlThreads) d[i] = 0;
+        __syncthreads();
+        for (uint32_t e = e0 + threadIdx.x; e < e1; e += kLvlThreads) {
             const int4 r = rects[rowlist[e]];
             atomicAdd(&d[r.x], 1);
             atomicAdd(&d[r.z + 1], -1);
         }
-        __syncwarp();
-        warp_inclusive_scan_smem(d, TX, lane);
-        uint32_t* out = M2 + (int64_t)s * T + (int64_t)ty * TX;
-        for (int tx = lane; tx < TX; tx += 32) out[tx] = (uint32_t)d[tx];
-        __syncwarp();
+        __syncthreads();
+        if (warp == 0) {
+            warp_inclusive_scan_smem(d, TX, lane);
+            uint32_t* out = M2 + (int64_t)s * T + (int64_t)ty * TX;
+            for (int tx = lane; tx < TX; tx += 32) out[tx] = (uint32_t)d[tx];
+        }
+        __syncthreads();
     }
 }
 
-// Level 2c: each level-2 warp writes the ids of its segment into the row's
-// tile lists, in order, at the slots M2 (now bases) gives it.
+// Level 2c: per level-2 segment (one CTA) the 8 warps take consecutive
+// sub-ranges of the segment. Each warp counts its sub-range per tile, a
+// cross-warp exclusive prefix per tile (starting from the segment's first slot
+// in M2) gives every warp its own counters, and the warps write the ids of
+// their sub-range into the row's tile lists, in order.
 __global__ void __launch_bounds__(kLvlThreads)
 k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
               const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS,
@@ -599,22 +604,47 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
     if (overflow(d_K, cap)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_lvl) + warp * (TX + 1);
+    const int W1 = TX + 1;
+    int* d = s_lvl + warp * W1;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(d);
     const int64_t NS = *d_NS;
     const int T = TX * TY;
-    for (int64_t seg = (int64_t)blockIdx.x * kLvlWarps + warp; seg < NS; seg += (int64_t)gridDim.x * kLvlWarps) {
+    constexpr uint32_t kSub = kSegLen / kLvlWarps;
+    for (int64_t seg = blockIdx.x; seg < NS; seg += gridDim.x) {
         const int ty = segment_row(segoff, TY, (uint32_t)seg);
         const uint32_t s = (uint32_t)seg - segoff[ty];
         const uint32_t e0 = rowstart[ty] + s * kSegLen;
         const uint32_t e1 = min(e0 + kSegLen, rowstart[ty] + rowlen[ty]);
-        const uint32_t* base = M2 + (int64_t)s * T + (int64_t)ty * TX;
-        for (int tx = lane; tx < TX; tx += 32) cnt[tx] = base[tx];
+        const uint32_t w0 = min(e0 + (uint32_t)warp * kSub, e1);
+        const uint32_t w1 = min(w0 + kSub, e1);
+        // counts of this warp's sub-range
+        for (int i = lane; i < W1; i += 32) d[i] = 0;
         __syncwarp();
-        for (uint32_t eb = e0; eb < e1; eb += 32) {
+        for (uint32_t e = w0 + lane; e < w1; e += 32) {
+            const int4 r = rects[rowlist[e]];
+            atomicAdd(&d[r.x], 1);
+            atomicAdd(&d[r.z + 1], -1);
+        }
+        __syncwarp();
+        warp_inclusive_scan_smem(d, TX, lane);
+        __syncthreads();
+        // counters: the segment's first slot plus the counts of the earlier warps
+        const uint32_t* base = M2 + (int64_t)s * T + (int64_t)ty * TX;
+        for (int tx = threadIdx.x; tx < TX; tx += kLvlThreads) {
+            uint32_t run = base[tx];
+            for (int w = 0; w < kLvlWarps; ++w) {
+                uint32_t* c = reinterpret_cast<uint32_t*>(s_lvl + w * W1) + tx;
+                const uint32_t x = *c;
+                *c = run;
+                run += x;
+            }
+        }
+        __syncthreads();
+        for (uint32_t eb = w0; eb < w1; eb += 32) {
             const uint32_t e = eb + lane;
             uint32_t g = 0;
             int x0 = 0, nx = 0;
-            if (e < e1) {
+            if (e < w1) {
                 g = rowlist[e];
                 const int4 r = rects[g];
                 x0 = r.x;
@@ -645,7 +675,7 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
                 if (valid && (int64_t)pos < cap) out[pos] = o_g;
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -789,12 +819,13 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     k_scan_small<<<1, 1024, 0, st>>>(TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
     const int NSR = lvl2_rows(n);
     const size_t smem2 = (size_t)kLvlWarps * (TX + 1) * sizeof(int);
+    const size_t smem2h = (size_t)(TX + 1) * sizeof(int);
     if (smem2 > 48 * 1024) {
-        cudaFuncSetAttribute(k_seg_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        cudaFuncSetAttribute(k_seg_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2h);
         cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     }
     const int lvl2_blocks = 148 * 8;
-    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist, rc,
+    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2h, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist, rc,
                                                         num_pairs, capacity, w.M2);
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
     const dim3 g2((T + 255) / 256, nsb2);

@@ -56,13 +56,13 @@ struct ShLayout {
     static constexpr int WARP_WORDS = 32 * (3 + 3) + (STAGE ? 32 * S : 0);
 };
 
-template <int DEG, int DT>
+template <int DEG, int DT, int STRIDE = ShLayout<DEG, DT>::S>
 __device__ __forceinline__ void read_sh(const uint32_t* s_sh, const void* sh, int g, int lane,
                                         float (&c)[16][3])
 {
     using L = ShLayout<DEG, DT>;
     if constexpr (L::STAGE) {
-        const uint32_t* row = s_sh + lane * L::S;
+        const uint32_t* row = s_sh + lane * STRIDE;
         if constexpr (DT == GS_DTYPE_F32) {
 #pragma unroll
             for (int k = 0; k < L::K; ++k)
@@ -482,8 +482,11 @@ template <int DEG, int DT>
 struct FusedLayout {
     using L = ShLayout<DEG, DT>;
     static constexpr int KW = L::K * 3;                   // SH floats per Gaussian
-    static constexpr int GS = KW % 2 == 0 ? KW + 1 : KW;  // odd stride of the SH gradient rows
-    static constexpr int WARP_WORDS = L::WARP_WORDS + 32 * 7 + 32 * GS;
+    static constexpr int GS0 = KW % 2 == 0 ? KW + 1 : KW;  // odd stride of the SH gradient rows
+    // one region per lane row: first the staged SH coefficients, then (same lane,
+    // after it has read them) its SH gradients
+    static constexpr int GS = (L::STAGE && L::S > GS0) ? L::S : GS0;
+    static constexpr int WARP_WORDS = 32 * (3 + 3) + 32 * 7 + 32 * GS;
 };
 
 // Adam over the warp's contiguous segment [g0*W, (g0+rows)*W) of one tensor,
@@ -542,8 +545,10 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     }
 }
 
+// 6 CTAs per SM: the register cap (85) costs a few spills but the extra
+// warps hide more of the memory latency of this streaming pass
 template <int DEG, int DT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
 k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
                    const float4* __restrict__ grad2d, AdamDev a, float* __restrict__ pos_acc,
                    float* __restrict__ col_acc, int* __restrict__ count)
@@ -558,12 +563,12 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
     const int rows = min(32, n - g0);
     uint32_t* s_mean = smem + warp * F::WARP_WORDS;
     uint32_t* s_scale = s_mean + 32 * 3;
-    uint32_t* s_sh = s_scale + 32 * 3;
-    float* s_gms = reinterpret_cast<float*>(smem + warp * F::WARP_WORDS + L::WARP_WORDS);  // 32 x 7
-    float* s_gsh = s_gms + 32 * 7;                                                          // 32 x GS
+    float* s_gms = reinterpret_cast<float*>(s_scale + 32 * 3);  // 32 x 7
+    uint32_t* s_sh = reinterpret_cast<uint32_t*>(s_gms + 32 * 7);  // 32 rows of stride GS
+    float* s_gsh = reinterpret_cast<float*>(s_sh);
     warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[0]), n, g0, s_mean, lane);
     warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[1]), n, g0, s_scale, lane);
-    if constexpr (L::STAGE) warp_stage<L::W, L::S>(reinterpret_cast<const uint32_t*>(sh_store), n, g0, s_sh, lane);
+    if constexpr (L::STAGE) warp_stage<L::W, F::GS>(reinterpret_cast<const uint32_t*>(sh_store), n, g0, s_sh, lane);
     const int g = g0 + lane;
     const bool valid = g < n;
 
@@ -573,8 +578,7 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
     float* gshrow = s_gsh + lane * F::GS;
 #pragma unroll
     for (int j = 0; j < 6; ++j) grow[j] = 0.0f;
-#pragma unroll
-    for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
+    bool have_grad = false;
     if (valid) {
         float mean[3], ls[3];
 #pragma unroll
@@ -583,7 +587,7 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
             ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
         }
         float c[16][3];
-        read_sh<DEG, DT>(s_sh, sh_store, g, lane, c);
+        read_sh<DEG, DT, F::GS>(s_sh, sh_store, g, lane, c);
         Proj P;
         project_one<DEG>(cam, dil, mean, ls, reinterpret_cast<const float4*>(a.p[2])[g], a.p[3][g], c, P);
         if (!P.culled) {
@@ -596,13 +600,19 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
                 grow[j] = R.gm[j];
                 grow[3 + j] = R.gls[j];
             }
+            // the staged SH of this row was read into c above: the row now takes the gradients
 #pragma unroll
             for (int k = 0; k < K; ++k)
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) gshrow[3 * k + ch] = R.gsh[k][ch];
             gq = R.gq;
             glogit = R.glogit;
+            have_grad = true;
         }
+    }
+    if (!have_grad) {
+#pragma unroll
+        for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
     }
     __syncwarp();
     // coalesced Adam over the warp's rows of means, log-scales and SH
