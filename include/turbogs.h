@@ -177,6 +177,14 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
                            gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_tile_order -- a launch order for the blend kernels: the tile ids sorted
+ * by descending list length (end - start of ranges), bucketed 8 buckets per
+ * power of two. Started longest-first, the tiles of uneven load finish close
+ * together instead of leaving a tail. Inputs (device): ranges (num_tiles x 2).
+ * Output (device): order (num_tiles). */
+int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * gs_render_fwd -- front-to-back alpha blending (Sec. 3, Eq. 2) of the lattice
  * pixels of the dilated image (Sec. 3.1: tile lists from the downsampled grid,
  * Gaussian evaluated at the hr pixel (d*u + ox, d*v + oy), Eq. 5).
@@ -194,12 +202,15 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
  *   tile's CTA handles this many pixels: 0 = the library default, else 1 or 2
  *   for tile 8, 1, 2 or 4 for tile 16, 2 or 4 for tile 32 (whole warps, at
  *   most 512 threads; others give GS_ERR_ARG). Results are identical for
- *   every value. */
+ *   every value.
+ * tile_order (nullable, device, tiles_x*tiles_y entries): the tiles in the
+ *   order their CTAs should start, e.g. from gs_tile_order. Scheduling only:
+ *   the results do not depend on it. */
 int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
                       const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
                       const float* bg, float* img, float* t_final, uint32_t* last,
                       unsigned long long* counts, int32_t pixels_per_thread,
-                      gs_stream_t stream);
+                      const uint32_t* tile_order, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_loss_l1 -- L1 photometric loss of the rendered lattice pixels against the
@@ -220,13 +231,14 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
  * Inputs (device): as gs_render_fwd plus t_final, last and dl_dimg.
  * Output (device): grad2d (n x 12, layout above), accumulated with +=; with
  *   zero_grad2d != 0 the library first zeroes it on the stream.
- * pixels_per_thread: as for gs_render_fwd (results equal up to the order of
- *   the floating-point atomic additions). */
+ * pixels_per_thread, tile_order: as for gs_render_fwd (results equal up to
+ *   the order of the floating-point atomic additions). */
 int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
                       const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
                       const float* bg, const float* t_final, const uint32_t* last,
                       const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
-                      int32_t pixels_per_thread, gs_stream_t stream);
+                      int32_t pixels_per_thread, const uint32_t* tile_order,
+                      gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_project_bwd -- chain rule of gs_project: from grad2d to the parameter
@@ -248,7 +260,9 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * gs_project_bwd_adam -- gs_project_bwd, gs_densify_stats and gs_adam fused
  * into one pass over the Gaussians (the gradient of each Gaussian goes from
  * its 2D record straight into its Adam update, never through HBM). Results
- * equal gs_project_bwd followed by gs_adam with the same settings bit for bit.
+ * equal gs_project_bwd followed by gs_adam with the same settings up to FP32
+ * rounding (the two kernels may contract the shared gradient arithmetic into
+ * FMAs differently); the Adam update itself is the same pinned arithmetic.
  * adam->param[0..4] are the FP32 parameters (means, log_scales, quats,
  * opacity_logits, sh), updated in place; m, v their moments; lr per tensor.
  * sh_store (device) is the SH storage the forward projection read: adam->param[4]

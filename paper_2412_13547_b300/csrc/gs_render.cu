@@ -78,8 +78,8 @@ struct WarpBlock {
 template <int TILE, int PPT>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
-             Dil dil, float3 bg, float* __restrict__ img, float* __restrict__ t_final, uint32_t* __restrict__ last,
-             unsigned long long* __restrict__ counts)
+             const uint32_t* __restrict__ order, Dil dil, float3 bg, float* __restrict__ img,
+             float* __restrict__ t_final, uint32_t* __restrict__ last, unsigned long long* __restrict__ counts)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
@@ -89,7 +89,9 @@ k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     __shared__ float4 s_rgb[BATCH];
     __shared__ unsigned long long s_cnt[2];
 
-    const int tile = blockIdx.x;
+    // longest lists first when an order is given: the block scheduler then
+    // dispatches greedily longest-first
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
     const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
     const int u = tx * TILE + wb.lx;
@@ -240,8 +242,8 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& c
 template <int TILE, int PPT>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
-             Dil dil, float3 bg, const float* __restrict__ t_final, const uint32_t* __restrict__ last,
-             const float* __restrict__ dl_dimg, float* __restrict__ grad2d)
+             const uint32_t* __restrict__ order, Dil dil, float3 bg, const float* __restrict__ t_final,
+             const uint32_t* __restrict__ last, const float* __restrict__ dl_dimg, float* __restrict__ grad2d)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
@@ -253,7 +255,9 @@ k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     __shared__ float s_acc[BATCH][9];
     __shared__ uint32_t s_max_last;
 
-    const int tile = blockIdx.x;
+    // longest lists first when an order is given: the block scheduler then
+    // dispatches greedily longest-first
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
     const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
     const int lane = threadIdx.x & 31;
@@ -417,6 +421,41 @@ int resolve_ppt(int tile, int ppt)
     return ppt;
 }
 
+// Tile order, longest list first: 256 buckets of the list length (8 per
+// octave, descending), one block. Order inside a bucket is arbitrary; it only
+// affects scheduling, never results.
+__global__ void __launch_bounds__(1024) k_tile_order(int T, const uint2* __restrict__ ranges,
+                                                     uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_off[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    auto bucket = [](uint32_t len) -> int {
+        const uint32_t x = len + 1u;
+        const int e = 31 - __clz(x);
+        const int m = (int)((x >> (e > 3 ? e - 3 : 0)) << (e > 3 ? 0 : 3 - e)) & 7;
+        return 255 - min(255, e * 8 + m);
+    };
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&s_hist[bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < 256; ++b) {
+            s_off[b] = run;
+            run += s_hist[b];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&s_off[bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+
 bool check_render_args(int32_t n, const float* splats, const uint32_t* ids, const uint32_t* ranges)
 {
     if (n < 0) { gs_host::set_error("n must be >= 0"); return false; }
@@ -435,7 +474,8 @@ extern "C" {
 
 int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids, const uint32_t* ranges,
                       const GsCamera* cam, const GsDilation* dil, const float* bg, float* img, float* t_final,
-                      uint32_t* last, unsigned long long* counts, int32_t pixels_per_thread, gs_stream_t stream)
+                      uint32_t* last, unsigned long long* counts, int32_t pixels_per_thread,
+                      const uint32_t* tile_order, gs_stream_t stream)
 {
     using namespace gs;
     Dil d;
@@ -449,7 +489,7 @@ int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float4* sp = reinterpret_cast<const float4*>(splats);
     const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-#define GS_FWD(T_, P_) k_render_fwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, d, b, img, t_final, last, counts)
+#define GS_FWD(T_, P_) k_render_fwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, tile_order, d, b, img, t_final, last, counts)
     switch (d.tile * 8 + ppt) {
         case 8 * 8 + 1: GS_FWD(8, 1); break;
         case 8 * 8 + 2: GS_FWD(8, 2); break;
@@ -466,7 +506,7 @@ int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids
 int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids, const uint32_t* ranges,
                       const GsCamera* cam, const GsDilation* dil, const float* bg, const float* t_final,
                       const uint32_t* last, const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
-                      int32_t pixels_per_thread, gs_stream_t stream)
+                      int32_t pixels_per_thread, const uint32_t* tile_order, gs_stream_t stream)
 {
     using namespace gs;
     Dil d;
@@ -488,7 +528,7 @@ int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids
     const int tiles = d.tiles_x * d.tiles_y;
     const float4* sp = reinterpret_cast<const float4*>(splats);
     const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-#define GS_BWD(T_, P_) k_render_bwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, d, b, t_final, last, dl_dimg, grad2d)
+#define GS_BWD(T_, P_) k_render_bwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, tile_order, d, b, t_final, last, dl_dimg, grad2d)
     switch (d.tile * 8 + ppt) {
         case 8 * 8 + 1: GS_BWD(8, 1); break;
         case 8 * 8 + 2: GS_BWD(8, 2); break;
@@ -500,6 +540,19 @@ int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids
     }
 #undef GS_BWD
     return gs_host::check_launch("gs_render_bwd");
+}
+
+int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order, gs_stream_t stream)
+{
+    using namespace gs;
+    if (num_tiles < 0 || (num_tiles > 0 && (!ranges || !order))) {
+        gs_host::set_error("gs_tile_order: bad arguments");
+        return GS_ERR_ARG;
+    }
+    if (num_tiles == 0) return GS_OK;
+    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        num_tiles, reinterpret_cast<const uint2*>(ranges), order);
+    return gs_host::check_launch("gs_tile_order");
 }
 
 int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, float* dl_dimg,

@@ -54,9 +54,10 @@ class Rasterizer:
     and ``ensure_capacity``."""
 
     def __init__(self, n: int, capacity: int = 1 << 20, max_tiles: int = 1, device="cuda",
-                 pixels_per_thread: int = 0, max_grid=None):
+                 pixels_per_thread: int = 0, max_grid=None, longest_first: bool = True):
         self.device = torch.device(device)
         self.ppt = int(pixels_per_thread)
+        self.longest_first = bool(longest_first)
         self.n = int(n)
         self.splats = torch.zeros(self.n, R.SPLAT_FLOATS, device=self.device)
         self.radii = torch.zeros(self.n, dtype=torch.int32, device=self.device)
@@ -81,6 +82,7 @@ class Rasterizer:
         if num_tiles > self.max_tiles:
             self.max_tiles = int(num_tiles)
             self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
+            self.tile_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
 
     def ensure_grid(self, tiles_x: int, tiles_y: int):
         """Grow the workspace so that grids up to (tiles_x, tiles_y) can be binned."""
@@ -109,6 +111,8 @@ class Rasterizer:
             self.ensure_grid(tx, ty)
         R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, tx, ty, self.workspace, self.capacity,
                       self.sorted_ids, self.ranges, self.num_pairs_dev)
+        if self.longest_first:
+            R.gs_tile_order(self.ranges, tx * ty, self.tile_order)
         return w_ds, h_ds, tx, ty
 
     def bin_checked(self, cam, dil: Dilation):
@@ -122,11 +126,12 @@ class Rasterizer:
 
     def render(self, cam, dil: Dilation, bg, img, t_final, last, counts=None):
         R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts,
-                        pixels_per_thread=self.ppt)
+                        pixels_per_thread=self.ppt, tile_order=self.tile_order if self.longest_first else None)
 
     def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg):
         R.gs_render_bwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, t_final, last, dl_dimg,
-                        self.grad2d, zero_grad2d=True, pixels_per_thread=self.ppt)
+                        self.grad2d, zero_grad2d=True, pixels_per_thread=self.ppt,
+                        tile_order=self.tile_order if self.longest_first else None)
 
 
 def image_buffers(h_ds: int, w_ds: int, device="cuda"):

@@ -23,7 +23,7 @@ GRAD2D_FLOATS = 12
 ADAM_MAX_TENSORS = 8
 
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
-           "gs_bin_sort_static", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
+           "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
            "gs_project_bwd_adam", "gs_densify_stats", "gs_adam")
 
 
@@ -104,9 +104,10 @@ def load():
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
     lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
     lib.gs_bin_sort_static.argtypes = [i32, P, P, P, i32, i32, i64, P, P, P, P]
-    lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P]
+    lib.gs_tile_order.argtypes = [P, i32, P, P]
+    lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P, P]
     lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
-    lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, i32, P]
+    lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, i32, P, P]
     lib.gs_project_bwd.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P, P, P, P, P, P]
     lib.gs_densify_stats.argtypes = [i32, P, P, P, P, P, P]
     lib.gs_project_bwd_adam.argtypes = [i32, i32, i32, P, cam_p, dil_p, P, P, ctypes.POINTER(GsAdamParams), P, P,
@@ -199,11 +200,15 @@ def _bg(bg):
     return arr
 
 
+def gs_tile_order(ranges, num_tiles, order, stream=None):
+    _check(load().gs_tile_order(_ptr(ranges), int(num_tiles), _ptr(order), _stream(stream)), "gs_tile_order")
+
+
 def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, counts=None,
-                  pixels_per_thread=0, stream=None):
+                  pixels_per_thread=0, tile_order=None, stream=None):
     _check(load().gs_render_fwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last), _ptr(counts),
-                                int(pixels_per_thread), _stream(stream)), "gs_render_fwd")
+                                int(pixels_per_thread), _ptr(tile_order), _stream(stream)), "gs_render_fwd")
 
 
 def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
@@ -212,11 +217,11 @@ def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
 
 
 def gs_render_bwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, t_final, last, dl_dimg, grad2d,
-                  zero_grad2d=True, pixels_per_thread=0, stream=None):
+                  zero_grad2d=True, pixels_per_thread=0, tile_order=None, stream=None):
     _check(load().gs_render_bwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(t_final), _ptr(last), _ptr(dl_dimg),
-                                _ptr(grad2d), int(bool(zero_grad2d)), int(pixels_per_thread), _stream(stream)),
-           "gs_render_bwd")
+                                _ptr(grad2d), int(bool(zero_grad2d)), int(pixels_per_thread), _ptr(tile_order),
+                                _stream(stream)), "gs_render_bwd")
 
 
 def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, tiles_touched, grad2d,

@@ -59,14 +59,15 @@ def test_bad_arguments_are_rejected_before_launch():
     # bad dilation
     bad = R.GsDilation(0, 0, 0, 0, 16)
     assert lib.gs_render_fwd(0, None, None, P(16), ctypes.byref(cam), ctypes.byref(bad), None, None, None, None,
-                             None, 0, None) == R.GS_ERR_ARG
+                             None, 0, None, None) == R.GS_ERR_ARG
     # bad launch shape: 3 pixels per thread
     bg = (ctypes.c_float * 3)()
     assert lib.gs_render_fwd(0, P(16), P(16), P(16), ctypes.byref(cam), ctypes.byref(dil), bg, P(16), P(16), P(16),
-                             None, 3, None) == R.GS_ERR_ARG
+                             None, 3, None, None) == R.GS_ERR_ARG
     tile8 = R.GsDilation(1, 0, 0, 0, 8)  # 4 pixels per thread would leave a 16-thread CTA
     assert lib.gs_render_fwd(0, P(16), P(16), P(16), ctypes.byref(cam), ctypes.byref(tile8), bg, P(16), P(16),
-                             P(16), None, 4, None) == R.GS_ERR_ARG
+                             P(16), None, 4, None, None) == R.GS_ERR_ARG
+    assert lib.gs_tile_order(None, -1, None, None) == R.GS_ERR_ARG
     # capacity >= 2^31
     assert lib.gs_bin_sort(0, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None) == R.GS_ERR_ARG
     # adam: too many tensors, bad step

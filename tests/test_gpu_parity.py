@@ -223,6 +223,36 @@ def test_launch_shape_does_not_change_results(tile, ppts):
         assert U.max_rel(o[4], outs[0][4]) < 1e-5
 
 
+def test_longest_first_order_does_not_change_results():
+    """gs_tile_order only reorders the CTAs: forward bit-identical, backward equal
+    up to the order of floating-point atomics; the order is a permutation."""
+    p32, cam, _ = scene_sh3(200, 150)
+    dil = R.Dilation(1, 0, 0)
+    p = U.gpu_params(p32)
+    w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+    outs = []
+    for lf in (False, True):
+        rast = Rasterizer(p.n, capacity=1 << 17, max_grid=(tx, ty), longest_first=lf)
+        rast.project(p, cam, dil)
+        rast.bin_checked(cam, dil)
+        img, tf, last = image_buffers(h_ds, w_ds)
+        rast.render(cam, dil, (0.2, 0.2, 0.2), img, tf, last)
+        dl = torch.tensor(np.random.default_rng(1).standard_normal((h_ds, w_ds, 3)) * 1e-3, dtype=torch.float32,
+                          device=U.DEV)
+        rast.render_bwd(cam, dil, (0.2, 0.2, 0.2), tf, last, dl)
+        torch.cuda.synchronize()
+        outs.append((img.cpu().numpy(), tf.cpu().numpy(), last.cpu().numpy(), rast.grad2d.cpu().numpy()))
+        if lf:
+            order = rast.tile_order[:tx * ty].cpu().numpy()
+            assert sorted(order.tolist()) == list(range(tx * ty))
+            lens = (rast.ranges[:, 1] - rast.ranges[:, 0]).cpu().numpy()[order]
+            # non-increasing up to the bucketing (8 buckets per octave)
+            assert np.all(lens[:-1] + 1 >= (lens[1:] + 1) * 0.875)
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        np.testing.assert_array_equal(a, b)
+    assert U.max_rel(outs[1][3], outs[0][3]) < 1e-5
+
+
 def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
     out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg)
     rng = np.random.default_rng(seed)
@@ -379,9 +409,10 @@ def test_full_step_parity(dil):
 
 @pytest.mark.parametrize("sh_dtype,sparse", [(torch.float32, False), (torch.bfloat16, False), (torch.float32, True)])
 def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
-    """gs_project_bwd_adam equals gs_project_bwd followed by gs_adam bit for bit
-    (parameters, moments, BF16 shadow, gradients, densification statistics) when
-    both are given the same 2D gradients; three steps in a row."""
+    """gs_project_bwd_adam equals gs_project_bwd followed by gs_adam (parameters,
+    moments, BF16 shadow, gradients, densification statistics) when both are
+    given the same 2D gradients, three steps in a row: up to FP32 rounding of the
+    gradient arithmetic, which the two kernels may contract differently."""
     p32, cam, tgt = scene_sh3()
     dil = R.Dilation(2, 1, 0)
     out, rast, p, (img, tf, last) = U.run_forward(p32, cam, dil, sh_dtype=sh_dtype)
@@ -415,10 +446,15 @@ def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
                               pos_acc=b["stats"][0], col_acc=b["stats"][1], count=b["stats"][2], grads_out=gout)
         torch.cuda.synchronize()
         for x, y in zip(gout, g):
-            np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
-    flat = lambda d: d["p"] + d["m"] + d["v"] + d["stats"] + ([d["shadow"].float()] if d["shadow"] is not None else [])
-    for x, y in zip(flat(sets[0]), flat(sets[1])):
-        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+            assert U.max_rel(x.cpu().numpy(), y.cpu().numpy()) < 1e-6
+    for key, rtol in (("p", 1e-6), ("m", 1e-5), ("v", 1e-5), ("stats", 1e-6)):
+        for x, y in zip(sets[0][key], sets[1][key]):
+            a, b = x.float().cpu().numpy(), y.float().cpu().numpy()
+            assert U.max_rel(a, b) < rtol, key
+    if sets[0]["shadow"] is not None:
+        a, b = sets[0]["shadow"].float().cpu().numpy(), sets[1]["shadow"].float().cpu().numpy()
+        # BF16 copies of parameters equal to FP32 rounding: equal or one BF16 step apart
+        assert (np.abs(a - b) <= np.abs(b) * 2.0 ** -7 + 1e-30).all()
 
 
 # ---------------------------------------------------------------------------
