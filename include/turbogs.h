@@ -271,7 +271,11 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * Gaussians with tiles_touched == 0 are left untouched (no moment decay).
  * grads_out (nullable host array of 5 device pointers, each nullable) receives
  * the gradients as gs_project_bwd would write them. pos_acc/col_acc/count:
- * as in gs_project_bwd. */
+ * as in gs_project_bwd. bias_dev (nullable device pointer to two floats
+ * (1/(1-beta1^t), 1/(1-beta2^t)), as gs_adam_advance writes them) replaces the
+ * bias correction computed on the host from step, so that a CUDA graph
+ * holding this call stays valid while the step advances; step is then
+ * ignored. */
 typedef struct {
     float* param[5];
     float* m[5];
@@ -282,12 +286,21 @@ typedef struct {
     int32_t sparse;
     void* sh_shadow;
     int32_t sh_shadow_dtype;
+    const float* bias_dev;
 } GsAdamParams;
 int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
                             const GsCamera* cam, const GsDilation* dil,
                             const int32_t* tiles_touched, const float* grad2d,
                             const GsAdamParams* adam, float* pos_acc, float* col_acc,
                             int32_t* count, float* const* grads_out, gs_stream_t stream);
+
+/* gs_adam_advance -- one device thread adds 1 to *step_dev (device int32, the
+ * Adam step t, 0 before the first step) and writes the bias corrections of the
+ * new t to bias_dev[0..1] = (1/(1-beta1^t), 1/(1-beta2^t)), evaluated in
+ * double and rounded to float like the host path of gs_project_bwd_adam. One
+ * call per optimizer step, before the fused step that reads bias_dev. */
+int32_t gs_adam_advance(int32_t* step_dev, float beta1, float beta2, float* bias_dev,
+                        gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_densify_stats -- position-appearance densification scores (Sec. 3.3): for
@@ -322,6 +335,66 @@ typedef struct {
 } GsAdamTensor;
 int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float beta2,
                 float eps, int32_t step, const uint8_t* row_mask, gs_stream_t stream);
+
+/* ===========================================================================
+ * Batched views: several views (cameras, resolutions, dilations) of one set of
+ * Gaussians in one launch per stage. The view table is read on the host and
+ * passed to the kernels by value; every pointer in it is a device buffer owned
+ * by the caller, sized for that view as in the single-view calls. All views of
+ * a batch use the same tile size.
+ * =========================================================================== */
+#define GS_MAX_VIEWS 16
+typedef struct {
+    GsCamera cam;
+    GsDilation dil;
+    float* splats;             /* n x 12 (gs_project)                         */
+    int32_t* radii;            /* n                                            */
+    int32_t* rects;            /* n x 4                                        */
+    int32_t* tiles_touched;    /* n                                            */
+    uint32_t* sorted_ids;      /* from gs_bin_sort of this view                */
+    uint32_t* ranges;          /* tiles x 2                                    */
+    float* img;                /* h_ds x w_ds x 3                              */
+    float* t_final;            /* h_ds x w_ds                                  */
+    uint32_t* last;            /* h_ds x w_ds                                  */
+    const float* target;       /* height x width x 3 (hr)                      */
+    float* dl_dimg;            /* h_ds x w_ds x 3                              */
+    float* grad2d;             /* n x 12                                       */
+    float* loss;               /* one float                                    */
+} GsView;
+
+/* gs_project for every view of the table (one launch). */
+int32_t gs_project_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype,
+                         const float* means, const float* log_scales, const float* quats,
+                         const float* opacity_logits, const void* sh,
+                         const GsView* views, int32_t nviews, gs_stream_t stream);
+
+/* gs_tile_order over the tiles of all views, numbered view by view
+ * (view v's tiles follow those of views 0..v-1): order gets sum_v tiles_v ids,
+ * longest list first. This is the work queue of the batched blend launches. */
+int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream);
+
+/* gs_render_fwd / gs_loss_l1 / gs_render_bwd for every view in one launch each;
+ * the blend launches take the tiles of all views from one work queue
+ * (tile_order, nullable = view by view). counts as in gs_render_fwd, summed
+ * over views. gs_render_bwd_batch zeroes each view's grad2d first when
+ * zero_grad2d != 0. */
+int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
+                            const uint32_t* tile_order, unsigned long long* counts,
+                            int32_t pixels_per_thread, gs_stream_t stream);
+int32_t gs_loss_l1_batch(const GsView* views, int32_t nviews, gs_stream_t stream);
+int32_t gs_render_bwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
+                            const uint32_t* tile_order, int32_t zero_grad2d,
+                            int32_t pixels_per_thread, gs_stream_t stream);
+
+/* gs_project_bwd_adam over a batch: for each Gaussian the gradient is summed
+ * over the views (each view's projection backward from its own grad2d), the
+ * densification statistics accumulate once per view the Gaussian is visible
+ * in, and Adam is applied once with the summed gradient. Parameters, moments
+ * and the SH storage cross HBM once per batch. */
+int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                  const GsView* views, int32_t nviews, const GsAdamParams* adam,
+                                  float* pos_acc, float* col_acc, int32_t* count,
+                                  float* const* grads_out, gs_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,42 @@ bool make_dil(const GsCamera* cam, const GsDilation* in, gs::Dil* out)
     return true;
 }
 
+bool make_batch(const GsView* views, int nviews, gs::Batch* out)
+{
+    if (!views || nviews < 1 || nviews > GS_MAX_VIEWS) {
+        set_error("batch: need 1 <= nviews <= GS_MAX_VIEWS and a view table");
+        return false;
+    }
+    out->nviews = nviews;
+    int tiles = 0;
+    for (int i = 0; i < nviews; ++i) {
+        const GsView& in = views[i];
+        gs::ViewDev& v = out->v[i];
+        if (!make_cam(&in.cam, &v.cam) || !make_dil(&in.cam, &in.dil, &v.dil)) return false;
+        if (v.dil.tile != out->v[0].dil.tile) {
+            set_error("batch: all views must use the same tile size");
+            return false;
+        }
+        v.splats = reinterpret_cast<float4*>(in.splats);
+        v.radii = in.radii;
+        v.rects = reinterpret_cast<int4*>(in.rects);
+        v.tiles = in.tiles_touched;
+        v.ids = in.sorted_ids;
+        v.ranges = reinterpret_cast<const uint2*>(in.ranges);
+        v.img = in.img;
+        v.t_final = in.t_final;
+        v.last = in.last;
+        v.target = in.target;
+        v.dl = in.dl_dimg;
+        v.grad2d = reinterpret_cast<float4*>(in.grad2d);
+        v.loss = in.loss;
+        v.tile_begin = tiles;
+        tiles += v.dil.tiles_x * v.dil.tiles_y;
+    }
+    out->total_tiles = tiles;
+    return true;
+}
+
 }  // namespace gs_host
 
 extern "C" {

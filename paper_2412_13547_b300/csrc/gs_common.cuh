@@ -36,6 +36,41 @@ struct Dil {
     int w_ds, h_ds, tiles_x, tiles_y;
 };
 
+// One view of a batch, as the kernels see it.
+struct ViewDev {
+    Cam cam;
+    Dil dil;
+    float4* splats;
+    int* radii;
+    int4* rects;
+    int* tiles;
+    const uint32_t* ids;
+    const uint2* ranges;
+    float* img;
+    float* t_final;
+    uint32_t* last;
+    const float* target;
+    float* dl;
+    float4* grad2d;
+    float* loss;
+    int tile_begin;  // first global tile id of this view in the batch
+};
+
+struct Batch {
+    ViewDev v[GS_MAX_VIEWS];
+    int nviews;
+    int total_tiles;
+};
+
+// View of a global tile id (tiles numbered view by view).
+__device__ __forceinline__ int view_of_tile(const Batch& b, int gt)
+{
+    int v = 0;
+    for (int i = 1; i < b.nviews; ++i)
+        if (b.v[i].tile_begin <= gt) v = i;
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // Float-float arithmetic (error-free transformations with FMA). Used to carry
 // the hr image-plane centre with ~1e-6 px error at 4K, where plain FP32 loses
@@ -255,4 +290,7 @@ void set_error(const char* msg);
 int32_t check_launch(const char* what);
 bool make_cam(const GsCamera* in, gs::Cam* out);
 bool make_dil(const GsCamera* cam, const GsDilation* in, gs::Dil* out);
+// Fills the device view table from the caller's; checks cameras and dilations
+// (one tile size for all views).
+bool make_batch(const GsView* views, int nviews, gs::Batch* out);
 }  // namespace gs_host

@@ -215,12 +215,14 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     }
 }
 
+// Projection of every Gaussian into every view of the batch. The warp stages
+// its 32 parameter rows once and loops over the views, so the parameters are
+// read once per batch whatever the number of views.
 template <int DEG, int DT>
 __global__ void __launch_bounds__(kThreads)
 k_project(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
           const float4* __restrict__ quats, const float* __restrict__ logits, const void* __restrict__ sh,
-          Cam cam, Dil dil, float4* __restrict__ splats, int* __restrict__ radii,
-          int4* __restrict__ rects, int* __restrict__ tiles_touched)
+          const __grid_constant__ Batch b)
 {
     using L = ShLayout<DEG, DT>;
     extern __shared__ uint32_t smem[];
@@ -244,25 +246,29 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
     }
     float c[16][3];
     read_sh<DEG, DT>(s_sh, sh, g, lane, c);
-    Proj P;
-    project_one<DEG>(cam, dil, mean, ls, quats[g], logits[g], c, P);
-
-    float4* out = splats + 3 * (int64_t)g;
-    if (P.culled) {
-        out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
-        radii[g] = 0;
-        rects[g] = make_int4(0, 0, -1, -1);
-        tiles_touched[g] = 0;
-        return;
+    const float4 q = quats[g];
+    const float logit = logits[g];
+    for (int vi = 0; vi < b.nviews; ++vi) {
+        const ViewDev& V = b.v[vi];
+        Proj P;
+        project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
+        float4* out = V.splats + 3 * (int64_t)g;
+        if (P.culled) {
+            out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
+            V.radii[g] = 0;
+            V.rects[g] = make_int4(0, 0, -1, -1);
+            V.tiles[g] = 0;
+            continue;
+        }
+        out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
+        out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
+        out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
+        V.radii[g] = P.radius;
+        V.rects[g] = P.rect;
+        V.tiles[g] = P.tiles;
     }
-    out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
-    out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
-    out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
-    radii[g] = P.radius;
-    rects[g] = P.rect;
-    tiles_touched[g] = P.tiles;
 }
 
 // ---------------------------------------------------------------------------
@@ -472,6 +478,7 @@ struct AdamDev {
     float* v[5];
     float lr[5];
     float b1, b2, eps, inv_bc1, inv_bc2;
+    const float* bias;  // device (1/(1-b1^t), 1/(1-b2^t)) replacing inv_bc1/2 when set
     int sparse;
     void* shadow;
     int shadow_dtype;
@@ -489,13 +496,22 @@ struct FusedLayout {
     static constexpr int WARP_WORDS = 32 * (3 + 3) + 32 * 7 + 32 * GS;
 };
 
+// Visible in at least one view of the batch (the rows sparse Adam updates).
+__device__ __forceinline__ bool visible_any(const Batch& b, int g)
+{
+    for (int i = 0; i < b.nviews; ++i)
+        if (b.v[i].tiles[g] > 0) return true;
+    return false;
+}
+
 // Adam over the warp's contiguous segment [g0*W, (g0+rows)*W) of one tensor,
 // gradients read from shared memory rows of stride GSTRIDE at column offset
 // goff. A full, dense warp moves 16-byte vectors with several in flight per
-// lane; otherwise one element at a time.
+// lane; otherwise one element at a time. Bit r of vis marks row r visible
+// (sparse Adam updates only those rows).
 template <int W, int GSTRIDE>
 __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, int rows, const float* s_grad,
-                                             int goff, const int* tiles_touched, int lane, void* shadow,
+                                             int goff, unsigned vis, float bc1, float bc2, int lane, void* shadow,
                                              int shadow_dtype)
 {
     const int64_t base = (int64_t)g0 * W;
@@ -521,7 +537,7 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
             for (int c = 0; c < 4; ++c) {
                 const int e = 4 * q + c;
                 const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
-                adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[t]);
+                adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
                 if (shadow) store_as(shadow, shadow_dtype, base + e, pp[c]);
                 if (a.gout[t]) a.gout[t][base + e] = g;
             }
@@ -533,29 +549,66 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     }
     for (int e = lane; e < rows * W; e += 32) {
         const int row = e / W, col = e % W;
-        if (a.sparse && tiles_touched[g0 + row] <= 0) continue;
         const float g = s_grad[row * GSTRIDE + goff + col];
+        if (a.gout[t]) a.gout[t][base + e] = g;
+        if (a.sparse && !((vis >> row) & 1u)) continue;
         float p = P[e], m = M[e], v = V[e];
-        adam_step(p, g, m, v, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[t]);
+        adam_step(p, g, m, v, a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
         P[e] = p;
         M[e] = m;
         V[e] = v;
         if (shadow) store_as(shadow, shadow_dtype, base + e, p);
-        if (a.gout[t]) a.gout[t][base + e] = g;
     }
 }
 
+// Projection backward of one Gaussian in one view, written (ACC false) or
+// added (ACC true) into the gradient rows. False when the view culls it.
+template <int DEG, bool ACC>
+__device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const float* mean, const float* ls,
+                                                float4 q, float logit, const float (&c)[16][3], float* grow,
+                                                float* gshrow, float4& gq, float& glogit, float* pos_acc,
+                                                float* col_acc, int* count)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    Proj P;
+    project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
+    if (P.culled) return false;
+    const float4 G0 = V.grad2d[3 * (int64_t)g], G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
+    densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
+    ParamGrad R;
+    project_bwd_one<DEG>(V.cam, P, c, G0, G1, G2, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        grow[j] = ACC ? grow[j] + R.gm[j] : R.gm[j];
+        grow[3 + j] = ACC ? grow[3 + j] + R.gls[j] : R.gls[j];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gshrow[3 * k + ch] = ACC ? gshrow[3 * k + ch] + R.gsh[k][ch] : R.gsh[k][ch];
+    if (ACC) {
+        gq.x += R.gq.x; gq.y += R.gq.y; gq.z += R.gq.z; gq.w += R.gq.w;
+        glogit += R.glogit;
+    } else {
+        gq = R.gq;
+        glogit = R.glogit;
+    }
+    return true;
+}
+
+// One warp per 32 Gaussians: stage the parameters, project and differentiate
+// them in every view of the batch (gradients summed over views), then one
+// Adam step for the warp's rows. MULTI false is the one-view form, which
+// writes the gradients instead of accumulating them.
 // 6 CTAs per SM: the register cap (85) costs a few spills but the extra
 // warps hide more of the memory latency of this streaming pass
-template <int DEG, int DT>
-__global__ void __launch_bounds__(kThreads, 6)
-k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, const int* __restrict__ tiles_touched,
-                   const float4* __restrict__ grad2d, AdamDev a, float* __restrict__ pos_acc,
-                   float* __restrict__ col_acc, int* __restrict__ count)
+template <int DEG, int DT, bool MULTI>
+__global__ void __launch_bounds__(kThreads, MULTI ? 4 : 6)
+k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_constant__ Batch b, AdamDev a,
+                   float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
 {
     using L = ShLayout<DEG, DT>;
     using F = FusedLayout<DEG, DT>;
-    constexpr int K = L::K;
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g0 = (blockIdx.x * kWarps + warp) * 32;
@@ -588,26 +641,19 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
         }
         float c[16][3];
         read_sh<DEG, DT, F::GS>(s_sh, sh_store, g, lane, c);
-        Proj P;
-        project_one<DEG>(cam, dil, mean, ls, reinterpret_cast<const float4*>(a.p[2])[g], a.p[3][g], c, P);
-        if (!P.culled) {
-            const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
-            densify_one(g, tiles_touched, G0, G1, G2, pos_acc, col_acc, count);
-            ParamGrad R;
-            project_bwd_one<DEG>(cam, P, c, G0, G1, G2, R);
+        const float4 q = reinterpret_cast<const float4*>(a.p[2])[g];
+        const float logit = a.p[3][g];
+        // the staged SH of this row is in c now: the row takes the SH gradients
+        if constexpr (MULTI) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                grow[j] = R.gm[j];
-                grow[3 + j] = R.gls[j];
-            }
-            // the staged SH of this row was read into c above: the row now takes the gradients
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) gshrow[3 * k + ch] = R.gsh[k][ch];
-            gq = R.gq;
-            glogit = R.glogit;
+            for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
             have_grad = true;
+            for (int vi = 0; vi < b.nviews; ++vi)
+                fused_view_grad<DEG, true>(b.v[vi], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit, pos_acc,
+                                           col_acc, count);
+        } else {
+            have_grad = fused_view_grad<DEG, false>(b.v[0], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit,
+                                                    pos_acc, col_acc, count);
         }
     }
     if (!have_grad) {
@@ -615,30 +661,45 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, Cam cam, Dil dil, c
         for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
     }
     __syncwarp();
+    // a Gaussian is visible for sparse Adam when it touches a tile in any view
+    const unsigned vis = __ballot_sync(0xffffffffu, a.sparse && valid && visible_any(b, g));
     // coalesced Adam over the warp's rows of means, log-scales and SH
-    adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, tiles_touched, lane, nullptr, 0);
-    adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, tiles_touched, lane, nullptr, 0);
-    adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, tiles_touched, lane, a.shadow, a.shadow_dtype);
+    const float bc1 = a.bias ? a.bias[0] : a.inv_bc1, bc2 = a.bias ? a.bias[1] : a.inv_bc2;
+    adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
+    adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
+    adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
     // quaternions (16-byte rows) and opacity logits, one row per lane
-    if (valid && !(a.sparse && tiles_touched[g] <= 0)) {
+    if (valid) {
+        if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
+        if (a.gout[3]) a.gout[3][g] = glogit;
+    }
+    if (valid && !(a.sparse && !((vis >> lane) & 1u))) {
         float4 p = reinterpret_cast<float4*>(a.p[2])[g];
         float4 m = reinterpret_cast<float4*>(a.m[2])[g];
         float4 v = reinterpret_cast<float4*>(a.v[2])[g];
-        adam_step(p.x, gq.x, m.x, v.x, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
-        adam_step(p.y, gq.y, m.y, v.y, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
-        adam_step(p.z, gq.z, m.z, v.z, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
-        adam_step(p.w, gq.w, m.w, v.w, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[2]);
+        adam_step(p.x, gq.x, m.x, v.x, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.y, gq.y, m.y, v.y, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.z, gq.z, m.z, v.z, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.w, gq.w, m.w, v.w, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
         reinterpret_cast<float4*>(a.p[2])[g] = p;
         reinterpret_cast<float4*>(a.m[2])[g] = m;
         reinterpret_cast<float4*>(a.v[2])[g] = v;
-        if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
         float po = a.p[3][g], mo = a.m[3][g], vo = a.v[3][g];
-        adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, a.inv_bc1, a.inv_bc2, a.lr[3]);
+        adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, bc1, bc2, a.lr[3]);
         a.p[3][g] = po;
         a.m[3][g] = mo;
         a.v[3][g] = vo;
-        if (a.gout[3]) a.gout[3][g] = glogit;
     }
+}
+
+// Advances the device-side Adam step and writes the bias corrections of the
+// new step, evaluated in double like the host path.
+__global__ void k_adam_advance(int* step, float b1, float b2, float* bias)
+{
+    const int t = *step + 1;
+    *step = t;
+    bias[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    bias[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
 }
 
 __global__ void k_densify(int n, const int* __restrict__ tiles_touched, const float4* __restrict__ grad2d,
@@ -656,9 +717,8 @@ __global__ void k_densify(int n, const int* __restrict__ tiles_touched, const fl
 // Dispatch over (degree, dtype)
 // ---------------------------------------------------------------------------
 template <int DEG, int DT>
-int32_t launch_project(int n, const float* means, const float* log_scales, const float* quats,
-                       const float* logits, const void* sh, const Cam& cam, const Dil& dil, float* splats,
-                       int* radii, int* rects, int* tiles, cudaStream_t st)
+int32_t launch_project(int n, const float* means, const float* log_scales, const float* quats, const float* logits,
+                       const void* sh, const Batch& b, cudaStream_t st)
 {
     using L = ShLayout<DEG, DT>;
     size_t smem = sizeof(uint32_t) * L::WARP_WORDS * kWarps;
@@ -666,8 +726,7 @@ int32_t launch_project(int n, const float* means, const float* log_scales, const
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
     kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,
-                                         cam, dil, reinterpret_cast<float4*>(splats), radii,
-                                         reinterpret_cast<int4*>(rects), tiles);
+                                         b);
     return gs_host::check_launch("gs_project");
 }
 
@@ -689,17 +748,15 @@ int32_t launch_project_bwd(int n, const float* means, const float* log_scales, c
 }
 
 template <int DEG, int DT>
-int32_t launch_project_bwd_adam(int n, const void* sh_store, const Cam& cam, const Dil& dil, const int* tiles,
-                                const float* grad2d, const AdamDev& a, float* pos, float* col, int* cnt,
-                                cudaStream_t st)
+int32_t launch_project_bwd_adam(int n, const void* sh_store, const Batch& b, const AdamDev& a, float* pos, float* col,
+                                int* cnt, cudaStream_t st)
 {
     using F = FusedLayout<DEG, DT>;
     size_t smem = sizeof(uint32_t) * F::WARP_WORDS * kWarps;
-    auto kern = k_project_bwd_adam<DEG, DT>;
+    auto kern = b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    kern<<<blocks, kThreads, smem, st>>>(n, sh_store, cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), a,
-                                         pos, col, cnt);
+    kern<<<blocks, kThreads, smem, st>>>(n, sh_store, b, a, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd_adam");
 }
 
@@ -743,23 +800,39 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* 
                    const GsDilation* dil, float* splats, int32_t* radii, int32_t* rects, int32_t* tiles_touched,
                    gs_stream_t stream)
 {
+    if (!cam || !dil) { gs_host::set_error("gs_project: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v{};
+    v.cam = *cam;
+    v.dil = *dil;
+    v.splats = splats;
+    v.radii = radii;
+    v.rects = rects;
+    v.tiles_touched = tiles_touched;
+    return gs_project_batch(n, sh_degree, sh_dtype, means, log_scales, quats, opacity_logits, sh, &v, 1, stream);
+}
+
+int32_t gs_project_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* means, const float* log_scales,
+                         const float* quats, const float* opacity_logits, const void* sh, const GsView* views,
+                         int32_t nviews, gs_stream_t stream)
+{
     using namespace gs;
     if (!check_params(n, sh_degree, sh_dtype, means, log_scales, quats, opacity_logits, sh)) return GS_ERR_ARG;
-    Cam c;
-    Dil d;
-    if (!gs_host::make_cam(cam, &c) || !gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
-    if (n > 0 && (!splats || !radii || !rects || !tiles_touched)) {
-        gs_host::set_error("gs_project: null output pointer");
-        return GS_ERR_ARG;
-    }
-    if (n > 0 && (((reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(rects)) & 15) != 0)) {
-        gs_host::set_error("gs_project: splats and rects must be 16-byte aligned");
-        return GS_ERR_ARG;
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    for (int i = 0; i < nviews && n > 0; ++i) {
+        const ViewDev& v = b.v[i];
+        if (!v.splats || !v.radii || !v.rects || !v.tiles) {
+            gs_host::set_error("gs_project: null output pointer");
+            return GS_ERR_ARG;
+        }
+        if (((reinterpret_cast<uintptr_t>(v.splats) | reinterpret_cast<uintptr_t>(v.rects)) & 15) != 0) {
+            gs_host::set_error("gs_project: splats and rects must be 16-byte aligned");
+            return GS_ERR_ARG;
+        }
     }
     if (n == 0) return GS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project, n, means, log_scales, quats, opacity_logits, sh, c, d,
-                       splats, radii, rects, tiles_touched, st);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project, n, means, log_scales, quats, opacity_logits, sh, b, st);
 }
 
 int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* means, const float* log_scales,
@@ -797,24 +870,43 @@ int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, cons
                             const GsAdamParams* adam, float* pos_acc, float* col_acc, int32_t* count,
                             float* const* grads_out, gs_stream_t stream)
 {
+    if (!cam || !dil) { gs_host::set_error("gs_project_bwd_adam: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v{};
+    v.cam = *cam;
+    v.dil = *dil;
+    v.tiles_touched = const_cast<int32_t*>(tiles_touched);
+    v.grad2d = const_cast<float*>(grad2d);
+    return gs_project_bwd_adam_batch(n, sh_degree, sh_dtype, sh_store, &v, 1, adam, pos_acc, col_acc, count,
+                                     grads_out, stream);
+}
+
+int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                  const GsView* views, int32_t nviews, const GsAdamParams* adam, float* pos_acc,
+                                  float* col_acc, int32_t* count, float* const* grads_out, gs_stream_t stream)
+{
     using namespace gs;
     if (!adam) { gs_host::set_error("gs_project_bwd_adam: adam is null"); return GS_ERR_ARG; }
     if (!check_params(n, sh_degree, sh_dtype, adam->param[0], adam->param[1], adam->param[2], adam->param[3],
                       sh_store))
         return GS_ERR_ARG;
-    Cam c;
-    Dil d;
-    if (!gs_host::make_cam(cam, &c) || !gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
     if (n > 0) {
         for (int t = 0; t < 5; ++t)
             if (!adam->param[t] || !adam->m[t] || !adam->v[t]) {
                 gs_host::set_error("gs_project_bwd_adam: null parameter or moment pointer");
                 return GS_ERR_ARG;
             }
-        if (!tiles_touched || !grad2d) { gs_host::set_error("gs_project_bwd_adam: null pointer"); return GS_ERR_ARG; }
-        uintptr_t al = reinterpret_cast<uintptr_t>(grad2d) | reinterpret_cast<uintptr_t>(adam->param[2]) |
-                       reinterpret_cast<uintptr_t>(adam->m[2]) | reinterpret_cast<uintptr_t>(adam->v[2]);
+        uintptr_t al = reinterpret_cast<uintptr_t>(adam->param[2]) | reinterpret_cast<uintptr_t>(adam->m[2]) |
+                       reinterpret_cast<uintptr_t>(adam->v[2]);
         if (grads_out && grads_out[2]) al |= reinterpret_cast<uintptr_t>(grads_out[2]);
+        for (int i = 0; i < nviews; ++i) {
+            if (!b.v[i].tiles || !b.v[i].grad2d) {
+                gs_host::set_error("gs_project_bwd_adam: null tiles_touched or grad2d");
+                return GS_ERR_ARG;
+            }
+            al |= reinterpret_cast<uintptr_t>(b.v[i].grad2d);
+        }
         if ((al & 15) != 0) {
             gs_host::set_error("gs_project_bwd_adam: grad2d and the quaternion tensors must be 16-byte aligned");
             return GS_ERR_ARG;
@@ -824,8 +916,8 @@ int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, cons
         gs_host::set_error("gs_project_bwd_adam: pos_acc, col_acc and count must be all null or all set");
         return GS_ERR_ARG;
     }
-    if (adam->step < 1 || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) || !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) ||
-        !(adam->eps >= 0.0f) ||
+    if ((!adam->bias_dev && adam->step < 1) || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) ||
+        !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) || !(adam->eps >= 0.0f) ||
         (adam->sh_shadow && (adam->sh_shadow_dtype < GS_DTYPE_F32 || adam->sh_shadow_dtype > GS_DTYPE_F16))) {
         gs_host::set_error("gs_project_bwd_adam: need step >= 1, 0 <= beta < 1, eps >= 0, a valid shadow dtype");
         return GS_ERR_ARG;
@@ -840,14 +932,27 @@ int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, cons
         a.gout[t] = grads_out ? grads_out[t] : nullptr;
     }
     a.b1 = adam->beta1; a.b2 = adam->beta2; a.eps = adam->eps;
-    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)adam->step)));
-    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)adam->step)));
+    if (adam->bias_dev) {
+        a.bias = adam->bias_dev;
+    } else {
+        a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)adam->step)));
+        a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)adam->step)));
+    }
     a.sparse = adam->sparse;
     a.shadow = adam->sh_shadow;
     a.shadow_dtype = adam->sh_shadow_dtype;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, c, d, tiles_touched, grad2d, a,
-                       pos_acc, col_acc, count, st);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, b, a, pos_acc, col_acc, count, st);
+}
+
+int32_t gs_adam_advance(int32_t* step_dev, float beta1, float beta2, float* bias_dev, gs_stream_t stream)
+{
+    if (!step_dev || !bias_dev || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f)) {
+        gs_host::set_error("gs_adam_advance: need device step and bias pointers and 0 <= beta < 1");
+        return GS_ERR_ARG;
+    }
+    gs::k_adam_advance<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(step_dev, beta1, beta2, bias_dev);
+    return gs_host::check_launch("gs_adam_advance");
 }
 
 int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* grad2d, float* pos_acc,

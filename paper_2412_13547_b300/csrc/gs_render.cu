@@ -75,11 +75,13 @@ struct WarpBlock {
     }
 };
 
+// Blend of one tile (the body of the single-view and the batched kernels).
 template <int TILE, int PPT>
-__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
-k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
-             const uint32_t* __restrict__ order, Dil dil, float3 bg, float* __restrict__ img,
-             float* __restrict__ t_final, uint32_t* __restrict__ last, unsigned long long* __restrict__ counts)
+__device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restrict__ splats,
+                                                const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
+                                                const Dil& dil, float3 bg, float* __restrict__ img,
+                                                float* __restrict__ t_final, uint32_t* __restrict__ last,
+                                                unsigned long long* __restrict__ counts)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
@@ -89,9 +91,6 @@ k_render_fwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     __shared__ float4 s_rgb[BATCH];
     __shared__ unsigned long long s_cnt[2];
 
-    // longest lists first when an order is given: the block scheduler then
-    // dispatches greedily longest-first
-    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
     const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
     const int u = tx * TILE + wb.lx;
@@ -240,10 +239,11 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& c
 // per-batch shared-memory accumulator, and at the end of the batch each
 // (tile, Gaussian) gets one set of vector atomics.
 template <int TILE, int PPT>
-__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
-k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
-             const uint32_t* __restrict__ order, Dil dil, float3 bg, const float* __restrict__ t_final,
-             const uint32_t* __restrict__ last, const float* __restrict__ dl_dimg, float* __restrict__ grad2d)
+__device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restrict__ splats,
+                                                const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
+                                                const Dil& dil, float3 bg, const float* __restrict__ t_final,
+                                                const uint32_t* __restrict__ last, const float* __restrict__ dl_dimg,
+                                                float* __restrict__ grad2d)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
@@ -255,9 +255,6 @@ k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     __shared__ float s_acc[BATCH][9];
     __shared__ uint32_t s_max_last;
 
-    // longest lists first when an order is given: the block scheduler then
-    // dispatches greedily longest-first
-    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
     const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
     const int lane = threadIdx.x & 31;
@@ -378,10 +375,47 @@ k_render_bwd(const float4* __restrict__ splats, const uint32_t* __restrict__ ids
     }
 }
 
-__global__ void k_loss_l1(Dil dil, int width, const float* __restrict__ img, const float* __restrict__ target,
-                          float* __restrict__ dl, float* __restrict__ loss, float inv)
+// One CTA per tile of the batch; with an order, CTA i takes tile order[i]
+// (longest lists first, so the block scheduler dispatches greedily
+// longest-first across all views).
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
+k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
+             unsigned long long* __restrict__ counts)
 {
+    const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    render_fwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img, V.t_final, V.last,
+                               counts);
+}
+
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
+k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg)
+{
+    const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    render_bwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.t_final, V.last, V.dl,
+                               reinterpret_cast<float*>(V.grad2d));
+}
+
+__global__ void k_loss_zero(const __grid_constant__ Batch b)
+{
+    if ((int)threadIdx.x < b.nviews) *b.v[threadIdx.x].loss = 0.0f;
+}
+
+// L1 loss of each view (blockIdx.y) and its gradient sign/(3P) w.r.t. the
+// rendered pixels, against the hr target sampled at the view's lattice.
+__global__ void k_loss_l1(const __grid_constant__ Batch b)
+{
+    const ViewDev& V = b.v[blockIdx.y];
+    const Dil& dil = V.dil;
+    const int width = V.cam.width;
     const int64_t P = (int64_t)dil.w_ds * dil.h_ds;
+    const float inv = (float)(1.0 / (3.0 * (double)P));
+    const float* __restrict__ img = V.img;
+    const float* __restrict__ target = V.target;
+    float* __restrict__ dl = V.dl;
     float acc = 0.0f;
     for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < P;
          pix += (int64_t)gridDim.x * blockDim.x) {
@@ -402,7 +436,7 @@ __global__ void k_loss_l1(Dil dil, int width, const float* __restrict__ img, con
     if (threadIdx.x == 0) {
         float t = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
-        atomicAdd(loss, t * inv);
+        atomicAdd(V.loss, t * inv);
     }
 }
 
@@ -424,9 +458,15 @@ int resolve_ppt(int tile, int ppt)
 // Tile order, longest list first: 256 buckets of the list length (8 per
 // octave, descending), one block. Order inside a bucket is arbitrary; it only
 // affects scheduling, never results.
-__global__ void __launch_bounds__(1024) k_tile_order(int T, const uint2* __restrict__ ranges,
-                                                     uint32_t* __restrict__ order)
+__device__ __forceinline__ uint2 batch_range(const Batch& b, int gt)
 {
+    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    return V.ranges[gt - V.tile_begin];
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Batch b, uint32_t* __restrict__ order)
+{
+    const int T = b.total_tiles;
     __shared__ uint32_t s_hist[256];
     __shared__ uint32_t s_off[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
@@ -438,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(int T, const uint2* __restr
         return 255 - min(255, e * 8 + m);
     };
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint2 r = ranges[t];
+        const uint2 r = batch_range(b, t);
         atomicAdd(&s_hist[bucket(r.y - r.x)], 1u);
     }
     __syncthreads();
@@ -451,20 +491,54 @@ __global__ void __launch_bounds__(1024) k_tile_order(int T, const uint2* __restr
     }
     __syncthreads();
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint2 r = ranges[t];
+        const uint2 r = batch_range(b, t);
         order[atomicAdd(&s_off[bucket(r.y - r.x)], 1u)] = (uint32_t)t;
     }
 }
 
-bool check_render_args(int32_t n, const float* splats, const uint32_t* ids, const uint32_t* ranges)
+bool check_render_view(int32_t n, const ViewDev& v)
 {
-    if (n < 0) { gs_host::set_error("n must be >= 0"); return false; }
-    if (!ranges || (n > 0 && (!splats || !ids))) { gs_host::set_error("null pointer"); return false; }
-    if ((reinterpret_cast<uintptr_t>(splats) & 15) != 0 || (reinterpret_cast<uintptr_t>(ranges) & 7) != 0) {
+    if (!v.ranges || (n > 0 && (!v.splats || !v.ids))) {
+        gs_host::set_error("render: null splats, sorted_ids or ranges");
+        return false;
+    }
+    if ((reinterpret_cast<uintptr_t>(v.splats) & 15) != 0 || (reinterpret_cast<uintptr_t>(v.ranges) & 7) != 0) {
         gs_host::set_error("splats must be 16-byte and ranges 8-byte aligned");
         return false;
     }
     return true;
+}
+
+template <int TILE, int PPT>
+void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, cudaStream_t st)
+{
+    k_render_fwd<TILE, PPT><<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
+}
+
+template <int TILE, int PPT>
+void launch_bwd(const Batch& b, const uint32_t* order, float3 bg, cudaStream_t st)
+{
+    k_render_bwd<TILE, PPT><<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg);
+}
+
+// The instantiated (tile, pixels per thread) pairs.
+#define GS_TILE_SWITCH(tile, ppt, FN, ...)                \
+    switch ((tile) * 8 + (ppt)) {                         \
+        case 8 * 8 + 1: FN<8, 1>(__VA_ARGS__); break;     \
+        case 8 * 8 + 2: FN<8, 2>(__VA_ARGS__); break;     \
+        case 16 * 8 + 1: FN<16, 1>(__VA_ARGS__); break;   \
+        case 16 * 8 + 2: FN<16, 2>(__VA_ARGS__); break;   \
+        case 16 * 8 + 4: FN<16, 4>(__VA_ARGS__); break;   \
+        case 32 * 8 + 2: FN<32, 2>(__VA_ARGS__); break;   \
+        default: FN<32, 4>(__VA_ARGS__); break;           \
+    }
+
+GsView single_view(const GsCamera* cam, const GsDilation* dil)
+{
+    GsView v{};
+    v.cam = *cam;
+    v.dil = *dil;
+    return v;
 }
 
 }  // namespace
@@ -477,29 +551,38 @@ int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids
                       uint32_t* last, unsigned long long* counts, int32_t pixels_per_thread,
                       const uint32_t* tile_order, gs_stream_t stream)
 {
+    if (!cam || !dil) { gs_host::set_error("gs_render_fwd: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v = gs::single_view(cam, dil);
+    v.splats = const_cast<float*>(splats);
+    v.sorted_ids = const_cast<uint32_t*>(sorted_ids);
+    v.ranges = const_cast<uint32_t*>(ranges);
+    v.img = img;
+    v.t_final = t_final;
+    v.last = last;
+    return gs_render_fwd_batch(n, &v, 1, bg, tile_order, counts, pixels_per_thread, stream);
+}
+
+int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
+                            const uint32_t* tile_order, unsigned long long* counts, int32_t pixels_per_thread,
+                            gs_stream_t stream)
+{
     using namespace gs;
-    Dil d;
-    if (!gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
-    if (!check_render_args(n, splats, sorted_ids, ranges)) return GS_ERR_ARG;
-    if (!bg || !img || !t_final || !last) { gs_host::set_error("gs_render_fwd: null pointer"); return GS_ERR_ARG; }
-    const int ppt = resolve_ppt(d.tile, pixels_per_thread);
-    if (ppt < 0) return GS_ERR_ARG;
-    const float3 b = make_float3(bg[0], bg[1], bg[2]);
-    const int tiles = d.tiles_x * d.tiles_y;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const float4* sp = reinterpret_cast<const float4*>(splats);
-    const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-#define GS_FWD(T_, P_) k_render_fwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, tile_order, d, b, img, t_final, last, counts)
-    switch (d.tile * 8 + ppt) {
-        case 8 * 8 + 1: GS_FWD(8, 1); break;
-        case 8 * 8 + 2: GS_FWD(8, 2); break;
-        case 16 * 8 + 1: GS_FWD(16, 1); break;
-        case 16 * 8 + 2: GS_FWD(16, 2); break;
-        case 16 * 8 + 4: GS_FWD(16, 4); break;
-        case 32 * 8 + 2: GS_FWD(32, 2); break;
-        default: GS_FWD(32, 4); break;
+    if (n < 0) { gs_host::set_error("n must be >= 0"); return GS_ERR_ARG; }
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    for (int i = 0; i < nviews; ++i) {
+        if (!check_render_view(n, b.v[i])) return GS_ERR_ARG;
+        if (!b.v[i].img || !b.v[i].t_final || !b.v[i].last) {
+            gs_host::set_error("gs_render_fwd: null img, t_final or last");
+            return GS_ERR_ARG;
+        }
     }
-#undef GS_FWD
+    if (!bg) { gs_host::set_error("gs_render_fwd: bg is null"); return GS_ERR_ARG; }
+    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread);
+    if (ppt < 0) return GS_ERR_ARG;
+    const float3 c = make_float3(bg[0], bg[1], bg[2]);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GS_TILE_SWITCH(b.v[0].dil.tile, ppt, launch_fwd, b, tile_order, c, counts, st);
     return gs_host::check_launch("gs_render_fwd");
 }
 
@@ -508,37 +591,47 @@ int32_t gs_render_bwd(int32_t n, const float* splats, const uint32_t* sorted_ids
                       const uint32_t* last, const float* dl_dimg, float* grad2d, int32_t zero_grad2d,
                       int32_t pixels_per_thread, const uint32_t* tile_order, gs_stream_t stream)
 {
+    if (!cam || !dil) { gs_host::set_error("gs_render_bwd: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v = gs::single_view(cam, dil);
+    v.splats = const_cast<float*>(splats);
+    v.sorted_ids = const_cast<uint32_t*>(sorted_ids);
+    v.ranges = const_cast<uint32_t*>(ranges);
+    v.t_final = const_cast<float*>(t_final);
+    v.last = const_cast<uint32_t*>(last);
+    v.dl_dimg = const_cast<float*>(dl_dimg);
+    v.grad2d = grad2d;
+    return gs_render_bwd_batch(n, &v, 1, bg, tile_order, zero_grad2d, pixels_per_thread, stream);
+}
+
+int32_t gs_render_bwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
+                            const uint32_t* tile_order, int32_t zero_grad2d, int32_t pixels_per_thread,
+                            gs_stream_t stream)
+{
     using namespace gs;
-    Dil d;
-    if (!gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
-    if (!check_render_args(n, splats, sorted_ids, ranges)) return GS_ERR_ARG;
-    if (!bg || !t_final || !last || !dl_dimg || (n > 0 && !grad2d)) {
-        gs_host::set_error("gs_render_bwd: null pointer");
-        return GS_ERR_ARG;
+    if (n < 0) { gs_host::set_error("n must be >= 0"); return GS_ERR_ARG; }
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    for (int i = 0; i < nviews; ++i) {
+        const ViewDev& v = b.v[i];
+        if (!check_render_view(n, v)) return GS_ERR_ARG;
+        if (!v.t_final || !v.last || !v.dl || (n > 0 && !v.grad2d)) {
+            gs_host::set_error("gs_render_bwd: null t_final, last, dl_dimg or grad2d");
+            return GS_ERR_ARG;
+        }
+        if ((reinterpret_cast<uintptr_t>(v.grad2d) & 15) != 0) {
+            gs_host::set_error("gs_render_bwd: grad2d must be 16-byte aligned");
+            return GS_ERR_ARG;
+        }
     }
-    if ((reinterpret_cast<uintptr_t>(grad2d) & 15) != 0) {
-        gs_host::set_error("gs_render_bwd: grad2d must be 16-byte aligned");
-        return GS_ERR_ARG;
-    }
-    const int ppt = resolve_ppt(d.tile, pixels_per_thread);
+    if (!bg) { gs_host::set_error("gs_render_bwd: bg is null"); return GS_ERR_ARG; }
+    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread);
     if (ppt < 0) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (zero_grad2d && n > 0) cudaMemsetAsync(grad2d, 0, (size_t)n * GS_GRAD2D_FLOATS * sizeof(float), st);
-    const float3 b = make_float3(bg[0], bg[1], bg[2]);
-    const int tiles = d.tiles_x * d.tiles_y;
-    const float4* sp = reinterpret_cast<const float4*>(splats);
-    const uint2* rg = reinterpret_cast<const uint2*>(ranges);
-#define GS_BWD(T_, P_) k_render_bwd<T_, P_><<<tiles, TileGeom<T_, P_>::THREADS, 0, st>>>(sp, sorted_ids, rg, tile_order, d, b, t_final, last, dl_dimg, grad2d)
-    switch (d.tile * 8 + ppt) {
-        case 8 * 8 + 1: GS_BWD(8, 1); break;
-        case 8 * 8 + 2: GS_BWD(8, 2); break;
-        case 16 * 8 + 1: GS_BWD(16, 1); break;
-        case 16 * 8 + 2: GS_BWD(16, 2); break;
-        case 16 * 8 + 4: GS_BWD(16, 4); break;
-        case 32 * 8 + 2: GS_BWD(32, 2); break;
-        default: GS_BWD(32, 4); break;
-    }
-#undef GS_BWD
+    if (zero_grad2d && n > 0)
+        for (int i = 0; i < nviews; ++i)
+            cudaMemsetAsync(b.v[i].grad2d, 0, (size_t)n * GS_GRAD2D_FLOATS * sizeof(float), st);
+    const float3 c = make_float3(bg[0], bg[1], bg[2]);
+    GS_TILE_SWITCH(b.v[0].dil.tile, ppt, launch_bwd, b, tile_order, c, st);
     return gs_host::check_launch("gs_render_bwd");
 }
 
@@ -550,25 +643,59 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
         return GS_ERR_ARG;
     }
     if (num_tiles == 0) return GS_OK;
-    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        num_tiles, reinterpret_cast<const uint2*>(ranges), order);
+    Batch b{};
+    b.nviews = 1;
+    b.v[0].ranges = reinterpret_cast<const uint2*>(ranges);
+    b.total_tiles = num_tiles;
+    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
     return gs_host::check_launch("gs_tile_order");
+}
+
+int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream)
+{
+    using namespace gs;
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    for (int i = 0; i < nviews; ++i)
+        if (!b.v[i].ranges) { gs_host::set_error("gs_tile_order_batch: null ranges"); return GS_ERR_ARG; }
+    if (!order) { gs_host::set_error("gs_tile_order_batch: order is null"); return GS_ERR_ARG; }
+    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
+    return gs_host::check_launch("gs_tile_order_batch");
 }
 
 int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, float* dl_dimg,
                    float* loss, gs_stream_t stream)
 {
+    if (!cam || !dil) { gs_host::set_error("gs_loss_l1: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v = gs::single_view(cam, dil);
+    v.img = const_cast<float*>(img);
+    v.target = target;
+    v.dl_dimg = dl_dimg;
+    v.loss = loss;
+    return gs_loss_l1_batch(&v, 1, stream);
+}
+
+int32_t gs_loss_l1_batch(const GsView* views, int32_t nviews, gs_stream_t stream)
+{
     using namespace gs;
-    Dil d;
-    if (!gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
-    if (!img || !target || !dl_dimg || !loss) { gs_host::set_error("gs_loss_l1: null pointer"); return GS_ERR_ARG; }
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    int64_t pmax = 0;
+    for (int i = 0; i < nviews; ++i) {
+        const ViewDev& v = b.v[i];
+        if (!v.img || !v.target || !v.dl || !v.loss) {
+            gs_host::set_error("gs_loss_l1: null img, target, dl_dimg or loss");
+            return GS_ERR_ARG;
+        }
+        const int64_t P = (int64_t)v.dil.w_ds * v.dil.h_ds;
+        if (P > pmax) pmax = P;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaMemsetAsync(loss, 0, sizeof(float), st);
-    const int64_t P = (int64_t)d.w_ds * d.h_ds;
-    const float inv = (float)(1.0 / (3.0 * (double)P));
-    int blocks = (int)((P + 255) / 256);
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    k_loss_l1<<<blocks, 256, 0, st>>>(d, cam->width, img, target, dl_dimg, loss, inv);
+    k_loss_zero<<<1, 32, 0, st>>>(b);
+    int64_t bx = (pmax + 255) / 256;
+    const int64_t cap = (148 * 16 + nviews - 1) / nviews;
+    if (bx > cap) bx = cap;
+    k_loss_l1<<<dim3((unsigned)bx, (unsigned)nviews), 256, 0, st>>>(b);
     return gs_host::check_launch("gs_loss_l1");
 }
 

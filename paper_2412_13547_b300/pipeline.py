@@ -269,10 +269,220 @@ class TrainStep:
         mask = (rast.tiles_touched > 0).to(torch.uint8) if self.sparse else None
         R.gs_adam(entries, a.beta1, a.beta2, a.eps, self.step_count, row_mask=mask)
 
-    # kernels launched per step (project, bin_sort internals, render, loss, bwd, proj bwd, adam)
-    def launches_per_step(self, n_tiles: int, capacity: int) -> int:
-        bits = max(1, math.ceil(math.log2(max(2, n_tiles))))
-        tile_passes = (bits + 7) // 8
-        # gs_bin_sort: depth keys + 4 depth passes x 3 + scan 3 + emit + tile passes x 3 + ranges
-        binsort = 1 + 4 * 3 + 3 + 1 + tile_passes * 3 + 1
-        return 1 + binsort + 1 + 1 + 1 + 1 + 1
+    def launches_per_step(self) -> int:
+        """Kernels one step launches (memsets not counted): projection, the
+        binning, the tile order, blend, loss (zeroing + reduction), blend
+        backward, and the fused optimizer (or projection backward + Adam)."""
+        return 1 + BIN_SORT_KERNELS + int(self.rast.longest_first) + 1 + 2 + 1 + (1 if self.fused else 2)
+
+
+# kernels in one gs_bin_sort call: pair count, depth keys, a 4-pass radix sort
+# of the depths (3 kernels a pass), 6 + 2 for the row level, 7 for the tile level
+BIN_SORT_KERNELS = 2 + 4 * 3 + 6 + 2 + 7
+
+
+# ---------------------------------------------------------------------------
+# Several views per optimizer step
+# ---------------------------------------------------------------------------
+
+class BatchTrainStep:
+    """One optimizer step over a batch of views of uneven resolution: batched
+    projection, binning per view, ONE blend launch over the tiles of every
+    view (a work queue ordered longest list first), batched L1, ONE backward
+    blend launch, and ONE fused projection backward + densification statistics
+    + Adam launch whose gradient is the sum over the views.
+
+    Dilation (Sec. 3.1): with d > 1 each step renders one lattice offset per
+    view; view i at phase k takes the rotating offset of k + i, so the views
+    of one step cover different lattices and d*d phases cover all of them.
+    The Adam step count lives on the device, so ``capture()`` can record the
+    step of every phase into a CUDA graph that ``step()`` then replays; the
+    only host synchronisation is in ``overflowed()``."""
+
+    def __init__(self, params: GaussianParams, cams, targets, d: int = 1, adam: AdamConfig = AdamConfig(),
+                 bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
+                 pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
+                 capacity=None, headroom: float = 1.15, optimize: bool = True):
+        if not 1 <= len(cams) <= R.MAX_VIEWS:
+            raise ValueError(f"1..{R.MAX_VIEWS} views per batch")
+        dev = params.means.device
+        self.p, self.adam, self.bg, self.d = params, adam, tuple(bg), int(d)
+        self.cams, self.V = list(cams), len(cams)
+        self.sparse, self.densify, self.optimize_step = bool(sparse), bool(densify), bool(optimize)
+        self.tile, self.ppt, self.center_mode = int(tile), int(pixels_per_thread), int(center_mode)
+        self.longest_first = bool(longest_first)
+        n, V = params.n, self.V
+        self.targets = [t.contiguous() for t in targets]
+        for c, t in zip(self.cams, self.targets):
+            if tuple(t.shape) != (c.height, c.width, 3) or t.dtype != torch.float32:
+                raise ValueError("each target must be an FP32 height x width x 3 tensor on the device")
+        self.splats = torch.zeros(V, n, R.SPLAT_FLOATS, device=dev)
+        self.radii = torch.zeros(V, n, dtype=torch.int32, device=dev)
+        self.rects = torch.zeros(V, n, 4, dtype=torch.int32, device=dev)
+        self.tiles_touched = torch.zeros(V, n, dtype=torch.int32, device=dev)
+        self.grad2d = torch.zeros(V, n, R.GRAD2D_FLOATS, device=dev)
+        self.loss = torch.zeros(V, device=dev)
+        self.num_pairs = torch.zeros(V, dtype=torch.int64, device=dev)
+        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        # the largest grid of each view over the offsets (offset 0 renders the most pixels)
+        self.grid0 = [R.gs_grid(c, self._dil(0, 0)) for c in self.cams]
+        self.ranges = [torch.zeros(g[2] * g[3], 2, dtype=torch.int32, device=dev) for g in self.grid0]
+        self.img = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
+        self.t_final = [torch.empty(g[1], g[0], device=dev) for g in self.grid0]
+        self.last = [torch.empty(g[1], g[0], dtype=torch.int32, device=dev) for g in self.grid0]
+        self.dl = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
+        self.order = torch.zeros(sum(g[2] * g[3] for g in self.grid0), dtype=torch.int32, device=dev)
+        # moments, device-side Adam step and densification statistics
+        self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.bias_dev = torch.zeros(2, device=dev)
+        self.pos_acc = torch.zeros(n, device=dev)
+        self.col_acc = torch.zeros(n, device=dev)
+        self.vis_count = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.phase = 0
+        self._tables = {}
+        self.graphs = {}
+        self.capacity = self._capacities(headroom) if capacity is None else \
+            [int(c) for c in (capacity if hasattr(capacity, "__len__") else [capacity] * V)]
+        self.sorted_ids = [torch.empty(max(1, c), dtype=torch.int32, device=dev) for c in self.capacity]
+        ws = max(R.gs_bin_sort_workspace_size(n, c, g[2], g[3]) for c, g in zip(self.capacity, self.grid0))
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+
+    @property
+    def phases(self) -> int:
+        return self.d * self.d
+
+    def _dil(self, phase: int, view: int) -> Dilation:
+        from .scenes import rotating_offset
+        ox, oy = rotating_offset(phase + view, self.d)
+        return Dilation(self.d, ox, oy, self.center_mode, self.tile)
+
+    def _capacities(self, headroom: float):
+        """Pairs per view = sum of tiles touched (exact); the maximum over the
+        phases, with headroom for the parameters moving during the fit."""
+        best = [0] * self.V
+        for ph in range(self.phases):
+            self._project(self.table(ph, project_only=True))
+            k = self.tiles_touched.to(torch.int64).sum(1).tolist()
+            best = [max(a, b) for a, b in zip(best, k)]
+        return [int(math.ceil(k * headroom)) + 1024 for k in best]
+
+    def table(self, phase: int, project_only: bool = False) -> R.ViewTable:
+        key = (phase % self.phases, project_only)
+        if key not in self._tables:
+            views = []
+            for i, c in enumerate(self.cams):
+                dil = self._dil(key[0], i)
+                w_ds, h_ds, tx, ty = R.gs_grid(c, dil)
+                v = R.View(c, dil, splats=self.splats[i], radii=self.radii[i], rects=self.rects[i],
+                           tiles_touched=self.tiles_touched[i], grad2d=self.grad2d[i])
+                if not project_only:
+                    P = w_ds * h_ds
+                    v.sorted_ids, v.ranges = self.sorted_ids[i], self.ranges[i]
+                    v.img = self.img[i].view(-1)[:3 * P]
+                    v.t_final = self.t_final[i].view(-1)[:P]
+                    v.last = self.last[i].view(-1)[:P]
+                    v.dl_dimg = self.dl[i].view(-1)[:3 * P]
+                    v.target, v.loss = self.targets[i], self.loss[i:i + 1]
+                views.append(v)
+            self._tables[key] = R.ViewTable(views)
+        return self._tables[key]
+
+    def _project(self, t: R.ViewTable):
+        p = self.p
+        R.gs_project_batch(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, t)
+
+    # -- the step ---------------------------------------------------------------
+    def render_pass(self, phase: int, counts: bool = False):
+        """Everything up to the 2D gradients of every view (no parameter update)."""
+        t = self.table(phase)
+        self._project(t)
+        for i, v in enumerate(t.views):
+            _, _, tx, ty = R.gs_grid(v.cam, v.dil)
+            R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty, self.workspace,
+                          self.capacity[i], self.sorted_ids[i], self.ranges[i], self.num_pairs[i:i + 1])
+        order = None
+        if self.longest_first:
+            R.gs_tile_order_batch(t, self.order)
+            order = self.order
+        R.gs_render_fwd_batch(self.p.n, t, self.bg, tile_order=order, counts=self.counts if counts else None,
+                              pixels_per_thread=self.ppt)
+        R.gs_loss_l1_batch(t)
+        R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True, pixels_per_thread=self.ppt)
+
+    def optimize(self, phase: int):
+        p, a = self.p, self.adam
+        lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
+        shadow = p.sh_store if p.sh_store.data_ptr() != p.sh.data_ptr() else None
+        stats = (self.pos_acc, self.col_acc, self.vis_count) if self.densify else (None, None, None)
+        R.gs_adam_advance(self.step_dev, a.beta1, a.beta2, self.bias_dev)
+        R.gs_project_bwd_adam_batch(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, 1, p.sh_store,
+                                    self.table(phase), sparse=self.sparse, sh_shadow=shadow, pos_acc=stats[0],
+                                    col_acc=stats[1], count=stats[2], bias_dev=self.bias_dev)
+
+    def run(self, phase: int, counts: bool = False):
+        self.render_pass(phase, counts)
+        if self.optimize_step:
+            self.optimize(phase)
+
+    def capture(self):
+        """Record the step of every phase into a CUDA graph (each phase is run
+        eagerly once first; that run is a real step)."""
+        for ph in range(self.phases):
+            self.run(ph)
+        torch.cuda.synchronize()
+        for ph in range(self.phases):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.run(ph)
+            self.graphs[ph] = g
+        torch.cuda.synchronize()
+
+    def step(self, counts: bool = False):
+        ph = self.phase % self.phases
+        if ph in self.graphs and not counts:
+            self.graphs[ph].replay()
+        else:
+            self.run(ph, counts)
+        self.phase += 1
+        return self.loss
+
+    def overflowed(self) -> bool:
+        """True when a view had more pairs than its capacity in the last step
+        (its lists were then left empty). Host synchronisation."""
+        k = self.num_pairs.tolist()
+        return any(ki > ci for ki, ci in zip(k, self.capacity))
+
+    def launches_per_step(self) -> int:
+        """Kernels one step launches (memsets not counted): projection, the
+        binning of every view, the tile order, both blend launches, the loss
+        (zeroing + reduction), and the Adam step advance + the fused optimizer."""
+        return 1 + BIN_SORT_KERNELS * self.V + int(self.longest_first) + 1 + 2 + 1 + \
+            (2 if self.optimize_step else 0)
+
+
+def autotune_batch(params: GaussianParams, cams, targets, d: int = 1,
+                   candidates=((8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (32, 2), (32, 4)), iters: int = 3,
+                   **kw):
+    """Pick the tile size and pixels per thread of the blend launches for a
+    batch: time ``render_pass`` (projection, binning, both blend launches and
+    the loss: everything the launch shape affects) of every candidate with
+    CUDA events and return ((tile, ppt), {candidate: ms})."""
+    times = {}
+    for tile, ppt in candidates:
+        st = BatchTrainStep(params, cams, targets, d=d, tile=tile, pixels_per_thread=ppt, optimize=False, **kw)
+        for ph in range(st.phases):
+            st.render_pass(ph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(iters * st.phases):
+            st.render_pass(i % st.phases)
+        e1.record()
+        torch.cuda.synchronize()
+        times[(tile, ppt)] = e0.elapsed_time(e1) / (iters * st.phases)
+        del st
+        torch.cuda.empty_cache()
+    best = min(times, key=times.get)
+    return best, times

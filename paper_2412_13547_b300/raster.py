@@ -22,9 +22,13 @@ SPLAT_FLOATS = 12
 GRAD2D_FLOATS = 12
 ADAM_MAX_TENSORS = 8
 
+MAX_VIEWS = 16
+
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
            "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
-           "gs_project_bwd_adam", "gs_densify_stats", "gs_adam")
+           "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
+           "gs_tile_order_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
+           "gs_project_bwd_adam_batch")
 
 
 class GsError(RuntimeError):
@@ -53,7 +57,15 @@ class GsAdamParams(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p * 5), ("m", ctypes.c_void_p * 5), ("v", ctypes.c_void_p * 5),
                 ("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("step", ctypes.c_int32), ("sparse", ctypes.c_int32),
-                ("sh_shadow", ctypes.c_void_p), ("sh_shadow_dtype", ctypes.c_int32)]
+                ("sh_shadow", ctypes.c_void_p), ("sh_shadow_dtype", ctypes.c_int32), ("bias_dev", ctypes.c_void_p)]
+
+
+_VIEW_BUFFERS = ("splats", "radii", "rects", "tiles_touched", "sorted_ids", "ranges", "img", "t_final", "last",
+                 "target", "dl_dimg", "grad2d", "loss")
+
+
+class GsView(ctypes.Structure):
+    _fields_ = [("cam", GsCamera), ("dil", GsDilation)] + [(k, ctypes.c_void_p) for k in _VIEW_BUFFERS]
 
 
 @dataclass(frozen=True)
@@ -67,6 +79,50 @@ class Dilation:
 
     def c(self) -> GsDilation:
         return GsDilation(self.d, self.ox, self.oy, self.center_mode, self.tile)
+
+
+@dataclass
+class View:
+    """One view of a batch: its camera, dilation and the device buffers of
+    that view (any may be None when the call at hand does not use it)."""
+    cam: object
+    dil: Dilation
+    splats: torch.Tensor | None = None
+    radii: torch.Tensor | None = None
+    rects: torch.Tensor | None = None
+    tiles_touched: torch.Tensor | None = None
+    sorted_ids: torch.Tensor | None = None
+    ranges: torch.Tensor | None = None
+    img: torch.Tensor | None = None
+    t_final: torch.Tensor | None = None
+    last: torch.Tensor | None = None
+    target: torch.Tensor | None = None
+    dl_dimg: torch.Tensor | None = None
+    grad2d: torch.Tensor | None = None
+    loss: torch.Tensor | None = None
+
+
+class ViewTable:
+    """The GsView array of a batch, built once and reused by every batched
+    call (it holds only pointers, so refilled buffers need no rebuild)."""
+
+    def __init__(self, views):
+        views = list(views)
+        if not 1 <= len(views) <= MAX_VIEWS:
+            raise ValueError(f"a batch holds 1..{MAX_VIEWS} views")
+        self.views = views
+        self.n = len(views)
+        self.arr = (GsView * self.n)()
+        for i, v in enumerate(views):
+            self.arr[i].cam = camera(v.cam)
+            self.arr[i].dil = v.dil.c()
+            for k in _VIEW_BUFFERS:
+                t = getattr(v, k)
+                setattr(self.arr[i], k, None if t is None else _ptr(t).value)
+
+
+def _table(views) -> ViewTable:
+    return views if isinstance(views, ViewTable) else ViewTable(views)
 
 
 def camera(cam) -> GsCamera:
@@ -113,6 +169,15 @@ def load():
     lib.gs_project_bwd_adam.argtypes = [i32, i32, i32, P, cam_p, dil_p, P, P, ctypes.POINTER(GsAdamParams), P, P,
                                         P, P, P]
     lib.gs_adam.argtypes = [ctypes.POINTER(GsAdamTensor), i32, f32, f32, f32, i32, P, P]
+    lib.gs_adam_advance.argtypes = [P, f32, f32, P, P]
+    view_p = ctypes.POINTER(GsView)
+    lib.gs_project_batch.argtypes = [i32, i32, i32, P, P, P, P, P, view_p, i32, P]
+    lib.gs_tile_order_batch.argtypes = [view_p, i32, P, P]
+    lib.gs_render_fwd_batch.argtypes = [i32, view_p, i32, P, P, P, i32, P]
+    lib.gs_loss_l1_batch.argtypes = [view_p, i32, P]
+    lib.gs_render_bwd_batch.argtypes = [i32, view_p, i32, P, P, i32, i32, P]
+    lib.gs_project_bwd_adam_batch.argtypes = [i32, i32, i32, P, view_p, i32, ctypes.POINTER(GsAdamParams), P, P, P,
+                                              P, P]
     for name in SYMBOLS:
         if name not in ("gs_last_error", "gs_bin_sort_workspace_size"):
             getattr(lib, name).restype = i32
@@ -236,13 +301,7 @@ def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilat
                                  _stream(stream)), "gs_project_bwd")
 
 
-def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, cam, dil: Dilation, tiles_touched,
-                        grad2d, sparse=False, sh_shadow=None, pos_acc=None, col_acc=None, count=None,
-                        grads_out=None, stream=None):
-    """params, m, v: lists of the 5 FP32 tensors (means, log_scales, quats,
-    opacity_logits, sh), updated in place; lrs: 5 learning rates."""
-    n = params[0].shape[0]
-    deg = sh_degree_of(params[4])
+def _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev):
     a = GsAdamParams()
     for t in range(5):
         for arr, src in ((a.param, params), (a.m, m), (a.v, v)):
@@ -253,13 +312,79 @@ def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, ca
     a.beta1, a.beta2, a.eps, a.step, a.sparse = float(beta1), float(beta2), float(eps), int(step), int(bool(sparse))
     a.sh_shadow = sh_shadow.data_ptr() if sh_shadow is not None else None
     a.sh_shadow_dtype = _SH_DTYPE[sh_shadow.dtype] if sh_shadow is not None else GS_DTYPE_F32
-    gout = None
-    if grads_out is not None:
-        gout = (ctypes.c_void_p * 5)(*[g.data_ptr() if g is not None else None for g in grads_out])
+    a.bias_dev = _ptr(bias_dev).value if bias_dev is not None else None
+    return a
+
+
+def _grads_out(grads_out):
+    if grads_out is None:
+        return None
+    return (ctypes.c_void_p * 5)(*[g.data_ptr() if g is not None else None for g in grads_out])
+
+
+def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, cam, dil: Dilation, tiles_touched,
+                        grad2d, sparse=False, sh_shadow=None, pos_acc=None, col_acc=None, count=None,
+                        grads_out=None, bias_dev=None, stream=None):
+    """params, m, v: lists of the 5 FP32 tensors (means, log_scales, quats,
+    opacity_logits, sh), updated in place; lrs: 5 learning rates. bias_dev
+    (optional device float[2] from gs_adam_advance) replaces step."""
+    n = params[0].shape[0]
+    deg = sh_degree_of(params[4])
+    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev)
     _check(load().gs_project_bwd_adam(n, deg, _SH_DTYPE[sh_store.dtype], _ptr(sh_store), ctypes.byref(camera(cam)),
                                       ctypes.byref(dil.c()), _ptr(tiles_touched), _ptr(grad2d), ctypes.byref(a),
-                                      _ptr(pos_acc), _ptr(col_acc), _ptr(count), gout, _stream(stream)),
+                                      _ptr(pos_acc), _ptr(col_acc), _ptr(count), _grads_out(grads_out),
+                                      _stream(stream)),
            "gs_project_bwd_adam")
+
+
+def gs_adam_advance(step_dev, beta1, beta2, bias_dev, stream=None):
+    """Device-side Adam step: step_dev (int32[1]) += 1, bias_dev (float[2]) =
+    bias corrections of the new step."""
+    _check(load().gs_adam_advance(_ptr(step_dev), float(beta1), float(beta2), _ptr(bias_dev), _stream(stream)),
+           "gs_adam_advance")
+
+
+# -- batched views -----------------------------------------------------------
+
+def gs_project_batch(means, log_scales, quats, opacity_logits, sh, views, stream=None):
+    t = _table(views)
+    _check(load().gs_project_batch(means.shape[0], sh_degree_of(sh), _SH_DTYPE[sh.dtype], _ptr(means),
+                                   _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), t.arr, t.n,
+                                   _stream(stream)), "gs_project_batch")
+
+
+def gs_tile_order_batch(views, order, stream=None):
+    t = _table(views)
+    _check(load().gs_tile_order_batch(t.arr, t.n, _ptr(order), _stream(stream)), "gs_tile_order_batch")
+
+
+def gs_render_fwd_batch(n, views, bg, tile_order=None, counts=None, pixels_per_thread=0, stream=None):
+    t = _table(views)
+    _check(load().gs_render_fwd_batch(int(n), t.arr, t.n, _bg(bg), _ptr(tile_order), _ptr(counts),
+                                      int(pixels_per_thread), _stream(stream)), "gs_render_fwd_batch")
+
+
+def gs_loss_l1_batch(views, stream=None):
+    t = _table(views)
+    _check(load().gs_loss_l1_batch(t.arr, t.n, _stream(stream)), "gs_loss_l1_batch")
+
+
+def gs_render_bwd_batch(n, views, bg, tile_order=None, zero_grad2d=True, pixels_per_thread=0, stream=None):
+    t = _table(views)
+    _check(load().gs_render_bwd_batch(int(n), t.arr, t.n, _bg(bg), _ptr(tile_order), int(bool(zero_grad2d)),
+                                      int(pixels_per_thread), _stream(stream)), "gs_render_bwd_batch")
+
+
+def gs_project_bwd_adam_batch(params, m, v, lrs, beta1, beta2, eps, step, sh_store, views, sparse=False,
+                              sh_shadow=None, pos_acc=None, col_acc=None, count=None, grads_out=None, bias_dev=None,
+                              stream=None):
+    t = _table(views)
+    n = params[0].shape[0]
+    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev)
+    _check(load().gs_project_bwd_adam_batch(n, sh_degree_of(params[4]), _SH_DTYPE[sh_store.dtype], _ptr(sh_store),
+                                            t.arr, t.n, ctypes.byref(a), _ptr(pos_acc), _ptr(col_acc), _ptr(count),
+                                            _grads_out(grads_out), _stream(stream)), "gs_project_bwd_adam_batch")
 
 
 def gs_densify_stats(n, tiles_touched, grad2d, pos_acc, col_acc, count, stream=None):

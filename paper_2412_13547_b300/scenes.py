@@ -16,6 +16,11 @@ scene, cameras and targets):
   on a background shell of radius 3; log-scales N(-4, 0.5); SH degree 3 (DC
   drawn for a U[0,1] colour, higher bands N(0, 0.05)).
 * ``uhd``    -- 3840x2160, 3M Gaussians, same distribution.
+* ``batch``  -- 8 views of mixed resolution (2 x 1920x1080, 3 x 2560x1440,
+  3 x 3840x2160) at radius 2.6, random azimuth U[0, 360) and elevation
+  U[0, 60] degrees, around 2M Gaussians of the same distribution of which 20%
+  are packed into a ball at the origin whose image covers about 5% of a 4K
+  frame (a heavy-tailed tile load).
 
 Cameras look at the origin from radius 4 (small) or 2.6 (inside the background
 shell, outside the cluster cube's circumsphere) with a 60 degree horizontal
@@ -205,6 +210,31 @@ def workload_uhd(n=3_000_000):
     scene = cluster_scene(n, index=2)
     cam = look_at(orbit_eye(2.6, 30.0, 20.0), width=3840, height=2160)
     return scene, cam, target_image(3840, 2160, 2)
+
+
+BATCH_RESOLUTIONS = ((1920, 1080),) * 2 + ((2560, 1440),) * 3 + ((3840, 2160),) * 3
+
+
+def packed_ball_radius(frac_of_frame=0.05, width=3840, height=2160, distance=2.6, fov_x_deg=60.0):
+    """World radius of a ball at the origin whose image disc covers the given
+    fraction of a frame seen from ``distance``."""
+    f = 0.5 * width / math.tan(math.radians(fov_x_deg) / 2.0)
+    r_px = math.sqrt(frac_of_frame * width * height / math.pi)
+    return r_px * distance / f
+
+
+def workload_batch(n=2_000_000, resolutions=BATCH_RESOLUTIONS, with_targets=True):
+    """Mixed-resolution views of one clustered 2M-Gaussian scene with 20%
+    of the Gaussians packed into a ball covering ~5% of a 4K frame."""
+    scene = cluster_scene(n, index=3, packed_frac=0.2, packed_radius=packed_ball_radius())
+    _, rng, _ = streams(3)
+    cams = []
+    for w, h in resolutions:
+        az, el = rng.uniform(0.0, 360.0), rng.uniform(0.0, 60.0)
+        cams.append(look_at(orbit_eye(2.6, az, el), width=w, height=h))
+    targets = [target_image(c.width, c.height, 3, seed_offset=i + 1) for i, c in enumerate(cams)] \
+        if with_targets else None
+    return scene, cams, targets
 
 
 def rotating_offset(step: int, d: int):
