@@ -11,6 +11,12 @@ BF16-SH / d = 4 forms are measured beside it.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload (the oracle is the reference here).
+
+``--workload batch`` measures the batched form instead: 8 views per step of
+mixed resolution (2 x 1920x1080, 3 x 2560x1440, 3 x 3840x2160) around a
+2M-Gaussian scene with a heavy-tailed tile load, one launch per stage over
+all views, the step replayed from CUDA graphs, tile size and pixels per
+thread picked by the autotuner.
 """
 from __future__ import annotations
 
@@ -107,6 +113,8 @@ class ClockSampler:
 # Our arm
 # ---------------------------------------------------------------------------
 
+TILE = [16]  # tile side used by every dilation of the run (set from --tile)
+
 STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
 
 
@@ -197,7 +205,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
     for i in range(warmup):
         ox, oy = offsets[i]
-        timed.run(0, cam, R.Dilation(d, ox, oy), target_dev)
+        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0]), target_dev)
     torch.cuda.synchronize()
     step.counts.zero_()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -207,7 +215,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         start.record()
         for i in range(steps):
             ox, oy = offsets[warmup + i]
-            timed.run(i, cam, R.Dilation(d, ox, oy), target_dev, counts=True)
+            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0]), target_dev, counts=True)
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
@@ -314,7 +322,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
             issue_copy(i + 1)
         comp.wait_event(ready[b])
         ox, oy = scenes.rotating_offset(i, d)
-        loss = step(cam, R.Dilation(d, ox, oy), bufs[b])
+        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0]), bufs[b])
         free[b].record(comp)
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     end.record()
@@ -322,6 +330,82 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
     ms = start.elapsed_time(end)
     return dict(value=steps * 1000.0 / ms, unit=UNIT, h2d_bytes_per_step=int(target_np.nbytes),
                 d2h_bytes_per_step=4, ms_per_step=ms / steps)
+
+
+# ---------------------------------------------------------------------------
+# Batched views
+# ---------------------------------------------------------------------------
+
+def run_batch(args, device):
+    import torch
+    from paper_2412_13547_b300 import build_native, raster as R, scenes
+    from paper_2412_13547_b300.pipeline import GaussianParams, BatchTrainStep, autotune_batch
+
+    if not os.path.exists(R.LIB_PATH):
+        build_native.build()
+    scene, cams, targets = scenes.workload_batch(min(args.n, 2_000_000))
+    tg = [torch.tensor(t, device=device) for t in targets]
+    params = GaussianParams.from_arrays(scene.as_dict(), device)
+    d = args.d
+    (tile, ppt), table = autotune_batch(params, cams, tg, d=d, iters=2)
+    st = BatchTrainStep(params, cams, tg, d=d, tile=tile, pixels_per_thread=ppt)
+    # per-stage device times from one eager pass of every phase (events between the calls)
+    stage = {}
+    for ph in range(st.phases):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        st._project(st.table(ph))
+        ev[1].record()
+        t = st.table(ph)
+        for i, v in enumerate(t.views):
+            _, _, tx, ty = R.gs_grid(v.cam, v.dil)
+            R.gs_bin_sort(params.n, st.rects[i], st.tiles_touched[i], st.splats[i], tx, ty, st.workspace,
+                          st.capacity[i], st.sorted_ids[i], st.ranges[i], st.num_pairs[i:i + 1])
+        R.gs_tile_order_batch(t, st.order)
+        ev[2].record()
+        R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt)
+        R.gs_loss_l1_batch(t)
+        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.order, zero_grad2d=True, pixels_per_thread=ppt)
+        ev[3].record()
+        st.optimize(ph)
+        ev[4].record()
+        torch.cuda.synchronize()
+        for k, name in enumerate(("project_batch", "bin_sort_all_views", "blend_fwd_loss_bwd", "project_bwd_adam")):
+            stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1]) / st.phases
+    st.capture()
+    for _ in range(max(args.warmup, st.phases)):
+        st.step()
+    torch.cuda.synchronize()
+    steps = max(args.steps, st.phases)
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clocks:
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            st.step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    if st.overflowed():
+        raise RuntimeError("pair capacity exceeded during the batch run")
+    line = {
+        "metric": "batched fwd+bwd steps/sec (8 views per step)", "value": round(1000.0 / ms, 3),
+        "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "views_per_s": round(8000.0 / ms, 2),
+        "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": d,
+                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt,
+                   "resolutions": [[c.width, c.height] for c in cams], "n_gaussians": params.n,
+                   "graph": "one CUDA graph per offset phase, replayed", "l2": "inputs larger than L2"},
+        "autotune_ms": {f"tile{k[0]}_ppt{k[1]}": round(v, 3) for k, v in table.items()},
+        "stage_ms_eager": {k: round(v, 3) for k, v in stage.items()},
+        "pairs_per_view": st.num_pairs.tolist(),
+        "gpu_launches": st.launches_per_step() * steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -406,14 +490,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=3_000_000)
-    ap.add_argument("--workload", default="uhd", choices=["uhd", "hd"],
-                    help="uhd: 3840x2160, 3M Gaussians (the measured workload); hd: 1920x1080, 1M (profiling)")
+    ap.add_argument("--workload", default="uhd", choices=["uhd", "hd", "batch"],
+                    help="uhd: 3840x2160, 3M Gaussians (the measured workload); hd: 1920x1080, 1M (profiling); "
+                         "batch: 8 mixed-resolution views per step of a 2M-Gaussian scene")
+    ap.add_argument("--d", type=int, default=2, help="dilation of the batch workload")
     ap.add_argument("--oracle-tiles", type=int, default=16)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stages-json", default="")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
+    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile side of the lattice image")
     args = ap.parse_args()
+    TILE[0] = args.tile
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -425,6 +513,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if args.workload == "batch":
+        if world > 1:
+            raise SystemExit("--workload batch runs on one GPU")
+        return run_batch(args, device)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
@@ -438,13 +530,13 @@ def main():
     # pair capacity: the largest K over the forms measured, plus headroom (no host sync in the step)
     if args.workload != "uhd":
         args.no_cpu_baseline = True
-    w0, h0, tx0, ty0 = R.gs_grid(cam, R.Dilation(1, 0, 0))
+    w0, h0, tx0, ty0 = R.gs_grid(cam, R.Dilation(1, 0, 0, tile=TILE[0]))
     rast = Rasterizer(params.n, capacity=1 << 20, device=device, pixels_per_thread=args.ppt, max_grid=(tx0, ty0))
     kmax = 0
     for d in (1, 2, 4):
         for ox in range(d):
             for oy in range(d):
-                dil = R.Dilation(d, ox, oy)
+                dil = R.Dilation(d, ox, oy, tile=TILE[0])
                 rast.project(params, cam, dil)
                 rast.bin_checked(cam, dil)
                 kmax = max(kmax, rast.num_pairs())
@@ -452,8 +544,8 @@ def main():
 
     pk = peaks()
     clocks = ClockSampler(local)
-    head, _ = measure_variant(args, params, cam, target_dev, 2, torch.float32, args.steps, args.warmup, device,
-                              rast, snapshot, clocks=clocks)
+    head, head_step = measure_variant(args, params, cam, target_dev, 2, torch.float32, args.steps, args.warmup,
+                                      device, rast, snapshot, clocks=clocks)
     variants = {"dilated_d2_fp32": {k: v for k, v in head.items() if k != "stage_ms"}}
     stage_tables = {"dilated_d2_fp32": head["stage_ms"]}
     if not args.no_variants:
@@ -510,15 +602,14 @@ def main():
             cpu = {"value": None, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                    "sample": f"failed: {e}"}
 
-    n_tiles_d2 = R.gs_grid(cam, R.Dilation(2, 0, 0))
-    launches = 1 + (1 + 12 + 3 + 1 + 3 * 2 + 1) + 5
+    launches = head_step.launches_per_step()
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": ("uhd-3840x2160-3M-gaussians-sh3" if args.workload == "uhd" else
                                 "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
-                   "n_gaussians": params.n, "resolution": [cam.width, cam.height], "d": 2, "tile": 16,
+                   "n_gaussians": params.n, "resolution": [cam.width, cam.height], "d": 2, "tile": TILE[0],
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 "
                    "(params 708 MB, pair buffers > 1 GB)"},
         "blends_per_s": round(head["blends_evaluated_per_s"], 1),

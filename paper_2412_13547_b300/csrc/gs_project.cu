@@ -218,7 +218,7 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
 // Projection of every Gaussian into every view of the batch. The warp stages
 // its 32 parameter rows once and loops over the views, so the parameters are
 // read once per batch whatever the number of views.
-template <int DEG, int DT>
+template <int DEG, int DT, bool MULTI>
 __global__ void __launch_bounds__(kThreads)
 k_project(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
           const float4* __restrict__ quats, const float* __restrict__ logits, const void* __restrict__ sh,
@@ -248,8 +248,9 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
     read_sh<DEG, DT>(s_sh, sh, g, lane, c);
     const float4 q = quats[g];
     const float logit = logits[g];
-    for (int vi = 0; vi < b.nviews; ++vi) {
-        const ViewDev& V = b.v[vi];
+    const int nv = MULTI ? b.nviews : 1;
+    for (int vi = 0; vi < nv; ++vi) {
+        const ViewDev& V = b.v[MULTI ? vi : 0];
         Proj P;
         project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
         float4* out = V.splats + 3 * (int64_t)g;
@@ -722,7 +723,7 @@ int32_t launch_project(int n, const float* means, const float* log_scales, const
 {
     using L = ShLayout<DEG, DT>;
     size_t smem = sizeof(uint32_t) * L::WARP_WORDS * kWarps;
-    auto kern = k_project<DEG, DT>;
+    auto kern = b.nviews > 1 ? k_project<DEG, DT, true> : k_project<DEG, DT, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
     kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,

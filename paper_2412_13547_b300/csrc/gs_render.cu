@@ -378,23 +378,24 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 // One CTA per tile of the batch; with an order, CTA i takes tile order[i]
 // (longest lists first, so the block scheduler dispatches greedily
 // longest-first across all views).
-template <int TILE, int PPT>
+// MULTI false: one view, whose fields the kernel reads at fixed offsets.
+template <int TILE, int PPT, bool MULTI>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
              unsigned long long* __restrict__ counts)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
-    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
     render_fwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img, V.t_final, V.last,
                                counts);
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool MULTI>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
-    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
     render_bwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.t_final, V.last, V.dl,
                                reinterpret_cast<float*>(V.grad2d));
 }
@@ -512,13 +513,15 @@ bool check_render_view(int32_t n, const ViewDev& v)
 template <int TILE, int PPT>
 void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, cudaStream_t st)
 {
-    k_render_fwd<TILE, PPT><<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
+    auto kern = b.nviews > 1 ? k_render_fwd<TILE, PPT, true> : k_render_fwd<TILE, PPT, false>;
+    kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
 }
 
 template <int TILE, int PPT>
 void launch_bwd(const Batch& b, const uint32_t* order, float3 bg, cudaStream_t st)
 {
-    k_render_bwd<TILE, PPT><<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg);
+    auto kern = b.nviews > 1 ? k_render_bwd<TILE, PPT, true> : k_render_bwd<TILE, PPT, false>;
+    kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg);
 }
 
 // The instantiated (tile, pixels per thread) pairs.
