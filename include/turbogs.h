@@ -396,6 +396,78 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
                                   float* pos_acc, float* col_acc, int32_t* count,
                                   float* const* grads_out, gs_stream_t stream);
 
+/* ===========================================================================
+ * Densification and pruning under a Gaussian budget (Sec. 3.2, Sec. 3.3).
+ * Run once per densification interval. The host reads the device counts the
+ * selection calls write (num_selected, num_keep) to size the next arrays.
+ * =========================================================================== */
+
+/* Bytes of the workspace gs_densify_select and gs_prune_select need for n
+ * Gaussians (device memory, caller-owned, any alignment). */
+size_t gs_densify_workspace_size(int32_t n);
+
+/* gs_densify_select -- position-appearance densification (Sec. 3.3) with the
+ * budget cut. For every i < n with count[i] > 0, in FP32 with IEEE division:
+ *   sp = pos_acc[i] / count[i];  sc = col_acc[i] / count[i]
+ *   candidate  <=>  sp > tau_pos  or  (color_branch != 0 and sc > tau_color)
+ *   score = max(sp / tau_pos, color_branch ? sc / tau_color : 0)
+ * (the paper takes tau_color = 0.01 tau_pos and activates the colour branch
+ * with probability 0.2; the caller draws it). When there are more than
+ * max_new candidates, the max_new with the highest score are kept, equal
+ * scores in index order. selected (device, >= min(n, max_new) entries)
+ * receives the kept indices in ascending order, *num_selected (device) their
+ * count. pos_acc, col_acc, count: device, n entries (gs_densify_stats). */
+int32_t gs_densify_select(int32_t n, const float* pos_acc, const float* col_acc, const int32_t* count,
+                          float tau_pos, float tau_color, int32_t color_branch, int32_t max_new,
+                          void* workspace, size_t workspace_bytes, int32_t* selected,
+                          int32_t* num_selected, gs_stream_t stream);
+
+/* gs_prune_select -- indices (ascending, device, n entries) of the Gaussians
+ * kept: opacity_logits[i] >= logit_min (the opacity sigmoid(logit) is at
+ * least sigmoid(logit_min)) and, when log_scales (n x 3, nullable) is given,
+ * max_k log_scales[i][k] <= log_scale_max. *num_keep (device): their count. */
+int32_t gs_prune_select(int32_t n, const float* opacity_logits, float logit_min,
+                        const float* log_scales, float log_scale_max, void* workspace,
+                        size_t workspace_bytes, int32_t* keep, int32_t* num_keep,
+                        gs_stream_t stream);
+
+/* A row tensor: one row of row_bytes (a multiple of 4) per Gaussian, from
+ * src to dst (distinct device buffers). role tells the growth what to do with
+ * it; the gather copies every role but GS_ROW_ZERO. */
+#define GS_MAX_ROW_TENSORS 24
+#define GS_ROW_COPY 0        /* copied (opacity, SH, their BF16/FP16 copy, ...)   */
+#define GS_ROW_MEANS 1       /* 3 floats: moved for split children                */
+#define GS_ROW_LOG_SCALES 2  /* 3 floats: reduced by log(1.6) for split children  */
+#define GS_ROW_QUATS 3       /* 4 floats (w,x,y,z), 16-byte aligned: copied       */
+#define GS_ROW_STATE 4       /* optimizer moments: zero for new rows and split parents */
+#define GS_ROW_ZERO 5        /* zeroed in every row (densification statistics)    */
+typedef struct {
+    const void* src;
+    void* dst;
+    int32_t row_bytes;
+    int32_t role;
+} GsRowTensor;
+
+/* gs_gather_rows -- dst row i = src row index[i] for i < n_out (index: device
+ * int32, e.g. gs_prune_select's keep list); GS_ROW_ZERO tensors are zeroed.
+ * The tensor table is read on the host. */
+int32_t gs_gather_rows(int32_t n_out, const int32_t* index, const GsRowTensor* tensors,
+                       int32_t count, gs_stream_t stream);
+
+/* gs_densify_grow -- clone / split of the m selected Gaussians (the 3DGS
+ * baseline Sec. 3.3 follows), from n_old rows in src to n_old + m rows in dst:
+ * rows < n_old are copied, row n_old + j is a copy of row selected[j]. A
+ * selected Gaussian whose largest log-scale exceeds log_split_scale is split:
+ * its two children sit at mean + R(q) diag(exp(log_scales)) z_k with the
+ * standard normals z_k = noise[6 j + 3 k .. +3] (device, m x 2 x 3, drawn by
+ * the caller), their log-scales reduced by log(1.6); child 0 replaces the
+ * parent, child 1 is row n_old + j. GS_ROW_STATE rows of new rows and of split
+ * parents are zero; GS_ROW_ZERO tensors are zero. Needs exactly one MEANS, one
+ * LOG_SCALES and one QUATS tensor. selected: device, ascending or not. */
+int32_t gs_densify_grow(int32_t n_old, int32_t m, const int32_t* selected, const float* noise,
+                        float log_split_scale, const GsRowTensor* tensors, int32_t count,
+                        gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -28,7 +29,11 @@ SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_
            "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
            "gs_tile_order_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
-           "gs_project_bwd_adam_batch")
+           "gs_project_bwd_adam_batch", "gs_densify_workspace_size", "gs_densify_select", "gs_prune_select",
+           "gs_gather_rows", "gs_densify_grow")
+
+GS_MAX_ROW_TENSORS = 24
+GS_ROW_COPY, GS_ROW_MEANS, GS_ROW_LOG_SCALES, GS_ROW_QUATS, GS_ROW_STATE, GS_ROW_ZERO = range(6)
 
 
 class GsError(RuntimeError):
@@ -62,6 +67,11 @@ class GsAdamParams(ctypes.Structure):
 
 _VIEW_BUFFERS = ("splats", "radii", "rects", "tiles_touched", "sorted_ids", "ranges", "img", "t_final", "last",
                  "target", "dl_dimg", "grad2d", "loss")
+
+
+class GsRowTensor(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("row_bytes", ctypes.c_int32),
+                ("role", ctypes.c_int32)]
 
 
 class GsView(ctypes.Structure):
@@ -178,8 +188,15 @@ def load():
     lib.gs_render_bwd_batch.argtypes = [i32, view_p, i32, P, P, i32, i32, P]
     lib.gs_project_bwd_adam_batch.argtypes = [i32, i32, i32, P, view_p, i32, ctypes.POINTER(GsAdamParams), P, P, P,
                                               P, P]
+    lib.gs_densify_workspace_size.argtypes = [i32]
+    lib.gs_densify_workspace_size.restype = ctypes.c_size_t
+    lib.gs_densify_select.argtypes = [i32, P, P, P, f32, f32, i32, i32, P, ctypes.c_size_t, P, P, P]
+    lib.gs_prune_select.argtypes = [i32, P, f32, P, f32, P, ctypes.c_size_t, P, P, P]
+    rows_p = ctypes.POINTER(GsRowTensor)
+    lib.gs_gather_rows.argtypes = [i32, P, rows_p, i32, P]
+    lib.gs_densify_grow.argtypes = [i32, i32, P, P, f32, rows_p, i32, P]
     for name in SYMBOLS:
-        if name not in ("gs_last_error", "gs_bin_sort_workspace_size"):
+        if name not in ("gs_last_error", "gs_bin_sort_workspace_size", "gs_densify_workspace_size"):
             getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -413,3 +430,49 @@ def gs_adam(entries, beta1, beta2, eps, step, row_mask=None, stream=None):
         arr[i].lr = float(e["lr"])
     _check(load().gs_adam(arr, len(entries), float(beta1), float(beta2), float(eps), int(step), _ptr(row_mask),
                           _stream(stream)), "gs_adam")
+
+
+# -- densification and pruning ----------------------------------------------
+
+def gs_densify_workspace_size(n: int) -> int:
+    return int(load().gs_densify_workspace_size(int(n)))
+
+
+def gs_densify_select(n, pos_acc, col_acc, count, tau_pos, tau_color, color_branch, max_new, workspace, selected,
+                      num_selected, stream=None):
+    _check(load().gs_densify_select(int(n), _ptr(pos_acc), _ptr(col_acc), _ptr(count), float(tau_pos),
+                                    float(tau_color), int(bool(color_branch)), int(max_new), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _ptr(selected),
+                                    _ptr(num_selected), _stream(stream)), "gs_densify_select")
+
+
+def gs_prune_select(n, opacity_logits, logit_min, log_scales, log_scale_max, workspace, keep, num_keep,
+                    stream=None):
+    _check(load().gs_prune_select(int(n), _ptr(opacity_logits), float(logit_min), _ptr(log_scales),
+                                  float(log_scale_max), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                  _ptr(keep), _ptr(num_keep), _stream(stream)), "gs_prune_select")
+
+
+def _rows(entries):
+    """entries: (src tensor or None, dst tensor, role); rows = first dimension."""
+    arr = (GsRowTensor * len(entries))()
+    for i, (src, dst, role) in enumerate(entries):
+        rb = int(np.prod(dst.shape[1:], dtype=np.int64)) * dst.element_size()
+        if src is not None and (src.dtype != dst.dtype or src.shape[1:] != dst.shape[1:]):
+            raise ValueError(f"row tensor {i}: src and dst rows differ")
+        arr[i].src = None if src is None else _ptr(src).value
+        arr[i].dst = _ptr(dst).value
+        arr[i].row_bytes = int(rb)
+        arr[i].role = int(role)
+    return arr
+
+
+def gs_gather_rows(n_out, index, entries, stream=None):
+    arr = _rows(entries)
+    _check(load().gs_gather_rows(int(n_out), _ptr(index), arr, len(entries), _stream(stream)), "gs_gather_rows")
+
+
+def gs_densify_grow(n_old, m, selected, noise, log_split_scale, entries, stream=None):
+    arr = _rows(entries)
+    _check(load().gs_densify_grow(int(n_old), int(m), _ptr(selected), _ptr(noise), float(log_split_scale), arr,
+                                  len(entries), _stream(stream)), "gs_densify_grow")
