@@ -114,8 +114,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 TILE = [16]  # tile side used by every dilation of the run (set from --tile)
+SHIFT = [0]  # binning tiles are TILE << SHIFT (set from --bin-shift)
 
-STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
+STAGES = ("project", "bin_sort", "render_fwd", "loss", "zero_grad2d", "render_bwd", "project_bwd_adam")
+# stages that are one kernel launch each (the roofline's candidates for the dominant kernel)
+KERNEL_OF_STAGE = {"project": "k_project", "render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd",
+                   "project_bwd_adam": "k_project_bwd_adam"}
 
 
 def setup(args, device):
@@ -168,8 +172,11 @@ class TimedStep:
         mark("loss", 0)
         R.gs_loss_l1(cam, dil, img, target, dl, st.loss)
         mark("loss", 1)
+        mark("zero_grad2d", 0)
+        rast.grad2d.zero_()
+        mark("zero_grad2d", 1)
         mark("render_bwd", 0)
-        rast.render_bwd(cam, dil, st.bg, t_final, last, dl)
+        rast.render_bwd(cam, dil, st.bg, t_final, last, dl, zero_grad2d=False)
         mark("render_bwd", 1)
         st.step_count += 1
         mark("project_bwd_adam", 0)
@@ -205,7 +212,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
     for i in range(warmup):
         ox, oy = offsets[i]
-        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0]), target_dev)
+        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), target_dev)
     torch.cuda.synchronize()
     step.counts.zero_()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -215,7 +222,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         start.record()
         for i in range(steps):
             ox, oy = offsets[warmup + i]
-            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0]), target_dev, counts=True)
+            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), target_dev, counts=True)
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
@@ -260,6 +267,8 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     # blend forward: ~20 FP32 flops per evaluated (pixel, entry)
     rows["render_fwd"] = ("alu", 20.0 * res["evaluated_per_step"])
     rows["loss"] = ("hbm", 36.0 * step_pixels)
+    # zeroing of the 2D-gradient buffer the backward blend accumulates into
+    rows["zero_grad2d"] = ("hbm", 48.0 * n)
     # blend backward: ~45 FP32 flops per replayed (pixel, entry)
     rows["render_bwd"] = ("alu", 45.0 * res["replayed_per_step"])
     # projection backward + densification statistics + Adam, fused: parameters, moments and the
@@ -322,7 +331,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
             issue_copy(i + 1)
         comp.wait_event(ready[b])
         ox, oy = scenes.rotating_offset(i, d)
-        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0]), bufs[b])
+        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), bufs[b])
         free[b].record(comp)
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     end.record()
@@ -347,8 +356,8 @@ def run_batch(args, device):
     tg = [torch.tensor(t, device=device) for t in targets]
     params = GaussianParams.from_arrays(scene.as_dict(), device)
     d = args.d
-    (tile, ppt), table = autotune_batch(params, cams, tg, d=d, iters=2)
-    st = BatchTrainStep(params, cams, tg, d=d, tile=tile, pixels_per_thread=ppt)
+    (tile, ppt, shift), table = autotune_batch(params, cams, tg, d=d, iters=2)
+    st = BatchTrainStep(params, cams, tg, d=d, tile=tile, pixels_per_thread=ppt, bin_shift=shift)
     # per-stage device times from one eager pass of every phase (events between the calls)
     stage = {}
     for ph in range(st.phases):
@@ -358,7 +367,7 @@ def run_batch(args, device):
         ev[1].record()
         t = st.table(ph)
         for i, v in enumerate(t.views):
-            _, _, tx, ty = R.gs_grid(v.cam, v.dil)
+            tx, ty = R.gs_bin_grid(v.cam, v.dil)
             R.gs_bin_sort(params.n, st.rects[i], st.tiles_touched[i], st.splats[i], tx, ty, st.workspace,
                           st.capacity[i], st.sorted_ids[i], st.ranges[i], st.num_pairs[i:i + 1])
         R.gs_tile_order_batch(t, st.order)
@@ -395,10 +404,10 @@ def run_batch(args, device):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "views_per_s": round(8000.0 / ms, 2),
         "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": d,
-                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt,
+                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt, "bin_tile": tile << shift,
                    "resolutions": [[c.width, c.height] for c in cams], "n_gaussians": params.n,
                    "graph": "one CUDA graph per offset phase, replayed", "l2": "inputs larger than L2"},
-        "autotune_ms": {f"tile{k[0]}_ppt{k[1]}": round(v, 3) for k, v in table.items()},
+        "autotune_ms": {f"tile{k[0]}_ppt{k[1]}_bin{k[0] << k[2]}": round(v, 3) for k, v in table.items()},
         "stage_ms_eager": {k: round(v, 3) for k, v in stage.items()},
         "pairs_per_view": st.num_pairs.tolist(),
         "gpu_launches": st.launches_per_step() * steps,
@@ -500,8 +509,11 @@ def main():
     ap.add_argument("--stages-json", default="")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile side of the lattice image")
+    ap.add_argument("--bin-shift", type=int, default=1, choices=[0, 1, 2],
+                    help="bin with tiles of tile << bin-shift, blend per tile")
     args = ap.parse_args()
     TILE[0] = args.tile
+    SHIFT[0] = args.bin_shift
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -530,13 +542,13 @@ def main():
     # pair capacity: the largest K over the forms measured, plus headroom (no host sync in the step)
     if args.workload != "uhd":
         args.no_cpu_baseline = True
-    w0, h0, tx0, ty0 = R.gs_grid(cam, R.Dilation(1, 0, 0, tile=TILE[0]))
-    rast = Rasterizer(params.n, capacity=1 << 20, device=device, pixels_per_thread=args.ppt, max_grid=(tx0, ty0))
+    rast = Rasterizer(params.n, capacity=1 << 20, device=device, pixels_per_thread=args.ppt,
+                      max_grid=R.gs_bin_grid(cam, R.Dilation(1, 0, 0, tile=TILE[0], bin_shift=SHIFT[0])))
     kmax = 0
     for d in (1, 2, 4):
         for ox in range(d):
             for oy in range(d):
-                dil = R.Dilation(d, ox, oy, tile=TILE[0])
+                dil = R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0])
                 rast.project(params, cam, dil)
                 rast.bin_checked(cam, dil)
                 kmax = max(kmax, rast.num_pairs())
@@ -570,19 +582,20 @@ def main():
     sh_bytes = 48 * 4
     roof = stage_roofline(head, params.n, sh_bytes, pk, R.gs_grid(cam, R.Dilation(2, 1, 0))[0] *
                           R.gs_grid(cam, R.Dilation(2, 1, 0))[1])
-    dom = max(roof, key=lambda s: roof[s]["ms"])
+    dom = max(KERNEL_OF_STAGE, key=lambda s: roof[s]["ms"])
     dr = roof[dom]
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
             tj = json.load(open(tpath))
-            if tj.get("kernel_stage") == dom and tj.get("source_hash") == _source_hash():
-                traffic = tj.get("bytes_per_launch")
+            ent = tj.get("kernels", {}).get(KERNEL_OF_STAGE[dom])
+            if ent and tj.get("source_hash") == _source_hash() and tj.get("workload") == args.workload:
+                traffic = ent.get("bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": dr["bound"], "achieved": round(dr["achieved"], 3), "peak": dr["peak"], "unit": dr["unit"],
-                "frac": round(dr["frac"], 4), "traffic": traffic, "kernel": dom,
+                "frac": round(dr["frac"], 4), "traffic": traffic, "kernel": KERNEL_OF_STAGE[dom],
                 "peak_source": pk["src"] if dr["bound"] == "hbm" else "derived: 148 SM x 128 FP32 lanes x 2 x "
                 f"{pk['sm_max_mhz']:.0f} MHz",
                 "stages": {s: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
@@ -610,6 +623,7 @@ def main():
         "config": {"workload": ("uhd-3840x2160-3M-gaussians-sh3" if args.workload == "uhd" else
                                 "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
                    "n_gaussians": params.n, "resolution": [cam.width, cam.height], "d": 2, "tile": TILE[0],
+                   "bin_tile": TILE[0] << SHIFT[0],
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 "
                    "(params 708 MB, pair buffers > 1 GB)"},
         "blends_per_s": round(head["blends_evaluated_per_s"], 1),

@@ -62,19 +62,26 @@ typedef struct {
  * center_mode 0 bins a Gaussian around the downsampled centre (p - o)/d, the
  * lattice the offset renders; 1 uses (p - (d-1)/2)/d, Eq. 3 combined with the
  * pixel map of Eq. 5. Eq. 4: the downsampled radius is r/d. tile is the tile
- * edge in downsampled pixels (Sec. 3.1 fixes 16; 8 and 32 are accepted). */
+ * edge in downsampled pixels (Sec. 3.1 fixes 16; 8 and 32 are accepted): the
+ * unit of the tile-Gaussian lists the blend walks.
+ * bin_shift (0, 1 or 2) coarsens only the binning: pairs are formed with tiles
+ * of tile << bin_shift pixels (fewer pairs to bin), and each blend tile keeps
+ * from its binning tile's list exactly the entries of its own list, in order.
+ * Images, transmittances and gradients do not depend on it; only the list
+ * positions stored in `last` do. */
 typedef struct {
-    int32_t d, ox, oy, center_mode, tile;
+    int32_t d, ox, oy, center_mode, tile, bin_shift;
 } GsDilation;
 
 /* Width of the per-Gaussian records below, in floats. */
-#define GS_SPLAT_FLOATS 12
+#define GS_SPLAT_FLOATS 16
 #define GS_GRAD2D_FLOATS 12
 
-/* Splat record written by gs_project (48 bytes per Gaussian):
+/* Splat record written by gs_project (64 bytes per Gaussian):
  *   [0] x_hi  [1] y_hi  [2] conic A  [3] conic B
  *   [4] conic C  [5] opacity  [6] r  [7] g
  *   [8] b  [9] depth t_z  [10] x_lo  [11] y_lo
+ *   [12..15] int32 x0, y0, x1, y1: inclusive rectangle of blend tiles touched
  * The hr image-plane centre is (x_hi + x_lo, y_hi + y_lo), kept as an unevaluated
  * float-float sum so that pixel offsets at 4K stay accurate. The conic is the
  * inverse 2D covariance: G = exp(-(A dx^2 + C dy^2)/2 - B dx dy) (Sec. 3, Eq. 1).
@@ -88,9 +95,14 @@ typedef struct {
 int32_t gs_version(void);
 const char* gs_last_error(void);
 
-/* Size of the downsampled image and of its tile grid (host arithmetic only). */
+/* Size of the downsampled image and of its blend tile grid (host arithmetic
+ * only; the grid of the blend launches and of the tile orders). */
 int32_t gs_grid(const GsCamera* cam, const GsDilation* dil,
                 int32_t* w_ds, int32_t* h_ds, int32_t* tiles_x, int32_t* tiles_y);
+
+/* The binning tile grid: ceil(tiles_x / 2^bin_shift) x ceil(tiles_y /
+ * 2^bin_shift) (the grid of rects, gs_bin_sort and ranges). */
+int32_t gs_bin_grid(const GsCamera* cam, const GsDilation* dil, int32_t* bin_tiles_x, int32_t* bin_tiles_y);
 
 /* ---------------------------------------------------------------------------
  * gs_project -- Sec. 3 (Sigma = R S S^T R^T, opacity, SH colour) and Sec. 3.1
@@ -103,9 +115,12 @@ int32_t gs_grid(const GsCamera* cam, const GsDilation* dil,
  *   K = (sh_degree+1)^2, sh_degree <= 3, of type sh_dtype): device inputs.
  *   Colour = max(0, sum_k Y_k(dir) sh_k + 0.5), dir = unit(mean - camera centre),
  *   real SH with Condon-Shortley phase, index l*l + l + m.
- * Outputs (device): splats (n x 12, layout above), radii (n, 0 = culled),
- *   rects (n x 4: x0, y0, x1, y1 inclusive tile indices; culled: 0, 0, -1, -1),
- *   tiles_touched (n).
+ * Outputs (device): splats (n x 16, layout above), radii (n, 0 = culled),
+ *   rects (n x 4: x0, y0, x1, y1 inclusive binning tile indices, the blend
+ *   tile rectangle shifted right by bin_shift; culled: 0, 0, -1, -1),
+ *   tiles_touched (n: binning tiles in the rect; > 0 = visible).
+ *   A Gaussian is culled (radius 0, empty rect) when its blend tile rectangle
+ *   is empty, whatever bin_shift.
  * Errors: GS_ERR_ARG for n < 0, a null pointer with n > 0, sh_degree outside
  *   0..3, a bad dtype, d < 1 or d > 64, offsets outside [0, d), tile not in
  *   {8, 16, 32}, or a non-positive image size or focal length. */
@@ -122,9 +137,9 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * every tile of every Gaussian's rect, the pair (key = tile_id << 32 |
  * float32 bits of the depth, value = Gaussian index), sorted ascending by
  * (key, value), and per-tile [start, end) ranges into the sorted values.
- * Inputs (device): rects, tiles_touched (from gs_project for the same grid),
- *   splats (depth = [9]). Rects outside the grid are not trusted: the
- *   counting path ignores them and the sort path writes no range for them.
+ * Inputs (device): rects, tiles_touched (from gs_project for the same
+ *   dilation), splats (depth = [9]); tiles_x, tiles_y: the binning grid
+ *   (gs_bin_grid). Rects outside the grid are ignored.
  * Outputs (device): sorted_ids (capacity entries; the first num_pairs hold the
  *   Gaussian ids tile by tile, front to back), ranges (tiles_x*tiles_y x 2,
  *   uint32 start/end; (0, 0) for a tile no Gaussian touches), num_pairs (one
@@ -137,12 +152,11 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  *   tiles_x, tiles_y) bytes, 256-byte aligned; its contents need no init. The
  *   size also covers every smaller grid (tx <= tiles_x, ty <= tiles_y), so one
  *   workspace serves all dilations of an image.
- * Method: when the grid's (tiles_y+1) x (tiles_x+1) difference array fits in
- *   shared memory (<= 51,200 cells; 3840x2160 at d = 1 with 16 px tiles has
- *   32,776) the pairs are never sorted: per-chunk tile counts of the
- *   depth-sorted Gaussians give every pair its final slot (counting scatter).
- *   Larger grids emit the pairs and radix-sort their tile bits. Both give the
- *   same result bit for bit.
+ * Method: the pairs are never materialised with keys nor sorted. The
+ *   Gaussians are radix-sorted by (depth bits, id); a two-level counting
+ *   scatter then writes every id straight into its slot: first into per-row
+ *   lists (one entry per tile row of the rect), then each row list into its
+ *   tiles, both levels stable. tiles_x, tiles_y <= 4096.
  * Errors: GS_ERR_ARG for bad sizes, null pointers or a short workspace. */
 size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, int32_t tiles_y);
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
@@ -181,7 +195,8 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
  * by descending list length (end - start of ranges), bucketed 8 buckets per
  * power of two. Started longest-first, the tiles of uneven load finish close
  * together instead of leaving a tail. Inputs (device): ranges (num_tiles x 2).
- * Output (device): order (num_tiles). */
+ * Output (device): order (num_tiles). For a dilation with bin_shift > 0 (blend
+ * tiles differ from binning tiles) use gs_tile_order_batch. */
 int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -194,8 +209,12 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
  * C += T * bg.
  * Inputs (device): splats, sorted_ids, ranges (from gs_bin_sort). bg: host
  *   float[3].
+ * Each blend tile walks its binning tile's list (the same list when
+ *   bin_shift is 0) and keeps the entries whose splat record rectangle
+ *   ([12..15]) contains it: its own list, in depth order.
  * Outputs (device): img (h_ds x w_ds x 3), t_final (h_ds x w_ds), last
- *   (h_ds x w_ds: list position + 1 of the last blended entry, 0 if none),
+ *   (h_ds x w_ds: position + 1, in the binning tile's list, of the last
+ *   blended entry, 0 if none),
  *   counts (nullable, 2 x uint64 accumulated with +=: list entries evaluated
  *   and entries blended; the caller zeroes it).
  * pixels_per_thread: launch shape, not semantics -- each thread of the
@@ -203,9 +222,9 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
  *   for tile 8, 1, 2 or 4 for tile 16, 2 or 4 for tile 32 (whole warps, at
  *   most 512 threads; others give GS_ERR_ARG). Results are identical for
  *   every value.
- * tile_order (nullable, device, tiles_x*tiles_y entries): the tiles in the
- *   order their CTAs should start, e.g. from gs_tile_order. Scheduling only:
- *   the results do not depend on it. */
+ * tile_order (nullable, device, tiles_x*tiles_y entries): the blend tiles in
+ *   the order their CTAs should start, e.g. from gs_tile_order_batch.
+ *   Scheduling only: the results do not depend on it. */
 int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids,
                       const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
                       const float* bg, float* img, float* t_final, uint32_t* last,
@@ -347,12 +366,12 @@ int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float b
 typedef struct {
     GsCamera cam;
     GsDilation dil;
-    float* splats;             /* n x 12 (gs_project)                         */
+    float* splats;             /* n x 16 (gs_project)                         */
     int32_t* radii;            /* n                                            */
     int32_t* rects;            /* n x 4                                        */
     int32_t* tiles_touched;    /* n                                            */
     uint32_t* sorted_ids;      /* from gs_bin_sort of this view                */
-    uint32_t* ranges;          /* tiles x 2                                    */
+    uint32_t* ranges;          /* binning tiles x 2                            */
     float* img;                /* h_ds x w_ds x 3                              */
     float* t_final;            /* h_ds x w_ds                                  */
     uint32_t* last;            /* h_ds x w_ds                                  */
@@ -368,9 +387,10 @@ int32_t gs_project_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype,
                          const float* opacity_logits, const void* sh,
                          const GsView* views, int32_t nviews, gs_stream_t stream);
 
-/* gs_tile_order over the tiles of all views, numbered view by view
+/* gs_tile_order over the blend tiles of all views, numbered view by view
  * (view v's tiles follow those of views 0..v-1): order gets sum_v tiles_v ids,
- * longest list first. This is the work queue of the batched blend launches. */
+ * longest (binning tile) list first. This is the work queue of the batched
+ * blend launches. */
 int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream);
 
 /* gs_render_fwd / gs_loss_l1 / gs_render_bwd for every view in one launch each;

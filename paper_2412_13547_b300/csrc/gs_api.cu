@@ -66,11 +66,19 @@ bool make_dil(const GsCamera* cam, const GsDilation* in, gs::Dil* out)
         set_error("dilation: offset outside the image");
         return false;
     }
+    if (in->bin_shift < 0 || in->bin_shift > 2) {
+        set_error("dilation: bin_shift must be 0, 1 or 2");
+        return false;
+    }
     out->d = in->d; out->ox = in->ox; out->oy = in->oy; out->mode = in->center_mode; out->tile = in->tile;
     out->w_ds = (cam->width - in->ox + in->d - 1) / in->d;
     out->h_ds = (cam->height - in->oy + in->d - 1) / in->d;
     out->tiles_x = (out->w_ds + in->tile - 1) / in->tile;
     out->tiles_y = (out->h_ds + in->tile - 1) / in->tile;
+    out->shift = in->bin_shift;
+    const int step = 1 << in->bin_shift;
+    out->bin_tiles_x = (out->tiles_x + step - 1) / step;
+    out->bin_tiles_y = (out->tiles_y + step - 1) / step;
     return true;
 }
 
@@ -127,6 +135,15 @@ int32_t gs_grid(const GsCamera* cam, const GsDilation* dil, int32_t* w_ds, int32
     if (h_ds) *h_ds = d.h_ds;
     if (tiles_x) *tiles_x = d.tiles_x;
     if (tiles_y) *tiles_y = d.tiles_y;
+    return GS_OK;
+}
+
+int32_t gs_bin_grid(const GsCamera* cam, const GsDilation* dil, int32_t* bin_tiles_x, int32_t* bin_tiles_y)
+{
+    gs::Dil d;
+    if (!gs_host::make_dil(cam, dil, &d)) return GS_ERR_ARG;
+    if (bin_tiles_x) *bin_tiles_x = d.bin_tiles_x;
+    if (bin_tiles_y) *bin_tiles_y = d.bin_tiles_y;
     return GS_OK;
 }
 

@@ -272,7 +272,7 @@ __global__ void k_depth_keys(int n, const float4* __restrict__ splats, const int
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
-    float depth = splats[3 * (int64_t)g + 2].y;
+    float depth = splats[4 * (int64_t)g + 2].y;
     // depth > z_near > 0 for visible Gaussians: the float bits order like the value
     keys[g] = tiles_touched[g] > 0 ? __float_as_uint(depth) : 0xffffffffu;
     ids[g] = (uint32_t)g;

@@ -31,10 +31,21 @@ struct Cam {
     float ccx, ccy, ccz;  // camera centre in world space, -R^T T
 };
 
+// Downsampled grid of a dilation. The blend works on tiles of `tile` pixels
+// (tiles_x x tiles_y); the binning on tiles of tile << shift (bin_tiles_x x
+// bin_tiles_y), whose lists each blend tile filters down to its own.
 struct Dil {
     int d, ox, oy, mode, tile;
     int w_ds, h_ds, tiles_x, tiles_y;
+    int shift, bin_tiles_x, bin_tiles_y;
 };
+
+// Binning tile of a blend tile.
+__device__ __forceinline__ int bin_tile_of(const Dil& dil, int tile)
+{
+    const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
+    return (ty >> dil.shift) * dil.bin_tiles_x + (tx >> dil.shift);
+}
 
 // One view of a batch, as the kernels see it.
 struct ViewDev {

@@ -99,7 +99,8 @@ struct Proj {
     float dir[3], inv_vlen;
     float rgb_raw[3];
     float opacity;
-    int4 rect;
+    int4 rect;   // binning tiles
+    int4 frect;  // blend tiles
     int tiles;
 };
 
@@ -196,8 +197,10 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     x1 = min(x1, dil.tiles_x - 1);
     y1 = min(y1, dil.tiles_y - 1);
     if (P.radius <= 0 || x0 > x1 || y0 > y1) return;
-    P.rect = make_int4(x0, y0, x1, y1);
-    P.tiles = (x1 - x0 + 1) * (y1 - y0 + 1);
+    P.frect = make_int4(x0, y0, x1, y1);
+    // binning tiles: floor(v / (tile 2^s)) = floor(v / tile) >> s for the clipped bounds
+    P.rect = make_int4(x0 >> dil.shift, y0 >> dil.shift, x1 >> dil.shift, y1 >> dil.shift);
+    P.tiles = (P.rect.z - P.rect.x + 1) * (P.rect.w - P.rect.y + 1);
     P.culled = false;
 
     // view-dependent colour
@@ -253,11 +256,12 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
         const ViewDev& V = b.v[MULTI ? vi : 0];
         Proj P;
         project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
-        float4* out = V.splats + 3 * (int64_t)g;
+        float4* out = V.splats + 4 * (int64_t)g;
         if (P.culled) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
+            out[3] = make_float4(0.f, 0.f, __int_as_float(-1), __int_as_float(-1));
             V.radii[g] = 0;
             V.rects[g] = make_int4(0, 0, -1, -1);
             V.tiles[g] = 0;
@@ -266,6 +270,8 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
         out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
         out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
         out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
+        out[3] = make_float4(__int_as_float(P.frect.x), __int_as_float(P.frect.y), __int_as_float(P.frect.z),
+                             __int_as_float(P.frect.w));
         V.radii[g] = P.radius;
         V.rects[g] = P.rect;
         V.tiles[g] = P.tiles;

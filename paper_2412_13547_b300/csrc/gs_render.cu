@@ -13,9 +13,9 @@ namespace {
 __device__ __forceinline__ void load_stage(const float4* __restrict__ splats, uint32_t g, float X0, float Y0,
                                            float2& p, float4& co, float4& rgb)
 {
-    const float4 v0 = __ldg(splats + 3 * (int64_t)g);
-    const float4 v1 = __ldg(splats + 3 * (int64_t)g + 1);
-    const float4 v2 = __ldg(splats + 3 * (int64_t)g + 2);
+    const float4 v0 = __ldg(splats + 4 * (int64_t)g);
+    const float4 v1 = __ldg(splats + 4 * (int64_t)g + 1);
+    const float4 v2 = __ldg(splats + 4 * (int64_t)g + 2);
     p.x = __fadd_rn(__fsub_rn(v0.x, X0), v2.z);
     p.y = __fadd_rn(__fsub_rn(v0.y, Y0), v2.w);
     co = make_float4(v0.z, v0.w, v1.x, v1.y);
@@ -38,6 +38,41 @@ __device__ __forceinline__ float4 gate_box(float2 p, float4 co)
     const float ey = sqrtf(tau * co.x / detK) * 1.001f + 0.01f;
     if (!(detK > 0.0f) || !(ex < 1e30f) || !(ey < 1e30f)) return make_float4(-inf, inf, -inf, inf);
     return make_float4(p.x - ex, p.x + ex, p.y - ey, p.y + ey);
+}
+
+// Whether blend tile (tx, ty) lies in the blend-tile rectangle of record g
+// (its own tile list holds g iff so).
+__device__ __forceinline__ bool in_blend_rect(const float4* __restrict__ splats, uint32_t g, int tx, int ty)
+{
+    const float4 r = __ldg(splats + 4 * (int64_t)g + 3);
+    return __float_as_int(r.x) <= tx && tx <= __float_as_int(r.z) && __float_as_int(r.y) <= ty &&
+           ty <= __float_as_int(r.w);
+}
+
+// Exclusive rank of this thread's flag in its CTA of NT threads; *total gets
+// the CTA's count. s_w: NT/32 + 1 ints of shared memory.
+template <int NT>
+__device__ __forceinline__ int cta_rank(bool flag, int* s_w, int* total)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned ball = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) s_w[warp] = __popc(ball);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const int c = s_w[w];
+            s_w[w] = run;
+            run += c;
+        }
+        s_w[NW] = run;
+    }
+    __syncthreads();
+    const int r = s_w[warp] + __popc(ball & ((1u << lane) - 1u));
+    *total = s_w[NW];
+    __syncthreads();
+    return r;
 }
 
 // Pixels of a CTA: each warp owns a compact 8-column block of 4*PPT rows and
@@ -76,7 +111,9 @@ struct WarpBlock {
 };
 
 // Blend of one tile (the body of the single-view and the batched kernels).
-template <int TILE, int PPT>
+// FILTER: the list is the binning tile's; entries outside this blend tile are
+// dropped while staging (what remains is this tile's own list, in order).
+template <int TILE, int PPT, bool FILTER>
 __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restrict__ splats,
                                                 const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
                                                 const Dil& dil, float3 bg, float* __restrict__ img,
@@ -89,6 +126,8 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     __shared__ float4 s_box[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
+    __shared__ uint32_t s_pos[FILTER ? BATCH : 1];
+    __shared__ int s_w[NT / 32 + 1];
     __shared__ unsigned long long s_cnt[2];
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
@@ -99,7 +138,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     const float xr = (float)(dil.d * wb.lx);
 
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0ull;
-    const uint2 rg = ranges[tile];
+    const uint2 rg = ranges[FILTER ? bin_tile_of(dil, tile) : tile];
     float T[PPT], C0[PPT], C1[PPT], C2[PPT], yr[PPT];
     uint32_t last_pos[PPT];
     bool done[PPT];
@@ -113,16 +152,47 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     }
     uint32_t n_eval = 0, n_blend = 0;
 
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+    uint32_t next = rg.x;
+    while (next < rg.y) {
         if (__syncthreads_count(n_live == 0) == NT) break;
-        const int cnt = (int)((rg.y - start) < (uint32_t)BATCH ? (rg.y - start) : (uint32_t)BATCH);
-        for (int i = threadIdx.x; i < cnt; i += NT) {
-            float2 p; float4 co, rgb;
-            load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
-            s_p[i] = p;
-            s_box[i] = gate_box(p, co);
-            s_co[i] = co;
-            s_rgb[i] = rgb;
+        const uint32_t start = next;
+        int cnt;
+        if constexpr (!FILTER) {
+            cnt = (int)((rg.y - next) < (uint32_t)BATCH ? (rg.y - next) : (uint32_t)BATCH);
+            for (int i = threadIdx.x; i < cnt; i += NT) {
+                float2 p; float4 co, rgb;
+                load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
+                s_p[i] = p;
+                s_box[i] = gate_box(p, co);
+                s_co[i] = co;
+                s_rgb[i] = rgb;
+            }
+            next += (uint32_t)cnt;
+        } else {
+            // rounds of NT candidates until the batch is full or the list ends
+            cnt = 0;
+            while (cnt + NT <= BATCH && next < rg.y) {
+                const uint32_t e = next + threadIdx.x;
+                uint32_t g = 0;
+                bool keep = false;
+                if (e < rg.y) {
+                    g = __ldg(ids + e);
+                    keep = in_blend_rect(splats, g, tx, ty);
+                }
+                int total;
+                const int r = cta_rank<NT>(keep, s_w, &total);
+                if (keep) {
+                    float2 p; float4 co, rgb;
+                    load_stage(splats, g, X0, Y0, p, co, rgb);
+                    s_p[cnt + r] = p;
+                    s_box[cnt + r] = gate_box(p, co);
+                    s_co[cnt + r] = co;
+                    s_rgb[cnt + r] = rgb;
+                    s_pos[cnt + r] = e - rg.x + 1;
+                }
+                cnt += total;
+                next = (rg.y - next) < (uint32_t)NT ? rg.y : next + NT;
+            }
         }
         __syncthreads();
         if (n_live > 0) {
@@ -150,7 +220,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     C1[k] = fmaf(c.y, w, C1[k]);
                     C2[k] = fmaf(c.z, w, C2[k]);
                     T[k] = Tn;
-                    last_pos[k] = start + j - rg.x + 1;
+                    last_pos[k] = FILTER ? s_pos[j] : start + j - rg.x + 1;
                     ++n_blend;
                 }
                 if (n_live == 0) break;
@@ -238,7 +308,7 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& c
 // warp sums them (warp_sum9), one lane per component adds the total into a
 // per-batch shared-memory accumulator, and at the end of the batch each
 // (tile, Gaussian) gets one set of vector atomics.
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool FILTER>
 __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restrict__ splats,
                                                 const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
                                                 const Dil& dil, float3 bg, const float* __restrict__ t_final,
@@ -253,6 +323,8 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_id[BATCH];
     __shared__ float s_acc[BATCH][9];
+    __shared__ uint32_t s_rel[FILTER ? BATCH : 1];
+    __shared__ int s_w[NT / 32 + 1];
     __shared__ uint32_t s_max_last;
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
@@ -261,7 +333,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     const int u = tx * TILE + wb.lx;
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
     const float xr = (float)(dil.d * wb.lx);
-    const uint2 rg = ranges[tile];
+    const uint2 rg = ranges[FILTER ? bin_tile_of(dil, tile) : tile];
 
     float T[PPT], S0[PPT], S1[PPT], S2[PPT], g0[PPT], g1[PPT], g2[PPT], yr[PPT];
     uint32_t n_last[PPT];
@@ -290,27 +362,55 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     const uint32_t n_proc = s_max_last;
     if (n_proc == 0) return;
 
-    for (int b = (int)((n_proc - 1) / BATCH); b >= 0; --b) {
-        const uint32_t bstart = (uint32_t)b * BATCH;
-        const int cnt = (int)((n_proc - bstart) < (uint32_t)BATCH ? (n_proc - bstart) : (uint32_t)BATCH);
+    // batches walk the list positions [0, n_proc) back to front; with FILTER a
+    // batch holds the entries of one round of NT candidate positions [lo, hi)
+    uint32_t hi = n_proc;
+    while (hi > 0) {
+        const uint32_t lo = FILTER ? (hi > (uint32_t)NT ? hi - NT : 0u)
+                                   : (hi > (uint32_t)BATCH ? hi - BATCH : 0u);
+        int cnt;
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += NT) {
-            const uint32_t g = __ldg(ids + rg.x + bstart + i);
-            float2 p; float4 co, rgb;
-            load_stage(splats, g, X0, Y0, p, co, rgb);
-            s_p[i] = p;
-            s_box[i] = gate_box(p, co);
-            s_co[i] = co;
-            s_rgb[i] = rgb;
-            s_id[i] = g;
+        if constexpr (!FILTER) {
+            cnt = (int)(hi - lo);
+            for (int i = threadIdx.x; i < cnt; i += NT) {
+                const uint32_t g = __ldg(ids + rg.x + lo + i);
+                float2 p; float4 co, rgb;
+                load_stage(splats, g, X0, Y0, p, co, rgb);
+                s_p[i] = p;
+                s_box[i] = gate_box(p, co);
+                s_co[i] = co;
+                s_rgb[i] = rgb;
+                s_id[i] = g;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_acc[i][k] = 0.0f;
+                for (int k = 0; k < 9; ++k) s_acc[i][k] = 0.0f;
+            }
+        } else {
+            const uint32_t rel = lo + threadIdx.x;
+            uint32_t g = 0;
+            bool keep = false;
+            if (rel < hi) {
+                g = __ldg(ids + rg.x + rel);
+                keep = in_blend_rect(splats, g, tx, ty);
+            }
+            const int r = cta_rank<NT>(keep, s_w, &cnt);
+            if (keep) {
+                float2 p; float4 co, rgb;
+                load_stage(splats, g, X0, Y0, p, co, rgb);
+                s_p[r] = p;
+                s_box[r] = gate_box(p, co);
+                s_co[r] = co;
+                s_rgb[r] = rgb;
+                s_id[r] = g;
+                s_rel[r] = rel;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) s_acc[r][k] = 0.0f;
+            }
         }
         __syncthreads();
-        const int j_top = warp_max > bstart ? (int)min((uint32_t)cnt, warp_max - bstart) - 1 : -1;
-        for (int j = j_top; j >= 0; --j) {
+        for (int j = cnt - 1; j >= 0; --j) {
+            const uint32_t pos = FILTER ? s_rel[j] : lo + (uint32_t)j;
+            if (pos >= warp_max) continue;  // past the last contributor of all this warp's pixels
             if (wb.misses(s_box[j])) continue;
-            const uint32_t pos = bstart + (uint32_t)j;
             float r[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) r[k] = 0.0f;
@@ -372,6 +472,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 atomicAdd(dst + 8, a[8]);
             }
         }
+        hi = lo;
     }
 }
 
@@ -379,25 +480,26 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 // (longest lists first, so the block scheduler dispatches greedily
 // longest-first across all views).
 // MULTI false: one view, whose fields the kernel reads at fixed offsets.
-template <int TILE, int PPT, bool MULTI>
+// FILTER: the views bin with coarser tiles than they blend (bin_shift > 0).
+template <int TILE, int PPT, bool MULTI, bool FILTER>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
              unsigned long long* __restrict__ counts)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
-    render_fwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img, V.t_final, V.last,
-                               counts);
+    render_fwd_tile<TILE, PPT, FILTER>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img, V.t_final,
+                                       V.last, counts);
 }
 
-template <int TILE, int PPT, bool MULTI>
+template <int TILE, int PPT, bool MULTI, bool FILTER>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
 k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
-    render_bwd_tile<TILE, PPT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.t_final, V.last, V.dl,
-                               reinterpret_cast<float*>(V.grad2d));
+    render_bwd_tile<TILE, PPT, FILTER>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.t_final, V.last,
+                                       V.dl, reinterpret_cast<float*>(V.grad2d));
 }
 
 __global__ void k_loss_zero(const __grid_constant__ Batch b)
@@ -462,7 +564,7 @@ int resolve_ppt(int tile, int ppt)
 __device__ __forceinline__ uint2 batch_range(const Batch& b, int gt)
 {
     const ViewDev& V = b.v[view_of_tile(b, gt)];
-    return V.ranges[gt - V.tile_begin];
+    return V.ranges[bin_tile_of(V.dil, gt - V.tile_begin)];
 }
 
 __global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Batch b, uint32_t* __restrict__ order)
@@ -510,17 +612,28 @@ bool check_render_view(int32_t n, const ViewDev& v)
     return true;
 }
 
+bool any_shift(const Batch& b)
+{
+    for (int i = 0; i < b.nviews; ++i)
+        if (b.v[i].dil.shift > 0) return true;
+    return false;
+}
+
 template <int TILE, int PPT>
 void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, cudaStream_t st)
 {
-    auto kern = b.nviews > 1 ? k_render_fwd<TILE, PPT, true> : k_render_fwd<TILE, PPT, false>;
+    const bool multi = b.nviews > 1, filter = any_shift(b);
+    auto kern = multi ? (filter ? k_render_fwd<TILE, PPT, true, true> : k_render_fwd<TILE, PPT, true, false>)
+                      : (filter ? k_render_fwd<TILE, PPT, false, true> : k_render_fwd<TILE, PPT, false, false>);
     kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
 }
 
 template <int TILE, int PPT>
 void launch_bwd(const Batch& b, const uint32_t* order, float3 bg, cudaStream_t st)
 {
-    auto kern = b.nviews > 1 ? k_render_bwd<TILE, PPT, true> : k_render_bwd<TILE, PPT, false>;
+    const bool multi = b.nviews > 1, filter = any_shift(b);
+    auto kern = multi ? (filter ? k_render_bwd<TILE, PPT, true, true> : k_render_bwd<TILE, PPT, true, false>)
+                      : (filter ? k_render_bwd<TILE, PPT, false, true> : k_render_bwd<TILE, PPT, false, false>);
     kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg);
 }
 
@@ -649,6 +762,9 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
     Batch b{};
     b.nviews = 1;
     b.v[0].ranges = reinterpret_cast<const uint2*>(ranges);
+    // one row of num_tiles blend tiles, each its own binning tile
+    b.v[0].dil.tiles_x = b.v[0].dil.bin_tiles_x = num_tiles;
+    b.v[0].dil.tiles_y = b.v[0].dil.bin_tiles_y = 1;
     b.total_tiles = num_tiles;
     k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
     return gs_host::check_launch("gs_tile_order");

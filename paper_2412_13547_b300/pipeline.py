@@ -79,13 +79,14 @@ class Rasterizer:
         self.capacity = capacity
 
     def ensure_tiles(self, num_tiles: int):
+        """Room for num_tiles binning tiles (ranges) and blend tiles (launch order)."""
         if num_tiles > self.max_tiles:
             self.max_tiles = int(num_tiles)
             self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
             self.tile_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
 
     def ensure_grid(self, tiles_x: int, tiles_y: int):
-        """Grow the workspace so that grids up to (tiles_x, tiles_y) can be binned."""
+        """Grow the workspace so that binning grids up to (tiles_x, tiles_y) fit."""
         self.ensure_tiles(tiles_x * tiles_y)
         need = R.gs_bin_sort_workspace_size(self.n, self.capacity, tiles_x, tiles_y)
         if tiles_x > self.grid[0] or tiles_y > self.grid[1] or need > self.workspace.numel():
@@ -107,12 +108,17 @@ class Rasterizer:
 
     def bin(self, cam, dil: Dilation):
         w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-        if tx > self.grid[0] or ty > self.grid[1]:
-            self.ensure_grid(tx, ty)
-        R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, tx, ty, self.workspace, self.capacity,
+        btx, bty = R.gs_bin_grid(cam, dil)
+        if btx > self.grid[0] or bty > self.grid[1]:
+            self.ensure_grid(btx, bty)
+        self.ensure_tiles(tx * ty)
+        R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, btx, bty, self.workspace, self.capacity,
                       self.sorted_ids, self.ranges, self.num_pairs_dev)
         if self.longest_first:
-            R.gs_tile_order(self.ranges, tx * ty, self.tile_order)
+            if dil.bin_shift:
+                R.gs_tile_order_batch([R.View(cam, dil, ranges=self.ranges)], self.tile_order)
+            else:
+                R.gs_tile_order(self.ranges, tx * ty, self.tile_order)
         return w_ds, h_ds, tx, ty
 
     def bin_checked(self, cam, dil: Dilation):
@@ -128,9 +134,9 @@ class Rasterizer:
         R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts,
                         pixels_per_thread=self.ppt, tile_order=self.tile_order if self.longest_first else None)
 
-    def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg):
+    def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg, zero_grad2d: bool = True):
         R.gs_render_bwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, t_final, last, dl_dimg,
-                        self.grad2d, zero_grad2d=True, pixels_per_thread=self.ppt,
+                        self.grad2d, zero_grad2d=zero_grad2d, pixels_per_thread=self.ppt,
                         tile_order=self.tile_order if self.longest_first else None)
 
 
@@ -152,8 +158,8 @@ class _RasterizeFn(torch.autograd.Function):
         n = means.shape[0]
         p = GaussianParams(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
                            opacity_logits.contiguous(), sh.contiguous(), sh.contiguous())
-        w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-        rast = Rasterizer(n, capacity=cap_hint[0], device=means.device, max_grid=(tx, ty))
+        w_ds, h_ds, _, _ = R.gs_grid(cam, dil)
+        rast = Rasterizer(n, capacity=cap_hint[0], device=means.device, max_grid=R.gs_bin_grid(cam, dil))
         rast.project(p, cam, dil)
         rast.bin_checked(cam, dil)
         cap_hint[0] = max(cap_hint[0], rast.capacity)
@@ -302,7 +308,7 @@ class BatchTrainStep:
     def __init__(self, params: GaussianParams, cams, targets, d: int = 1, adam: AdamConfig = AdamConfig(),
                  bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
                  pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
-                 capacity=None, headroom: float = 1.15, optimize: bool = True):
+                 capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0):
         if not 1 <= len(cams) <= R.MAX_VIEWS:
             raise ValueError(f"1..{R.MAX_VIEWS} views per batch")
         dev = params.means.device
@@ -310,6 +316,7 @@ class BatchTrainStep:
         self.cams, self.V = list(cams), len(cams)
         self.sparse, self.densify, self.optimize_step = bool(sparse), bool(densify), bool(optimize)
         self.tile, self.ppt, self.center_mode = int(tile), int(pixels_per_thread), int(center_mode)
+        self.bin_shift = int(bin_shift)
         self.longest_first = bool(longest_first)
         n, V = params.n, self.V
         self.targets = [t.contiguous() for t in targets]
@@ -326,7 +333,8 @@ class BatchTrainStep:
         self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
         # the largest grid of each view over the offsets (offset 0 renders the most pixels)
         self.grid0 = [R.gs_grid(c, self._dil(0, 0)) for c in self.cams]
-        self.ranges = [torch.zeros(g[2] * g[3], 2, dtype=torch.int32, device=dev) for g in self.grid0]
+        self.bgrid0 = [R.gs_bin_grid(c, self._dil(0, 0)) for c in self.cams]
+        self.ranges = [torch.zeros(g[0] * g[1], 2, dtype=torch.int32, device=dev) for g in self.bgrid0]
         self.img = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
         self.t_final = [torch.empty(g[1], g[0], device=dev) for g in self.grid0]
         self.last = [torch.empty(g[1], g[0], dtype=torch.int32, device=dev) for g in self.grid0]
@@ -346,7 +354,7 @@ class BatchTrainStep:
         self.capacity = self._capacities(headroom) if capacity is None else \
             [int(c) for c in (capacity if hasattr(capacity, "__len__") else [capacity] * V)]
         self.sorted_ids = [torch.empty(max(1, c), dtype=torch.int32, device=dev) for c in self.capacity]
-        ws = max(R.gs_bin_sort_workspace_size(n, c, g[2], g[3]) for c, g in zip(self.capacity, self.grid0))
+        ws = max(R.gs_bin_sort_workspace_size(n, c, g[0], g[1]) for c, g in zip(self.capacity, self.bgrid0))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
 
     @property
@@ -356,7 +364,7 @@ class BatchTrainStep:
     def _dil(self, phase: int, view: int) -> Dilation:
         from .scenes import rotating_offset
         ox, oy = rotating_offset(phase + view, self.d)
-        return Dilation(self.d, ox, oy, self.center_mode, self.tile)
+        return Dilation(self.d, ox, oy, self.center_mode, self.tile, self.bin_shift)
 
     def _capacities(self, headroom: float):
         """Pairs per view = sum of tiles touched (exact); the maximum over the
@@ -399,7 +407,7 @@ class BatchTrainStep:
         t = self.table(phase)
         self._project(t)
         for i, v in enumerate(t.views):
-            _, _, tx, ty = R.gs_grid(v.cam, v.dil)
+            tx, ty = R.gs_bin_grid(v.cam, v.dil)
             R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty, self.workspace,
                           self.capacity[i], self.sorted_ids[i], self.ranges[i], self.num_pairs[i:i + 1])
         order = None
@@ -463,15 +471,18 @@ class BatchTrainStep:
 
 
 def autotune_batch(params: GaussianParams, cams, targets, d: int = 1,
-                   candidates=((8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (32, 2), (32, 4)), iters: int = 3,
-                   **kw):
-    """Pick the tile size and pixels per thread of the blend launches for a
-    batch: time ``render_pass`` (projection, binning, both blend launches and
-    the loss: everything the launch shape affects) of every candidate with
-    CUDA events and return ((tile, ppt), {candidate: ms})."""
+                   candidates=((8, 2, 0), (8, 2, 1), (16, 2, 0), (16, 4, 0), (16, 2, 1), (16, 4, 1), (32, 4, 0)),
+                   iters: int = 3, **kw):
+    """Pick the launch shape of a batch: blend tile size, pixels per thread of
+    the blend CTAs and binning tile shift. Times ``render_pass`` (projection,
+    binning, both blend launches and the loss: everything the shape affects)
+    of every candidate (tile, ppt[, bin_shift]) with CUDA events and returns
+    ((tile, ppt, bin_shift), {candidate: ms})."""
     times = {}
-    for tile, ppt in candidates:
-        st = BatchTrainStep(params, cams, targets, d=d, tile=tile, pixels_per_thread=ppt, optimize=False, **kw)
+    for cand in candidates:
+        tile, ppt, shift = (tuple(cand) + (0,))[:3]
+        st = BatchTrainStep(params, cams, targets, d=d, tile=tile, pixels_per_thread=ppt, bin_shift=shift,
+                            optimize=False, **kw)
         for ph in range(st.phases):
             st.render_pass(ph)
         torch.cuda.synchronize()
@@ -481,7 +492,7 @@ def autotune_batch(params: GaussianParams, cams, targets, d: int = 1,
             st.render_pass(i % st.phases)
         e1.record()
         torch.cuda.synchronize()
-        times[(tile, ppt)] = e0.elapsed_time(e1) / (iters * st.phases)
+        times[(tile, ppt, shift)] = e0.elapsed_time(e1) / (iters * st.phases)
         del st
         torch.cuda.empty_cache()
     best = min(times, key=times.get)

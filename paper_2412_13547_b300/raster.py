@@ -19,13 +19,13 @@ LIB_PATH = os.path.join(_PKG, "libturbogs.so")
 
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT = 0, 1, 2, 3, 4
 GS_DTYPE_F32, GS_DTYPE_BF16, GS_DTYPE_F16 = 0, 1, 2
-SPLAT_FLOATS = 12
+SPLAT_FLOATS = 16
 GRAD2D_FLOATS = 12
 ADAM_MAX_TENSORS = 8
 
 MAX_VIEWS = 16
 
-SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
+SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_bin_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
            "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
            "gs_tile_order_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
@@ -48,7 +48,7 @@ class GsCamera(ctypes.Structure):
 
 class GsDilation(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("ox", ctypes.c_int32), ("oy", ctypes.c_int32),
-                ("center_mode", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("center_mode", ctypes.c_int32), ("tile", ctypes.c_int32), ("bin_shift", ctypes.c_int32)]
 
 
 class GsAdamTensor(ctypes.Structure):
@@ -80,15 +80,17 @@ class GsView(ctypes.Structure):
 
 @dataclass(frozen=True)
 class Dilation:
-    """Sec. 3.1: render the lattice (d*u + ox, d*v + oy) of the hr image."""
+    """Sec. 3.1: render the lattice (d*u + ox, d*v + oy) of the hr image.
+    tile: blend tile edge; bin_shift: bin with tiles of tile << bin_shift."""
     d: int = 1
     ox: int = 0
     oy: int = 0
     center_mode: int = 0
     tile: int = 16
+    bin_shift: int = 0
 
     def c(self) -> GsDilation:
-        return GsDilation(self.d, self.ox, self.oy, self.center_mode, self.tile)
+        return GsDilation(self.d, self.ox, self.oy, self.center_mode, self.tile, self.bin_shift)
 
 
 @dataclass
@@ -165,6 +167,7 @@ def load():
     lib.gs_version.restype = i32
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_grid.argtypes = [cam_p, dil_p, P, P, P, P]
+    lib.gs_bin_grid.argtypes = [cam_p, dil_p, P, P]
     lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P]
     lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32, i32]
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
@@ -245,10 +248,36 @@ def gs_grid(cam, dil: Dilation):
     return tuple(int(o.value) for o in out)
 
 
+def gs_bin_grid(cam, dil: Dilation):
+    """(bin_tiles_x, bin_tiles_y): the grid gs_bin_sort and the ranges use."""
+    out = [ctypes.c_int32() for _ in range(2)]
+    _check(load().gs_bin_grid(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), *[ctypes.byref(o) for o in out]),
+           "gs_bin_grid")
+    return tuple(int(o.value) for o in out)
+
+
+def _need(t, numel, what):
+    """The C ABI takes plain pointers: check here that a buffer holds what the call writes."""
+    if t is not None and t.numel() < numel:
+        raise ValueError(f"{what}: {t.numel()} elements, the call needs {numel}")
+
+
+def _need_image(dil, cam, img=None, t_final=None, last=None, dl=None):
+    w_ds, h_ds, _, _ = gs_grid(cam, dil)
+    P = w_ds * h_ds
+    _need(img, 3 * P, "img")
+    _need(t_final, P, "t_final")
+    _need(last, P, "last")
+    _need(dl, 3 * P, "dl_dimg")
+
+
 def gs_project(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, splats, radii, rects,
                tiles_touched, stream=None):
     n = means.shape[0]
     deg = sh_degree_of(sh)
+    for t, w, name in ((splats, SPLAT_FLOATS, "splats"), (radii, 1, "radii"), (rects, 4, "rects"),
+                       (tiles_touched, 1, "tiles_touched")):
+        _need(t, n * w, name)
     _check(load().gs_project(n, deg, _SH_DTYPE[sh.dtype], _ptr(means), _ptr(log_scales), _ptr(quats),
                              _ptr(opacity_logits), _ptr(sh), ctypes.byref(camera(cam)), ctypes.byref(dil.c()),
                              _ptr(splats), _ptr(radii), _ptr(rects), _ptr(tiles_touched), _stream(stream)),
@@ -261,6 +290,8 @@ def gs_bin_sort_workspace_size(n: int, capacity: int, tiles_x: int, tiles_y: int
 
 def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, capacity, sorted_ids, ranges,
                 num_pairs, stream=None):
+    _need(ranges, 2 * int(tiles_x) * int(tiles_y), "ranges")
+    _need(sorted_ids, int(capacity), "sorted_ids")
     _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x), int(tiles_y),
                               _ptr(workspace), workspace.numel() * workspace.element_size(), int(capacity),
                               _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)), "gs_bin_sort")
@@ -288,18 +319,23 @@ def gs_tile_order(ranges, num_tiles, order, stream=None):
 
 def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, counts=None,
                   pixels_per_thread=0, tile_order=None, stream=None):
+    _need_image(dil, cam, img, t_final, last)
     _check(load().gs_render_fwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last), _ptr(counts),
                                 int(pixels_per_thread), _ptr(tile_order), _stream(stream)), "gs_render_fwd")
 
 
 def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
+    _need_image(dil, cam, img=img, dl=dl_dimg)
+    _need(target, 3 * int(cam.width) * int(cam.height), "target")
     _check(load().gs_loss_l1(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
                              _ptr(dl_dimg), _ptr(loss), _stream(stream)), "gs_loss_l1")
 
 
 def gs_render_bwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, t_final, last, dl_dimg, grad2d,
                   zero_grad2d=True, pixels_per_thread=0, tile_order=None, stream=None):
+    _need_image(dil, cam, t_final=t_final, last=last, dl=dl_dimg)
+    _need(grad2d, int(n) * GRAD2D_FLOATS, "grad2d")
     _check(load().gs_render_bwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(t_final), _ptr(last), _ptr(dl_dimg),
                                 _ptr(grad2d), int(bool(zero_grad2d)), int(pixels_per_thread), _ptr(tile_order),

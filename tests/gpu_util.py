@@ -27,7 +27,8 @@ def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capac
     """GPU project + bin + blend. Returns numpy outputs and the rasterizer."""
     p = gpu_params(p32, sh_dtype)
     w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
-    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(tx, ty))
+    btx, bty = R.gs_bin_grid(cam, dil)
+    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(btx, bty))
     rast.project(p, cam, dil)
     if capacity is None:
         rast.bin_checked(cam, dil)
@@ -38,7 +39,7 @@ def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capac
     rast.render(cam, dil, bg, img, t_final, last, counts)
     torch.cuda.synchronize()
     k = rast.num_pairs()
-    ntile = tx * ty
+    ntile = btx * bty
     out = dict(
         splats=rast.splats.cpu().numpy(), radii=rast.radii.cpu().numpy(), rects=rast.rects.cpu().numpy(),
         tiles_touched=rast.tiles_touched.cpu().numpy(), k=k,

@@ -27,6 +27,24 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(names) == set(R.SYMBOLS)
 
 
+def test_python_constants_match_the_header():
+    """Buffer sizes the binding allocates follow the header's #defines."""
+    src = open(os.path.join(ROOT, "include", "turbogs.h")).read()
+    defs = {m.group(1): m.group(2) for m in re.finditer(r"#define\s+(GS_[A-Z0-9_]+)\s+\(?([0-9]+)u?(?:\s*<<\s*([0-9]+))?",
+                                                          src)}
+    shifts = {m.group(1): int(m.group(2)) << int(m.group(3)) for m in
+              re.finditer(r"#define\s+(GS_[A-Z0-9_]+)\s+\(([0-9]+)u\s*<<\s*([0-9]+)\)", src)}
+    assert int(defs["GS_SPLAT_FLOATS"]) == R.SPLAT_FLOATS
+    assert int(defs["GS_GRAD2D_FLOATS"]) == R.GRAD2D_FLOATS
+    assert int(defs["GS_ADAM_MAX_TENSORS"]) == R.ADAM_MAX_TENSORS
+    assert int(defs["GS_MAX_VIEWS"]) == R.MAX_VIEWS
+    assert int(defs["GS_MAX_ROW_TENSORS"]) == R.GS_MAX_ROW_TENSORS
+    assert shifts["GS_BIN_SORT_STATIC_SCRATCH_BYTES"] == R.BIN_SORT_STATIC_SCRATCH_BYTES
+    for role in ("COPY", "MEANS", "LOG_SCALES", "QUATS", "STATE", "ZERO"):
+        assert int(defs["GS_ROW_" + role]) == getattr(R, "GS_ROW_" + role)
+    assert ctypes.sizeof(R.GsDilation) == 6 * 4
+
+
 def test_host_only_calls():
     assert R.gs_version() >= 100
     cam = type("C", (), dict(R=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], T=[0, 0, 0], fx=100.0, fy=100.0, cx=63.5,

@@ -128,9 +128,8 @@ def test_binning_bitexact_many_pairs(dil):
 
 @pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0, tile=8), R.Dilation(2, 1, 0, tile=8)], ids=_dil_id)
 def test_binning_bitexact_both_paths(dil):
-    """2560x1440 with 8 px tiles: d=1 (320x180 tiles) is beyond the counting path's
-    shared-memory difference array and takes the radix-sort path; d=2 (160x90)
-    takes the counting path. Both must equal the oracle bit for bit."""
+    """2560x1440 with 8 px tiles: d=1 gives 320x180 tiles (long rows for the
+    tile-level scatter), d=2 160x90. Both must equal the oracle bit for bit."""
     p32, cam, _ = scene_clusters(n=60000, w=2560, h=1440, index=6)
     out, *_ = U.run_forward(p32, cam, dil)
     check_binning(out)
