@@ -122,6 +122,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
+    constexpr int ROUND = NT < BATCH ? NT : BATCH;  // candidates per filtering round
     __shared__ float2 s_p[BATCH];
     __shared__ float4 s_box[BATCH];
     __shared__ float4 s_co[BATCH];
@@ -169,13 +170,13 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
             }
             next += (uint32_t)cnt;
         } else {
-            // rounds of NT candidates until the batch is full or the list ends
+            // rounds of ROUND candidates until the batch is full or the list ends
             cnt = 0;
-            while (cnt + NT <= BATCH && next < rg.y) {
+            while (cnt + ROUND <= BATCH && next < rg.y) {
                 const uint32_t e = next + threadIdx.x;
                 uint32_t g = 0;
                 bool keep = false;
-                if (e < rg.y) {
+                if ((int)threadIdx.x < ROUND && e < rg.y) {
                     g = __ldg(ids + e);
                     keep = in_blend_rect(splats, g, tx, ty);
                 }
@@ -191,7 +192,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     s_pos[cnt + r] = e - rg.x + 1;
                 }
                 cnt += total;
-                next = (rg.y - next) < (uint32_t)NT ? rg.y : next + NT;
+                next = (rg.y - next) < (uint32_t)ROUND ? rg.y : next + ROUND;
             }
         }
         __syncthreads();
@@ -317,6 +318,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
+    constexpr int ROUND = NT < BATCH ? NT : BATCH;  // candidates per filtering round
     __shared__ float2 s_p[BATCH];
     __shared__ float4 s_box[BATCH];
     __shared__ float4 s_co[BATCH];
@@ -362,16 +364,19 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     const uint32_t n_proc = s_max_last;
     if (n_proc == 0) return;
 
-    // batches walk the list positions [0, n_proc) back to front; with FILTER a
-    // batch holds the entries of one round of NT candidate positions [lo, hi)
+    // batches walk the list positions [0, n_proc) back to front. With FILTER a
+    // batch gathers rounds of ROUND candidate positions, highest first, into the
+    // top of the staging arrays until the next round might not fit; the kept
+    // entries then sit in slots [base, BATCH) in ascending list order.
     uint32_t hi = n_proc;
     while (hi > 0) {
-        const uint32_t lo = FILTER ? (hi > (uint32_t)NT ? hi - NT : 0u)
-                                   : (hi > (uint32_t)BATCH ? hi - BATCH : 0u);
-        int cnt;
+        int cnt, base;
+        uint32_t lo = 0;
         __syncthreads();
         if constexpr (!FILTER) {
+            lo = hi > (uint32_t)BATCH ? hi - BATCH : 0u;
             cnt = (int)(hi - lo);
+            base = 0;
             for (int i = threadIdx.x; i < cnt; i += NT) {
                 const uint32_t g = __ldg(ids + rg.x + lo + i);
                 float2 p; float4 co, rgb;
@@ -384,30 +389,41 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 #pragma unroll
                 for (int k = 0; k < 9; ++k) s_acc[i][k] = 0.0f;
             }
+            hi = lo;
         } else {
-            const uint32_t rel = lo + threadIdx.x;
-            uint32_t g = 0;
-            bool keep = false;
-            if (rel < hi) {
-                g = __ldg(ids + rg.x + rel);
-                keep = in_blend_rect(splats, g, tx, ty);
-            }
-            const int r = cta_rank<NT>(keep, s_w, &cnt);
-            if (keep) {
-                float2 p; float4 co, rgb;
-                load_stage(splats, g, X0, Y0, p, co, rgb);
-                s_p[r] = p;
-                s_box[r] = gate_box(p, co);
-                s_co[r] = co;
-                s_rgb[r] = rgb;
-                s_id[r] = g;
-                s_rel[r] = rel;
+            int filled = 0;
+            while (filled + ROUND <= BATCH && hi > 0) {
+                lo = hi > (uint32_t)ROUND ? hi - ROUND : 0u;
+                const uint32_t rel = lo + threadIdx.x;
+                uint32_t g = 0;
+                bool keep = false;
+                if ((int)threadIdx.x < ROUND && rel < hi) {
+                    g = __ldg(ids + rg.x + rel);
+                    keep = in_blend_rect(splats, g, tx, ty);
+                }
+                int total;
+                const int r = cta_rank<NT>(keep, s_w, &total);
+                if (keep) {
+                    const int slot = BATCH - filled - total + r;
+                    float2 p; float4 co, rgb;
+                    load_stage(splats, g, X0, Y0, p, co, rgb);
+                    s_p[slot] = p;
+                    s_box[slot] = gate_box(p, co);
+                    s_co[slot] = co;
+                    s_rgb[slot] = rgb;
+                    s_id[slot] = g;
+                    s_rel[slot] = rel;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) s_acc[r][k] = 0.0f;
+                    for (int k = 0; k < 9; ++k) s_acc[slot][k] = 0.0f;
+                }
+                filled += total;
+                hi = lo;
             }
+            cnt = filled;
+            base = BATCH - filled;
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
+        for (int j = base + cnt - 1; j >= base; --j) {
             const uint32_t pos = FILTER ? s_rel[j] : lo + (uint32_t)j;
             if (pos >= warp_max) continue;  // past the last contributor of all this warp's pixels
             if (wb.misses(s_box[j])) continue;
@@ -460,7 +476,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += NT) {
+        for (int i = base + (int)threadIdx.x; i < base + cnt; i += NT) {
             const float* a = s_acc[i];
             bool any = false;
 #pragma unroll
@@ -472,7 +488,6 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 atomicAdd(dst + 8, a[8]);
             }
         }
-        hi = lo;
     }
 }
 

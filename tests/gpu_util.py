@@ -23,12 +23,12 @@ def gpu_params(p32, sh_dtype=torch.float32):
     return GaussianParams.from_arrays(p32, DEV, sh_dtype)
 
 
-def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capacity=None):
+def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capacity=None, ppt=0):
     """GPU project + bin + blend. Returns numpy outputs and the rasterizer."""
     p = gpu_params(p32, sh_dtype)
     w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
     btx, bty = R.gs_bin_grid(cam, dil)
-    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(btx, bty))
+    rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(btx, bty), pixels_per_thread=ppt)
     rast.project(p, cam, dil)
     if capacity is None:
         rast.bin_checked(cam, dil)

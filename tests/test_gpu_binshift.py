@@ -28,12 +28,15 @@ def _scene(kind):
     return U.params_np(s), cam
 
 
-CASES = [("small", 16, 1, 1), ("small", 8, 1, 2), ("clusters", 16, 1, 1), ("clusters", 16, 2, 2),
-         ("clusters", 8, 2, 1), ("clusters", 8, 1, 3)]
+# (scene, tile, bin_shift, d, pixels per thread): every launch shape of the blend,
+# including CTAs wider than a staging batch (tile 32 at 2 pixels per thread)
+CASES = [("small", 16, 1, 1, 0), ("small", 8, 1, 2, 0), ("small", 8, 1, 1, 1), ("clusters", 16, 1, 1, 0),
+         ("clusters", 16, 2, 2, 0), ("clusters", 16, 1, 2, 1), ("clusters", 16, 1, 1, 4), ("clusters", 8, 2, 1, 0),
+         ("clusters", 8, 1, 3, 0), ("clusters", 32, 1, 1, 2), ("clusters", 32, 1, 2, 4)]
 
 
 def _ids(c):
-    return f"{c[0]}-t{c[1]}-s{c[2]}-d{c[3]}"
+    return f"{c[0]}-t{c[1]}-s{c[2]}-d{c[3]}-ppt{c[4]}"
 
 
 def _fine_index_of(out_c, out_f, dil, grid):
@@ -63,12 +66,12 @@ def _fine_index_of(out_c, out_f, dil, grid):
 
 @pytest.mark.parametrize("case", CASES, ids=_ids)
 def test_coarse_binning_gives_the_same_render(case):
-    kind, tile, shift, d = case
+    kind, tile, shift, d, ppt = case
     p32, cam = _scene(kind)
     dil0 = R.Dilation(d, d - 1, 0, tile=tile)
     dil1 = R.Dilation(d, d - 1, 0, tile=tile, bin_shift=shift)
-    out0, rast0, p, bufs0 = U.run_forward(p32, cam, dil0, BG)
-    out1, rast1, _, bufs1 = U.run_forward(p32, cam, dil1, BG)
+    out0, rast0, p, bufs0 = U.run_forward(p32, cam, dil0, BG, ppt=ppt)
+    out1, rast1, _, bufs1 = U.run_forward(p32, cam, dil1, BG, ppt=ppt)
     # projection: identical record (with the blend rect), rects and counts at the binning tiles
     np.testing.assert_array_equal(out1["splats"], out0["splats"])
     np.testing.assert_array_equal(out1["radii"], out0["radii"])
