@@ -114,7 +114,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 TILE = [16]  # tile side used by every dilation of the run (set from --tile)
-SHIFT = [0]  # binning tiles are TILE << SHIFT (set from --bin-shift)
+SHIFT = [-1]  # binning tiles are TILE << SHIFT (set from --bin-shift; -1: bin_shift_for(d))
+
+
+def bin_shift_for(d: int) -> int:
+    """Binning shift of a dilation: --bin-shift, or by default binning tiles of
+    about 128 hr pixels (tile 16: shift 2 at d = 1 and 2, 1 at d = 4, 0 above)."""
+    if SHIFT[0] >= 0:
+        return SHIFT[0]
+    return max(0, min(2, 3 - int(math.log2(max(1, d)))))
 
 STAGES = ("project", "bin_sort", "render_fwd", "loss", "zero_grad2d", "render_bwd", "project_bwd_adam")
 # stages that are one kernel launch each (the roofline's candidates for the dominant kernel)
@@ -212,7 +220,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
     for i in range(warmup):
         ox, oy = offsets[i]
-        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), target_dev)
+        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev)
     torch.cuda.synchronize()
     step.counts.zero_()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -222,7 +230,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         start.record()
         for i in range(steps):
             ox, oy = offsets[warmup + i]
-            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), target_dev, counts=True)
+            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
@@ -235,13 +243,14 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
                blends_evaluated_per_s=float(counts[0]) * 1000.0 / total_ms,
                blends_contributing_per_s=float(counts[1]) * 1000.0 / total_ms,
                pairs_mean=float(ks.mean()), loss=float(step.loss.item()), d=d,
+               tile=TILE[0], bin_tile=TILE[0] << bin_shift_for(d),
                sh_dtype=str(sh_dtype).replace("torch.", ""))
     if want_stage:
         res["stage_ms"] = timed.stage_ms(steps)
         res["evaluated_per_step"] = float(counts[0]) / steps
         res["blended_per_step"] = float(counts[1]) / steps
         # back-to-front replay work: sum over pixels of the list prefix they replay
-        res["replayed_per_step"] = float(step.last.float().sum().item()) if d >= 1 else 0.0
+        res["replayed_per_step"] = float(counts[2]) / steps
     return res, step
 
 
@@ -331,7 +340,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
             issue_copy(i + 1)
         comp.wait_event(ready[b])
         ox, oy = scenes.rotating_offset(i, d)
-        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0]), bufs[b])
+        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), bufs[b])
         free[b].record(comp)
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     end.record()
@@ -503,15 +512,20 @@ def main():
                     help="uhd: 3840x2160, 3M Gaussians (the measured workload); hd: 1920x1080, 1M (profiling); "
                          "batch: 8 mixed-resolution views per step of a 2M-Gaussian scene")
     ap.add_argument("--d", type=int, default=2, help="dilation of the batch workload")
+    ap.add_argument("--write-traffic", default="",
+                    help="ncu --csv log of dram__bytes_read/write.sum per launch: write profiles/traffic.json "
+                         "(DRAM bytes per launch of each kernel, tagged with the current sources) and exit")
     ap.add_argument("--oracle-tiles", type=int, default=16)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stages-json", default="")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile side of the lattice image")
-    ap.add_argument("--bin-shift", type=int, default=1, choices=[0, 1, 2],
-                    help="bin with tiles of tile << bin-shift, blend per tile")
+    ap.add_argument("--bin-shift", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="bin with tiles of tile << bin-shift, blend per tile (-1: about 128 hr px)")
     args = ap.parse_args()
+    if args.write_traffic:
+        return write_traffic(args.write_traffic, args.workload)
     TILE[0] = args.tile
     SHIFT[0] = args.bin_shift
     if args.warmup < 3:
@@ -543,12 +557,12 @@ def main():
     if args.workload != "uhd":
         args.no_cpu_baseline = True
     rast = Rasterizer(params.n, capacity=1 << 20, device=device, pixels_per_thread=args.ppt,
-                      max_grid=R.gs_bin_grid(cam, R.Dilation(1, 0, 0, tile=TILE[0], bin_shift=SHIFT[0])))
+                      max_grid=R.gs_bin_grid(cam, R.Dilation(1, 0, 0, tile=TILE[0], bin_shift=0)))
     kmax = 0
     for d in (1, 2, 4):
         for ox in range(d):
             for oy in range(d):
-                dil = R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=SHIFT[0])
+                dil = R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d))
                 rast.project(params, cam, dil)
                 rast.bin_checked(cam, dil)
                 kmax = max(kmax, rast.num_pairs())
@@ -623,7 +637,7 @@ def main():
         "config": {"workload": ("uhd-3840x2160-3M-gaussians-sh3" if args.workload == "uhd" else
                                 "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
                    "n_gaussians": params.n, "resolution": [cam.width, cam.height], "d": 2, "tile": TILE[0],
-                   "bin_tile": TILE[0] << SHIFT[0],
+                   "bin_tile": TILE[0] << bin_shift_for(2),
                    "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 "
                    "(params 708 MB, pair buffers > 1 GB)"},
         "blends_per_s": round(head["blends_evaluated_per_s"], 1),
@@ -644,6 +658,34 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def write_traffic(csv_path, workload):
+    """Mean DRAM bytes (read + write) per launch of each of our kernels in an
+    ncu CSV log, tagged with the hash of the kernel sources they came from."""
+    import csv
+    import re
+    rows = {}
+    with open(csv_path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        m = re.search(r"(k_[a-z_0-9]+)", r["Kernel Name"])
+        if not m:
+            continue
+        ent = rows.setdefault(r["ID"], {"kernel": m.group(1)})
+        ent[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    per = {}
+    for ent in rows.values():
+        if "dram__bytes_read.sum" not in ent:
+            continue
+        per.setdefault(ent["kernel"], []).append(ent["dram__bytes_read.sum"] + ent.get("dram__bytes_write.sum", 0.0))
+    out = {"source_hash": _source_hash(), "workload": workload, "from": os.path.basename(csv_path),
+           "kernels": {k: {"bytes_per_launch": statistics.mean(v), "launches": len(v)} for k, v in per.items()}}
+    os.makedirs(os.path.join(ROOT, "profiles"), exist_ok=True)
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
     return 0
 
 

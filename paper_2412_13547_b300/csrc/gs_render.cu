@@ -129,7 +129,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_pos[FILTER ? BATCH : 1];
     __shared__ int s_w[NT / 32 + 1];
-    __shared__ unsigned long long s_cnt[2];
+    __shared__ unsigned long long s_cnt[3];
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
     const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
@@ -138,15 +138,15 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
     const float xr = (float)(dil.d * wb.lx);
 
-    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
     const uint2 rg = ranges[FILTER ? bin_tile_of(dil, tile) : tile];
     float T[PPT], C0[PPT], C1[PPT], C2[PPT], yr[PPT];
-    uint32_t last_pos[PPT];
+    uint32_t last_pos[PPT], last_own[PPT];  // last blended entry: binning-list and own-list position + 1
     bool done[PPT];
     int n_live = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        T[k] = 1.0f; C0[k] = C1[k] = C2[k] = 0.0f; last_pos[k] = 0;
+        T[k] = 1.0f; C0[k] = C1[k] = C2[k] = 0.0f; last_pos[k] = 0; last_own[k] = 0;
         yr[k] = (float)(dil.d * (wb.ly0 + k));
         done[k] = !(u < dil.w_ds && ty * TILE + wb.ly0 + k < dil.h_ds);
         n_live += done[k] ? 0 : 1;
@@ -154,6 +154,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     uint32_t n_eval = 0, n_blend = 0;
 
     uint32_t next = rg.x;
+    uint32_t own_base = 0;  // entries of this tile's own list staged before the batch
     while (next < rg.y) {
         if (__syncthreads_count(n_live == 0) == NT) break;
         const uint32_t start = next;
@@ -222,11 +223,13 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     C2[k] = fmaf(c.z, w, C2[k]);
                     T[k] = Tn;
                     last_pos[k] = FILTER ? s_pos[j] : start + j - rg.x + 1;
+                    last_own[k] = own_base + j + 1;
                     ++n_blend;
                 }
                 if (n_live == 0) break;
             }
         }
+        own_base += (uint32_t)cnt;
     }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -241,21 +244,26 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
         }
     }
     if (counts != nullptr) {
-        unsigned long long e = n_eval, b = n_blend;
+        unsigned long long e = n_eval, b = n_blend, r = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) r += last_own[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_down_sync(0xffffffffu, e, o);
             b += __shfl_down_sync(0xffffffffu, b, o);
+            r += __shfl_down_sync(0xffffffffu, r, o);
         }
         __syncthreads();
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&s_cnt[0], e);
             atomicAdd(&s_cnt[1], b);
+            atomicAdd(&s_cnt[2], r);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             atomicAdd(&counts[0], s_cnt[0]);
             atomicAdd(&counts[1], s_cnt[1]);
+            atomicAdd(&counts[2], s_cnt[2]);
         }
     }
 }

@@ -228,7 +228,7 @@ class TrainStep:
         self.last = torch.empty(max_pixels, dtype=torch.int32, device=dev)
         self.dl = torch.empty(max_pixels * 3, device=dev)
         self.loss = torch.zeros(1, device=dev)
-        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.counts = torch.zeros(3, dtype=torch.int64, device=dev)
         n = params.n
         self.densify = densify
         self.pos_acc = torch.zeros(n, device=dev)
@@ -330,7 +330,7 @@ class BatchTrainStep:
         self.grad2d = torch.zeros(V, n, R.GRAD2D_FLOATS, device=dev)
         self.loss = torch.zeros(V, device=dev)
         self.num_pairs = torch.zeros(V, dtype=torch.int64, device=dev)
-        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.counts = torch.zeros(3, dtype=torch.int64, device=dev)
         # the largest grid of each view over the offsets (offset 0 renders the most pixels)
         self.grid0 = [R.gs_grid(c, self._dil(0, 0)) for c in self.cams]
         self.bgrid0 = [R.gs_bin_grid(c, self._dil(0, 0)) for c in self.cams]
@@ -471,7 +471,8 @@ class BatchTrainStep:
 
 
 def autotune_batch(params: GaussianParams, cams, targets, d: int = 1,
-                   candidates=((8, 2, 0), (8, 2, 1), (16, 2, 0), (16, 4, 0), (16, 2, 1), (16, 4, 1), (32, 4, 0)),
+                   candidates=((8, 2, 1), (16, 2, 0), (16, 4, 0), (16, 2, 1), (16, 4, 1), (16, 2, 2), (16, 4, 2),
+                               (32, 4, 0), (32, 4, 1)),
                    iters: int = 3, **kw):
     """Pick the launch shape of a batch: blend tile size, pixels per thread of
     the blend CTAs and binning tile shift. Times ``render_pass`` (projection,

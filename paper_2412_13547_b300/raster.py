@@ -320,6 +320,7 @@ def gs_tile_order(ranges, num_tiles, order, stream=None):
 def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, counts=None,
                   pixels_per_thread=0, tile_order=None, stream=None):
     _need_image(dil, cam, img, t_final, last)
+    _need(counts, 3, "counts")
     _check(load().gs_render_fwd(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
                                 ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last), _ptr(counts),
                                 int(pixels_per_thread), _ptr(tile_order), _stream(stream)), "gs_render_fwd")
@@ -414,6 +415,7 @@ def gs_tile_order_batch(views, order, stream=None):
 
 def gs_render_fwd_batch(n, views, bg, tile_order=None, counts=None, pixels_per_thread=0, stream=None):
     t = _table(views)
+    _need(counts, 3, "counts")
     _check(load().gs_render_fwd_batch(int(n), t.arr, t.n, _bg(bg), _ptr(tile_order), _ptr(counts),
                                       int(pixels_per_thread), _stream(stream)), "gs_render_fwd_batch")
 

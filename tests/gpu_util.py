@@ -35,7 +35,7 @@ def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capac
     else:
         rast.bin(cam, dil)
     img, t_final, last = image_buffers(h_ds, w_ds, DEV)
-    counts = torch.zeros(2, dtype=torch.int64, device=DEV)
+    counts = torch.zeros(3, dtype=torch.int64, device=DEV)
     rast.render(cam, dil, bg, img, t_final, last, counts)
     torch.cuda.synchronize()
     k = rast.num_pairs()

@@ -98,7 +98,7 @@ def single_forward(V, i, ppt=0):
     img = torch.zeros(h_ds, w_ds, 3, device=DEV)
     tf = torch.zeros(h_ds, w_ds, device=DEV)
     last = torch.zeros(h_ds, w_ds, dtype=torch.int32, device=DEV)
-    counts = torch.zeros(2, dtype=torch.int64, device=DEV)
+    counts = torch.zeros(3, dtype=torch.int64, device=DEV)
     R.gs_render_fwd(V.p.n, b["splats"], b["sorted_ids"], b["ranges"], c, d, BG, img, tf, last, counts,
                     pixels_per_thread=ppt)
     return img, tf, last, counts
@@ -147,10 +147,10 @@ def test_render_fwd_batch_equals_single_views(batch, use_order):
     V.project()
     V.bin()
     order = V.order() if use_order else None
-    counts = torch.zeros(2, dtype=torch.int64, device=DEV)
+    counts = torch.zeros(3, dtype=torch.int64, device=DEV)
     R.gs_render_fwd_batch(V.p.n, V.table(), BG, tile_order=order, counts=counts)
     torch.cuda.synchronize()
-    total = np.zeros(2, np.int64)
+    total = np.zeros(3, np.int64)
     for i in range(len(V.bufs)):
         img, tf, last, c = single_forward(V, i)
         torch.cuda.synchronize()

@@ -183,6 +183,9 @@ def test_render_fwd_parity(dil):
     np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
     assert out["counts"][0] == of["n_eval"] or excl.any()
     assert out["counts"][1] == of["n_blend"] or excl.any()
+    # the backward's replay work: the sum of the pixels' last positions in their tile lists
+    assert out["counts"][2] == int(out["last"].astype(np.int64).sum())
+    assert out["counts"][2] == int(of["last"].astype(np.int64).sum()) or excl.any()
 
 
 def test_render_fwd_parity_sh3_ragged():
@@ -208,7 +211,7 @@ def test_launch_shape_does_not_change_results(tile, ppts):
         rast.project(p, cam, dil)
         rast.bin_checked(cam, dil)
         img, tf, last = image_buffers(h_ds, w_ds)
-        counts = torch.zeros(2, dtype=torch.int64, device=U.DEV)
+        counts = torch.zeros(3, dtype=torch.int64, device=U.DEV)
         rast.render(cam, dil, (0.1, 0.2, 0.3), img, tf, last, counts)
         dl = torch.tensor(np.random.default_rng(0).standard_normal((h_ds, w_ds, 3)) * 1e-3, dtype=torch.float32,
                           device=U.DEV)
