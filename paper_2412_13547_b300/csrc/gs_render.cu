@@ -205,19 +205,25 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 const float2 p = s_p[j];
                 const float4 co = s_co[j];
                 const float dx = __fsub_rn(xr, p.x);
+                // the gates of all this thread's pixels first, free of branches so that
+                // their dependency chains interleave; then the blends, in pixel order
+                float alpha[PPT];
+                bool use[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (done[k]) continue;
-                    ++n_eval;
                     const float dy = __fsub_rn(yr[k], p.y);
                     const float power = splat_power(dx, dy, co.x, co.y, co.z);
-                    if (power > 0.0f) continue;
-                    const float alpha = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
-                    if (alpha < kAlphaMin) continue;
-                    const float Tn = T[k] * (1.0f - alpha);
+                    alpha[k] = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
+                    use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
+                }
+                n_eval += n_live;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!use[k]) continue;
+                    const float Tn = T[k] * (1.0f - alpha[k]);
                     if (Tn < kTStop) { done[k] = true; --n_live; continue; }
                     const float4 c = s_rgb[j];
-                    const float w = alpha * T[k];
+                    const float w = alpha[k] * T[k];
                     C0[k] = fmaf(c.x, w, C0[k]);
                     C1[k] = fmaf(c.y, w, C1[k]);
                     C2[k] = fmaf(c.z, w, C2[k]);
@@ -443,24 +449,30 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
             const float4 co = s_co[j];
             const float4 c = s_rgb[j];
             const float dx = __fsub_rn(xr, p.x);
+            // gates of all this thread's pixels first (branch-free), then the replay
+            float dyk[PPT], Gk[PPT], ark[PPT];
+            bool use[PPT];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (pos >= n_last[k]) continue;
-                const float dy = __fsub_rn(yr[k], p.y);
-                const float power = splat_power(dx, dy, co.x, co.y, co.z);
-                if (power > 0.0f) continue;
-                const float G = __expf(power);
-                const float a_raw = __fmul_rn(co.w, G);  // as splat_alpha_raw
+                dyk[k] = __fsub_rn(yr[k], p.y);
+                const float power = splat_power(dx, dyk[k], co.x, co.y, co.z);
+                Gk[k] = __expf(power);
+                ark[k] = __fmul_rn(co.w, Gk[k]);  // as splat_alpha_raw
+                use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!use[k]) continue;
+                const float dy = dyk[k], G = Gk[k], a_raw = ark[k];
                 const float alpha = fminf(kAlphaMax, a_raw);
-                if (alpha < kAlphaMin) continue;
                 contrib = true;
-                const float one_m = 1.0f - alpha;
-                const float Ti = T[k] / one_m;
+                // one correctly rounded reciprocal serves both divisions by (1 - alpha)
+                const float inv = __frcp_rn(1.0f - alpha);
+                const float Ti = T[k] * inv;
                 const float w = alpha * Ti;
                 r[6] = fmaf(w, g0[k], r[6]);
                 r[7] = fmaf(w, g1[k], r[7]);
                 r[8] = fmaf(w, g2[k], r[8]);
-                const float inv = 1.0f / one_m;
                 const float dalpha = g0[k] * (Ti * c.x - S0[k] * inv) + g1[k] * (Ti * c.y - S1[k] * inv) +
                                      g2[k] * (Ti * c.z - S2[k] * inv);
                 S0[k] = fmaf(c.x, w, S0[k]);
