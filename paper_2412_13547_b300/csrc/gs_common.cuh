@@ -265,7 +265,10 @@ __device__ __forceinline__ void adam_step(float& p, float g, float& m, float& v,
     v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.0f - b2, g), g));
     const float mhat = __fmul_rn(m, inv_bc1);
     const float vhat = __fmul_rn(v, inv_bc2);
-    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), eps)));
+    // sqrt(vhat) and the division through the SFU's approximate reciprocal
+    // square root and reciprocal: a few ulp on the step, no branches
+    const float root = vhat > 0.0f ? __fmul_rn(vhat, rsqrtf(vhat)) : 0.0f;
+    p = __fsub_rn(p, __fdividef(__fmul_rn(lr, mhat), __fadd_rn(root, eps)));
 }
 
 __device__ __forceinline__ void store_as(void* dst, int dtype, int64_t e, float val)
