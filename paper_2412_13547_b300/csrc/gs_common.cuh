@@ -131,14 +131,15 @@ __device__ __forceinline__ ff ff_dot3_add(float a0, float b0, float a1, float b1
     return acc;
 }
 
-// (a.hi + a.lo) / (b.hi + b.lo) as float-float
-__device__ __forceinline__ ff ff_div(ff a, ff b)
+// a / b as float-float given rb ~ 1 / b.hi (a few ulp): the leading quotient's
+// remainder is exact through the FMA, so the pair stays accurate to ~2^-46.
+__device__ __forceinline__ ff ff_div_rcp(ff a, ff b, float rb)
 {
-    float q = __fdiv_rn(a.hi, b.hi);
-    float r = __fmaf_rn(-q, b.hi, a.hi);  // exact remainder of the leading term
+    float q = __fmul_rn(a.hi, rb);
+    float r = __fmaf_rn(-q, b.hi, a.hi);
     r = __fadd_rn(r, __fsub_rn(a.lo, __fmul_rn(q, b.lo)));
-    float q2 = __fdiv_rn(r, b.hi);
-    return fast_two_sum(q, q2);
+    float q2 = __fmul_rn(r, rb);
+    return two_sum(q, q2);
 }
 
 // f * (u.hi + u.lo) + c as float-float (f, c exact floats)

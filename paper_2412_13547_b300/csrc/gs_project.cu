@@ -114,12 +114,14 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     P.rect = make_int4(0, 0, -1, -1);
     P.tiles = 0;
     P.radius = 0;
-    P.opacity = 1.0f / (1.0f + expf(-logit));
+    // the SFU's exp, reciprocal and reciprocal square root (a few ulp) throughout:
+    // no IEEE division or square-root sequences with their slow-path branches
+    P.opacity = __fdividef(1.0f, 1.0f + __expf(-logit));
 #pragma unroll
-    for (int j = 0; j < 3; ++j) P.s[j] = expf(log_scale[j]);
+    for (int j = 0; j < 3; ++j) P.s[j] = __expf(log_scale[j]);
     float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
     if (!(qn2 > 0.0f)) return;
-    P.inv_qnorm = 1.0f / sqrtf(qn2);
+    P.inv_qnorm = rsqrtf(qn2);
     P.qn[0] = q.x * P.inv_qnorm; P.qn[1] = q.y * P.inv_qnorm;
     P.qn[2] = q.z * P.inv_qnorm; P.qn[3] = q.w * P.inv_qnorm;
     quat_rot(P.qn[0], P.qn[1], P.qn[2], P.qn[3], P.R);
@@ -134,7 +136,8 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     ff tz = ff_dot3_add(cam.R[6], mean[0], cam.R[7], mean[1], cam.R[8], mean[2], cam.T[2]);
     P.tz = tz.hi;
     if (!(P.tz > cam.z_near)) return;
-    ff u = ff_div(tx, tz), v = ff_div(ty, tz);
+    const float itz = __fdividef(1.0f, tz.hi);
+    ff u = ff_div_rcp(tx, tz, itz), v = ff_div_rcp(ty, tz, itz);
     P.u = u.hi;
     P.v = v.hi;
     P.clamp_x = fabsf(P.u) > cam.lim_x;
@@ -143,8 +146,8 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     P.vc = P.clamp_y ? copysignf(cam.lim_y, P.v) : P.v;
 
     // Tm = J W with J = [[fx/tz, 0, -fx uc/tz], [0, fy/tz, -fy vc/tz]]
-    float j00 = cam.fx / P.tz, j02 = -cam.fx * P.uc / P.tz;
-    float j11 = cam.fy / P.tz, j12 = -cam.fy * P.vc / P.tz;
+    float j00 = cam.fx * itz, j02 = -cam.fx * P.uc * itz;
+    float j11 = cam.fy * itz, j12 = -cam.fy * P.vc * itz;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         P.Tm[j] = j00 * cam.R[j] + j02 * cam.R[6 + j];
@@ -169,14 +172,15 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     P.c = c0 + kLowPass;
     P.det = det0 + kLowPass * (a0 + c0) + kLowPass * kLowPass;
     if (!(P.det > 0.0f)) return;
-    float inv_det = 1.0f / P.det;
+    float inv_det = __fdividef(1.0f, P.det);
     P.A = P.c * inv_det;
     P.B = -P.b * inv_det;
     P.C = P.a * inv_det;
     float hd = 0.5f * (P.a - P.c);
     float disc = hd * hd + P.b * P.b;  // = mid^2 - det, without cancellation
-    float lam = 0.5f * (P.a + P.c) + sqrtf(fmaxf(disc, kDiscFloor));
-    P.radius = (int)ceilf(3.0f * sqrtf(lam));
+    const float dfl = fmaxf(disc, kDiscFloor);
+    float lam = 0.5f * (P.a + P.c) + dfl * rsqrtf(dfl);
+    P.radius = (int)ceilf(3.0f * (lam * rsqrtf(lam)));
 
     P.px = ff_affine(cam.fx, u, cam.cx);
     P.py = ff_affine(cam.fy, v, cam.cy);
@@ -205,7 +209,7 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
 
     // view-dependent colour
     float vx = mean[0] - cam.ccx, vy = mean[1] - cam.ccy, vz = mean[2] - cam.ccz;
-    P.inv_vlen = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+    P.inv_vlen = rsqrtf(vx * vx + vy * vy + vz * vz);
     P.dir[0] = vx * P.inv_vlen; P.dir[1] = vy * P.inv_vlen; P.dir[2] = vz * P.inv_vlen;
     float Y[16];
     sh_basis(DEG, P.dir[0], P.dir[1], P.dir[2], Y);
@@ -351,7 +355,7 @@ __device__ __forceinline__ void project_bwd_one(const Cam& cam, const Proj& P, c
     float dJ02 = dTm[0] * cam.R[6] + dTm[1] * cam.R[7] + dTm[2] * cam.R[8];
     float dJ11 = dTm[3] * cam.R[3] + dTm[4] * cam.R[4] + dTm[5] * cam.R[5];
     float dJ12 = dTm[3] * cam.R[6] + dTm[4] * cam.R[7] + dTm[5] * cam.R[8];
-    const float tz = P.tz, itz = 1.0f / tz, itz2 = itz * itz;
+    const float tz = P.tz, itz = __fdividef(1.0f, tz), itz2 = itz * itz;
     float dt0 = 0.f, dt1 = 0.f, dt2 = 0.f;
     dt2 += -(dJ00 * cam.fx + dJ11 * cam.fy) * itz2;
     if (P.clamp_x) {
