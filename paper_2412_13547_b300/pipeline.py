@@ -308,7 +308,12 @@ class BatchTrainStep:
     def __init__(self, params: GaussianParams, cams, targets, d: int = 1, adam: AdamConfig = AdamConfig(),
                  bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
                  pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
-                 capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0):
+                 capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0,
+                 state=None):
+        """cams/targets: the views of the batch (any later batch given to
+        run(table=views_table(...)) must have no larger images). state: optional
+        dict of m, v (lists), pos_acc, col_acc, count and step_dev to continue
+        from instead of fresh moments and statistics."""
         if not 1 <= len(cams) <= R.MAX_VIEWS:
             raise ValueError(f"1..{R.MAX_VIEWS} views per batch")
         dev = params.means.device
@@ -341,13 +346,14 @@ class BatchTrainStep:
         self.dl = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
         self.order = torch.zeros(sum(g[2] * g[3] for g in self.grid0), dtype=torch.int32, device=dev)
         # moments, device-side Adam step and densification statistics
-        self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
-        self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
-        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        st = state or {}
+        self.m = st.get("m") or [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.v = st.get("v") or [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
+        self.step_dev = st.get("step_dev", torch.zeros(1, dtype=torch.int32, device=dev))
         self.bias_dev = torch.zeros(2, device=dev)
-        self.pos_acc = torch.zeros(n, device=dev)
-        self.col_acc = torch.zeros(n, device=dev)
-        self.vis_count = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.pos_acc = st.get("pos_acc", torch.zeros(n, device=dev))
+        self.col_acc = st.get("col_acc", torch.zeros(n, device=dev))
+        self.vis_count = st.get("count", torch.zeros(n, dtype=torch.int32, device=dev))
         self.phase = 0
         self._tables = {}
         self.graphs = {}
@@ -376,11 +382,20 @@ class BatchTrainStep:
             best = [max(a, b) for a, b in zip(best, k)]
         return [int(math.ceil(k * headroom)) + 1024 for k in best]
 
-    def table(self, phase: int, project_only: bool = False) -> R.ViewTable:
+    def views_table(self, cams, targets, phase: int = 0) -> R.ViewTable:
+        """A table for other views of the same count and no larger images
+        (e.g. a fresh draw of training cameras), not cached."""
+        if len(cams) != self.V or len(targets) != self.V:
+            raise ValueError(f"{self.V} views per batch")
+        return self.table(phase, cams=list(cams), targets=[t.contiguous() for t in targets])
+
+    def table(self, phase: int, project_only: bool = False, cams=None, targets=None) -> R.ViewTable:
         key = (phase % self.phases, project_only)
-        if key not in self._tables:
+        if cams is not None or key not in self._tables:
+            cams = self.cams if cams is None else cams
+            targets = self.targets if targets is None else targets
             views = []
-            for i, c in enumerate(self.cams):
+            for i, c in enumerate(cams):
                 dil = self._dil(key[0], i)
                 w_ds, h_ds, tx, ty = R.gs_grid(c, dil)
                 v = R.View(c, dil, splats=self.splats[i], radii=self.radii[i], rects=self.rects[i],
@@ -392,9 +407,12 @@ class BatchTrainStep:
                     v.t_final = self.t_final[i].view(-1)[:P]
                     v.last = self.last[i].view(-1)[:P]
                     v.dl_dimg = self.dl[i].view(-1)[:3 * P]
-                    v.target, v.loss = self.targets[i], self.loss[i:i + 1]
+                    v.target, v.loss = targets[i], self.loss[i:i + 1]
                 views.append(v)
-            self._tables[key] = R.ViewTable(views)
+            t = R.ViewTable(views)
+            if cams is not self.cams:
+                return t
+            self._tables[key] = t
         return self._tables[key]
 
     def _project(self, t: R.ViewTable):
@@ -402,9 +420,9 @@ class BatchTrainStep:
         R.gs_project_batch(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, t)
 
     # -- the step ---------------------------------------------------------------
-    def render_pass(self, phase: int, counts: bool = False):
+    def render_pass(self, phase: int, counts: bool = False, table=None):
         """Everything up to the 2D gradients of every view (no parameter update)."""
-        t = self.table(phase)
+        t = self.table(phase) if table is None else table
         self._project(t)
         for i, v in enumerate(t.views):
             tx, ty = R.gs_bin_grid(v.cam, v.dil)
@@ -419,20 +437,21 @@ class BatchTrainStep:
         R.gs_loss_l1_batch(t)
         R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True, pixels_per_thread=self.ppt)
 
-    def optimize(self, phase: int):
+    def optimize(self, phase: int, table=None):
         p, a = self.p, self.adam
         lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
         shadow = p.sh_store if p.sh_store.data_ptr() != p.sh.data_ptr() else None
         stats = (self.pos_acc, self.col_acc, self.vis_count) if self.densify else (None, None, None)
         R.gs_adam_advance(self.step_dev, a.beta1, a.beta2, self.bias_dev)
         R.gs_project_bwd_adam_batch(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, 1, p.sh_store,
-                                    self.table(phase), sparse=self.sparse, sh_shadow=shadow, pos_acc=stats[0],
+                                    self.table(phase) if table is None else table, sparse=self.sparse,
+                                    sh_shadow=shadow, pos_acc=stats[0],
                                     col_acc=stats[1], count=stats[2], bias_dev=self.bias_dev)
 
-    def run(self, phase: int, counts: bool = False):
-        self.render_pass(phase, counts)
+    def run(self, phase: int, counts: bool = False, table=None):
+        self.render_pass(phase, counts, table)
         if self.optimize_step:
-            self.optimize(phase)
+            self.optimize(phase, table)
 
     def capture(self):
         """Record the step of every phase into a CUDA graph (each phase is run

@@ -237,6 +237,32 @@ def workload_batch(n=2_000_000, resolutions=BATCH_RESOLUTIONS, with_targets=True
     return scene, cams, targets
 
 
+def fit_workload(n_gt=2_000_000, n_init=100_000, n_train=200, n_eval=10, width=3840, height=2160, index=4):
+    """A scene to fit: a clustered SH-3 ground truth (the hd distribution),
+    training and held-out cameras on a jittered ring/hemisphere (radius
+    2.6 +- U(0.1), elevation U[0, 60] degrees, look-at jitter N(0, 0.02)), and
+    an initialisation of n_init points drawn from the ground-truth means with
+    N(0, 0.02) noise, log-scale -4.5, random rotations, opacity 0.1 and the DC
+    colour of the Gaussian each point was drawn from plus N(0, 0.05) noise."""
+    gt = cluster_scene(n_gt, index=index)
+    _, rng_cam, rng_init = streams(index)
+    cams = []
+    for _ in range(n_train + n_eval):
+        r = 2.6 + rng_cam.uniform(-0.1, 0.1)
+        eye = orbit_eye(r, rng_cam.uniform(0.0, 360.0), rng_cam.uniform(0.0, 60.0))
+        cams.append(look_at(eye, target=tuple(rng_cam.normal(0.0, 0.02, 3)), width=width, height=height))
+    src = rng_init.integers(0, n_gt, n_init)
+    k = gt.sh.shape[1]
+    sh = np.zeros((n_init, k, 3), np.float32)
+    sh[:, 0, :] = gt.sh[src, 0, :] + rng_init.normal(0.0, 0.05, (n_init, 3))
+    init = dict(means=(gt.means[src] + rng_init.normal(0.0, 0.02, (n_init, 3))).astype(np.float32),
+                log_scales=np.full((n_init, 3), -4.5, np.float32),
+                quats=_unit_quats(rng_init, n_init),
+                opacity_logits=np.full(n_init, math.log(0.1 / 0.9), np.float32),
+                sh=sh)
+    return gt, init, cams[:n_train], cams[n_train:]
+
+
 def rotating_offset(step: int, d: int):
     """Seeded rotation through the d*d offsets: step -> (ox, oy)."""
     k = step % (d * d)

@@ -212,3 +212,12 @@ def test_prune_keeps_order():
     assert od.prune_keep(p["opacity_logits"], -1.5).tolist() == [0, 1, 2]
     assert od.prune_keep(p["opacity_logits"], -1.5, p["log_scales"], math.log(0.25)).tolist() == [0, 2]
     assert od.prune_keep(p["opacity_logits"], 5.0).tolist() == []
+
+
+def test_time_to_psnr_interpolates_between_evaluations():
+    from paper_2412_13547_b300.fit import time_to_psnr
+    hist = [dict(seconds=0.0, psnr=20.0), dict(seconds=10.0, psnr=24.0), dict(seconds=20.0, psnr=26.0)]
+    assert time_to_psnr(hist, 20.0) == 0.0
+    assert time_to_psnr(hist, 22.0) == pytest.approx(5.0)
+    assert time_to_psnr(hist, 25.0) == pytest.approx(15.0)
+    assert time_to_psnr(hist, 27.0) is None
