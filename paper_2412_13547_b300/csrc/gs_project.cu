@@ -104,12 +104,61 @@ struct Proj {
     int tiles;
 };
 
+// View-dependent colour (Sec. 3: SH coefficients): the unit direction from the
+// camera centre, its inverse distance and rgb_raw = sum_k Y_k(dir) sh_k + 0.5
+// (the colour is max(0, rgb_raw)).
 template <int DEG>
-__device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, const float* mean,
-                                            const float* log_scale, float4 q, float logit,
-                                            const float (&sh)[16][3], Proj& P)
+__device__ __forceinline__ void sh_colour(const Cam& cam, const float* mean, const float (&sh)[16][3], float* dir,
+                                          float& inv_vlen, float* rgb_raw)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
+    float vx = mean[0] - cam.ccx, vy = mean[1] - cam.ccy, vz = mean[2] - cam.ccz;
+    inv_vlen = rsqrtf(vx * vx + vy * vy + vz * vz);
+    dir[0] = vx * inv_vlen; dir[1] = vy * inv_vlen; dir[2] = vz * inv_vlen;
+    float Y[16];
+    sh_basis(DEG, dir[0], dir[1], dir[2], Y);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
+        rgb_raw[ch] = acc + 0.5f;
+    }
+}
+
+// Backward of sh_colour for dL/drgb = grgb (zero where the colour was clamped):
+// dL/dsh_k = Y_k grgb into gsh[3k + ch] (written, or added when ACC), and the
+// mean's gradient through the direction into gm.
+template <int DEG, bool ACC>
+__device__ __forceinline__ void sh_colour_bwd(const float* dir, float inv_vlen, const float* rgb_raw,
+                                              const float (&c)[16][3], float g0, float g1, float g2, float* gsh,
+                                              float* gm)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float grgb[3] = {rgb_raw[0] > 0.0f ? g0 : 0.0f, rgb_raw[1] > 0.0f ? g1 : 0.0f,
+                           rgb_raw[2] > 0.0f ? g2 : 0.0f};
+    float Y[16];
+    sh_basis(DEG, dir[0], dir[1], dir[2], Y);
+    float wsh[16];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        wsh[k] = grgb[0] * c[k][0] + grgb[1] * c[k][1] + grgb[2] * c[k][2];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = ACC ? gsh[3 * k + ch] + Y[k] * grgb[ch] : Y[k] * grgb[ch];
+    }
+    float gdx, gdy, gdz;
+    sh_basis_vjp(DEG, dir[0], dir[1], dir[2], wsh, gdx, gdy, gdz);
+    const float dd = gdx * dir[0] + gdy * dir[1] + gdz * dir[2];
+    gm[0] = (gdx - dir[0] * dd) * inv_vlen;
+    gm[1] = (gdy - dir[1] * dd) * inv_vlen;
+    gm[2] = (gdz - dir[2] * dd) * inv_vlen;
+}
+
+// Geometry of the projection: everything of project_one but the colour.
+template <int DEG>
+__device__ __forceinline__ void project_geometry(const Cam& cam, const Dil& dil, const float* mean,
+                                                 const float* log_scale, float4 q, float logit, Proj& P)
+{
     P.culled = true;
     P.rect = make_int4(0, 0, -1, -1);
     P.tiles = 0;
@@ -206,20 +255,15 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
     P.rect = make_int4(x0 >> dil.shift, y0 >> dil.shift, x1 >> dil.shift, y1 >> dil.shift);
     P.tiles = (P.rect.z - P.rect.x + 1) * (P.rect.w - P.rect.y + 1);
     P.culled = false;
+}
 
-    // view-dependent colour
-    float vx = mean[0] - cam.ccx, vy = mean[1] - cam.ccy, vz = mean[2] - cam.ccz;
-    P.inv_vlen = rsqrtf(vx * vx + vy * vy + vz * vz);
-    P.dir[0] = vx * P.inv_vlen; P.dir[1] = vy * P.inv_vlen; P.dir[2] = vz * P.inv_vlen;
-    float Y[16];
-    sh_basis(DEG, P.dir[0], P.dir[1], P.dir[2], Y);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
-        P.rgb_raw[ch] = acc + 0.5f;
-    }
+template <int DEG>
+__device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, const float* mean,
+                                            const float* log_scale, float4 q, float logit,
+                                            const float (&sh)[16][3], Proj& P)
+{
+    project_geometry<DEG>(cam, dil, mean, log_scale, q, logit, P);
+    if (!P.culled) sh_colour<DEG>(cam, mean, sh, P.dir, P.inv_vlen, P.rgb_raw);
 }
 
 // Projection of every Gaussian into every view of the batch. The warp stages
@@ -290,41 +334,19 @@ struct ParamGrad {
     float gm[3], gls[3];
     float4 gq;
     float glogit;
-    float gsh[16][3];
 };
 
-// Gradients of one visible Gaussian from its 2D gradient record (G0, G1, G2).
-template <int DEG>
-__device__ __forceinline__ void project_bwd_one(const Cam& cam, const Proj& P, const float (&c)[16][3],
-                                                float4 G0, float4 G1, float4 G2, ParamGrad& R)
+// Gradients of one visible Gaussian from its 2D gradient record (G0, G1):
+// everything but the colour (sh_colour_bwd), with R.gm starting from gm0 (the
+// mean's gradient through the view direction).
+__device__ __forceinline__ void project_bwd_one(const Cam& cam, const Proj& P, float4 G0, float4 G1,
+                                                const float* gm0, ParamGrad& R)
 {
-    constexpr int K = (DEG + 1) * (DEG + 1);
     const float gpx = G0.x, gpy = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y;
-    float grgb[3] = {G1.z, G1.w, G2.x};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) R.gm[j] = 0.0f;
+    for (int j = 0; j < 3; ++j) R.gm[j] = gm0[j];
     // opacity = sigmoid(logit)
     R.glogit = gop * P.opacity * (1.0f - P.opacity);
-
-    // colour: SH coefficients and the view direction
-    float Y[16];
-    sh_basis(DEG, P.dir[0], P.dir[1], P.dir[2], Y);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-        if (!(P.rgb_raw[ch] > 0.0f)) grgb[ch] = 0.0f;
-    float wsh[16];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        wsh[k] = grgb[0] * c[k][0] + grgb[1] * c[k][1] + grgb[2] * c[k][2];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) R.gsh[k][ch] = Y[k] * grgb[ch];
-    }
-    float gdx, gdy, gdz;
-    sh_basis_vjp(DEG, P.dir[0], P.dir[1], P.dir[2], wsh, gdx, gdy, gdz);
-    float dd = gdx * P.dir[0] + gdy * P.dir[1] + gdz * P.dir[2];
-    R.gm[0] += (gdx - P.dir[0] * dd) * P.inv_vlen;
-    R.gm[1] += (gdy - P.dir[1] * dd) * P.inv_vlen;
-    R.gm[2] += (gdz - P.dir[2] * dd) * P.inv_vlen;
 
     // conic = inverse of Sigma': dL/dSigma' = -K Gk K, Gk = [[gA, gB/2], [gB/2, gC]]
     float k00 = P.A * gA + P.B * 0.5f * gB, k01 = P.A * 0.5f * gB + P.B * gC;
@@ -462,8 +484,10 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
     }
     const float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
     densify_one(g, tiles_touched, G0, G1, G2, pos_acc, col_acc, count);
+    float gm_dir[3];
+    sh_colour_bwd<DEG, false>(P.dir, P.inv_vlen, P.rgb_raw, c, G1.z, G1.w, G2.x, gsh, gm_dir);
     ParamGrad R;
-    project_bwd_one<DEG>(cam, P, c, G0, G1, G2, R);
+    project_bwd_one(cam, P, G0, G1, gm_dir, R);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         d_means[3 * (int64_t)g + j] = R.gm[j];
@@ -471,10 +495,6 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
     }
     d_quats[g] = R.gq;
     d_logits[g] = R.glogit;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = R.gsh[k][ch];
 }
 
 // ---------------------------------------------------------------------------
@@ -572,38 +592,31 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     }
 }
 
-// Projection backward of one Gaussian in one view, written (ACC false) or
-// added (ACC true) into the gradient rows. False when the view culls it.
-template <int DEG, bool ACC>
+// Projection backward of one Gaussian in one view, added into the gradient
+// rows (the batched form; the one-view form takes the colour part first).
+// False when the view culls it.
+template <int DEG>
 __device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const float* mean, const float* ls,
                                                 float4 q, float logit, const float (&c)[16][3], float* grow,
                                                 float* gshrow, float4& gq, float& glogit, float* pos_acc,
                                                 float* col_acc, int* count)
 {
-    constexpr int K = (DEG + 1) * (DEG + 1);
     Proj P;
     project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
     if (P.culled) return false;
     const float4 G0 = V.grad2d[3 * (int64_t)g], G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
     densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
+    float gm_dir[3];
+    sh_colour_bwd<DEG, true>(P.dir, P.inv_vlen, P.rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
     ParamGrad R;
-    project_bwd_one<DEG>(V.cam, P, c, G0, G1, G2, R);
+    project_bwd_one(V.cam, P, G0, G1, gm_dir, R);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        grow[j] = ACC ? grow[j] + R.gm[j] : R.gm[j];
-        grow[3 + j] = ACC ? grow[3 + j] + R.gls[j] : R.gls[j];
+        grow[j] += R.gm[j];
+        grow[3 + j] += R.gls[j];
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gshrow[3 * k + ch] = ACC ? gshrow[3 * k + ch] + R.gsh[k][ch] : R.gsh[k][ch];
-    if (ACC) {
-        gq.x += R.gq.x; gq.y += R.gq.y; gq.z += R.gq.z; gq.w += R.gq.w;
-        glogit += R.glogit;
-    } else {
-        gq = R.gq;
-        glogit = R.glogit;
-    }
+    gq.x += R.gq.x; gq.y += R.gq.y; gq.z += R.gq.z; gq.w += R.gq.w;
+    glogit += R.glogit;
     return true;
 }
 
@@ -660,11 +673,32 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
             for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
             have_grad = true;
             for (int vi = 0; vi < b.nviews; ++vi)
-                fused_view_grad<DEG, true>(b.v[vi], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit, pos_acc,
-                                           col_acc, count);
+                fused_view_grad<DEG>(b.v[vi], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit, pos_acc, col_acc,
+                                     count);
         } else {
-            have_grad = fused_view_grad<DEG, false>(b.v[0], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit,
-                                                    pos_acc, col_acc, count);
+            // the colour part first, so the SH coefficients are dead before the geometry: a
+            // Gaussian the view culls was not rendered, its 2D gradient is zero and so is all this
+            const ViewDev& V = b.v[0];
+            const float4 G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
+            float dir[3], inv_vlen, rgb_raw[3], gm_dir[3];
+            sh_colour<DEG>(V.cam, mean, c, dir, inv_vlen, rgb_raw);
+            sh_colour_bwd<DEG, false>(dir, inv_vlen, rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
+            have_grad = true;
+            Proj P;
+            project_geometry<DEG>(V.cam, V.dil, mean, ls, q, logit, P);
+            if (!P.culled) {
+                const float4 G0 = V.grad2d[3 * (int64_t)g];
+                densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
+                ParamGrad R;
+                project_bwd_one(V.cam, P, G0, G1, gm_dir, R);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    grow[j] = R.gm[j];
+                    grow[3 + j] = R.gls[j];
+                }
+                gq = R.gq;
+                glogit = R.glogit;
+            }
         }
     }
     if (!have_grad) {
