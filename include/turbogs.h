@@ -215,8 +215,10 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
  * Outputs (device): img (h_ds x w_ds x 3), t_final (h_ds x w_ds), last
  *   (h_ds x w_ds: position + 1, in the binning tile's list, of the last
  *   blended entry, 0 if none),
- *   counts (nullable, 2 x uint64 accumulated with +=: list entries evaluated
- *   and entries blended; the caller zeroes it).
+ *   counts (nullable, 3 x uint64 accumulated with +=: list entries evaluated,
+ *   entries blended, and entries the backward replays, i.e. the sum over
+ *   pixels of the own-list position of their last blended entry; the caller
+ *   zeroes it).
  * pixels_per_thread: launch shape, not semantics -- each thread of the
  *   tile's CTA handles this many pixels: 0 = the library default, else 1 or 2
  *   for tile 8, 1, 2 or 4 for tile 16, 2 or 4 for tile 32 (whole warps, at
