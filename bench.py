@@ -273,13 +273,17 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     rows["project"] = ("hbm", params_b + n * (48 + 4 + 16 + 4))
     # binning floor: one read and one write of (key, value) per pair plus the per-Gaussian keys/rects
     rows["bin_sort"] = ("hbm", 24.0 * k + n * (48 + 16 + 4 + 8))
-    # blend forward: ~20 FP32 flops per evaluated (pixel, entry)
-    rows["render_fwd"] = ("alu", 20.0 * res["evaluated_per_step"])
+    # blend forward: 12 FP32 operations per evaluated (pixel, entry) -- the offset, the
+    # exponent (7), its scaling for the SFU exp, alpha, the clamp and the gate -- and 7 more
+    # per blended one (transmittance, weight, three colour FMAs, the stop test)
+    rows["render_fwd"] = ("alu", 12.0 * res["evaluated_per_step"] + 7.0 * res["blended_per_step"])
     rows["loss"] = ("hbm", 36.0 * step_pixels)
     # zeroing of the 2D-gradient buffer the backward blend accumulates into
     rows["zero_grad2d"] = ("hbm", 48.0 * n)
-    # blend backward: ~45 FP32 flops per replayed (pixel, entry)
-    rows["render_bwd"] = ("alu", 45.0 * res["replayed_per_step"])
+    # blend backward: the same 12 gate operations per replayed (pixel, entry) and 41 per
+    # contributing one (the replayed blends: transmittance recovery, the colour, alpha,
+    # exponent, conic and centre gradients)
+    rows["render_bwd"] = ("alu", 12.0 * res["replayed_per_step"] + 41.0 * res["blended_per_step"])
     # projection backward + densification statistics + Adam, fused: parameters, moments and the
     # 2D record read, parameters and moments written, statistics read-modify-written
     rows["project_bwd_adam"] = ("hbm", 3 * params_b + n * 48 + 3 * n * 59 * 4 + n * (24 + 4))
