@@ -88,25 +88,36 @@ struct TileGeom {
     static constexpr int WCOLS = TILE / 8;       // warp blocks across the tile
 };
 
+// Bit w set when the gate box meets the pixel block of warp w (the blocks of
+// WarpBlock below): computed once per staged entry, so a warp walks only the
+// entries that can reach its pixels.
+template <int TILE, int PPT>
+__device__ __forceinline__ uint32_t warp_mask(float4 box, int d)
+{
+    using Geo = TileGeom<TILE, PPT>;
+    constexpr int NW = Geo::THREADS / 32;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int bx = w % Geo::WCOLS, by = w / Geo::WCOLS;
+        const float wx0 = (float)(d * bx * 8), wx1 = (float)(d * (bx * 8 + 7));
+        const float wy0 = (float)(d * by * Geo::WROWS), wy1 = (float)(d * (by * Geo::WROWS + Geo::WROWS - 1));
+        const bool miss = box.x > wx1 || box.y < wx0 || box.z > wy1 || box.w < wy0;
+        m |= miss ? 0u : (1u << w);
+    }
+    return m;
+}
+
 template <int TILE, int PPT>
 struct WarpBlock {
-    int lx, ly0;           // this thread's column and first row in the tile
-    float wx0, wx1, wy0, wy1;  // the warp's pixel block, tile-relative hr pixels
-    __device__ __forceinline__ WarpBlock(int tid, int d)
+    int lx, ly0;  // this thread's column and first row in the tile
+    __device__ __forceinline__ WarpBlock(int tid)
     {
         using Geo = TileGeom<TILE, PPT>;
         const int warp = tid >> 5, lane = tid & 31;
         const int bx = warp % Geo::WCOLS, by = warp / Geo::WCOLS;
         lx = bx * 8 + (lane & 7);
         ly0 = by * Geo::WROWS + (lane >> 3) * PPT;
-        wx0 = (float)(d * bx * 8);
-        wx1 = (float)(d * (bx * 8 + 7));
-        wy0 = (float)(d * by * Geo::WROWS);
-        wy1 = (float)(d * (by * Geo::WROWS + Geo::WROWS - 1));
-    }
-    __device__ __forceinline__ bool misses(float4 box) const
-    {
-        return box.x > wx1 || box.y < wx0 || box.z > wy1 || box.w < wy0;
     }
 };
 
@@ -124,7 +135,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
     constexpr int ROUND = NT < BATCH ? NT : BATCH;  // candidates per filtering round
     __shared__ float2 s_p[BATCH];
-    __shared__ float4 s_box[BATCH];
+    __shared__ uint32_t s_mask[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_pos[FILTER ? BATCH : 1];
@@ -132,7 +143,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     __shared__ unsigned long long s_cnt[3];
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
+    const WarpBlock<TILE, PPT> wb(threadIdx.x);
     const int u = tx * TILE + wb.lx;
     // hr origin of the tile and this thread's hr offsets from it (small exact floats)
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
@@ -165,7 +176,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 float2 p; float4 co, rgb;
                 load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
                 s_p[i] = p;
-                s_box[i] = gate_box(p, co);
+                s_mask[i] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
                 s_co[i] = co;
                 s_rgb[i] = rgb;
             }
@@ -187,52 +198,65 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     float2 p; float4 co, rgb;
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[cnt + r] = p;
-                    s_box[cnt + r] = gate_box(p, co);
+                    s_mask[cnt + r] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
                     s_co[cnt + r] = co;
                     s_rgb[cnt + r] = rgb;
                     s_pos[cnt + r] = e - rg.x + 1;
                 }
                 cnt += total;
                 next = (rg.y - next) < (uint32_t)ROUND ? rg.y : next + ROUND;
-            }
+                }
         }
         __syncthreads();
-        if (n_live > 0) {
-            for (int j = 0; j < cnt; ++j) {
-                // every live pixel visits the entry (the blend count of the method);
-                // a warp whose block lies outside the entry's gate box skips the arithmetic
-                if (wb.misses(s_box[j])) { n_eval += n_live; continue; }
-                const float2 p = s_p[j];
-                const float4 co = s_co[j];
-                const float dx = __fsub_rn(xr, p.x);
-                // the gates of all this thread's pixels first, free of branches so that
-                // their dependency chains interleave; then the blends, in pixel order
-                float alpha[PPT];
-                bool use[PPT];
+        {
+            // every live pixel visits every entry (the blend count of the method); a warp
+            // takes only the entries whose gate box meets its pixel block, 32 at a time.
+            // The loops below are uniform over the warp (they hold warp votes): a thread whose
+            // pixels are done keeps stepping with its warp and does nothing.
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                if (!__any_sync(0xffffffffu, n_live > 0)) break;
+                const int c1 = min(cnt, c0 + 32);
+                const bool hit = c0 + lane < c1 && ((s_mask[c0 + lane] >> warp) & 1u);
+                uint32_t m = __ballot_sync(0xffffffffu, hit);
+                int next_j = c0;  // entries before next_j are counted in n_eval
+                while (m != 0u) {
+                    const int j = c0 + __ffs(m) - 1;
+                    m &= m - 1u;
+                    n_eval += (uint32_t)n_live * (uint32_t)(j - next_j + 1);
+                    next_j = j + 1;
+                    const float2 p = s_p[j];
+                    const float4 co = s_co[j];
+                    const float dx = __fsub_rn(xr, p.x);
+                    // the gates of all this thread's pixels first, free of branches so that
+                    // their dependency chains interleave; then the blends, in pixel order
+                    float alpha[PPT];
+                    bool use[PPT];
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const float dy = __fsub_rn(yr[k], p.y);
-                    const float power = splat_power(dx, dy, co.x, co.y, co.z);
-                    alpha[k] = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
-                    use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
-                }
-                n_eval += n_live;
+                    for (int k = 0; k < PPT; ++k) {
+                        const float dy = __fsub_rn(yr[k], p.y);
+                        const float power = splat_power(dx, dy, co.x, co.y, co.z);
+                        alpha[k] = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
+                        use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
+                    }
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (!use[k]) continue;
-                    const float Tn = T[k] * (1.0f - alpha[k]);
-                    if (Tn < kTStop) { done[k] = true; --n_live; continue; }
-                    const float4 c = s_rgb[j];
-                    const float w = alpha[k] * T[k];
-                    C0[k] = fmaf(c.x, w, C0[k]);
-                    C1[k] = fmaf(c.y, w, C1[k]);
-                    C2[k] = fmaf(c.z, w, C2[k]);
-                    T[k] = Tn;
-                    last_pos[k] = FILTER ? s_pos[j] : start + j - rg.x + 1;
-                    last_own[k] = own_base + j + 1;
-                    ++n_blend;
+                    for (int k = 0; k < PPT; ++k) {
+                        if (!use[k]) continue;
+                        const float Tn = T[k] * (1.0f - alpha[k]);
+                        if (Tn < kTStop) { done[k] = true; --n_live; continue; }
+                        const float4 c = s_rgb[j];
+                        const float w = alpha[k] * T[k];
+                        C0[k] = fmaf(c.x, w, C0[k]);
+                        C1[k] = fmaf(c.y, w, C1[k]);
+                        C2[k] = fmaf(c.z, w, C2[k]);
+                        T[k] = Tn;
+                        last_pos[k] = FILTER ? s_pos[j] : start + j - rg.x + 1;
+                        last_own[k] = own_base + j + 1;
+                        ++n_blend;
+                    }
+                    if (!__any_sync(0xffffffffu, n_live > 0)) break;
                 }
-                if (n_live == 0) break;
+                n_eval += (uint32_t)n_live * (uint32_t)(c1 - next_j);
             }
         }
         own_base += (uint32_t)cnt;
@@ -334,7 +358,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
     constexpr int ROUND = NT < BATCH ? NT : BATCH;  // candidates per filtering round
     __shared__ float2 s_p[BATCH];
-    __shared__ float4 s_box[BATCH];
+    __shared__ uint32_t s_mask[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_id[BATCH];
@@ -344,7 +368,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     __shared__ uint32_t s_max_last;
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const WarpBlock<TILE, PPT> wb(threadIdx.x, dil.d);
+    const WarpBlock<TILE, PPT> wb(threadIdx.x);
     const int lane = threadIdx.x & 31;
     const int u = tx * TILE + wb.lx;
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
@@ -396,7 +420,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 float2 p; float4 co, rgb;
                 load_stage(splats, g, X0, Y0, p, co, rgb);
                 s_p[i] = p;
-                s_box[i] = gate_box(p, co);
+                s_mask[i] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
                 s_co[i] = co;
                 s_rgb[i] = rgb;
                 s_id[i] = g;
@@ -422,7 +446,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     float2 p; float4 co, rgb;
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[slot] = p;
-                    s_box[slot] = gate_box(p, co);
+                    s_mask[slot] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
                     s_co[slot] = co;
                     s_rgb[slot] = rgb;
                     s_id[slot] = g;
@@ -437,64 +461,78 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
             base = BATCH - filled;
         }
         __syncthreads();
-        for (int j = base + cnt - 1; j >= base; --j) {
-            const uint32_t pos = FILTER ? s_rel[j] : lo + (uint32_t)j;
-            if (pos >= warp_max) continue;  // past the last contributor of all this warp's pixels
-            if (wb.misses(s_box[j])) continue;
-            float r[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) r[k] = 0.0f;
-            bool contrib = false;
-            const float2 p = s_p[j];
-            const float4 co = s_co[j];
-            const float4 c = s_rgb[j];
-            const float dx = __fsub_rn(xr, p.x);
-            // gates of all this thread's pixels first (branch-free), then the replay
-            float dyk[PPT], Gk[PPT], ark[PPT];
-            bool use[PPT];
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                dyk[k] = __fsub_rn(yr[k], p.y);
-                const float power = splat_power(dx, dyk[k], co.x, co.y, co.z);
-                Gk[k] = __expf(power);
-                ark[k] = __fmul_rn(co.w, Gk[k]);  // as splat_alpha_raw
-                use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
+        const int warp = threadIdx.x >> 5;
+        // 32 entries at a time, from the top: those whose gate box meets this warp's pixel
+        // block and that lie before the last contributor of one of its pixels
+        for (int c1 = base + cnt; c1 > base; c1 -= 32) {
+            const int c0 = max(base, c1 - 32);
+            const int jj = c0 + lane;
+            bool hit = false;
+            if (jj < c1) {
+                const uint32_t pj = FILTER ? s_rel[jj] : lo + (uint32_t)jj;
+                hit = pj < warp_max && ((s_mask[jj] >> warp) & 1u);
             }
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            while (m != 0u) {
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const int j = c0 + bit;
+                const uint32_t pos = FILTER ? s_rel[j] : lo + (uint32_t)j;
+                float r[9];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (!use[k]) continue;
-                const float dy = dyk[k], G = Gk[k], a_raw = ark[k];
-                const float alpha = fminf(kAlphaMax, a_raw);
-                contrib = true;
-                // one SFU reciprocal serves both divisions by (1 - alpha) >= 0.01 (a few
-                // ulp per replayed entry, far inside the gradient tolerance)
-                const float inv = __fdividef(1.0f, 1.0f - alpha);
-                const float Ti = T[k] * inv;
-                const float w = alpha * Ti;
-                r[6] = fmaf(w, g0[k], r[6]);
-                r[7] = fmaf(w, g1[k], r[7]);
-                r[8] = fmaf(w, g2[k], r[8]);
-                const float dalpha = g0[k] * (Ti * c.x - S0[k] * inv) + g1[k] * (Ti * c.y - S1[k] * inv) +
-                                     g2[k] * (Ti * c.z - S2[k] * inv);
-                S0[k] = fmaf(c.x, w, S0[k]);
-                S1[k] = fmaf(c.y, w, S1[k]);
-                S2[k] = fmaf(c.z, w, S2[k]);
-                T[k] = Ti;
-                if (a_raw < kAlphaMax) {
-                    const float dpower = a_raw * dalpha;
-                    r[5] = fmaf(G, dalpha, r[5]);
-                    r[2] = fmaf(-0.5f * dx * dx, dpower, r[2]);
-                    r[3] = fmaf(-dx * dy, dpower, r[3]);
-                    r[4] = fmaf(-0.5f * dy * dy, dpower, r[4]);
-                    r[0] = fmaf(dpower, co.x * dx + co.y * dy, r[0]);
-                    r[1] = fmaf(dpower, co.z * dy + co.y * dx, r[1]);
+                for (int k = 0; k < 9; ++k) r[k] = 0.0f;
+                bool contrib = false;
+                const float2 p = s_p[j];
+                const float4 co = s_co[j];
+                const float4 c = s_rgb[j];
+                const float dx = __fsub_rn(xr, p.x);
+                // gates of all this thread's pixels first (branch-free), then the replay
+                float dyk[PPT], Gk[PPT], ark[PPT];
+                bool use[PPT];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    dyk[k] = __fsub_rn(yr[k], p.y);
+                    const float power = splat_power(dx, dyk[k], co.x, co.y, co.z);
+                    Gk[k] = __expf(power);
+                    ark[k] = __fmul_rn(co.w, Gk[k]);  // as splat_alpha_raw
+                    use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                int comp;
-                const float z = warp_sum9(r, lane, comp);
-                if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], z);
-            }
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!use[k]) continue;
+                    const float dy = dyk[k], G = Gk[k], a_raw = ark[k];
+                    const float alpha = fminf(kAlphaMax, a_raw);
+                    contrib = true;
+                    // one SFU reciprocal serves both divisions by (1 - alpha) >= 0.01 (a few
+                    // ulp per replayed entry, far inside the gradient tolerance)
+                    const float inv = __fdividef(1.0f, 1.0f - alpha);
+                    const float Ti = T[k] * inv;
+                    const float w = alpha * Ti;
+                    r[6] = fmaf(w, g0[k], r[6]);
+                    r[7] = fmaf(w, g1[k], r[7]);
+                    r[8] = fmaf(w, g2[k], r[8]);
+                    const float dalpha = g0[k] * (Ti * c.x - S0[k] * inv) + g1[k] * (Ti * c.y - S1[k] * inv) +
+                                         g2[k] * (Ti * c.z - S2[k] * inv);
+                    S0[k] = fmaf(c.x, w, S0[k]);
+                    S1[k] = fmaf(c.y, w, S1[k]);
+                    S2[k] = fmaf(c.z, w, S2[k]);
+                    T[k] = Ti;
+                    if (a_raw < kAlphaMax) {
+                        const float dpower = a_raw * dalpha;
+                        r[5] = fmaf(G, dalpha, r[5]);
+                        r[2] = fmaf(-0.5f * dx * dx, dpower, r[2]);
+                        r[3] = fmaf(-dx * dy, dpower, r[3]);
+                        r[4] = fmaf(-0.5f * dy * dy, dpower, r[4]);
+                        r[0] = fmaf(dpower, co.x * dx + co.y * dy, r[0]);
+                        r[1] = fmaf(dpower, co.z * dy + co.y * dx, r[1]);
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    int comp;
+                    const float z = warp_sum9(r, lane, comp);
+                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], z);
+                }
+        }
         }
         __syncthreads();
         for (int i = base + (int)threadIdx.x; i < base + cnt; i += NT) {
