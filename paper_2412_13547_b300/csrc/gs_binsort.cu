@@ -404,18 +404,27 @@ __global__ void k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint
     SS[(int64_t)blockIdx.y * Cc + c] = sum;
 }
 
+// One warp per column: exclusive scan of the column's nsb segment sums in
+// place (32 segments per step), the column total into total[c].
 __global__ void k_col_totals(int nsb, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
                              const int64_t* __restrict__ d_K, int64_t cap)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Cc || overflow(d_K, cap)) return;
+    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
     uint32_t run = 0;
-    for (int b = 0; b < nsb; ++b) {
-        const uint32_t x = SS[(int64_t)b * Cc + c];
-        SS[(int64_t)b * Cc + c] = run;
-        run += x;
+    for (int b0 = 0; b0 < nsb; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t x = b < nsb ? SS[(int64_t)b * Cc + c] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (b < nsb) SS[(int64_t)b * Cc + c] = run + inc - x;
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    total[c] = run;
+    if (lane == 0) total[c] = run;
 }
 
 // Single block: exclusive scan of x[0..len) -> start; the sum -> *sum (nullable).
@@ -809,7 +818,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
     const dim3 g1((TY + 255) / 256, nsb1);
     k_col_segsum<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, 1, num_pairs, capacity);
-    k_col_totals<<<(TY + 255) / 256, 256, 0, st>>>(nsb1, TY, w.SS1, w.rowlen, num_pairs, capacity);
+    k_col_totals<<<(TY * 32 + 255) / 256, 256, 0, st>>>(nsb1, TY, w.SS1, w.rowlen, num_pairs, capacity);
     k_scan_small<<<1, 1024, 0, st>>>(TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
     k_col_base<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, 1, num_pairs, capacity);
     k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, tiles_touched, rc, TX, TY, w.M1,
@@ -830,7 +839,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
     const dim3 g2((T + 255) / 256, nsb2);
     k_col_segsum<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, TX, num_pairs, capacity);
-    k_col_totals<<<(T + 255) / 256, 256, 0, st>>>(nsb2, T, w.SS2, w.tcount, num_pairs, capacity);
+    k_col_totals<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(nsb2, T, w.SS2, w.tcount, num_pairs,
+                                                                      capacity);
     k_scan_small<<<1, 1024, 0, st>>>(T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
     k_col_base<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, TX, num_pairs, capacity);
     k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
