@@ -6,7 +6,8 @@
 // (key, id): every tile's list of Gaussian ids, front to back. It is built
 // without materialising or sorting pair keys:
 //   1. the Gaussians are sorted by (depth bits, id) with a stable LSD radix
-//      sort of 32-bit keys (N items, 4 passes);
+//      sort of 32-bit keys (N items, 4 passes; culled Gaussians carry the
+//      all-ones key, so the sorted keys also tell which entries are visible);
 //   2. a two-level counting scatter (rows, then tiles within a row) writes each
 //      id straight into its final slot (see the section comment below).
 // The pair count K stays on the device; every kernel checks it against the
@@ -27,10 +28,10 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kItemsPerThread = 16;
-constexpr int kTileItems = kSortThreads * kItemsPerThread;  // 4096
+constexpr int kItemsPerThread = 8;
+constexpr int kTileItems = kSortThreads * kItemsPerThread;  // 2048
 constexpr int kRadixBins = 256;
-constexpr int kMaxSortBlocks = 148 * 4;
+constexpr int kMaxSortBlocks = 148 * 4;  // one wave of the downsweep (64 registers: 4 CTAs per SM)
 
 __device__ __forceinline__ int64_t sort_count(const int64_t* d_num, int64_t cap)
 {
@@ -138,7 +139,7 @@ k_radix_scan(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ totals)
     if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                   uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                   const int64_t* __restrict__ d_num, int64_t cap, int shift, uint32_t mask,
@@ -168,26 +169,29 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
     for (int64_t tile = begin; tile < end; tile += kTileItems) {
         for (int i = threadIdx.x; i < kSortWarps * kRadixBins; i += kSortThreads) (&s_warp[0][0])[i] = 0u;
         __syncthreads();
-        uint32_t k[kItemsPerThread], v[kItemsPerThread], dg[kItemsPerThread], rk[kItemsPerThread];
+        // per item: its key, value and rank among the warp's items of its digit (the digit
+        // is recomputed from the key where needed, to keep the registers for 4 CTAs per SM)
+        uint32_t k[kItemsPerThread], v[kItemsPerThread], rk[kItemsPerThread];
         const int64_t wbase = tile + warp * (32 * kItemsPerThread);
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
             int64_t idx = wbase + j * 32 + lane;
             bool ok = idx < end;
             k[j] = ok ? keys_in[idx] : 0u;
-            v[j] = ok ? vals_in[idx] : 0u;
-            dg[j] = ok ? ((k[j] >> shift) & mask) : 0xffffffffu;
+            v[j] = ok ? (vals_in != nullptr ? vals_in[idx] : (uint32_t)idx) : 0u;
         }
         // stable rank within the warp: rounds in order, lanes in order
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
-            uint32_t peers = __match_any_sync(0xffffffffu, dg[j]);
+            const bool ok = wbase + j * 32 + lane < end;
+            const uint32_t dg = ok ? ((k[j] >> shift) & mask) : 0xffffffffu;
+            uint32_t peers = __match_any_sync(0xffffffffu, dg);
             uint32_t pre = __popc(peers & lt_mask);
             int leader = __ffs(peers) - 1;
-            uint32_t basec = (dg[j] != 0xffffffffu) ? s_warp[warp][dg[j]] : 0u;
+            uint32_t basec = ok ? s_warp[warp][dg] : 0u;
             rk[j] = basec + pre;
             __syncwarp();
-            if (lane == leader && dg[j] != 0xffffffffu) s_warp[warp][dg[j]] = basec + __popc(peers);
+            if (lane == leader && ok) s_warp[warp][dg] = basec + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -209,8 +213,9 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
-            if (dg[j] == 0xffffffffu) continue;
-            uint32_t lp = s_start[dg[j]] + s_warp[warp][dg[j]] + rk[j];
+            if (wbase + j * 32 + lane >= end) continue;
+            const uint32_t dg = (k[j] >> shift) & mask;
+            uint32_t lp = s_start[dg] + s_warp[warp][dg] + rk[j];
             s_keys[lp] = k[j];
             s_vals[lp] = v[j];
         }
@@ -231,6 +236,7 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
 
 struct SortBufs {
     uint32_t *keys0, *vals0, *keys1, *vals1;
+    bool iota_vals;  // vals0 holds 0, 1, 2, ... on entry: the first pass makes them instead of reading them
 };
 
 // Sorts (keys0, vals0) by bits [0, bits) of the keys; the result lands in
@@ -248,7 +254,8 @@ int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, u
         uint32_t mask = (nb >= 32) ? 0xffffffffu : ((1u << nb) - 1u);
         k_radix_upsweep<<<G, kSortThreads, 0, st>>>(ki, d_num, cap, shift, mask, hist);
         k_radix_scan<<<kRadixBins, kSortThreads, 0, st>>>(hist, G, totals);
-        k_radix_downsweep<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_num, cap, shift, mask, hist, totals);
+        const uint32_t* vin = (p == 0 && b.iota_vals) ? nullptr : vi;
+        k_radix_downsweep<<<G, kSortThreads, 0, st>>>(ki, vin, ko, vo, d_num, cap, shift, mask, hist, totals);
         uint32_t* t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
@@ -267,45 +274,66 @@ int sort_blocks(int64_t cap)
 // ---------------------------------------------------------------------------
 // Depth keys and the pair count
 // ---------------------------------------------------------------------------
-__global__ void k_depth_keys(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
-                             uint32_t* __restrict__ keys, uint32_t* __restrict__ ids)
-{
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    float depth = splats[4 * (int64_t)g + 2].y;
-    // depth > z_near > 0 for visible Gaussians: the float bits order like the value
-    keys[g] = tiles_touched[g] > 0 ? __float_as_uint(depth) : 0xffffffffu;
-    ids[g] = (uint32_t)g;
-}
-
 __device__ __forceinline__ bool rect_in_grid(int4 r, int TX, int TY)
 {
     return r.x >= 0 && r.y >= 0 && r.x <= r.z && r.y <= r.w && r.z < TX && r.w < TY;
 }
 
-// K = the number of (Gaussian, tile) pairs: the rect areas of the visible
-// Gaussians (equal to their tiles_touched), accumulated into *total (zeroed by
-// the caller). Counting from the rects the scatters use keeps every row list
-// within K slots.
-__global__ void k_sum_tiles(int n, const int* __restrict__ tiles_touched, const int4* __restrict__ rects, int TX,
-                            int TY, unsigned long long* __restrict__ total)
+constexpr int kKeyThreads = 256;
+constexpr int kKeysPerThread = 4;
+
+// One pass over the Gaussians: the depth sort key of each (the float bits of
+// the view depth, which order like the value since depth > z_near > 0 for a
+// visible Gaussian; all ones for a culled one), and K, the number of
+// (Gaussian, tile) pairs: the rect areas of the visible Gaussians (equal to
+// their tiles_touched), accumulated into *total (zeroed by the caller).
+// Counting from the rects the scatters use keeps every row list within K
+// slots. Each thread takes kKeysPerThread Gaussians a block apart, loads first.
+__global__ void __launch_bounds__(kKeyThreads)
+k_keys_and_pairs(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
+                 const int4* __restrict__ rects, int TX, int TY, uint32_t* __restrict__ keys,
+                 unsigned long long* __restrict__ total)
 {
+    __shared__ unsigned long long s_sum[kKeyThreads / 32];
+    const int64_t g0 = (int64_t)blockIdx.x * (kKeyThreads * kKeysPerThread) + threadIdx.x;
+    int tt[kKeysPerThread];
+#pragma unroll
+    for (int j = 0; j < kKeysPerThread; ++j) {
+        const int64_t g = g0 + j * kKeyThreads;
+        tt[j] = g < n ? tiles_touched[g] : 0;
+    }
     unsigned long long s = 0;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        const int4 r = rects[g];
-        if (tiles_touched[g] > 0 && rect_in_grid(r, TX, TY))
-            s += (unsigned long long)(r.z - r.x + 1) * (unsigned long long)(r.w - r.y + 1);
+#pragma unroll
+    for (int j = 0; j < kKeysPerThread; ++j) {
+        const int64_t g = g0 + j * kKeyThreads;
+        if (g >= n) break;
+        uint32_t key = 0xffffffffu;
+        if (tt[j] > 0) {
+            // all ones marks a culled Gaussian: a visible one never takes it (even with bad input)
+            key = min(__float_as_uint(splats[4 * g + 2].y), 0xfffffffeu);
+            const int4 r = rects[g];
+            if (rect_in_grid(r, TX, TY))
+                s += (unsigned long long)(r.z - r.x + 1) * (unsigned long long)(r.w - r.y + 1);
+        }
+        keys[g] = key;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+#pragma unroll
+        for (int w = 0; w < kKeyThreads / 32; ++w) b += s_sum[w];
+        if (b) atomicAdd(total, b);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Two-level counting scatter. The pairs are never stored with keys nor sorted:
 //   level 1 bins the depth-ordered Gaussians into per-row lists (one entry per
-//   tile row a Gaussian's rect spans), level 2 bins each row list into the
-//   row's tiles. Each level is a counting scatter: per-warp counts from a
+//   tile row a Gaussian's rect spans, carrying the rect's x-extent), level 2
+//   bins each row list into the row's tiles. Each level is a counting scatter: per-warp counts from a
 //   difference array, exclusive scans down the columns of the count matrix for
 //   every warp's first slot in every bin, then each warp regenerates its items
 //   in order and ranks them per bin with __match_any_sync and shared counters.
@@ -355,14 +383,26 @@ __device__ __forceinline__ int owner_lane(uint32_t begin, uint32_t j)
     return lo;
 }
 
+// Level-1 input of sorted position k: the Gaussian id and whether it is
+// visible (its sorted depth key is not the culled key).
+__device__ __forceinline__ uint32_t lvl1_id(const uint32_t* perm, const uint32_t* skeys, int k, int k1, bool& vis)
+{
+    vis = false;
+    if (k >= k1) return 0u;
+    vis = skeys[k] != 0xffffffffu;
+    return perm[k];
+}
+
 // Level 1a: per level-1 warp (chunk of kRowChunk depth-ordered Gaussians), the
 // number of its Gaussians whose rect spans each tile row -> M1[chunk][row].
+// The rects of four rounds are fetched together.
 __global__ void __launch_bounds__(kLvlThreads)
-k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
+k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
            const int4* __restrict__ rects, int TX, int TY, const int64_t* __restrict__ d_K, int64_t cap,
            uint32_t* __restrict__ M1)
 {
     extern __shared__ int s_lvl[];
+    constexpr int U = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * kLvlWarps + warp;
     if (c >= C1 || overflow(d_K, cap)) return;
@@ -370,13 +410,20 @@ k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const int* __restri
     for (int i = lane; i <= TY; i += 32) d[i] = 0;
     __syncwarp();
     const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
-    for (int k = k0 + lane; k < k1; k += 32) {
-        const uint32_t g = perm[k];
-        if (tiles_touched[g] <= 0) continue;
-        const int4 r = rects[g];
-        if (!rect_in_grid(r, TX, TY)) continue;
-        atomicAdd(&d[r.y], 1);
-        atomicAdd(&d[r.w + 1], -1);
+    for (int kb = k0 + lane; kb < k1; kb += 32 * U) {
+        uint32_t g[U];
+        bool vis[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) g[j] = lvl1_id(perm, skeys, kb + 32 * j, k1, vis[j]);
+        int4 r[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) r[j] = vis[j] ? rects[g[j]] : make_int4(0, 0, -1, -1);
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (!vis[j] || !rect_in_grid(r[j], TX, TY)) continue;
+            atomicAdd(&d[r[j].y], 1);
+            atomicAdd(&d[r[j].w + 1], -1);
+        }
     }
     __syncwarp();
     warp_inclusive_scan_smem(d, TY, lane);
@@ -391,17 +438,21 @@ __device__ __forceinline__ int active_rows(const uint32_t* active, int col_div, 
     return active ? min(R, (int)active[c / col_div]) : R;
 }
 
-__global__ void k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict__ SS,
-                             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
-                             int64_t cap)
+// One warp per (column, block of kScanRows = 32 rows), lane = row: blocks of
+// 8 warps take 8 consecutive columns.
+constexpr int kColsPerBlock = kLvlWarps;
+
+__global__ void __launch_bounds__(kLvlThreads)
+k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict__ SS,
+             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K, int64_t cap)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Cc || overflow(d_K, cap)) return;
-    const int r0 = blockIdx.y * kScanRows;
-    const int r1 = min(r0 + kScanRows, active_rows(active, col_div, c, R));
-    uint32_t sum = 0;
-    for (int r = r0; r < r1; ++r) sum += M[(int64_t)r * Cc + c];
-    SS[(int64_t)blockIdx.y * Cc + c] = sum;
+    const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
+    const int r = blockIdx.y * kScanRows + lane;
+    uint32_t x = r < active_rows(active, col_div, c, R) ? M[(int64_t)r * Cc + c] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) SS[(int64_t)blockIdx.y * Cc + c] = x;
 }
 
 // One warp per column: exclusive scan of the column's nsb segment sums in
@@ -469,29 +520,38 @@ __global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __
     if (threadIdx.x == 0 && sum) *sum = (int64_t)carry;
 }
 
-// M[r][c] <- start[c] + (sum of M[r'][c] for r' < r): the first slot of row r in bin c.
-__global__ void k_col_base(int R, int Cc, uint32_t* __restrict__ M, const uint32_t* __restrict__ SS,
-                           const uint32_t* __restrict__ start, const uint32_t* __restrict__ active, int col_div,
-                           const int64_t* __restrict__ d_K, int64_t cap)
+// M[r][c] <- start[c] + (sum of M[r'][c] for r' < r): the first slot of row r
+// in bin c. Same warp layout as k_col_segsum.
+__global__ void __launch_bounds__(kLvlThreads)
+k_col_base(int R, int Cc, uint32_t* __restrict__ M, const uint32_t* __restrict__ SS,
+           const uint32_t* __restrict__ start, const uint32_t* __restrict__ active, int col_div,
+           const int64_t* __restrict__ d_K, int64_t cap)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Cc || overflow(d_K, cap)) return;
-    const int r0 = blockIdx.y * kScanRows;
-    const int r1 = min(r0 + kScanRows, active_rows(active, col_div, c, R));
-    uint32_t run = start[c] + SS[(int64_t)blockIdx.y * Cc + c];
-    for (int r = r0; r < r1; ++r) {
-        const uint32_t h = M[(int64_t)r * Cc + c];
-        M[(int64_t)r * Cc + c] = run;
-        run += h;
+    const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
+    const int r = blockIdx.y * kScanRows + lane;
+    const bool act = r < active_rows(active, col_div, c, R);
+    const uint32_t h = act ? M[(int64_t)r * Cc + c] : 0u;
+    uint32_t inc = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (act) M[(int64_t)r * Cc + c] = start[c] + SS[(int64_t)blockIdx.y * Cc + c] + inc - h;
 }
 
-// Level 1c: each level-1 warp writes the ids of its Gaussians into the row
-// lists, in depth order, at the slots M1 (now bases) gives it.
+// A row-list entry: the Gaussian id and its rect's x-extent (x0 in the low
+// 16 bits, the tile count in the high 16), so that level 2 needs no rect.
+__device__ __forceinline__ uint32_t pack_x(int4 r) { return (uint32_t)r.x | ((uint32_t)(r.z - r.x + 1) << 16); }
+
+// Level 1c: each level-1 warp writes its Gaussians into the row lists, in
+// depth order, at the slots M1 (now bases) gives it. The ids and rects of the
+// next round are fetched while the current round is written.
 __global__ void __launch_bounds__(kLvlThreads)
-k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const int* __restrict__ tiles_touched,
+k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
               const int4* __restrict__ rects, int TX, int TY, const uint32_t* __restrict__ M1,
-              const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ rowlist)
+              const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ rowlist)
 {
     extern __shared__ int s_lvl[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -502,18 +562,23 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const int* __res
     for (int ty = lane; ty < TY; ty += 32) cnt[ty] = M1[(int64_t)c * TY + ty];
     __syncwarp();
     const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    bool vis_n;
+    uint32_t g_n = lvl1_id(perm, skeys, k0 + lane, k1, vis_n);
+    int4 r_n = vis_n ? rects[g_n] : make_int4(0, 0, -1, -1);
     for (int kb = k0; kb < k1; kb += 32) {
-        const int k = kb + lane;
-        uint32_t g = 0;
-        int y0 = 0, nr = 0;
-        if (k < k1) {
-            g = perm[k];
-            const int4 r = rects[g];
-            if (tiles_touched[g] > 0 && rect_in_grid(r, TX, TY)) {
-                y0 = r.y;
-                nr = r.w - r.y + 1;
-            }
+        const uint32_t g = g_n;
+        const bool vis = vis_n;
+        const int4 r = r_n;
+        if (kb + 32 < k1) {
+            g_n = lvl1_id(perm, skeys, kb + 32 + lane, k1, vis_n);
+            r_n = vis_n ? rects[g_n] : make_int4(0, 0, -1, -1);
         }
+        int y0 = 0, nr = 0;
+        if (vis && rect_in_grid(r, TX, TY)) {
+            y0 = r.y;
+            nr = r.w - r.y + 1;
+        }
+        const uint32_t xp = pack_x(r);
         uint32_t inc = (uint32_t)nr;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -528,6 +593,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const int* __res
             const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
             const int o_y0 = __shfl_sync(0xffffffffu, y0, o);
             const uint32_t o_g = __shfl_sync(0xffffffffu, g, o);
+            const uint32_t o_xp = __shfl_sync(0xffffffffu, xp, o);
             const bool valid = j < total;
             const uint32_t row = valid ? (uint32_t)o_y0 + (j - o_begin) : 0xffffffffu;
             const uint32_t peers = __match_any_sync(0xffffffffu, row);
@@ -536,7 +602,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const int* __res
             __syncwarp();
             if (valid && lane == __ffs(peers) - 1) cnt[row] += __popc(peers);
             __syncwarp();
-            if (valid && (int64_t)pos < cap) rowlist[pos] = o_g;
+            if (valid && (int64_t)pos < cap) rowlist[pos] = make_uint2(o_g, o_xp);
         }
     }
 }
@@ -567,8 +633,8 @@ __device__ __forceinline__ int segment_row(const uint32_t* segoff, int TY, uint3
 // spanning each tile of the row -> M2[segment][tile].
 __global__ void __launch_bounds__(kLvlThreads)
 k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
-           const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint32_t* __restrict__ rowlist,
-           const int4* __restrict__ rects, const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ M2)
+           const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint2* __restrict__ rowlist,
+           const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ M2)
 {
     extern __shared__ int s_lvl[];
     if (overflow(d_K, cap)) return;
@@ -584,9 +650,9 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
         for (int i = threadIdx.x; i <= TX; i += kLvlThreads) d[i] = 0;
         __syncthreads();
         for (uint32_t e = e0 + threadIdx.x; e < e1; e += kLvlThreads) {
-            const int4 r = rects[rowlist[e]];
-            atomicAdd(&d[r.x], 1);
-            atomicAdd(&d[r.z + 1], -1);
+            const uint32_t xp = rowlist[e].y;
+            atomicAdd(&d[xp & 0xffffu], 1);
+            atomicAdd(&d[(xp & 0xffffu) + (xp >> 16)], -1);
         }
         __syncthreads();
         if (warp == 0) {
@@ -606,7 +672,7 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
 __global__ void __launch_bounds__(kLvlThreads)
 k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
               const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS,
-              const uint32_t* __restrict__ rowlist, const int4* __restrict__ rects, const uint32_t* __restrict__ M2,
+              const uint2* __restrict__ rowlist, const uint32_t* __restrict__ M2,
               const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ out)
 {
     extern __shared__ int s_lvl[];
@@ -629,10 +695,11 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
         // counts of this warp's sub-range
         for (int i = lane; i < W1; i += 32) d[i] = 0;
         __syncwarp();
+#pragma unroll 4
         for (uint32_t e = w0 + lane; e < w1; e += 32) {
-            const int4 r = rects[rowlist[e]];
-            atomicAdd(&d[r.x], 1);
-            atomicAdd(&d[r.z + 1], -1);
+            const uint32_t xp = rowlist[e].y;
+            atomicAdd(&d[xp & 0xffffu], 1);
+            atomicAdd(&d[(xp & 0xffffu) + (xp >> 16)], -1);
         }
         __syncwarp();
         warp_inclusive_scan_smem(d, TX, lane);
@@ -649,16 +716,14 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
             }
         }
         __syncthreads();
+        uint2 ent_n = w0 + lane < w1 ? rowlist[w0 + lane] : make_uint2(0u, 0u);
         for (uint32_t eb = w0; eb < w1; eb += 32) {
-            const uint32_t e = eb + lane;
-            uint32_t g = 0;
-            int x0 = 0, nx = 0;
-            if (e < w1) {
-                g = rowlist[e];
-                const int4 r = rects[g];
-                x0 = r.x;
-                nx = r.z - r.x + 1;
-            }
+            // this round's entries; the next round's are fetched while these are written
+            const uint2 ent = ent_n;
+            if (eb + 32 < w1) ent_n = eb + 32 + lane < w1 ? rowlist[eb + 32 + lane] : make_uint2(0u, 0u);
+            const uint32_t g = ent.x;
+            const int x0 = (int)(ent.y & 0xffffu);
+            const int nx = (int)(ent.y >> 16);
             uint32_t inc = (uint32_t)nx;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -704,7 +769,8 @@ __global__ void k_ranges_from_counts(int T, const uint32_t* __restrict__ count, 
 struct Ws {
     uint32_t *dkeys0, *dkeys1, *perm0, *perm1;
     uint32_t *hist, *totals;
-    uint32_t *M1, *SS1, *rowlen, *rowstart, *rowlist;
+    uint32_t *M1, *SS1, *rowlen, *rowstart;
+    uint2* rowlist;
     uint32_t *nseg, *segoff;
     int64_t *R, *NS;
     uint32_t *M2, *SS2, *tcount, *tstart;
@@ -742,7 +808,7 @@ Ws carve(void* base, int n, int64_t cap, int tiles_x, int tiles_y)
     w.SS1 = (uint32_t*)take((size_t)((C1 + kScanRows - 1) / kScanRows) * TY * 4);
     w.rowlen = (uint32_t*)take(TY * 4);
     w.rowstart = (uint32_t*)take(TY * 4);
-    w.rowlist = (uint32_t*)take(rows_cap * 4);
+    w.rowlist = (uint2*)take(rows_cap * 8);
     w.nseg = (uint32_t*)take(TY * 4);
     w.segoff = (uint32_t*)take(TY * 4);
     w.R = (int64_t*)take(8);
@@ -799,12 +865,11 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     }
     const int4* rc = reinterpret_cast<const int4*>(rects);
     // K, and the depth order of the Gaussians: a stable LSD radix sort of (depth bits, id)
-    k_sum_tiles<<<148 * 4, 256, 0, st>>>(n, tiles_touched, rc, TX, TY,
-                                         reinterpret_cast<unsigned long long*>(num_pairs));
-    k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched,
-                                                  w.dkeys0, w.perm0);
-    radix_sort(SortBufs{w.dkeys0, w.perm0, w.dkeys1, w.perm1}, nullptr, n, 32, sort_blocks(n), w.hist, w.totals,
-               st);  // 4 passes: the order is back in perm0
+    k_keys_and_pairs<<<(n + kKeyThreads * kKeysPerThread - 1) / (kKeyThreads * kKeysPerThread), kKeyThreads, 0,
+                       st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched, rc, TX, TY, w.dkeys0,
+                             reinterpret_cast<unsigned long long*>(num_pairs));
+    radix_sort(SortBufs{w.dkeys0, w.perm0, w.dkeys1, w.perm1, true}, nullptr, n, 32, sort_blocks(n), w.hist,
+               w.totals, st);  // 4 passes: the sorted keys and the order are back in dkeys0, perm0
     // level 1: rows
     const int C1 = lvl1_warps(n);
     const int lvl1_blocks = (C1 + kLvlWarps - 1) / kLvlWarps;
@@ -813,15 +878,15 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     }
-    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, tiles_touched, rc, TX, TY, num_pairs,
+    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs,
                                                         capacity, w.M1);
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
-    const dim3 g1((TY + 255) / 256, nsb1);
-    k_col_segsum<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, 1, num_pairs, capacity);
+    const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, nsb1);
+    k_col_segsum<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, 1, num_pairs, capacity);
     k_col_totals<<<(TY * 32 + 255) / 256, 256, 0, st>>>(nsb1, TY, w.SS1, w.rowlen, num_pairs, capacity);
     k_scan_small<<<1, 1024, 0, st>>>(TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
-    k_col_base<<<g1, 256, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, 1, num_pairs, capacity);
-    k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, tiles_touched, rc, TX, TY, w.M1,
+    k_col_base<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, 1, num_pairs, capacity);
+    k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, w.M1,
                                                            num_pairs, capacity, w.rowlist);
     // level 2: tiles within each row
     k_row_segments<<<(TY + 255) / 256, 256, 0, st>>>(TY, w.rowlen, w.nseg, num_pairs, capacity);
@@ -834,20 +899,20 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     }
     const int lvl2_blocks = 148 * 8;
-    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2h, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist, rc,
+    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2h, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist,
                                                         num_pairs, capacity, w.M2);
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
-    const dim3 g2((T + 255) / 256, nsb2);
-    k_col_segsum<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, TX, num_pairs, capacity);
+    const dim3 g2((T + kColsPerBlock - 1) / kColsPerBlock, nsb2);
+    k_col_segsum<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, TX, num_pairs, capacity);
     k_col_totals<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(nsb2, T, w.SS2, w.tcount, num_pairs,
                                                                       capacity);
     k_scan_small<<<1, 1024, 0, st>>>(T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
-    k_col_base<<<g2, 256, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, TX, num_pairs, capacity);
+    k_col_base<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, TX, num_pairs, capacity);
     k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
                                                          reinterpret_cast<uint2*>(ranges));
     if (capacity > 0)
         k_seg_scatter<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
-                                                               w.rowlist, rc, w.M2, num_pairs, capacity, sorted_ids);
+                                                               w.rowlist, w.M2, num_pairs, capacity, sorted_ids);
     return gs_host::check_launch("gs_bin_sort");
 }
 
