@@ -208,6 +208,9 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 }
         }
         __syncthreads();
+        int lj[PPT];  // batch slot of the pixel's last blended entry in this batch, or -1
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) lj[k] = -1;
         {
             // every live pixel visits every entry (the blend count of the method); a warp
             // takes only the entries whose gate box meets its pixel block, 32 at a time.
@@ -250,14 +253,20 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                         C1[k] = fmaf(c.y, w, C1[k]);
                         C2[k] = fmaf(c.z, w, C2[k]);
                         T[k] = Tn;
-                        last_pos[k] = FILTER ? s_pos[j] : start + j - rg.x + 1;
-                        last_own[k] = own_base + j + 1;
+                        lj[k] = j;
                         ++n_blend;
                     }
                     if (!__any_sync(0xffffffffu, n_live > 0)) break;
                 }
                 n_eval += (uint32_t)n_live * (uint32_t)(c1 - next_j);
             }
+        }
+        // positions of the last blended entries, read before the next batch is staged
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (lj[k] < 0) continue;
+            last_pos[k] = FILTER ? s_pos[lj[k]] : start + (uint32_t)lj[k] - rg.x + 1;
+            last_own[k] = own_base + (uint32_t)lj[k] + 1;
         }
         own_base += (uint32_t)cnt;
     }
