@@ -22,22 +22,65 @@ __device__ __forceinline__ void load_stage(const float4* __restrict__ splats, ui
     rgb = make_float4(v1.z, v1.w, v2.x, 0.0f);
 }
 
-// Bounding box (x0, x1, y0, y1; tile-relative hr pixels) of the region where a
-// splat can pass the alpha gate: o exp(-q/2) >= 1/255 <=> q = d^T K d <= tau =
-// 2 ln(255 o), an ellipse whose half-extents are sqrt(tau Sigma_xx),
+// The region where a splat can pass the alpha gate: o exp(-q/2) >= 1/255 <=>
+// q = d^T K d <= tau = 2 ln(255 o), an ellipse. Gate::box is its bounding box
+// (x0, x1, y0, y1; tile-relative hr pixels), half-extents sqrt(tau Sigma_xx),
 // sqrt(tau Sigma_yy) with Sigma = K^-1. tau and the extents are padded well
-// beyond the FP32 error of the gate itself, so every pixel outside the box
+// beyond the FP32 error of the gate itself, so every pixel outside the region
 // fails the gate in the kernel's own arithmetic: skipping it changes nothing.
-__device__ __forceinline__ float4 gate_box(float2 p, float4 co)
+// exact = false when only the box may be used (a degenerate conic).
+struct Gate {
+    float4 box;
+    float tau;
+    bool exact;
+};
+
+__device__ __forceinline__ Gate gate_region(float2 p, float4 co)
 {
     const float inf = __int_as_float(0x7f800000);
-    if (!(co.w * 255.0f >= 1.0f)) return make_float4(inf, -inf, inf, -inf);  // never passes
+    Gate G;
+    G.tau = 0.0f;
+    G.exact = false;
+    if (!(co.w * 255.0f >= 1.0f)) {  // never passes
+        G.box = make_float4(inf, -inf, inf, -inf);
+        return G;
+    }
     const float detK = det2(co.x, co.y, co.y, co.z);  // A C - B^2, FMA-exact
-    const float tau = fmaxf(2.0f * logf(255.0f * co.w), 0.0f) * 1.001f + 1e-3f;
-    const float ex = sqrtf(tau * co.z / detK) * 1.001f + 0.01f;
-    const float ey = sqrtf(tau * co.x / detK) * 1.001f + 0.01f;
-    if (!(detK > 0.0f) || !(ex < 1e30f) || !(ey < 1e30f)) return make_float4(-inf, inf, -inf, inf);
-    return make_float4(p.x - ex, p.x + ex, p.y - ey, p.y + ey);
+    const float tau = fmaxf(2.0f * __logf(255.0f * co.w), 0.0f) * 1.001f + 1e-3f;
+    const float s = tau * __fdividef(1.0f, detK);
+    const float ex = sqrtf(s * co.z) * 1.001f + 0.01f;
+    const float ey = sqrtf(s * co.x) * 1.001f + 0.01f;
+    if (!(detK > 0.0f) || !(co.x > 0.0f) || !(co.z > 0.0f) || !(ex < 1e30f) || !(ey < 1e30f)) {
+        G.box = make_float4(-inf, inf, -inf, inf);
+        return G;
+    }
+    G.box = make_float4(p.x - ex, p.x + ex, p.y - ey, p.y + ey);
+    G.tau = tau;
+    G.exact = true;
+    return G;
+}
+
+// Lower bound of q = A u^2 + 2 B u v + C v^2 at (u, v), less a relative margin
+// for the rounding of its terms.
+__device__ __forceinline__ float quad_lo(float4 co, float u, float v)
+{
+    const float a = co.x * u * u, c = co.z * v * v, b = 2.0f * co.y * u * v;
+    return (a + c + b) - 1e-5f * (a + c + fabsf(b));
+}
+
+// Whether the ellipse q(x - p) <= tau meets the rectangle [x0, x1] x [y0, y1]
+// (coordinates relative to p): the centre is inside, or the minimum of the
+// convex q over one of the four edges is within tau (each edge minimum is the
+// unconstrained one along the edge, clamped to it).
+__device__ __forceinline__ bool ellipse_meets_rect(float4 co, float kv, float ku, float tau, float x0, float x1,
+                                                   float y0, float y1)
+{
+    if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) return true;
+    float q = quad_lo(co, x0, fminf(fmaxf(kv * x0, y0), y1));
+    q = fminf(q, quad_lo(co, x1, fminf(fmaxf(kv * x1, y0), y1)));
+    q = fminf(q, quad_lo(co, fminf(fmaxf(ku * y0, x0), x1), y0));
+    q = fminf(q, quad_lo(co, fminf(fmaxf(ku * y1, x0), x1), y1));
+    return q <= tau;
 }
 
 // Whether blend tile (tx, ty) lies in the blend-tile rectangle of record g
@@ -88,22 +131,29 @@ struct TileGeom {
     static constexpr int WCOLS = TILE / 8;       // warp blocks across the tile
 };
 
-// Bit w set when the gate box meets the pixel block of warp w (the blocks of
-// WarpBlock below): computed once per staged entry, so a warp walks only the
-// entries that can reach its pixels.
+// Bit w set when the gate region meets the pixel block of warp w (the blocks
+// of WarpBlock below): computed once per staged entry, so a warp walks only
+// the entries that can reach its pixels. A block must meet the region's box
+// and, for a regular conic, the ellipse itself.
 template <int TILE, int PPT>
-__device__ __forceinline__ uint32_t warp_mask(float4 box, int d)
+__device__ __forceinline__ uint32_t warp_mask(float2 p, float4 co, int d)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NW = Geo::THREADS / 32;
+    const Gate G = gate_region(p, co);
+    const float4 box = G.box;
+    // minimisers of q along an edge: v = -B u / C on x = const, u = -B v / A on y = const
+    const float kv = -co.y * __fdividef(1.0f, co.z), ku = -co.y * __fdividef(1.0f, co.x);
     uint32_t m = 0u;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const int bx = w % Geo::WCOLS, by = w / Geo::WCOLS;
         const float wx0 = (float)(d * bx * 8), wx1 = (float)(d * (bx * 8 + 7));
         const float wy0 = (float)(d * by * Geo::WROWS), wy1 = (float)(d * (by * Geo::WROWS + Geo::WROWS - 1));
-        const bool miss = box.x > wx1 || box.y < wx0 || box.z > wy1 || box.w < wy0;
-        m |= miss ? 0u : (1u << w);
+        bool hit = !(box.x > wx1 || box.y < wx0 || box.z > wy1 || box.w < wy0);
+        if (hit && G.exact)
+            hit = ellipse_meets_rect(co, kv, ku, G.tau, wx0 - p.x, wx1 - p.x, wy0 - p.y, wy1 - p.y);
+        m |= hit ? (1u << w) : 0u;
     }
     return m;
 }
@@ -176,7 +226,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 float2 p; float4 co, rgb;
                 load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
                 s_p[i] = p;
-                s_mask[i] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
+                s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
                 s_co[i] = co;
                 s_rgb[i] = rgb;
             }
@@ -198,7 +248,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     float2 p; float4 co, rgb;
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[cnt + r] = p;
-                    s_mask[cnt + r] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
+                    s_mask[cnt + r] = warp_mask<TILE, PPT>(p, co, dil.d);
                     s_co[cnt + r] = co;
                     s_rgb[cnt + r] = rgb;
                     s_pos[cnt + r] = e - rg.x + 1;
@@ -429,7 +479,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 float2 p; float4 co, rgb;
                 load_stage(splats, g, X0, Y0, p, co, rgb);
                 s_p[i] = p;
-                s_mask[i] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
+                s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
                 s_co[i] = co;
                 s_rgb[i] = rgb;
                 s_id[i] = g;
@@ -455,7 +505,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     float2 p; float4 co, rgb;
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[slot] = p;
-                    s_mask[slot] = warp_mask<TILE, PPT>(gate_box(p, co), dil.d);
+                    s_mask[slot] = warp_mask<TILE, PPT>(p, co, dil.d);
                     s_co[slot] = co;
                     s_rgb[slot] = rgb;
                     s_id[slot] = g;
@@ -564,8 +614,18 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 // longest-first across all views).
 // MULTI false: one view, whose fields the kernel reads at fixed offsets.
 // FILTER: the views bin with coarser tiles than they blend (bin_shift > 0).
+// With up to 2 pixels per thread the forward is held to 64 registers (1024
+// threads' worth of CTAs per SM), which it fits without spilling; the
+// backward keeps what it needs (about 72), measured faster than spilling for
+// the extra CTA.
+template <int TILE, int PPT>
+constexpr int fwd_min_blocks()
+{
+    return PPT <= 2 ? 1024 / TileGeom<TILE, PPT>::THREADS : 1;
+}
+
 template <int TILE, int PPT, bool MULTI, bool FILTER>
-__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (fwd_min_blocks<TILE, PPT>()))
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
              unsigned long long* __restrict__ counts)
 {

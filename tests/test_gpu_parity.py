@@ -188,6 +188,41 @@ def test_render_fwd_parity(dil):
     assert out["counts"][2] == int(of["last"].astype(np.int64).sum()) or excl.any()
 
 
+def scene_needles(n=1500, w=203, h=157, index=17):
+    """Thin, rotated, mostly opaque Gaussians (aspect ratios up to ~50): their
+    gate ellipses cover a small part of their bounding boxes, which is where the
+    blend kernels' per-warp-block ellipse test skips work."""
+    rng = np.random.default_rng(index)
+    s = scenes.small_scene(n, index=index, sh_degree=0, log_scale_mean=-2.4)
+    ls = np.stack([rng.normal(-1.9, 0.3, n), rng.normal(-5.2, 0.5, n), rng.normal(-3.5, 0.8, n)], 1)
+    s.log_scales = ls.astype(np.float32)
+    q = rng.normal(size=(n, 4))
+    s.quats = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    # opacities from barely above the 1/255 gate to nearly 1
+    s.opacity_logits = rng.uniform(-5.5, 5.0, n).astype(np.float32)
+    cam = scenes.look_at(scenes.orbit_eye(2.8, 40.0, 30.0), width=w, height=h)
+    return U.params_np(s), cam
+
+
+@pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0), R.Dilation(1, 0, 0, tile=8),
+                                 R.Dilation(2, 0, 1, tile=32), R.Dilation(3, 2, 1)], ids=_dil_id)
+def test_render_fwd_parity_needles(dil):
+    """No pixel that passes the gate is skipped: the blend order, counts and
+    images equal the oracle's, which evaluates every pixel against every entry."""
+    p32, cam = scene_needles()
+    out, rast, p, bufs, o, of, excl = render_case(p32, cam, dil)
+    assert excl.mean() < 5e-3
+    keep = ~excl
+    assert out["counts"][1] > 0
+    assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
+    np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
+    assert out["counts"][1] == of["n_blend"] or excl.any()
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil)
+    gg = U.split_grad2d(g2d)
+    for k in ("dxy", "dconic", "dopacity", "drgb"):
+        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
+
+
 def test_render_fwd_parity_sh3_ragged():
     p32, cam, _ = scene_sh3(131, 97)
     for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1), R.Dilation(3, 0, 2, tile=8)]:
