@@ -383,6 +383,78 @@ __device__ __forceinline__ int owner_lane(uint32_t begin, uint32_t j)
     return lo;
 }
 
+__device__ __forceinline__ uint32_t shfl_val(uint32_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ uint2 shfl_val(uint2 v, int src)
+{
+    return make_uint2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// One round of a warp's counting scatter. Lane i holds an item val spanning
+// bins [b0, b0 + nb) (nb = 0: none); cnt[b] is the warp's next free slot of
+// bin b. Every item is written to each of its bins, in lane order within a
+// bin, and cnt is advanced. When the round's bins lie within 32 consecutive
+// ones, one ballot per bin gives every lane its rank directly (scratch: 64
+// words of the warp's shared memory); otherwise the items are flattened 32
+// at a time and ranked per bin with __match_any_sync.
+template <typename V>
+__device__ __forceinline__ void scatter_round(V val, int b0, int nb, uint32_t* cnt, uint32_t* scratch, V* out,
+                                              int64_t cap, int lane)
+{
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const bool has = nb > 0;
+    const int lo = __reduce_min_sync(0xffffffffu, has ? b0 : 0x7fffffff);
+    const int hi = __reduce_max_sync(0xffffffffu, has ? b0 + nb - 1 : -1);
+    if (lo > hi) return;  // no items in the round (uniform)
+    if (hi - lo < 32) {
+        uint32_t my_m = 0u;  // lane t: the lanes whose items cover bin lo + t
+        for (int t = 0; t <= hi - lo; ++t) {
+            const int b = lo + t;
+            const uint32_t m = __ballot_sync(0xffffffffu, has && b0 <= b && b < b0 + nb);
+            my_m = lane == t ? m : my_m;
+        }
+        uint32_t* s_base = scratch;
+        uint32_t* s_mask = scratch + 32;
+        if (lane <= hi - lo) {
+            const uint32_t base = cnt[lo + lane];
+            s_base[lane] = base;
+            s_mask[lane] = my_m;
+            cnt[lo + lane] = base + __popc(my_m);
+        }
+        __syncwarp();
+        for (int k = 0; k < nb; ++k) {
+            const int t = b0 + k - lo;
+            const uint32_t pos = s_base[t] + __popc(s_mask[t] & lt_mask);
+            if ((int64_t)pos < cap) out[pos] = val;
+        }
+        __syncwarp();
+        return;
+    }
+    uint32_t inc = (uint32_t)nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t begin = inc - (uint32_t)nb;
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const int o = owner_lane(begin, j);
+        const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
+        const int o_b0 = __shfl_sync(0xffffffffu, b0, o);
+        const V o_val = shfl_val(val, o);
+        const bool valid = j < total;
+        const uint32_t bin = valid ? (uint32_t)o_b0 + (j - o_begin) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+        uint32_t pos = 0;
+        if (valid) pos = cnt[bin] + __popc(peers & lt_mask);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[bin] += __popc(peers);
+        __syncwarp();
+        if (valid && (int64_t)pos < cap) out[pos] = o_val;
+    }
+}
+
 // Level-1 input of sorted position k: the Gaussian id and whether it is
 // visible (its sorted depth key is not the culled key).
 __device__ __forceinline__ uint32_t lvl1_id(const uint32_t* perm, const uint32_t* skeys, int k, int k1, bool& vis)
@@ -430,38 +502,54 @@ k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __r
     for (int ty = lane; ty < TY; ty += 32) M1[(int64_t)c * TY + ty] = (uint32_t)d[ty];
 }
 
-// Column scans of a count matrix M (R rows x Cc columns, row-major). Column c
-// uses only its first active(c) rows when `active` is given (active(c) =
-// active[c / col_div]); the others count as zero.
+// Column scans of a count matrix M (R rows x Cc columns). Level 1 stores it
+// row-major (element (r, c) at r * Cc + c). Level 2 stores only the rows that
+// exist: column c = (ty, tx) of the tile grid (col_div = TX) has the rows of
+// its tile row's segments, element (r, c) at (rowbase[ty] + r) * TX + tx.
+// Column c uses only its first active(c) rows when `active` is given
+// (active(c) = active[c / col_div]); the others count as zero.
 __device__ __forceinline__ int active_rows(const uint32_t* active, int col_div, int c, int R)
 {
     return active ? min(R, (int)active[c / col_div]) : R;
 }
 
+__device__ __forceinline__ int64_t mat_at(const uint32_t* rowbase, int col_div, int Cc, int c, int r)
+{
+    return rowbase ? ((int64_t)rowbase[c / col_div] + r) * col_div + c % col_div : (int64_t)r * Cc + c;
+}
+
 // One warp per (column, block of kScanRows = 32 rows), lane = row: blocks of
-// 8 warps take 8 consecutive columns.
+// 8 warps take 8 consecutive columns and loop over the row blocks by
+// gridDim.y, up to the column's active rows.
 constexpr int kColsPerBlock = kLvlWarps;
 
 __global__ void __launch_bounds__(kLvlThreads)
 k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict__ SS,
-             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K, int64_t cap)
+             const uint32_t* __restrict__ active, const uint32_t* __restrict__ rowbase, int col_div,
+             const int64_t* __restrict__ d_K, int64_t cap)
 {
     const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
-    const int r = blockIdx.y * kScanRows + lane;
-    uint32_t x = r < active_rows(active, col_div, c, R) ? M[(int64_t)r * Cc + c] : 0u;
+    const int act = active_rows(active, col_div, c, R);
+    for (int by = blockIdx.y; by * kScanRows < act; by += gridDim.y) {
+        const int r = by * kScanRows + lane;
+        uint32_t x = r < act ? M[mat_at(rowbase, col_div, Cc, c, r)] : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) SS[(int64_t)blockIdx.y * Cc + c] = x;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) SS[(int64_t)by * Cc + c] = x;
+    }
 }
 
-// One warp per column: exclusive scan of the column's nsb segment sums in
-// place (32 segments per step), the column total into total[c].
-__global__ void k_col_totals(int nsb, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
-                             const int64_t* __restrict__ d_K, int64_t cap)
+// One warp per column: exclusive scan of the column's segment sums in place
+// (32 segments per step; only the ceil(active / kScanRows) segments that hold
+// active rows), the column total into total[c].
+__global__ void k_col_totals(int R, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
+                             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
+                             int64_t cap)
 {
     const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
+    const int nsb = (active_rows(active, col_div, c, R) + kScanRows - 1) / kScanRows;
     uint32_t run = 0;
     for (int b0 = 0; b0 < nsb; b0 += 32) {
         const int b = b0 + lane;
@@ -524,21 +612,25 @@ __global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __
 // in bin c. Same warp layout as k_col_segsum.
 __global__ void __launch_bounds__(kLvlThreads)
 k_col_base(int R, int Cc, uint32_t* __restrict__ M, const uint32_t* __restrict__ SS,
-           const uint32_t* __restrict__ start, const uint32_t* __restrict__ active, int col_div,
-           const int64_t* __restrict__ d_K, int64_t cap)
+           const uint32_t* __restrict__ start, const uint32_t* __restrict__ active,
+           const uint32_t* __restrict__ rowbase, int col_div, const int64_t* __restrict__ d_K, int64_t cap)
 {
     const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
-    const int r = blockIdx.y * kScanRows + lane;
-    const bool act = r < active_rows(active, col_div, c, R);
-    const uint32_t h = act ? M[(int64_t)r * Cc + c] : 0u;
-    uint32_t inc = h;
+    const int act = active_rows(active, col_div, c, R);
+    for (int by = blockIdx.y; by * kScanRows < act; by += gridDim.y) {
+        const int r = by * kScanRows + lane;
+        const bool in = r < act;
+        const int64_t at = mat_at(rowbase, col_div, Cc, c, r);
+        const uint32_t h = in ? M[at] : 0u;
+        uint32_t inc = h;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (in) M[at] = start[c] + SS[(int64_t)by * Cc + c] + inc - h;
     }
-    if (act) M[(int64_t)r * Cc + c] = start[c] + SS[(int64_t)blockIdx.y * Cc + c] + inc - h;
 }
 
 // A row-list entry: the Gaussian id and its rect's x-extent (x0 in the low
@@ -555,10 +647,10 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* 
 {
     extern __shared__ int s_lvl[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const int c = blockIdx.x * kLvlWarps + warp;
     if (c >= C1 || overflow(d_K, cap)) return;
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_lvl) + warp * (TY + 1);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_lvl) + warp * (TY + 1 + 64);
+    uint32_t* scratch = cnt + TY + 1;
     for (int ty = lane; ty < TY; ty += 32) cnt[ty] = M1[(int64_t)c * TY + ty];
     __syncwarp();
     const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
@@ -578,32 +670,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* 
             y0 = r.y;
             nr = r.w - r.y + 1;
         }
-        const uint32_t xp = pack_x(r);
-        uint32_t inc = (uint32_t)nr;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        const uint32_t begin = inc - (uint32_t)nr;
-        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            const int o = owner_lane(begin, j);
-            const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
-            const int o_y0 = __shfl_sync(0xffffffffu, y0, o);
-            const uint32_t o_g = __shfl_sync(0xffffffffu, g, o);
-            const uint32_t o_xp = __shfl_sync(0xffffffffu, xp, o);
-            const bool valid = j < total;
-            const uint32_t row = valid ? (uint32_t)o_y0 + (j - o_begin) : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, row);
-            uint32_t pos = 0;
-            if (valid) pos = cnt[row] + __popc(peers & lt_mask);
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) cnt[row] += __popc(peers);
-            __syncwarp();
-            if (valid && (int64_t)pos < cap) rowlist[pos] = make_uint2(o_g, o_xp);
-        }
+        scatter_round<uint2>(make_uint2(g, pack_x(r)), y0, nr, cnt, scratch, rowlist, cap, lane);
     }
 }
 
@@ -630,7 +697,7 @@ __device__ __forceinline__ int segment_row(const uint32_t* segoff, int TY, uint3
 }
 
 // Level 2a: per level-2 segment (one CTA), the number of its Gaussians
-// spanning each tile of the row -> M2[segment][tile].
+// spanning each tile of the row -> M2[segment][tile of the row].
 __global__ void __launch_bounds__(kLvlThreads)
 k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
            const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint2* __restrict__ rowlist,
@@ -641,7 +708,6 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* d = s_lvl;
     const int64_t NS = *d_NS;
-    const int T = TX * TY;
     for (int64_t seg = blockIdx.x; seg < NS; seg += gridDim.x) {
         const int ty = segment_row(segoff, TY, (uint32_t)seg);
         const uint32_t s = (uint32_t)seg - segoff[ty];
@@ -657,7 +723,7 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
         __syncthreads();
         if (warp == 0) {
             warp_inclusive_scan_smem(d, TX, lane);
-            uint32_t* out = M2 + (int64_t)s * T + (int64_t)ty * TX;
+            uint32_t* out = M2 + seg * TX;
             for (int tx = lane; tx < TX; tx += 32) out[tx] = (uint32_t)d[tx];
         }
         __syncthreads();
@@ -678,12 +744,12 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
     extern __shared__ int s_lvl[];
     if (overflow(d_K, cap)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const int W1 = TX + 1;
-    int* d = s_lvl + warp * W1;
+    const int WS = W1 + 64;  // per warp: counters, then the scatter scratch
+    int* d = s_lvl + warp * WS;
     uint32_t* cnt = reinterpret_cast<uint32_t*>(d);
+    uint32_t* scratch = cnt + W1;
     const int64_t NS = *d_NS;
-    const int T = TX * TY;
     constexpr uint32_t kSub = kSegLen / kLvlWarps;
     for (int64_t seg = blockIdx.x; seg < NS; seg += gridDim.x) {
         const int ty = segment_row(segoff, TY, (uint32_t)seg);
@@ -705,11 +771,11 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
         warp_inclusive_scan_smem(d, TX, lane);
         __syncthreads();
         // counters: the segment's first slot plus the counts of the earlier warps
-        const uint32_t* base = M2 + (int64_t)s * T + (int64_t)ty * TX;
+        const uint32_t* base = M2 + seg * TX;
         for (int tx = threadIdx.x; tx < TX; tx += kLvlThreads) {
             uint32_t run = base[tx];
             for (int w = 0; w < kLvlWarps; ++w) {
-                uint32_t* c = reinterpret_cast<uint32_t*>(s_lvl + w * W1) + tx;
+                uint32_t* c = reinterpret_cast<uint32_t*>(s_lvl + w * WS) + tx;
                 const uint32_t x = *c;
                 *c = run;
                 run += x;
@@ -721,33 +787,7 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
             // this round's entries; the next round's are fetched while these are written
             const uint2 ent = ent_n;
             if (eb + 32 < w1) ent_n = eb + 32 + lane < w1 ? rowlist[eb + 32 + lane] : make_uint2(0u, 0u);
-            const uint32_t g = ent.x;
-            const int x0 = (int)(ent.y & 0xffffu);
-            const int nx = (int)(ent.y >> 16);
-            uint32_t inc = (uint32_t)nx;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-            const uint32_t begin = inc - (uint32_t)nx;
-            for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-                const uint32_t j = j0 + lane;
-                const int o = owner_lane(begin, j);
-                const uint32_t o_begin = __shfl_sync(0xffffffffu, begin, o);
-                const int o_x0 = __shfl_sync(0xffffffffu, x0, o);
-                const uint32_t o_g = __shfl_sync(0xffffffffu, g, o);
-                const bool valid = j < total;
-                const uint32_t tx = valid ? (uint32_t)o_x0 + (j - o_begin) : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, tx);
-                uint32_t pos = 0;
-                if (valid) pos = cnt[tx] + __popc(peers & lt_mask);
-                __syncwarp();
-                if (valid && lane == __ffs(peers) - 1) cnt[tx] += __popc(peers);
-                __syncwarp();
-                if (valid && (int64_t)pos < cap) out[pos] = o_g;
-            }
+            scatter_round<uint32_t>(ent.x, (int)(ent.y & 0xffffu), (int)(ent.y >> 16), cnt, scratch, out, cap, lane);
         }
         __syncthreads();
     }
@@ -781,6 +821,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int lvl1_warps(int n) { return (n + kRowChunk - 1) / kRowChunk; }
 int lvl2_rows(int n) { return (n + kSegLen - 1) / kSegLen; }  // segments per row, at most
+// segments over all rows, at most: sum over rows of ceil(rowlen / kSegLen) for row lists of rows_cap entries
+int64_t lvl2_segments(int64_t rows_cap, int TY) { return rows_cap / kSegLen + TY; }
+constexpr int kScanGridY = 64;  // row-block parallelism of the column scans (they loop beyond it)
 
 Ws carve(void* base, int n, int64_t cap, int tiles_x, int tiles_y)
 {
@@ -813,7 +856,7 @@ Ws carve(void* base, int n, int64_t cap, int tiles_x, int tiles_y)
     w.segoff = (uint32_t*)take(TY * 4);
     w.R = (int64_t*)take(8);
     w.NS = (int64_t*)take(8);
-    w.M2 = (uint32_t*)take((size_t)NSR * T * 4);
+    w.M2 = (uint32_t*)take((size_t)lvl2_segments((int64_t)rows_cap, (int)TY) * (size_t)tiles_x * 4);
     w.SS2 = (uint32_t*)take((size_t)((NSR + kScanRows - 1) / kScanRows) * T * 4);
     w.tcount = (uint32_t*)take(T * 4);
     w.tstart = (uint32_t*)take(T * 4);
@@ -873,7 +916,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     // level 1: rows
     const int C1 = lvl1_warps(n);
     const int lvl1_blocks = (C1 + kLvlWarps - 1) / kLvlWarps;
-    const size_t smem1 = (size_t)kLvlWarps * (TY + 1) * sizeof(int);
+    const size_t smem1 = (size_t)kLvlWarps * (TY + 1 + 64) * sizeof(int);
     if (smem1 > 48 * 1024) {
         cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
@@ -881,18 +924,19 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs,
                                                         capacity, w.M1);
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
-    const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, nsb1);
-    k_col_segsum<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, 1, num_pairs, capacity);
-    k_col_totals<<<(TY * 32 + 255) / 256, 256, 0, st>>>(nsb1, TY, w.SS1, w.rowlen, num_pairs, capacity);
+    const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb1, kScanGridY));
+    k_col_segsum<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
+    k_col_totals<<<(TY * 32 + 255) / 256, 256, 0, st>>>(C1, TY, w.SS1, w.rowlen, nullptr, 1, num_pairs, capacity);
     k_scan_small<<<1, 1024, 0, st>>>(TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
-    k_col_base<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, 1, num_pairs, capacity);
+    k_col_base<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, nullptr, 1, num_pairs,
+                                           capacity);
     k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, w.M1,
                                                            num_pairs, capacity, w.rowlist);
     // level 2: tiles within each row
     k_row_segments<<<(TY + 255) / 256, 256, 0, st>>>(TY, w.rowlen, w.nseg, num_pairs, capacity);
     k_scan_small<<<1, 1024, 0, st>>>(TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
     const int NSR = lvl2_rows(n);
-    const size_t smem2 = (size_t)kLvlWarps * (TX + 1) * sizeof(int);
+    const size_t smem2 = (size_t)kLvlWarps * (TX + 1 + 64) * sizeof(int);
     const size_t smem2h = (size_t)(TX + 1) * sizeof(int);
     if (smem2 > 48 * 1024) {
         cudaFuncSetAttribute(k_seg_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2h);
@@ -902,12 +946,13 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2h, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist,
                                                         num_pairs, capacity, w.M2);
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
-    const dim3 g2((T + kColsPerBlock - 1) / kColsPerBlock, nsb2);
-    k_col_segsum<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, TX, num_pairs, capacity);
-    k_col_totals<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(nsb2, T, w.SS2, w.tcount, num_pairs,
+    const dim3 g2((T + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb2, kScanGridY));
+    k_col_segsum<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, w.segoff, TX, num_pairs, capacity);
+    k_col_totals<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(NSR, T, w.SS2, w.tcount, w.nseg, TX, num_pairs,
                                                                       capacity);
     k_scan_small<<<1, 1024, 0, st>>>(T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
-    k_col_base<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, TX, num_pairs, capacity);
+    k_col_base<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, w.segoff, TX, num_pairs,
+                                           capacity);
     k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
                                                          reinterpret_cast<uint2*>(ranges));
     if (capacity > 0)
