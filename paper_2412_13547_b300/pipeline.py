@@ -282,9 +282,9 @@ class TrainStep:
         return 1 + BIN_SORT_KERNELS + int(self.rast.longest_first) + 1 + 2 + 1 + (1 if self.fused else 2)
 
 
-# kernels in one gs_bin_sort call: pair count, depth keys, a 4-pass radix sort
+# kernels in one gs_bin_sort call: depth keys with the pair count, a 4-pass radix sort
 # of the depths (3 kernels a pass), 6 + 2 for the row level, 7 for the tile level
-BIN_SORT_KERNELS = 2 + 4 * 3 + 6 + 2 + 7
+BIN_SORT_KERNELS = 1 + 4 * 3 + 6 + 2 + 7
 
 
 # ---------------------------------------------------------------------------
