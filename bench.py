@@ -376,10 +376,7 @@ def run_batch(args, device):
         st._project(st.table(ph))
         ev[1].record()
         t = st.table(ph)
-        for i, v in enumerate(t.views):
-            tx, ty = R.gs_bin_grid(v.cam, v.dil)
-            R.gs_bin_sort(params.n, st.rects[i], st.tiles_touched[i], st.splats[i], tx, ty, st.workspace,
-                          st.capacity[i], st.sorted_ids[i], st.ranges[i], st.num_pairs[i:i + 1])
+        st.bin_views(t)
         R.gs_tile_order_batch(t, st.order)
         ev[2].record()
         R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt)

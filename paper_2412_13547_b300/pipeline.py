@@ -360,8 +360,11 @@ class BatchTrainStep:
         self.capacity = self._capacities(headroom) if capacity is None else \
             [int(c) for c in (capacity if hasattr(capacity, "__len__") else [capacity] * V)]
         self.sorted_ids = [torch.empty(max(1, c), dtype=torch.int32, device=dev) for c in self.capacity]
-        ws = max(R.gs_bin_sort_workspace_size(n, c, g[0], g[1]) for c, g in zip(self.capacity, self.bgrid0))
-        self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+        # the views bin concurrently, each on its own stream with its own workspace: one view's
+        # binning is a chain of small kernels that leaves most of the GPU idle
+        self.workspaces = [torch.empty(R.gs_bin_sort_workspace_size(n, c, g[0], g[1]), dtype=torch.uint8, device=dev)
+                           for c, g in zip(self.capacity, self.bgrid0)]
+        self.bin_streams = [torch.cuda.Stream(device=dev) for _ in range(V)]
 
     @property
     def phases(self) -> int:
@@ -420,14 +423,26 @@ class BatchTrainStep:
         R.gs_project_batch(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, t)
 
     # -- the step ---------------------------------------------------------------
+    def bin_views(self, t: R.ViewTable):
+        """Bins every view of the table, each on its own stream forked from and
+        joined back into the current one (also inside a graph capture)."""
+        main = torch.cuda.current_stream()
+        for i, v in enumerate(t.views):
+            tx, ty = R.gs_bin_grid(v.cam, v.dil)
+            s = self.bin_streams[i]
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty,
+                              self.workspaces[i], self.capacity[i], self.sorted_ids[i], self.ranges[i],
+                              self.num_pairs[i:i + 1])
+        for s in self.bin_streams[:len(t.views)]:
+            main.wait_stream(s)
+
     def render_pass(self, phase: int, counts: bool = False, table=None):
         """Everything up to the 2D gradients of every view (no parameter update)."""
         t = self.table(phase) if table is None else table
         self._project(t)
-        for i, v in enumerate(t.views):
-            tx, ty = R.gs_bin_grid(v.cam, v.dil)
-            R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty, self.workspace,
-                          self.capacity[i], self.sorted_ids[i], self.ranges[i], self.num_pairs[i:i + 1])
+        self.bin_views(t)
         order = None
         if self.longest_first:
             R.gs_tile_order_batch(t, self.order)
