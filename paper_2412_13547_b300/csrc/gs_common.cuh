@@ -206,27 +206,32 @@ __device__ __forceinline__ ShConst sh_const()
 // Basis values Y[0..(deg+1)^2) at the unit direction (x, y, z).
 __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y)
 {
+    // every operation rounded explicitly (no contraction left to the compiler), so the
+    // forward projection and every backward pass that recomputes the colour agree bit for
+    // bit, down to the clamp of a colour channel at zero
     const ShConst c = sh_const();
     Y[0] = c.k0;
     if (deg < 1) return;
-    Y[1] = -c.k1 * y;
-    Y[2] = c.k1 * z;
-    Y[3] = -c.k1 * x;
+    Y[1] = __fmul_rn(-c.k1, y);
+    Y[2] = __fmul_rn(c.k1, z);
+    Y[3] = __fmul_rn(-c.k1, x);
     if (deg < 2) return;
-    float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = c.k2a * x * y;
-    Y[5] = -c.k2a * y * z;
-    Y[6] = c.k2b * (2.0f * zz - xx - yy);
-    Y[7] = -c.k2a * x * z;
-    Y[8] = c.k2c * (xx - yy);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    Y[4] = __fmul_rn(__fmul_rn(c.k2a, x), y);
+    Y[5] = __fmul_rn(__fmul_rn(-c.k2a, y), z);
+    Y[6] = __fmul_rn(c.k2b, __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), xx), yy));
+    Y[7] = __fmul_rn(__fmul_rn(-c.k2a, x), z);
+    Y[8] = __fmul_rn(c.k2c, __fsub_rn(xx, yy));
     if (deg < 3) return;
-    Y[9] = -c.k3a * y * (3.0f * xx - yy);
-    Y[10] = c.k3b * x * y * z;
-    Y[11] = -c.k3c * y * (4.0f * zz - xx - yy);
-    Y[12] = c.k3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-    Y[13] = -c.k3c * x * (4.0f * zz - xx - yy);
-    Y[14] = c.k3e * z * (xx - yy);
-    Y[15] = -c.k3a * x * (xx - 3.0f * yy);
+    const float xx3 = __fmul_rn(3.0f, xx), yy3 = __fmul_rn(3.0f, yy);
+    const float t4 = __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy);
+    Y[9] = __fmul_rn(__fmul_rn(-c.k3a, y), __fsub_rn(xx3, yy));
+    Y[10] = __fmul_rn(__fmul_rn(__fmul_rn(c.k3b, x), y), z);
+    Y[11] = __fmul_rn(__fmul_rn(-c.k3c, y), t4);
+    Y[12] = __fmul_rn(__fmul_rn(c.k3d, z), __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), xx3), yy3));
+    Y[13] = __fmul_rn(__fmul_rn(-c.k3c, x), t4);
+    Y[14] = __fmul_rn(__fmul_rn(c.k3e, z), __fsub_rn(xx, yy));
+    Y[15] = __fmul_rn(__fmul_rn(-c.k3a, x), __fsub_rn(xx, yy3));
 }
 
 // Gradient of sum_k w_k Y_k(x, y, z) with respect to (x, y, z), for weights w.

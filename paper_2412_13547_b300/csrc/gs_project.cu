@@ -112,17 +112,22 @@ __device__ __forceinline__ void sh_colour(const Cam& cam, const float* mean, con
                                           float& inv_vlen, float* rgb_raw)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    float vx = mean[0] - cam.ccx, vy = mean[1] - cam.ccy, vz = mean[2] - cam.ccz;
-    inv_vlen = rsqrtf(vx * vx + vy * vy + vz * vz);
-    dir[0] = vx * inv_vlen; dir[1] = vy * inv_vlen; dir[2] = vz * inv_vlen;
+    // rounding pinned with intrinsics (as in sh_basis): the colour, and so the clamp of each
+    // channel, is the same in the forward and in every backward that recomputes it
+    const float vx = __fsub_rn(mean[0], cam.ccx), vy = __fsub_rn(mean[1], cam.ccy), vz = __fsub_rn(mean[2], cam.ccz);
+    // a Gaussian at the camera centre (culled: depth 0) gets the zero direction, so that
+    // its colour and colour gradients stay finite instead of 0 * inf
+    const float len2 = __fmaf_rn(vx, vx, __fmaf_rn(vy, vy, __fmul_rn(vz, vz)));
+    inv_vlen = len2 > 0.0f ? rsqrtf(len2) : 0.0f;
+    dir[0] = __fmul_rn(vx, inv_vlen); dir[1] = __fmul_rn(vy, inv_vlen); dir[2] = __fmul_rn(vz, inv_vlen);
     float Y[16];
     sh_basis(DEG, dir[0], dir[1], dir[2], Y);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.0f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
-        rgb_raw[ch] = acc + 0.5f;
+        for (int k = 0; k < K; ++k) acc = __fmaf_rn(Y[k], sh[k][ch], acc);
+        rgb_raw[ch] = __fadd_rn(acc, 0.5f);
     }
 }
 
@@ -592,22 +597,69 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     }
 }
 
+// The SH coefficients of Gaussian g straight from the storage array (one
+// lane's own row): 16-byte vector loads when rows are whole 16-byte units and
+// the array is 16-byte aligned, else element by element. Used by the batched
+// optimizer pass, which re-reads them per view (from L1 after the first).
+template <int DEG, int DT>
+__device__ __forceinline__ void load_sh_row(const void* sh, int g, float (&c)[16][3])
+{
+    constexpr int K = (DEG + 1) * (DEG + 1), E = K * 3;
+    constexpr int EB = DT == GS_DTYPE_F32 ? 4 : 2;
+    if constexpr ((E * EB) % 16 == 0) {
+        if ((reinterpret_cast<uintptr_t>(sh) & 15) == 0) {
+            constexpr int NV = E * EB / 16;
+            const uint4* row = reinterpret_cast<const uint4*>(static_cast<const char*>(sh) + (int64_t)g * E * EB);
+            uint32_t w[NV * 4];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const uint4 x = __ldg(row + v);
+                w[4 * v] = x.x; w[4 * v + 1] = x.y; w[4 * v + 2] = x.z; w[4 * v + 3] = x.w;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if constexpr (DT == GS_DTYPE_F32) {
+                    c[e / 3][e % 3] = __uint_as_float(w[e]);
+                } else {
+                    const uint16_t hv = (e & 1) ? (uint16_t)(w[e >> 1] >> 16) : (uint16_t)(w[e >> 1] & 0xffffu);
+                    if constexpr (DT == GS_DTYPE_BF16) c[e / 3][e % 3] = __bfloat162float(__ushort_as_bfloat16(hv));
+                    else c[e / 3][e % 3] = __half2float(__ushort_as_half(hv));
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) c[e / 3][e % 3] = load_sh_elem(sh, (int64_t)g * E + e, DT);
+}
+
 // Projection backward of one Gaussian in one view, added into the gradient
-// rows (the batched form; the one-view form takes the colour part first).
-// False when the view culls it.
-template <int DEG>
+// rows (the batched form). A view that did not render the Gaussian (no tile
+// touched) gave it a zero 2D gradient and is skipped, and so is a view whose
+// recomputed projection culls it (as the one-view backward does). The SH
+// coefficients are re-read for the view inside the colour part, so that they
+// are live only there. False when the view is skipped.
+template <int DEG, int DT>
 __device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const float* mean, const float* ls,
-                                                float4 q, float logit, const float (&c)[16][3], float* grow,
+                                                float4 q, float logit, const void* sh_store, float* grow,
                                                 float* gshrow, float4& gq, float& glogit, float* pos_acc,
                                                 float* col_acc, int* count)
 {
+    if (V.tiles[g] <= 0) return false;
     Proj P;
-    project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
+    project_geometry<DEG>(V.cam, V.dil, mean, ls, q, logit, P);
     if (P.culled) return false;
-    const float4 G0 = V.grad2d[3 * (int64_t)g], G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
-    densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
+    const float4 G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
     float gm_dir[3];
-    sh_colour_bwd<DEG, true>(P.dir, P.inv_vlen, P.rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
+    {
+        float c[16][3];
+        load_sh_row<DEG, DT>(sh_store, g, c);
+        float dir[3], inv_vlen, rgb_raw[3];
+        sh_colour<DEG>(V.cam, mean, c, dir, inv_vlen, rgb_raw);
+        sh_colour_bwd<DEG, true>(dir, inv_vlen, rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
+    }
+    const float4 G0 = V.grad2d[3 * (int64_t)g];
+    densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
     ParamGrad R;
     project_bwd_one(V.cam, P, G0, G1, gm_dir, R);
 #pragma unroll
@@ -645,7 +697,9 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
     float* s_gsh = reinterpret_cast<float*>(s_sh);
     warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[0]), n, g0, s_mean, lane);
     warp_stage<3, 3>(reinterpret_cast<const uint32_t*>(a.p[1]), n, g0, s_scale, lane);
-    if constexpr (L::STAGE) warp_stage<L::W, F::GS>(reinterpret_cast<const uint32_t*>(sh_store), n, g0, s_sh, lane);
+    // the one-view form stages the SH rows; the batched form re-reads each row per view
+    if constexpr (L::STAGE && !MULTI)
+        warp_stage<L::W, F::GS>(reinterpret_cast<const uint32_t*>(sh_store), n, g0, s_sh, lane);
     const int g = g0 + lane;
     const bool valid = g < n;
 
@@ -663,21 +717,21 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
             mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
             ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
         }
-        float c[16][3];
-        read_sh<DEG, DT, F::GS>(s_sh, sh_store, g, lane, c);
         const float4 q = reinterpret_cast<const float4*>(a.p[2])[g];
         const float logit = a.p[3][g];
-        // the staged SH of this row is in c now: the row takes the SH gradients
         if constexpr (MULTI) {
 #pragma unroll
             for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
             have_grad = true;
             for (int vi = 0; vi < b.nviews; ++vi)
-                fused_view_grad<DEG>(b.v[vi], g, mean, ls, q, logit, c, grow, gshrow, gq, glogit, pos_acc, col_acc,
-                                     count);
-        } else {
-            // the colour part first, so the SH coefficients are dead before the geometry: a
-            // Gaussian the view culls was not rendered, its 2D gradient is zero and so is all this
+                fused_view_grad<DEG, DT>(b.v[vi], g, mean, ls, q, logit, sh_store, grow, gshrow, gq, glogit,
+                                         pos_acc, col_acc, count);
+        } else if (b.v[0].tiles[g] > 0) {
+            // the colour part first, so the SH coefficients are dead before the geometry (the
+            // staged SH of this row is read into c, then the row takes the SH gradients). A
+            // Gaussian the view did not render has a zero 2D gradient: the zero rows below.
+            float c[16][3];
+            read_sh<DEG, DT, F::GS>(s_sh, sh_store, g, lane, c);
             const ViewDev& V = b.v[0];
             const float4 G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
             float dir[3], inv_vlen, rgb_raw[3], gm_dir[3];
@@ -686,7 +740,12 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
             have_grad = true;
             Proj P;
             project_geometry<DEG>(V.cam, V.dil, mean, ls, q, logit, P);
-            if (!P.culled) {
+            if (P.culled) {
+                // only with tiles counted at other parameters than these: no gradient, as in
+                // the unfused backward
+#pragma unroll
+                for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
+            } else {
                 const float4 G0 = V.grad2d[3 * (int64_t)g];
                 densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
                 ParamGrad R;

@@ -267,12 +267,18 @@ def test_fused_batch_equals_summed_single_views(batch, sparse):
     vis_any = torch.stack([b["tiles_touched"] > 0 for b in V.bufs]).any(0)
     mask = vis_any.to(torch.uint8) if sparse else None
     for step in (1, 2):
-        gsum = None
+        # each step starts both paths from the same state: two trajectories would drift apart by
+        # rounding and could then take a colour channel's clamp at zero differently
+        for key in ("p", "m", "v"):
+            for x, y in zip(ref[key], fused[key]):
+                x.copy_(y)
+        gsum = gabs = None
         for i, b in enumerate(V.bufs):
             g = [torch.empty_like(x) for x in ref["p"]]
             R.gs_project_bwd(*ref["p"][:4], ref["p"][4], V.cams[i], V.dils[i], b["tiles_touched"], b["grad2d"], *g,
                              *ref["stats"])
             gsum = g if gsum is None else [x + y for x, y in zip(gsum, g)]
+            gabs = [x.abs() for x in g] if gabs is None else [x + y.abs() for x, y in zip(gabs, g)]
         ent = [dict(param=ref["p"][j], grad=gsum[j], m=ref["m"][j], v=ref["v"][j], lr=lrs[j]) for j in range(5)]
         R.gs_adam(ent, 0.9, 0.999, 1e-15, step, row_mask=mask)
         gout = [torch.full_like(x, 7.0) for x in fused["p"]]
@@ -280,8 +286,11 @@ def test_fused_batch_equals_summed_single_views(batch, sparse):
                                     t, sparse=sparse, pos_acc=fused["stats"][0], col_acc=fused["stats"][1],
                                     count=fused["stats"][2], grads_out=gout)
         torch.cuda.synchronize()
-        for x, y in zip(gout, gsum):
-            assert U.max_rel(x.cpu().numpy(), y.cpu().numpy()) < 1e-5
+        # the views' terms may cancel: the rounding of their sum is bounded relative to the sum
+        # of their magnitudes, and the two paths round it in different orders
+        for x, y, z in zip(gout, gsum, gabs):
+            err = np.abs(x.cpu().numpy().astype(np.float64) - y.cpu().numpy()).max()
+            assert err <= 1e-5 * float(z.max().item()), err
     for key, rtol in (("p", 1e-6), ("m", 1e-5), ("v", 1e-5), ("stats", 1e-6)):
         for x, y in zip(ref[key], fused[key]):
             assert U.max_rel(x.float().cpu().numpy(), y.float().cpu().numpy()) < rtol, key

@@ -17,7 +17,8 @@ import torch
 from oracle import oracle as orc
 from paper_2412_13547_b300 import raster as R
 from paper_2412_13547_b300 import scenes
-from paper_2412_13547_b300.pipeline import GaussianParams, Rasterizer, TrainStep, AdamConfig, image_buffers
+from paper_2412_13547_b300.pipeline import (AdamConfig, BatchTrainStep, GaussianParams, Rasterizer, TrainStep,
+                                            image_buffers)
 
 import gpu_util as U
 
@@ -497,6 +498,34 @@ def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
+
+def _camera_centre(cam):
+    """-R^T T evaluated as the library does (double, then FP32)."""
+    Rm = np.asarray(cam.R, np.float32).reshape(-1).astype(np.float64)
+    T = np.asarray(cam.T, np.float32).reshape(-1).astype(np.float64)
+    return np.array([-(Rm[j] * T[0] + Rm[3 + j] * T[1] + Rm[6 + j] * T[2]) for j in range(3)], np.float32)
+
+
+@pytest.mark.parametrize("views", [1, 2])
+def test_gaussian_at_the_camera_centre_stays_finite(views):
+    """A Gaussian exactly at the camera centre is culled (depth 0); its view
+    direction has zero length. The fused optimizer passes (one view, and the
+    batched form) must leave every parameter and moment finite."""
+    p32, cam, tgt = scene_sh3()
+    p32 = {k: v.copy() for k, v in p32.items()}
+    p32["means"][0] = _camera_centre(cam)
+    p = U.gpu_params(p32)
+    cams = [cam, scenes.look_at(scenes.orbit_eye(3.0, 150.0, 20.0), width=cam.width, height=cam.height)][:views]
+    targets = [torch.tensor(scenes.target_image(c.width, c.height, 11 + i), device=U.DEV) for i, c in enumerate(cams)]
+    step = BatchTrainStep(p, cams, targets, d=2)
+    for ph in range(3):
+        step.run(ph)
+    torch.cuda.synchronize()
+    assert not step.overflowed()
+    for t in list(p.tensors()) + step.m + step.v:
+        assert bool(torch.isfinite(t).all())
+    assert int(step.vis_count[0].item()) == 0
+
 
 def test_empty_and_all_culled():
     _, cam, _ = scene_small()
