@@ -300,15 +300,20 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
         mean[j] = __uint_as_float(s_mean[lane * 3 + j]);
         ls[j] = __uint_as_float(s_scale[lane * 3 + j]);
     }
-    float c[16][3];
-    read_sh<DEG, DT>(s_sh, sh, g, lane, c);
     const float4 q = quats[g];
     const float logit = logits[g];
     const int nv = MULTI ? b.nviews : 1;
     for (int vi = 0; vi < nv; ++vi) {
         const ViewDev& V = b.v[MULTI ? vi : 0];
+        // project_one, with the SH coefficients read from the staged row only for a view
+        // that keeps the Gaussian (they are live for its colour alone)
         Proj P;
-        project_one<DEG>(V.cam, V.dil, mean, ls, q, logit, c, P);
+        project_geometry<DEG>(V.cam, V.dil, mean, ls, q, logit, P);
+        if (!P.culled) {
+            float c[16][3];
+            read_sh<DEG, DT>(s_sh, sh, g, lane, c);
+            sh_colour<DEG>(V.cam, mean, c, P.dir, P.inv_vlen, P.rgb_raw);
+        }
         float4* out = V.splats + 4 * (int64_t)g;
         if (P.culled) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
