@@ -381,7 +381,8 @@ def run_batch(args, device):
         ev[2].record()
         R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt)
         R.gs_loss_l1_batch(t)
-        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.order, zero_grad2d=True, pixels_per_thread=ppt)
+        R.gs_tile_order_by_last_batch(t, st.bwd_order)
+        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.bwd_order, zero_grad2d=True, pixels_per_thread=ppt)
         ev[3].record()
         st.optimize(ph)
         ev[4].record()

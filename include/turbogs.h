@@ -395,6 +395,19 @@ int32_t gs_project_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * blend launches. */
 int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream);
 
+/* gs_tile_order_by_last_batch -- the launch order for the backward blend
+ * (gs_render_bwd_batch, or gs_render_bwd with a one-view table), after the
+ * forward: the blend tiles of all views, numbered as in gs_tile_order_batch,
+ * longest-first by the largest `last` over each tile's pixels (the list
+ * positions its backward replays), 8 buckets per power of two. With coarse
+ * binning this ranks the blend tiles of one binning tile by their own work,
+ * which the list length cannot. Inputs (device): each view's last
+ * (h_ds x w_ds) and ranges. Output (device): order (sum_v tiles_v). Above
+ * 49152 tiles in all, the keys do not fit the sort's shared memory and the
+ * list-length order of gs_tile_order_batch is written instead. Scheduling
+ * only: the backward's results do not depend on it. */
+int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream);
+
 /* gs_render_fwd / gs_loss_l1 / gs_render_bwd for every view in one launch each;
  * the blend launches take the tiles of all views from one work queue
  * (tile_order, nullable = view by view). counts as in gs_render_fwd, summed

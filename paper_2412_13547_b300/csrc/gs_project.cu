@@ -275,7 +275,7 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
 // its 32 parameter rows once and loops over the views, so the parameters are
 // read once per batch whatever the number of views.
 template <int DEG, int DT, bool MULTI>
-__global__ void __launch_bounds__(kThreads, MULTI ? 1 : 6)
+__global__ void __launch_bounds__(kThreads, MULTI ? 1 : 8)
 k_project(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
           const float4* __restrict__ quats, const float* __restrict__ logits, const void* __restrict__ sh,
           const __grid_constant__ Batch b)

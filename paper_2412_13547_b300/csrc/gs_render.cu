@@ -704,6 +704,15 @@ int resolve_ppt(int tile, int ppt)
 // Tile order, longest list first: 256 buckets of the list length (8 per
 // octave, descending), one block. Order inside a bucket is arbitrary; it only
 // affects scheduling, never results.
+// Longest-first bucket of a work key: 8 buckets per power of two, descending.
+__device__ __forceinline__ int order_bucket(uint32_t len)
+{
+    const uint32_t x = len + 1u;
+    const int e = 31 - __clz(x);
+    const int m = (int)((x >> (e > 3 ? e - 3 : 0)) << (e > 3 ? 0 : 3 - e)) & 7;
+    return 255 - min(255, e * 8 + m);
+}
+
 __device__ __forceinline__ uint2 batch_range(const Batch& b, int gt)
 {
     const ViewDev& V = b.v[view_of_tile(b, gt)];
@@ -717,15 +726,9 @@ __global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Bat
     __shared__ uint32_t s_off[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    auto bucket = [](uint32_t len) -> int {
-        const uint32_t x = len + 1u;
-        const int e = 31 - __clz(x);
-        const int m = (int)((x >> (e > 3 ? e - 3 : 0)) << (e > 3 ? 0 : 3 - e)) & 7;
-        return 255 - min(255, e * 8 + m);
-    };
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         const uint2 r = batch_range(b, t);
-        atomicAdd(&s_hist[bucket(r.y - r.x)], 1u);
+        atomicAdd(&s_hist[order_bucket(r.y - r.x)], 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -738,9 +741,57 @@ __global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Bat
     __syncthreads();
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         const uint2 r = batch_range(b, t);
-        order[atomicAdd(&s_off[bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+        order[atomicAdd(&s_off[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
     }
 }
+
+// Backward work key of every blend tile of the batch: the largest `last` over
+// its pixels (the list positions its backward replays), one warp per tile,
+// written to key[global tile].
+__global__ void __launch_bounds__(256) k_tile_last_max(const __grid_constant__ Batch b, uint32_t* __restrict__ key)
+{
+    const int gt = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (gt >= b.total_tiles) return;  // uniform over the warp
+    const ViewDev& V = b.v[view_of_tile(b, gt)];
+    const int t = gt - V.tile_begin, T = V.dil.tile;
+    const int tx = t % V.dil.tiles_x, ty = t / V.dil.tiles_x;
+    const int u0 = tx * T, v0 = ty * T;
+    const int w = min(T, V.dil.w_ds - u0), h = min(T, V.dil.h_ds - v0);
+    uint32_t m = 0u;
+    for (int i = lane; i < w * h; i += 32) {
+        const int du = i % w, dv = i / w;
+        m = max(m, V.last[(int64_t)(v0 + dv) * V.dil.w_ds + u0 + du]);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) key[gt] = m;
+}
+
+// Longest-first order of the tiles by the keys in `order` (read into shared
+// memory first, then overwritten by the order). One CTA; T keys fit in
+// its dynamic shared memory.
+__global__ void __launch_bounds__(1024) k_tile_order_keys(int T, uint32_t* __restrict__ order)
+{
+    extern __shared__ uint32_t s_key[];
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_off[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) s_key[t] = order[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&s_hist[order_bucket(s_key[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int k = 0; k < 256; ++k) {
+            s_off[k] = run;
+            run += s_hist[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        order[atomicAdd(&s_off[order_bucket(s_key[t])], 1u)] = (uint32_t)t;
+}
+
+constexpr int kMaxKeyedOrderTiles = 48 * 1024;  // keys held in 192 KB of shared memory
 
 bool check_render_view(int32_t n, const ViewDev& v)
 {
@@ -923,6 +974,31 @@ int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order
     if (!order) { gs_host::set_error("gs_tile_order_batch: order is null"); return GS_ERR_ARG; }
     k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
     return gs_host::check_launch("gs_tile_order_batch");
+}
+
+int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream)
+{
+    using namespace gs;
+    Batch b;
+    if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    for (int i = 0; i < nviews; ++i)
+        if (!b.v[i].last || !b.v[i].ranges) {
+            gs_host::set_error("gs_tile_order_by_last_batch: null last or ranges");
+            return GS_ERR_ARG;
+        }
+    if (!order) { gs_host::set_error("gs_tile_order_by_last_batch: order is null"); return GS_ERR_ARG; }
+    const int T = b.total_tiles;
+    if (T == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (T > kMaxKeyedOrderTiles) {  // more keys than shared memory holds: the list-length order
+        k_tile_order<<<1, 1024, 0, st>>>(b, order);
+        return gs_host::check_launch("gs_tile_order_by_last_batch");
+    }
+    k_tile_last_max<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(b, order);
+    const size_t smem = (size_t)T * sizeof(uint32_t);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_order_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tile_order_keys<<<1, 1024, smem, st>>>(T, order);
+    return gs_host::check_launch("gs_tile_order_by_last_batch");
 }
 
 int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, float* dl_dimg,

@@ -84,6 +84,7 @@ class Rasterizer:
             self.max_tiles = int(num_tiles)
             self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
             self.tile_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
+            self.bwd_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
 
     def ensure_grid(self, tiles_x: int, tiles_y: int):
         """Grow the workspace so that binning grids up to (tiles_x, tiles_y) fit."""
@@ -135,9 +136,13 @@ class Rasterizer:
                         pixels_per_thread=self.ppt, tile_order=self.tile_order if self.longest_first else None)
 
     def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg, zero_grad2d: bool = True):
+        order = None
+        if self.longest_first:
+            # the backward's own launch order: tiles by the list positions they replay
+            R.gs_tile_order_by_last_batch([R.View(cam, dil, ranges=self.ranges, last=last)], self.bwd_order)
+            order = self.bwd_order
         R.gs_render_bwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, t_final, last, dl_dimg,
-                        self.grad2d, zero_grad2d=zero_grad2d, pixels_per_thread=self.ppt,
-                        tile_order=self.tile_order if self.longest_first else None)
+                        self.grad2d, zero_grad2d=zero_grad2d, pixels_per_thread=self.ppt, tile_order=order)
 
 
 def image_buffers(h_ds: int, w_ds: int, device="cuda"):
@@ -279,7 +284,7 @@ class TrainStep:
         """Kernels one step launches (memsets not counted): projection, the
         binning, the tile order, blend, loss (zeroing + reduction), blend
         backward, and the fused optimizer (or projection backward + Adam)."""
-        return 1 + BIN_SORT_KERNELS + int(self.rast.longest_first) + 1 + 2 + 1 + (1 if self.fused else 2)
+        return 1 + BIN_SORT_KERNELS + 3 * int(self.rast.longest_first) + 1 + 2 + 1 + (1 if self.fused else 2)
 
 
 # kernels in one gs_bin_sort call: depth keys with the pair count, a 4-pass radix sort
@@ -345,6 +350,7 @@ class BatchTrainStep:
         self.last = [torch.empty(g[1], g[0], dtype=torch.int32, device=dev) for g in self.grid0]
         self.dl = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
         self.order = torch.zeros(sum(g[2] * g[3] for g in self.grid0), dtype=torch.int32, device=dev)
+        self.bwd_order = torch.zeros_like(self.order)
         # moments, device-side Adam step and densification statistics
         st = state or {}
         self.m = st.get("m") or [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -450,6 +456,9 @@ class BatchTrainStep:
         R.gs_render_fwd_batch(self.p.n, t, self.bg, tile_order=order, counts=self.counts if counts else None,
                               pixels_per_thread=self.ppt)
         R.gs_loss_l1_batch(t)
+        if self.longest_first:
+            R.gs_tile_order_by_last_batch(t, self.bwd_order)
+            order = self.bwd_order
         R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True, pixels_per_thread=self.ppt)
 
     def optimize(self, phase: int, table=None):
@@ -498,9 +507,10 @@ class BatchTrainStep:
 
     def launches_per_step(self) -> int:
         """Kernels one step launches (memsets not counted): projection, the
-        binning of every view, the tile order, both blend launches, the loss
+        binning of every view, the tile orders (the forward's, and the
+        backward's from `last`: two kernels), both blend launches, the loss
         (zeroing + reduction), and the Adam step advance + the fused optimizer."""
-        return 1 + BIN_SORT_KERNELS * self.V + int(self.longest_first) + 1 + 2 + 1 + \
+        return 1 + BIN_SORT_KERNELS * self.V + 3 * int(self.longest_first) + 1 + 2 + 1 + \
             (2 if self.optimize_step else 0)
 
 

@@ -28,7 +28,7 @@ MAX_VIEWS = 16
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_bin_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
            "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
-           "gs_tile_order_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
+           "gs_tile_order_batch", "gs_tile_order_by_last_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
            "gs_project_bwd_adam_batch", "gs_densify_workspace_size", "gs_densify_select", "gs_prune_select",
            "gs_gather_rows", "gs_densify_grow")
 
@@ -186,6 +186,7 @@ def load():
     view_p = ctypes.POINTER(GsView)
     lib.gs_project_batch.argtypes = [i32, i32, i32, P, P, P, P, P, view_p, i32, P]
     lib.gs_tile_order_batch.argtypes = [view_p, i32, P, P]
+    lib.gs_tile_order_by_last_batch.argtypes = [view_p, i32, P, P]
     lib.gs_render_fwd_batch.argtypes = [i32, view_p, i32, P, P, P, i32, P]
     lib.gs_loss_l1_batch.argtypes = [view_p, i32, P]
     lib.gs_render_bwd_batch.argtypes = [i32, view_p, i32, P, P, i32, i32, P]
@@ -408,9 +409,23 @@ def gs_project_batch(means, log_scales, quats, opacity_logits, sh, views, stream
                                    _stream(stream)), "gs_project_batch")
 
 
+def _total_tiles(t: ViewTable) -> int:
+    return sum(g[2] * g[3] for g in (gs_grid(v.cam, v.dil) for v in t.views))
+
+
 def gs_tile_order_batch(views, order, stream=None):
     t = _table(views)
+    _need(order, _total_tiles(t), "order")
     _check(load().gs_tile_order_batch(t.arr, t.n, _ptr(order), _stream(stream)), "gs_tile_order_batch")
+
+
+def gs_tile_order_by_last_batch(views, order, stream=None):
+    """Backward launch order: tiles longest-first by the largest `last` over
+    their pixels (call after the forward)."""
+    t = _table(views)
+    _need(order, _total_tiles(t), "order")
+    _check(load().gs_tile_order_by_last_batch(t.arr, t.n, _ptr(order), _stream(stream)),
+           "gs_tile_order_by_last_batch")
 
 
 def gs_render_fwd_batch(n, views, bg, tile_order=None, counts=None, pixels_per_thread=0, stream=None):

@@ -291,6 +291,43 @@ def test_longest_first_order_does_not_change_results():
     assert U.max_rel(outs[1][3], outs[0][3]) < 1e-5
 
 
+def _tile_max_last(last, tile, tx, ty):
+    h, w = last.shape
+    pad = np.zeros((ty * tile, tx * tile), np.int64)
+    pad[:h, :w] = last
+    return pad.reshape(ty, tile, tx, tile).max(axis=(1, 3)).reshape(-1)
+
+
+@pytest.mark.parametrize("shift", [0, 2])
+def test_backward_order_by_last(shift):
+    """gs_tile_order_by_last_batch: a permutation of all blend tiles of all
+    views, non-increasing (up to the 8-per-octave bucketing) in the largest
+    `last` of each tile, also with coarse binning, where the tiles of one
+    binning tile share a list length but not their work."""
+    p32, cam, _ = scene_clusters(20000, 400, 256)
+    cams = [cam, scenes.look_at(scenes.orbit_eye(2.6, 150.0, 35.0), width=301, height=207)]
+    dils = [R.Dilation(2, 1, 0, bin_shift=shift), R.Dilation(1, 0, 0, bin_shift=shift)]
+    keys, total = [], 0
+    views, alive = [], []
+    for c, d in zip(cams, dils):
+        out, rast, p, (img, tf, last) = U.run_forward(p32, c, d)
+        w_ds, h_ds, tx, ty = R.gs_grid(c, d)
+        keys.append(_tile_max_last(out["last"].astype(np.int64), d.tile, tx, ty))
+        views.append(R.View(c, d, ranges=rast.ranges, last=last))
+        total += tx * ty
+        alive.append((rast, last))
+    order = torch.full((total,), -1, dtype=torch.int32, device=U.DEV)
+    R.gs_tile_order_by_last_batch(views, order)
+    torch.cuda.synchronize()
+    o = order.cpu().numpy()
+    assert sorted(o.tolist()) == list(range(total))
+    k = np.concatenate(keys)[o]
+    assert k.max() > 0
+    assert np.all(k[:-1] + 1 >= (k[1:] + 1) * 0.875)
+    with pytest.raises(ValueError):
+        R.gs_tile_order_by_last_batch(views, order[:total - 1])
+
+
 def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
     out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg)
     rng = np.random.default_rng(seed)
