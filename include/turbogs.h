@@ -401,8 +401,8 @@ int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order
  * longest-first by the largest `last` over each tile's pixels (the list
  * positions its backward replays), 8 buckets per power of two. With coarse
  * binning this ranks the blend tiles of one binning tile by their own work,
- * which the list length cannot. Inputs (device): each view's last
- * (h_ds x w_ds) and ranges. Output (device): order (sum_v tiles_v). Above
+ * which the list length cannot. Input (device): each view's last
+ * (h_ds x w_ds). Output (device): order (sum_v tiles_v). Above
  * 49152 tiles in all, the keys do not fit the sort's shared memory and the
  * list-length order of gs_tile_order_batch is written instead. Scheduling
  * only: the backward's results do not depend on it. */

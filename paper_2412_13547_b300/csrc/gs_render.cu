@@ -982,8 +982,8 @@ int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_
     Batch b;
     if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
     for (int i = 0; i < nviews; ++i)
-        if (!b.v[i].last || !b.v[i].ranges) {
-            gs_host::set_error("gs_tile_order_by_last_batch: null last or ranges");
+        if (!b.v[i].last) {
+            gs_host::set_error("gs_tile_order_by_last_batch: null last");
             return GS_ERR_ARG;
         }
     if (!order) { gs_host::set_error("gs_tile_order_by_last_batch: order is null"); return GS_ERR_ARG; }

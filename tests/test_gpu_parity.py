@@ -326,6 +326,10 @@ def test_backward_order_by_last(shift):
     assert np.all(k[:-1] + 1 >= (k[1:] + 1) * 0.875)
     with pytest.raises(ValueError):
         R.gs_tile_order_by_last_batch(views, order[:total - 1])
+    # the forward's order of the same views is a permutation too
+    R.gs_tile_order_batch([R.View(v.cam, v.dil, ranges=v.ranges) for v in views], order)
+    torch.cuda.synchronize()
+    assert sorted(order.cpu().numpy().tolist()) == list(range(total))
 
 
 def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
