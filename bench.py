@@ -536,6 +536,16 @@ def oracle_sample(n_arg, d=2, n_tiles=16, seed=0):
                            adam_s=t4 - t3, tiles=n_tiles, tiles_total=tx * ty, sample_wall_s=t4 - t0)
 
 
+def headline_config(workload, n, width, height, world):
+    """The workload description both arms print (the same dict for the same run)."""
+    return {"workload": ("uhd-3840x2160-3M-gaussians-sh3" if workload == "uhd" else
+                         "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
+            "n_gaussians": n, "resolution": [width, height], "d": 2, "tile": TILE[0],
+            "bin_tile": TILE[0] << bin_shift_for(2),
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (params 708 MB, pair buffers > 1 GB)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -556,8 +566,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "uhd-3840x2160-3M-gaussians-sh3", "d": 2, "offset": "rotating",
-                       "n_gaussians": args.n, "resolution": [3840, 2160]},
+            "config": headline_config("uhd", args.n, 3840, 2160, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -710,12 +719,7 @@ def main():
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("uhd-3840x2160-3M-gaussians-sh3" if args.workload == "uhd" else
-                                "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
-                   "n_gaussians": params.n, "resolution": [cam.width, cam.height], "d": 2, "tile": TILE[0],
-                   "bin_tile": TILE[0] << bin_shift_for(2),
-                   "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 "
-                   "(params 708 MB, pair buffers > 1 GB)"},
+        "config": headline_config(args.workload, params.n, cam.width, cam.height, world),
         "blends_per_s": round(head["blends_evaluated_per_s"], 1),
         "blends_contributing_per_s": round(head["blends_contributing_per_s"], 1),
         "variants": variants, "stage_ms": stage_tables,
