@@ -434,7 +434,10 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     const float xr = (float)(dil.d * wb.lx);
     const uint2 rg = ranges[FILTER ? bin_tile_of(dil, tile) : tile];
 
-    float T[PPT], S0[PPT], S1[PPT], S2[PPT], g0[PPT], g1[PPT], g2[PPT], yr[PPT];
+    // gS: the pixel's colour gradient dotted with the colour accumulated behind the entry
+    // being replayed (starting with T_final * bg). dL/dalpha only needs that dot product,
+    // so one scalar per pixel replaces the three accumulated channels.
+    float T[PPT], gS[PPT], g0[PPT], g1[PPT], g2[PPT], yr[PPT];
     uint32_t n_last[PPT];
     uint32_t my_max = 0;
 #pragma unroll
@@ -450,7 +453,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
             g1[k] = dl_dimg[3 * pix + 1];
             g2[k] = dl_dimg[3 * pix + 2];
         }
-        S0[k] = T[k] * bg.x; S1[k] = T[k] * bg.y; S2[k] = T[k] * bg.z;
+        gS[k] = T[k] * (g0[k] * bg.x + g1[k] * bg.y + g2[k] * bg.z);
         my_max = max(my_max, n_last[k]);
     }
     const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
@@ -570,11 +573,10 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     r[6] = fmaf(w, g0[k], r[6]);
                     r[7] = fmaf(w, g1[k], r[7]);
                     r[8] = fmaf(w, g2[k], r[8]);
-                    const float dalpha = g0[k] * (Ti * c.x - S0[k] * inv) + g1[k] * (Ti * c.y - S1[k] * inv) +
-                                         g2[k] * (Ti * c.z - S2[k] * inv);
-                    S0[k] = fmaf(c.x, w, S0[k]);
-                    S1[k] = fmaf(c.y, w, S1[k]);
-                    S2[k] = fmaf(c.z, w, S2[k]);
+                    // dL/dalpha = sum_ch g_ch (T_i c_ch - S_ch / (1 - alpha)) = (T g.c - g.S) / (1 - alpha)
+                    const float gc = fmaf(g2[k], c.z, fmaf(g1[k], c.y, g0[k] * c.x));
+                    const float dalpha = inv * fmaf(T[k], gc, -gS[k]);
+                    gS[k] = fmaf(w, gc, gS[k]);
                     T[k] = Ti;
                     if (a_raw < kAlphaMax) {
                         const float dpower = a_raw * dalpha;
