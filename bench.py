@@ -382,7 +382,8 @@ def run_batch(args, device):
         R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt)
         R.gs_loss_l1_batch(t)
         R.gs_tile_order_by_last_batch(t, st.bwd_order)
-        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.bwd_order, zero_grad2d=True, pixels_per_thread=ppt)
+        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.bwd_order, zero_grad2d=True,
+                              pixels_per_thread=st.bwd_ppt)
         ev[3].record()
         st.optimize(ph)
         ev[4].record()
@@ -412,7 +413,8 @@ def run_batch(args, device):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "views_per_s": round(8000.0 / ms, 2),
         "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": d,
-                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt, "bin_tile": tile << shift,
+                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt,
+                   "bwd_pixels_per_thread": "library default for the tile (4 at tile 16)", "bin_tile": tile << shift,
                    "resolutions": [[c.width, c.height] for c in cams], "n_gaussians": params.n,
                    "graph": "one CUDA graph per offset phase, replayed", "l2": "inputs larger than L2"},
         "autotune_ms": {f"tile{k[0]}_ppt{k[1]}_bin{k[0] << k[2]}": round(v, 3) for k, v in table.items()},

@@ -314,7 +314,7 @@ class BatchTrainStep:
                  bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
                  pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
                  capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0,
-                 state=None):
+                 state=None, bwd_pixels_per_thread: int = 0):
         """cams/targets: the views of the batch (any later batch given to
         run(table=views_table(...)) must have no larger images). state: optional
         dict of m, v (lists), pos_acc, col_acc, count and step_dev to continue
@@ -326,6 +326,7 @@ class BatchTrainStep:
         self.cams, self.V = list(cams), len(cams)
         self.sparse, self.densify, self.optimize_step = bool(sparse), bool(densify), bool(optimize)
         self.tile, self.ppt, self.center_mode = int(tile), int(pixels_per_thread), int(center_mode)
+        self.bwd_ppt = int(bwd_pixels_per_thread)  # 0: the library's default for the backward
         self.bin_shift = int(bin_shift)
         self.longest_first = bool(longest_first)
         n, V = params.n, self.V
@@ -459,7 +460,8 @@ class BatchTrainStep:
         if self.longest_first:
             R.gs_tile_order_by_last_batch(t, self.bwd_order)
             order = self.bwd_order
-        R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True, pixels_per_thread=self.ppt)
+        R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True,
+                              pixels_per_thread=self.bwd_ppt)
 
     def optimize(self, phase: int, table=None):
         p, a = self.p, self.adam
@@ -519,7 +521,8 @@ def autotune_batch(params: GaussianParams, cams, targets, d: int = 1,
                                (32, 4, 0), (32, 4, 1)),
                    iters: int = 3, **kw):
     """Pick the launch shape of a batch: blend tile size, pixels per thread of
-    the blend CTAs and binning tile shift. Times ``render_pass`` (projection,
+    the forward blend CTAs (the backward takes the library's default for the
+    tile) and binning tile shift. Times ``render_pass`` (projection,
     binning, both blend launches and the loss: everything the shape affects)
     of every candidate (tile, ppt[, bin_shift]) with CUDA events and returns
     ((tile, ppt, bin_shift), {candidate: ms})."""
