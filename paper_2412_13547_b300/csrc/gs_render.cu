@@ -126,7 +126,9 @@ template <int TILE, int PPT>
 struct TileGeom {
     static constexpr int PIXELS = TILE * TILE;
     static constexpr int THREADS = PIXELS / PPT;
-    static constexpr int BATCH = PIXELS < 256 ? PIXELS : 256;
+    // staged list entries per batch: 256, but 192 for the 64-thread CTAs of tile 16 at 4 pixels per
+    // thread (the backward's default), whose staging arrays then leave room for more CTAs per SM
+    static constexpr int BATCH = (TILE == 16 && PPT == 4) ? 192 : (PIXELS < 256 ? PIXELS : 256);
     static constexpr int WROWS = 4 * PPT;        // rows of a warp's block
     static constexpr int WCOLS = TILE / 8;       // warp blocks across the tile
 };
