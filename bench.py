@@ -414,7 +414,7 @@ def run_batch(args, device):
         "views_per_s": round(8000.0 / ms, 2),
         "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": d,
                    "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt,
-                   "bwd_pixels_per_thread": "library default for the tile (4 at tile 16)", "bin_tile": tile << shift,
+                   "bwd_pixels_per_thread": "library default (4 at tile 16 from 4096 tiles, else 2)", "bin_tile": tile << shift,
                    "resolutions": [[c.width, c.height] for c in cams], "n_gaussians": params.n,
                    "graph": "one CUDA graph per offset phase, replayed", "l2": "inputs larger than L2"},
         "autotune_ms": {f"tile{k[0]}_ppt{k[1]}_bin{k[0] << k[2]}": round(v, 3) for k, v in table.items()},

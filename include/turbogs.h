@@ -221,9 +221,10 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
  *   zeroes it).
  * pixels_per_thread: launch shape, not semantics -- each thread of the
  *   tile's CTA handles this many pixels: 0 = the library default (1 for tile
- *   8, else 2; gs_render_bwd: 4 for tile 16), else 1 or 2 for tile 8, 1, 2 or
- *   4 for tile 16, 2 or 4 for tile 32 (whole warps, at most 512 threads;
- *   others give GS_ERR_ARG). Results are identical for every value.
+ *   8, else 2; gs_render_bwd: 4 for tile 16 when the launch has at least 4096
+ *   tiles), else 1 or 2 for tile 8, 1, 2 or 4 for tile 16, 2 or 4 for tile 32
+ *   (whole warps, at most 512 threads; others give GS_ERR_ARG). Results are
+ *   identical for every value.
  * tile_order (nullable, device, tiles_x*tiles_y entries): the blend tiles in
  *   the order their CTAs should start, e.g. from gs_tile_order_batch.
  *   Scheduling only: the results do not depend on it. */

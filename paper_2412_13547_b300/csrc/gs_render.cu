@@ -693,12 +693,16 @@ __global__ void k_loss_l1(const __grid_constant__ Batch b)
 // Pixels per thread: 0 picks the default; otherwise 1, 2 or 4 such that the
 // CTA is whole warps and at most 512 threads (tile 8: 1 or 2; tile 32: 2 or 4).
 // The kernels use full-warp shuffles and votes, so a partial warp is refused.
-// Defaults: the forward 1 at tile 8, else 2; the backward the same but 4 at
-// tile 16, where its per-entry warp reduction then serves 128 pixels (measured
-// 5% faster on the 4K step than 2; the forward is faster at 2).
-int resolve_ppt(int tile, int ppt, bool bwd)
+// Defaults: the forward 1 at tile 8, else 2; the backward the same, but 4 at
+// tile 16 when the launch has at least kWideBwdTiles tiles: its per-entry warp
+// reduction then serves 128 pixels (8% faster on the 4K step, 8160 tiles),
+// while on fewer tiles the halved warps per CTA leave the SMs short of warps
+// (30% slower at 1920x1080 d=2, 2040 tiles). The forward is fastest at 2.
+constexpr int kWideBwdTiles = 4096;
+
+int resolve_ppt(int tile, int ppt, bool bwd, int tiles)
 {
-    if (ppt == 0) return tile == 8 ? 1 : ((bwd && tile == 16) ? 4 : 2);
+    if (ppt == 0) return tile == 8 ? 1 : ((bwd && tile == 16 && tiles >= kWideBwdTiles) ? 4 : 2);
     const int threads = (ppt == 1 || ppt == 2 || ppt == 4) ? tile * tile / ppt : 0;
     if (threads < 32 || threads > 512 || threads % 32 != 0) {
         gs_host::set_error("pixels_per_thread must be 0 (default), 1, 2 or 4, giving 32..512 threads per tile "
@@ -895,7 +899,7 @@ int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, cons
         }
     }
     if (!bg) { gs_host::set_error("gs_render_fwd: bg is null"); return GS_ERR_ARG; }
-    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread, false);
+    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread, false, b.total_tiles);
     if (ppt < 0) return GS_ERR_ARG;
     const float3 c = make_float3(bg[0], bg[1], bg[2]);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -941,7 +945,7 @@ int32_t gs_render_bwd_batch(int32_t n, const GsView* views, int32_t nviews, cons
         }
     }
     if (!bg) { gs_host::set_error("gs_render_bwd: bg is null"); return GS_ERR_ARG; }
-    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread, true);
+    const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread, true, b.total_tiles);
     if (ppt < 0) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (zero_grad2d && n > 0)
