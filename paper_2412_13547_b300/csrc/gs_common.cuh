@@ -284,6 +284,24 @@ __device__ __forceinline__ void store_as(void* dst, int dtype, int64_t e, float 
     else reinterpret_cast<float*>(dst)[e] = val;
 }
 
+// Four consecutive values stored as one vector in the given dtype: 8 bytes for
+// BF16/FP16 at element e (e a multiple of 4 and the array 8-byte aligned), 16
+// bytes for FP32.
+__device__ __forceinline__ void store4_as(void* dst, int dtype, int64_t e, float4 v)
+{
+    if (dtype == GS_DTYPE_BF16) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        reinterpret_cast<uint2*>(dst)[e >> 2] =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+    } else if (dtype == GS_DTYPE_F16) {
+        const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        reinterpret_cast<uint2*>(dst)[e >> 2] =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+    } else {
+        reinterpret_cast<float4*>(dst)[e >> 2] = v;
+    }
+}
+
 // SH storage conversions
 __device__ __forceinline__ float load_sh_elem(const void* base, int64_t idx, int dtype)
 {

@@ -561,7 +561,12 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     float* V = a.v[t] + base;
     const uintptr_t al = reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) |
                          reinterpret_cast<uintptr_t>(V);
-    if (rows == 32 && !a.sparse && (al & 15) == 0) {
+    // the shadow copy is written 4 values at a time (8 bytes for BF16/FP16, 16 for FP32) when
+    // those vectors are aligned
+    const int64_t seb = shadow_dtype == GS_DTYPE_F32 ? 4 : 2;
+    const bool shadow4 = shadow != nullptr && base % 4 == 0 &&
+                         ((reinterpret_cast<uintptr_t>(shadow) + seb * base) & (uintptr_t)(4 * seb - 1)) == 0;
+    if (rows == 32 && !a.sparse && (al & 15) == 0 && (shadow == nullptr || shadow4)) {
         constexpr int Q = 8 * W;  // 16-byte vectors in the segment (32 W floats)
         float4* P4 = reinterpret_cast<float4*>(P);
         float4* M4 = reinterpret_cast<float4*>(M);
@@ -579,12 +584,12 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
                 const int e = 4 * q + c;
                 const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
                 adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
-                if (shadow) store_as(shadow, shadow_dtype, base + e, pp[c]);
                 if (a.gout[t]) a.gout[t][base + e] = g;
             }
             P4[q] = p;
             M4[q] = m;
             V4[q] = v;
+            if (shadow) store4_as(shadow, shadow_dtype, base + 4 * q, p);
         }
         return;
     }
