@@ -730,30 +730,64 @@ __device__ __forceinline__ uint2 batch_range(const Batch& b, int gt)
     return V.ranges[bin_tile_of(V.dil, gt - V.tile_begin)];
 }
 
-__global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Batch b, uint32_t* __restrict__ order)
+// Exclusive prefix sums of the 256 bucket counts in s_hist, into s_off (the
+// first 256 threads of a 1024-thread CTA; s_w: 9 words of scratch).
+__device__ __forceinline__ void scan_buckets(const uint32_t* s_hist, uint32_t* s_off, uint32_t* s_w)
 {
-    const int T = b.total_tiles;
-    __shared__ uint32_t s_hist[256];
-    __shared__ uint32_t s_off[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint2 r = batch_range(b, t);
-        atomicAdd(&s_hist[order_bucket(r.y - r.x)], 1u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = 0, inc = 0;
+    if (threadIdx.x < 256) {
+        x = s_hist[threadIdx.x];
+        inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
-        for (int b = 0; b < 256; ++b) {
-            s_off[b] = run;
-            run += s_hist[b];
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_w[w];
+            s_w[w] = run;
+            run += c;
         }
     }
     __syncthreads();
+    if (threadIdx.x < 256) s_off[threadIdx.x] = s_w[warp] + inc - x;
+    __syncthreads();
+}
+
+// Longest-first order of T tiles from their buckets (s_b, one byte per tile,
+// in shared memory): counts, prefix sums, then each tile takes the next slot
+// of its bucket. Slots within a bucket go in no particular order.
+__device__ __forceinline__ void order_from_buckets(int T, const uint8_t* s_b, uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_w[9];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&s_hist[s_b[t]], 1u);
+    __syncthreads();
+    scan_buckets(s_hist, s_off, s_w);
+    for (int t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&s_off[s_b[t]], 1u)] = (uint32_t)t;
+}
+
+// Longest-first order by list length (of the binning tile's list), one CTA:
+// the buckets are computed once into dynamic shared memory (T bytes).
+__global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Batch b, uint32_t* __restrict__ order)
+{
+    extern __shared__ uint8_t s_bkt[];
+    const int T = b.total_tiles;
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         const uint2 r = batch_range(b, t);
-        order[atomicAdd(&s_off[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+        s_bkt[t] = (uint8_t)order_bucket(r.y - r.x);
     }
+    __syncthreads();
+    order_from_buckets(T, s_bkt, order);
 }
 
 // Backward work key of every blend tile of the batch: the largest `last` over
@@ -780,29 +814,51 @@ __global__ void __launch_bounds__(256) k_tile_last_max(const __grid_constant__ B
 // Longest-first order of the tiles by the keys in `order` (read into shared
 // memory first, then overwritten by the order). One CTA; T keys fit in
 // its dynamic shared memory.
-__global__ void __launch_bounds__(1024) k_tile_order_keys(int T, uint32_t* __restrict__ order)
+// The same order for more tiles than shared memory holds buckets for: the
+// buckets are recomputed from global memory in both passes.
+__global__ void __launch_bounds__(1024) k_tile_order_global(const __grid_constant__ Batch b,
+                                                            uint32_t* __restrict__ order)
 {
-    extern __shared__ uint32_t s_key[];
+    const int T = b.total_tiles;
     __shared__ uint32_t s_hist[256];
     __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_w[9];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) s_key[t] = order[t];
     __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&s_hist[order_bucket(s_key[t])], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int k = 0; k < 256; ++k) {
-            s_off[k] = run;
-            run += s_hist[k];
-        }
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = batch_range(b, t);
+        atomicAdd(&s_hist[order_bucket(r.y - r.x)], 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        order[atomicAdd(&s_off[order_bucket(s_key[t])], 1u)] = (uint32_t)t;
+    scan_buckets(s_hist, s_off, s_w);
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = batch_range(b, t);
+        order[atomicAdd(&s_off[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
 }
 
-constexpr int kMaxKeyedOrderTiles = 48 * 1024;  // keys held in 192 KB of shared memory
+__global__ void __launch_bounds__(1024) k_tile_order_keys(int T, uint32_t* __restrict__ order)
+{
+    extern __shared__ uint8_t s_bkt[];
+    for (int t = threadIdx.x; t < T; t += blockDim.x) s_bkt[t] = (uint8_t)order_bucket(order[t]);
+    __syncthreads();
+    order_from_buckets(T, s_bkt, order);
+}
+
+constexpr int kMaxKeyedOrderTiles = 192 * 1024;  // one bucket byte per tile in shared memory
+
+// Longest-first order by list length, in shared memory when the buckets fit.
+int32_t launch_tile_order(const Batch& b, uint32_t* order, cudaStream_t st, const char* what)
+{
+    const int T = b.total_tiles;
+    if (T <= kMaxKeyedOrderTiles) {
+        if (T > 48 * 1024) cudaFuncSetAttribute(k_tile_order, cudaFuncAttributeMaxDynamicSharedMemorySize, T);
+        k_tile_order<<<1, 1024, (size_t)T, st>>>(b, order);
+    } else {
+        k_tile_order_global<<<1, 1024, 0, st>>>(b, order);
+    }
+    return gs_host::check_launch(what);
+}
 
 bool check_render_view(int32_t n, const ViewDev& v)
 {
@@ -971,8 +1027,7 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
     b.v[0].dil.tiles_x = b.v[0].dil.bin_tiles_x = num_tiles;
     b.v[0].dil.tiles_y = b.v[0].dil.bin_tiles_y = 1;
     b.total_tiles = num_tiles;
-    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
-    return gs_host::check_launch("gs_tile_order");
+    return launch_tile_order(b, order, reinterpret_cast<cudaStream_t>(stream), "gs_tile_order");
 }
 
 int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream)
@@ -983,8 +1038,7 @@ int32_t gs_tile_order_batch(const GsView* views, int32_t nviews, uint32_t* order
     for (int i = 0; i < nviews; ++i)
         if (!b.v[i].ranges) { gs_host::set_error("gs_tile_order_batch: null ranges"); return GS_ERR_ARG; }
     if (!order) { gs_host::set_error("gs_tile_order_batch: order is null"); return GS_ERR_ARG; }
-    k_tile_order<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(b, order);
-    return gs_host::check_launch("gs_tile_order_batch");
+    return launch_tile_order(b, order, reinterpret_cast<cudaStream_t>(stream), "gs_tile_order_batch");
 }
 
 int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_t* order, gs_stream_t stream)
@@ -1001,14 +1055,11 @@ int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_
     const int T = b.total_tiles;
     if (T == 0) return GS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (T > kMaxKeyedOrderTiles) {  // more keys than shared memory holds: the list-length order
-        k_tile_order<<<1, 1024, 0, st>>>(b, order);
-        return gs_host::check_launch("gs_tile_order_by_last_batch");
-    }
+    if (T > kMaxKeyedOrderTiles)  // more tiles than shared memory holds buckets for: the list-length order
+        return launch_tile_order(b, order, st, "gs_tile_order_by_last_batch");
     k_tile_last_max<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(b, order);
-    const size_t smem = (size_t)T * sizeof(uint32_t);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_order_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tile_order_keys<<<1, 1024, smem, st>>>(T, order);
+    if (T > 48 * 1024) cudaFuncSetAttribute(k_tile_order_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, T);
+    k_tile_order_keys<<<1, 1024, (size_t)T, st>>>(T, order);
     return gs_host::check_launch("gs_tile_order_by_last_batch");
 }
 
