@@ -214,7 +214,8 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
                  for ox in range(d) for oy in range(d))
     step = TrainStep(p, rast, AdamConfig(), max_pixels=max_px)
     timed = TimedStep(step, steps)
-    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps)]
+    n_count = d * d  # instrumented steps (every offset once) for the blend counts, after the timed ones
+    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps + n_count)]
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
     for i in range(warmup):
         ox, oy = offsets[i]
@@ -228,27 +229,36 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         start.record()
         for i in range(steps):
             ox, oy = offsets[warmup + i]
-            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
+            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev)
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
     total_ms = start.elapsed_time(end)
+    stage = timed.stage_ms(steps) if want_stage else None
     ks = k_hist.cpu().numpy()
     if ks.max() > rast.capacity:
         raise RuntimeError(f"pair capacity {rast.capacity} exceeded ({ks.max()}); rerun with more headroom")
-    counts = step.counts.cpu().numpy()
-    res = dict(ms_per_step=total_ms / steps, iters_per_s=steps * 1000.0 / total_ms,
-               blends_evaluated_per_s=float(counts[0]) * 1000.0 / total_ms,
-               blends_contributing_per_s=float(counts[1]) * 1000.0 / total_ms,
+    # the blend counts (instrumentation the training step does not need) from d*d further
+    # steps, one per lattice offset, outside the timed region
+    step.counts.zero_()
+    for i in range(n_count):
+        ox, oy = offsets[warmup + steps + i]
+        timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
+    torch.cuda.synchronize()
+    counts = step.counts.cpu().numpy() / n_count  # per step
+    iters_per_s = steps * 1000.0 / total_ms
+    res = dict(ms_per_step=total_ms / steps, iters_per_s=iters_per_s,
+               blends_evaluated_per_s=float(counts[0]) * iters_per_s,
+               blends_contributing_per_s=float(counts[1]) * iters_per_s,
                pairs_mean=float(ks.mean()), loss=float(step.loss.item()), d=d,
                tile=TILE[0], bin_tile=TILE[0] << bin_shift_for(d),
                sh_dtype=str(sh_dtype).replace("torch.", ""))
     if want_stage:
-        res["stage_ms"] = timed.stage_ms(steps)
-        res["evaluated_per_step"] = float(counts[0]) / steps
-        res["blended_per_step"] = float(counts[1]) / steps
+        res["stage_ms"] = stage
+        res["evaluated_per_step"] = float(counts[0])
+        res["blended_per_step"] = float(counts[1])
         # back-to-front replay work: sum over pixels of the list prefix they replay
-        res["replayed_per_step"] = float(counts[2]) / steps
+        res["replayed_per_step"] = float(counts[2])
     return res, step
 
 

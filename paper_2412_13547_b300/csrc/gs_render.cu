@@ -176,7 +176,9 @@ struct WarpBlock {
 // Blend of one tile (the body of the single-view and the batched kernels).
 // FILTER: the list is the binning tile's; entries outside this blend tile are
 // dropped while staging (what remains is this tile's own list, in order).
-template <int TILE, int PPT, bool FILTER>
+// COUNT: the blend counts are accumulated (instrumentation, compiled out
+// when the caller passes no counts).
+template <int TILE, int PPT, bool FILTER, bool COUNT>
 __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restrict__ splats,
                                                 const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
                                                 const Dil& dil, float3 bg, float* __restrict__ img,
@@ -278,8 +280,10 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 while (m != 0u) {
                     const int j = c0 + __ffs(m) - 1;
                     m &= m - 1u;
-                    n_eval += (uint32_t)n_live * (uint32_t)(j - next_j + 1);
-                    next_j = j + 1;
+                    if constexpr (COUNT) {
+                        n_eval += (uint32_t)n_live * (uint32_t)(j - next_j + 1);
+                        next_j = j + 1;
+                    }
                     const float2 p = s_p[j];
                     const float4 co = s_co[j];
                     const float dx = __fsub_rn(xr, p.x);
@@ -306,11 +310,11 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                         C2[k] = fmaf(c.z, w, C2[k]);
                         T[k] = Tn;
                         lj[k] = j;
-                        ++n_blend;
+                        if constexpr (COUNT) ++n_blend;
                     }
                     if (!__any_sync(0xffffffffu, n_live > 0)) break;
                 }
-                n_eval += (uint32_t)n_live * (uint32_t)(c1 - next_j);
+                if constexpr (COUNT) n_eval += (uint32_t)n_live * (uint32_t)(c1 - next_j);
             }
         }
         // positions of the last blended entries, read before the next batch is staged
@@ -318,7 +322,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
         for (int k = 0; k < PPT; ++k) {
             if (lj[k] < 0) continue;
             last_pos[k] = FILTER ? s_pos[lj[k]] : start + (uint32_t)lj[k] - rg.x + 1;
-            last_own[k] = own_base + (uint32_t)lj[k] + 1;
+            if constexpr (COUNT) last_own[k] = own_base + (uint32_t)lj[k] + 1;
         }
         own_base += (uint32_t)cnt;
     }
@@ -334,7 +338,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
             last[pix] = last_pos[k];
         }
     }
-    if (counts != nullptr) {
+    if constexpr (COUNT) {
         unsigned long long e = n_eval, b = n_blend, r = 0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) r += last_own[k];
@@ -628,15 +632,15 @@ constexpr int fwd_min_blocks()
     return PPT <= 2 ? 1024 / TileGeom<TILE, PPT>::THREADS : 1;
 }
 
-template <int TILE, int PPT, bool MULTI, bool FILTER>
+template <int TILE, int PPT, bool MULTI, bool FILTER, bool COUNT>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (fwd_min_blocks<TILE, PPT>()))
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
              unsigned long long* __restrict__ counts)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
-    render_fwd_tile<TILE, PPT, FILTER>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img, V.t_final,
-                                       V.last, counts);
+    render_fwd_tile<TILE, PPT, FILTER, COUNT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img,
+                                              V.t_final, V.last, counts);
 }
 
 template <int TILE, int PPT, bool MULTI, bool FILTER>
@@ -884,8 +888,12 @@ template <int TILE, int PPT>
 void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, cudaStream_t st)
 {
     const bool multi = b.nviews > 1, filter = any_shift(b);
-    auto kern = multi ? (filter ? k_render_fwd<TILE, PPT, true, true> : k_render_fwd<TILE, PPT, true, false>)
-                      : (filter ? k_render_fwd<TILE, PPT, false, true> : k_render_fwd<TILE, PPT, false, false>);
+    auto kern = counts != nullptr
+        ? (multi ? (filter ? k_render_fwd<TILE, PPT, true, true, true> : k_render_fwd<TILE, PPT, true, false, true>)
+                 : (filter ? k_render_fwd<TILE, PPT, false, true, true> : k_render_fwd<TILE, PPT, false, false, true>))
+        : (multi ? (filter ? k_render_fwd<TILE, PPT, true, true, false> : k_render_fwd<TILE, PPT, true, false, false>)
+                 : (filter ? k_render_fwd<TILE, PPT, false, true, false>
+                           : k_render_fwd<TILE, PPT, false, false, false>));
     kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
 }
 
