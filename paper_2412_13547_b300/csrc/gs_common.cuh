@@ -164,11 +164,24 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d)
 // The per-entry blend arithmetic, with rounding pinned by intrinsics so the
 // forward pass and the backward replay take identical skip/clamp decisions.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float splat_power(float dx, float dy, float A, float B, float C)
+// The exponent -(A dx^2 + C dy^2)/2 - B dx dy of a splat at pixel offset
+// (dx, dy), in two parts: the terms of dx alone (A dx^2 and B dx, shared by
+// the pixels of one column) and the rest per pixel. Every kernel evaluates it
+// this way, rounding pinned with intrinsics, so the forward and the backward
+// replay take the same gate decisions.
+struct SplatRow {
+    float adx2, bdx;
+};
+
+__device__ __forceinline__ SplatRow splat_row(float dx, float A, float B)
 {
-    // -(A dx^2 + C dy^2)/2 - B dx dy
-    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+    return SplatRow{__fmul_rn(A, __fmul_rn(dx, dx)), __fmul_rn(B, dx)};
+}
+
+__device__ __forceinline__ float splat_power(SplatRow r, float dy, float C)
+{
+    const float q = __fmaf_rn(C, __fmul_rn(dy, dy), r.adx2);
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(r.bdx, dy));
 }
 
 __device__ __forceinline__ float splat_alpha_raw(float power, float opacity)

@@ -287,6 +287,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     const float2 p = s_p[j];
                     const float4 co = s_co[j];
                     const float dx = __fsub_rn(xr, p.x);
+                    const SplatRow row = splat_row(dx, co.x, co.y);
                     // the gates of all this thread's pixels first, free of branches so that
                     // their dependency chains interleave; then the blends, in pixel order
                     float alpha[PPT];
@@ -294,7 +295,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         const float dy = __fsub_rn(yr[k], p.y);
-                        const float power = splat_power(dx, dy, co.x, co.y, co.z);
+                        const float power = splat_power(row, dy, co.z);
                         alpha[k] = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
                         use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
                     }
@@ -554,13 +555,14 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 const float4 co = s_co[j];
                 const float4 c = s_rgb[j];
                 const float dx = __fsub_rn(xr, p.x);
+                const SplatRow row = splat_row(dx, co.x, co.y);
                 // gates of all this thread's pixels first (branch-free), then the replay
                 float dyk[PPT], Gk[PPT], ark[PPT];
                 bool use[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     dyk[k] = __fsub_rn(yr[k], p.y);
-                    const float power = splat_power(dx, dyk[k], co.x, co.y, co.z);
+                    const float power = splat_power(row, dyk[k], co.z);
                     Gk[k] = __expf(power);
                     ark[k] = __fmul_rn(co.w, Gk[k]);  // as splat_alpha_raw
                     use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
