@@ -164,8 +164,27 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d)
 // The per-entry blend arithmetic, with rounding pinned by intrinsics so the
 // forward pass and the backward replay take identical skip/clamp decisions.
 // ---------------------------------------------------------------------------
+// 2^x on the SFU (ex2.approx, flush to zero): with the conic pre-scaled by
+// log2(e), G = exp(power) = 2^(power log2 e) is one SFU operation.
+__device__ __forceinline__ float exp2_sfu(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.44269504088896340736f;  // log2(e)
+constexpr float kLn2 = 0.693147180559945309417f;    // ln(2) = 1 / log2(e)
+
+// The conic (A, B, C) of a staged record scaled by log2(e), opacity kept: the
+// exponent below then comes out in base 2.
+__device__ __forceinline__ float4 conic_log2(float4 co)
+{
+    return make_float4(__fmul_rn(co.x, kLog2e), __fmul_rn(co.y, kLog2e), __fmul_rn(co.z, kLog2e), co.w);
+}
+
 // The exponent -(A dx^2 + C dy^2)/2 - B dx dy of a splat at pixel offset
-// (dx, dy), in two parts: the terms of dx alone (A dx^2 and B dx, shared by
+// (dx, dy) (in base 2 when the conic comes from conic_log2), in two parts: the terms of dx alone (A dx^2 and B dx, shared by
 // the pixels of one column) and the rest per pixel. Every kernel evaluates it
 // this way, rounding pinned with intrinsics, so the forward and the backward
 // replay take the same gate decisions.
@@ -184,10 +203,6 @@ __device__ __forceinline__ float splat_power(SplatRow r, float dy, float C)
     return __fmaf_rn(-0.5f, q, -__fmul_rn(r.bdx, dy));
 }
 
-__device__ __forceinline__ float splat_alpha_raw(float power, float opacity)
-{
-    return __fmul_rn(opacity, __expf(power));
-}
 
 // ---------------------------------------------------------------------------
 // Real spherical harmonics up to degree 3 (Condon-Shortley phase, index

@@ -231,7 +231,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
                 s_p[i] = p;
                 s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
-                s_co[i] = co;
+                s_co[i] = conic_log2(co);
                 s_rgb[i] = rgb;
             }
             next += (uint32_t)cnt;
@@ -253,7 +253,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[cnt + r] = p;
                     s_mask[cnt + r] = warp_mask<TILE, PPT>(p, co, dil.d);
-                    s_co[cnt + r] = co;
+                    s_co[cnt + r] = conic_log2(co);
                     s_rgb[cnt + r] = rgb;
                     s_pos[cnt + r] = e - rg.x + 1;
                 }
@@ -296,7 +296,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     for (int k = 0; k < PPT; ++k) {
                         const float dy = __fsub_rn(yr[k], p.y);
                         const float power = splat_power(row, dy, co.z);
-                        alpha[k] = fminf(kAlphaMax, splat_alpha_raw(power, co.w));
+                        alpha[k] = fminf(kAlphaMax, __fmul_rn(co.w, exp2_sfu(power)));
                         use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
                     }
 #pragma unroll
@@ -490,7 +490,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 load_stage(splats, g, X0, Y0, p, co, rgb);
                 s_p[i] = p;
                 s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
-                s_co[i] = co;
+                s_co[i] = conic_log2(co);
                 s_rgb[i] = rgb;
                 s_id[i] = g;
 #pragma unroll
@@ -516,7 +516,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[slot] = p;
                     s_mask[slot] = warp_mask<TILE, PPT>(p, co, dil.d);
-                    s_co[slot] = co;
+                    s_co[slot] = conic_log2(co);
                     s_rgb[slot] = rgb;
                     s_id[slot] = g;
                     s_rel[slot] = rel;
@@ -563,8 +563,8 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 for (int k = 0; k < PPT; ++k) {
                     dyk[k] = __fsub_rn(yr[k], p.y);
                     const float power = splat_power(row, dyk[k], co.z);
-                    Gk[k] = __expf(power);
-                    ark[k] = __fmul_rn(co.w, Gk[k]);  // as splat_alpha_raw
+                    Gk[k] = exp2_sfu(power);
+                    ark[k] = __fmul_rn(co.w, Gk[k]);  // alpha before the 0.99 clamp, as in the forward
                     use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
                 }
 #pragma unroll
@@ -599,7 +599,8 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 if (__any_sync(0xffffffffu, contrib)) {
                     int comp;
                     const float z = warp_sum9(r, lane, comp);
-                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], z);
+                    // the centre gradients (0, 1) were summed with the log2(e)-scaled conic
+                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], comp < 2 ? z * kLn2 : z);
                 }
         }
         }
