@@ -176,33 +176,34 @@ __device__ __forceinline__ float exp2_sfu(float x)
 constexpr float kLog2e = 1.44269504088896340736f;  // log2(e)
 constexpr float kLn2 = 0.693147180559945309417f;    // ln(2) = 1 / log2(e)
 
-// The conic (A, B, C) of a staged record scaled by log2(e), opacity kept: the
-// exponent below then comes out in base 2.
-__device__ __forceinline__ float4 conic_log2(float4 co)
+// The conic (A, B, C) of a staged record as the coefficients of the base-2
+// exponent: (a, b, c) = log2(e) (-A/2, -B, -C/2), opacity kept, so that
+// power2 = a dx^2 + b dx dy + c dy^2 = log2(e) (-(A dx^2 + C dy^2)/2 - B dx dy)
+// and G = 2^power2.
+__device__ __forceinline__ float4 conic_exp2(float4 co)
 {
-    return make_float4(__fmul_rn(co.x, kLog2e), __fmul_rn(co.y, kLog2e), __fmul_rn(co.z, kLog2e), co.w);
+    return make_float4(__fmul_rn(co.x, -0.5f * kLog2e), __fmul_rn(co.y, -kLog2e), __fmul_rn(co.z, -0.5f * kLog2e),
+                       co.w);
 }
 
-// The exponent -(A dx^2 + C dy^2)/2 - B dx dy of a splat at pixel offset
-// (dx, dy) (in base 2 when the conic comes from conic_log2), in two parts: the terms of dx alone (A dx^2 and B dx, shared by
-// the pixels of one column) and the rest per pixel. Every kernel evaluates it
-// this way, rounding pinned with intrinsics, so the forward and the backward
-// replay take the same gate decisions.
+// The base-2 exponent of a splat at pixel offset (dx, dy), in two parts: the
+// terms of dx alone (a dx^2 and b dx, shared by the pixels of one column) and
+// the rest per pixel. Every kernel evaluates it this way, rounding pinned with
+// intrinsics, so the forward and the backward replay take the same gate
+// decisions.
 struct SplatRow {
     float adx2, bdx;
 };
 
-__device__ __forceinline__ SplatRow splat_row(float dx, float A, float B)
+__device__ __forceinline__ SplatRow splat_row(float dx, float a, float b)
 {
-    return SplatRow{__fmul_rn(A, __fmul_rn(dx, dx)), __fmul_rn(B, dx)};
+    return SplatRow{__fmul_rn(a, __fmul_rn(dx, dx)), __fmul_rn(b, dx)};
 }
 
-__device__ __forceinline__ float splat_power(SplatRow r, float dy, float C)
+__device__ __forceinline__ float splat_power(SplatRow r, float dy, float c)
 {
-    const float q = __fmaf_rn(C, __fmul_rn(dy, dy), r.adx2);
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(r.bdx, dy));
+    return __fmaf_rn(r.bdx, dy, __fmaf_rn(c, __fmul_rn(dy, dy), r.adx2));
 }
-
 
 // ---------------------------------------------------------------------------
 // Real spherical harmonics up to degree 3 (Condon-Shortley phase, index

@@ -231,7 +231,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                 load_stage(splats, __ldg(ids + start + i), X0, Y0, p, co, rgb);
                 s_p[i] = p;
                 s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
-                s_co[i] = conic_log2(co);
+                s_co[i] = conic_exp2(co);
                 s_rgb[i] = rgb;
             }
             next += (uint32_t)cnt;
@@ -253,7 +253,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[cnt + r] = p;
                     s_mask[cnt + r] = warp_mask<TILE, PPT>(p, co, dil.d);
-                    s_co[cnt + r] = conic_log2(co);
+                    s_co[cnt + r] = conic_exp2(co);
                     s_rgb[cnt + r] = rgb;
                     s_pos[cnt + r] = e - rg.x + 1;
                 }
@@ -490,7 +490,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 load_stage(splats, g, X0, Y0, p, co, rgb);
                 s_p[i] = p;
                 s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
-                s_co[i] = conic_log2(co);
+                s_co[i] = conic_exp2(co);
                 s_rgb[i] = rgb;
                 s_id[i] = g;
 #pragma unroll
@@ -516,7 +516,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     load_stage(splats, g, X0, Y0, p, co, rgb);
                     s_p[slot] = p;
                     s_mask[slot] = warp_mask<TILE, PPT>(p, co, dil.d);
-                    s_co[slot] = conic_log2(co);
+                    s_co[slot] = conic_exp2(co);
                     s_rgb[slot] = rgb;
                     s_id[slot] = g;
                     s_rel[slot] = rel;
@@ -592,15 +592,17 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                         r[2] = fmaf(-0.5f * dx * dx, dpower, r[2]);
                         r[3] = fmaf(-dx * dy, dpower, r[3]);
                         r[4] = fmaf(-0.5f * dy * dy, dpower, r[4]);
-                        r[0] = fmaf(dpower, co.x * dx + co.y * dy, r[0]);
-                        r[1] = fmaf(dpower, co.z * dy + co.y * dx, r[1]);
+                        // with the staged (a, b, c): A dx + B dy = -(2a dx + b dy) ln 2, and
+                        // C dy + B dx = -(2c dy + b dx) ln 2; the -ln 2 is applied per entry below
+                        r[0] = fmaf(dpower, fmaf(co.y, dy, 2.0f * co.x * dx), r[0]);
+                        r[1] = fmaf(dpower, fmaf(co.y, dx, 2.0f * co.z * dy), r[1]);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     int comp;
                     const float z = warp_sum9(r, lane, comp);
-                    // the centre gradients (0, 1) were summed with the log2(e)-scaled conic
-                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], comp < 2 ? z * kLn2 : z);
+                    // the centre gradients (0, 1) were summed with the base-2 exponent's coefficients
+                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], comp < 2 ? z * -kLn2 : z);
                 }
         }
         }
