@@ -637,6 +637,15 @@ constexpr int fwd_min_blocks()
     return PPT <= 2 ? 1024 / TileGeom<TILE, PPT>::THREADS : 1;
 }
 
+// The backward at tile 16 and 4 pixels per thread (64-thread CTAs) is held to
+// 12 CTAs per SM (78 registers, no spills): 5% faster than the 92 registers it
+// takes unbounded; 14 or 16 CTAs gave no gain or spilled.
+template <int TILE, int PPT>
+constexpr int bwd_min_blocks()
+{
+    return (TILE == 16 && PPT == 4) ? 12 : 1;
+}
+
 template <int TILE, int PPT, bool MULTI, bool FILTER, bool COUNT>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (fwd_min_blocks<TILE, PPT>()))
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
@@ -649,7 +658,7 @@ k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order
 }
 
 template <int TILE, int PPT, bool MULTI, bool FILTER>
-__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS)
+__global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (bwd_min_blocks<TILE, PPT>()))
 k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg)
 {
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
