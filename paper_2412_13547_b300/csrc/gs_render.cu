@@ -634,7 +634,9 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 template <int TILE, int PPT>
 constexpr int fwd_min_blocks()
 {
-    return PPT <= 2 ? 1024 / TileGeom<TILE, PPT>::THREADS : 1;
+    // tile 16 at 2 pixels per thread: 9 CTAs of 128 threads (56 registers, no spills), 2% faster
+    // than 8; 10 spilled
+    return (TILE == 16 && PPT == 2) ? 9 : (PPT <= 2 ? 1024 / TileGeom<TILE, PPT>::THREADS : 1);
 }
 
 // The backward at tile 16 and 4 pixels per thread (64-thread CTAs) is held to
