@@ -567,29 +567,46 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
     const bool shadow4 = shadow != nullptr && base % 4 == 0 &&
                          ((reinterpret_cast<uintptr_t>(shadow) + seb * base) & (uintptr_t)(4 * seb - 1)) == 0;
     if (rows == 32 && !a.sparse && (al & 15) == 0 && (shadow == nullptr || shadow4)) {
-        constexpr int Q = 8 * W;  // 16-byte vectors in the segment (32 W floats)
+        constexpr int Q = 8 * W;            // 16-byte vectors in the segment (32 W floats)
+        constexpr int KN = (Q + 31) / 32;   // vectors per lane, the last one partial when Q % 32 != 0
+        constexpr int B = KN < 4 ? KN : 4;  // vectors of each array loaded before any is stored
         float4* P4 = reinterpret_cast<float4*>(P);
         float4* M4 = reinterpret_cast<float4*>(M);
         float4* V4 = reinterpret_cast<float4*>(V);
-#pragma unroll 4
-        for (int k = 0; k < (Q + 31) / 32; ++k) {
-            const int q = lane + 32 * k;
-            if (q >= Q) break;
-            float4 p = P4[q], m = M4[q], v = V4[q];
-            float* pp = &p.x;
-            float* mm = &m.x;
-            float* vv = &v.x;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int e = 4 * q + c;
-                const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
-                adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
-                if (a.gout[t]) a.gout[t][base + e] = g;
+        for (int k0 = 0; k0 < KN; k0 += B) {
+            // all loads of the group first: the stores of one vector could alias the next
+            // one's loads as far as the compiler knows, which would leave one vector per array
+            // in flight per lane
+            float4 p[B], m[B], v[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int q = lane + 32 * (k0 + u);
+                if (k0 + u < KN && q < Q) {
+                    p[u] = P4[q];
+                    m[u] = M4[q];
+                    v[u] = V4[q];
+                }
             }
-            P4[q] = p;
-            M4[q] = m;
-            V4[q] = v;
-            if (shadow) store4_as(shadow, shadow_dtype, base + 4 * q, p);
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int q = lane + 32 * (k0 + u);
+                if (k0 + u >= KN || q >= Q) continue;
+                float* pp = &p[u].x;
+                float* mm = &m[u].x;
+                float* vv = &v[u].x;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int e = 4 * q + c;
+                    const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
+                    adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
+                    if (a.gout[t]) a.gout[t][base + e] = g;
+                }
+                P4[q] = p[u];
+                M4[q] = m[u];
+                V4[q] = v[u];
+                if (shadow) store4_as(shadow, shadow_dtype, base + 4 * q, p[u]);
+            }
         }
         return;
     }
