@@ -703,10 +703,10 @@ __device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const f
 // them in every view of the batch (gradients summed over views), then one
 // Adam step for the warp's rows. MULTI false is the one-view form, which
 // writes the gradients instead of accumulating them.
-// 6 CTAs per SM: the register cap (85) costs a few spills but the extra
-// warps hide more of the memory latency of this streaming pass
+// 5 CTAs per SM (96 registers, no spills): with 4 vectors per array in flight per
+// lane in the Adam step, 5 beat 4 and 6 (spills) on this streaming pass
 template <int DEG, int DT, bool MULTI>
-__global__ void __launch_bounds__(kThreads, MULTI ? 4 : 6)
+__global__ void __launch_bounds__(kThreads, MULTI ? 4 : 5)
 k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_constant__ Batch b, AdamDev a,
                    float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
 {
