@@ -550,6 +550,9 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 float r[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) r[k] = 0.0f;
+                // dL/dpower summed over the thread's pixels, and times dy and dy^2: the conic and
+                // centre gradients are those three sums times per-entry factors of dx
+                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
                 bool contrib = false;
                 const float2 p = s_p[j];
                 const float4 co = s_co[j];
@@ -589,15 +592,20 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     if (a_raw < kAlphaMax) {
                         const float dpower = a_raw * dalpha;
                         r[5] = fmaf(G, dalpha, r[5]);
-                        r[2] = fmaf(-0.5f * dx * dx, dpower, r[2]);
-                        r[3] = fmaf(-dx * dy, dpower, r[3]);
-                        r[4] = fmaf(-0.5f * dy * dy, dpower, r[4]);
-                        // with the staged (a, b, c): A dx + B dy = -(2a dx + b dy) ln 2, and
-                        // C dy + B dx = -(2c dy + b dx) ln 2; the -ln 2 is applied per entry below
-                        r[0] = fmaf(dpower, fmaf(co.y, dy, 2.0f * co.x * dx), r[0]);
-                        r[1] = fmaf(dpower, fmaf(co.y, dx, 2.0f * co.z * dy), r[1]);
+                        const float t = dpower * dy;
+                        q0 += dpower;
+                        q1 += t;
+                        q2 = fmaf(t, dy, q2);
                     }
                 }
+                // dpower/dA = -dx^2/2, dpower/dB = -dx dy, dpower/dC = -dy^2/2. With the staged
+                // (a, b, c): A dx + B dy = -(2a dx + b dy) ln 2 and C dy + B dx = -(2c dy + b dx) ln 2;
+                // the -ln 2 is applied after the warp sum
+                r[2] = -0.5f * dx * dx * q0;
+                r[3] = -dx * q1;
+                r[4] = -0.5f * q2;
+                r[0] = fmaf(co.y, q1, 2.0f * co.x * dx * q0);
+                r[1] = fmaf(co.y * dx, q0, 2.0f * co.z * q1);
                 if (__any_sync(0xffffffffu, contrib)) {
                     int comp;
                     const float z = warp_sum9(r, lane, comp);
