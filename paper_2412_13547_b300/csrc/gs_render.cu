@@ -160,18 +160,27 @@ __device__ __forceinline__ uint32_t warp_mask(float2 p, float4 co, int d)
     return m;
 }
 
-template <int TILE, int PPT>
+// A warp covers an 8-column block of 4 PPT rows; lane l takes column l % 8 and,
+// with ILV (interleaved), rows l / 8 + 4k (k < PPT), else rows PPT (l / 8) + k.
+// Interleaved, the rows a small splat covers fall on fewer of the lanes' pixel
+// indices k, so a warp runs fewer of its per-pixel branches per entry.
+template <int TILE, int PPT, bool ILV>
 struct WarpBlock {
-    int lx, ly0;  // this thread's column and first row in the tile
+    static constexpr int RSTEP = ILV ? 4 : 1;  // rows between a thread's pixels
+    int lx, ly0;                               // this thread's column and first row in the tile
     __device__ __forceinline__ WarpBlock(int tid)
     {
         using Geo = TileGeom<TILE, PPT>;
         const int warp = tid >> 5, lane = tid & 31;
         const int bx = warp % Geo::WCOLS, by = warp / Geo::WCOLS;
         lx = bx * 8 + (lane & 7);
-        ly0 = by * Geo::WROWS + (lane >> 3) * PPT;
+        ly0 = by * Geo::WROWS + (lane >> 3) * (ILV ? 1 : PPT);
     }
+    __device__ __forceinline__ int row(int k) const { return ly0 + RSTEP * k; }
 };
+
+constexpr bool kFwdInterleave = true;
+constexpr bool kBwdInterleave = true;
 
 // Blend of one tile (the body of the single-view and the batched kernels).
 // FILTER: the list is the binning tile's; entries outside this blend tile are
@@ -197,7 +206,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     __shared__ unsigned long long s_cnt[3];
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const WarpBlock<TILE, PPT> wb(threadIdx.x);
+    const WarpBlock<TILE, PPT, kFwdInterleave> wb(threadIdx.x);
     const int u = tx * TILE + wb.lx;
     // hr origin of the tile and this thread's hr offsets from it (small exact floats)
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
@@ -212,8 +221,8 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         T[k] = 1.0f; C0[k] = C1[k] = C2[k] = 0.0f; last_pos[k] = 0; last_own[k] = 0;
-        yr[k] = (float)(dil.d * (wb.ly0 + k));
-        done[k] = !(u < dil.w_ds && ty * TILE + wb.ly0 + k < dil.h_ds);
+        yr[k] = (float)(dil.d * wb.row(k));
+        done[k] = !(u < dil.w_ds && ty * TILE + wb.row(k) < dil.h_ds);
         n_live += done[k] ? 0 : 1;
     }
     uint32_t n_eval = 0, n_blend = 0;
@@ -329,7 +338,7 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int v = ty * TILE + wb.ly0 + k;
+        const int v = ty * TILE + wb.row(k);
         if (u < dil.w_ds && v < dil.h_ds) {
             const int64_t pix = (int64_t)v * dil.w_ds + u;
             img[3 * pix] = fmaf(T[k], bg.x, C0[k]);
@@ -434,7 +443,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     __shared__ uint32_t s_max_last;
 
     const int tx = tile % dil.tiles_x, ty = tile / dil.tiles_x;
-    const WarpBlock<TILE, PPT> wb(threadIdx.x);
+    const WarpBlock<TILE, PPT, kBwdInterleave> wb(threadIdx.x);
     const int lane = threadIdx.x & 31;
     const int u = tx * TILE + wb.lx;
     const float X0 = (float)(dil.d * tx * TILE + dil.ox), Y0 = (float)(dil.d * ty * TILE + dil.oy);
@@ -449,8 +458,8 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
     uint32_t my_max = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int v = ty * TILE + wb.ly0 + k;
-        yr[k] = (float)(dil.d * (wb.ly0 + k));
+        const int v = ty * TILE + wb.row(k);
+        yr[k] = (float)(dil.d * wb.row(k));
         T[k] = 1.0f; g0[k] = g1[k] = g2[k] = 0.0f; n_last[k] = 0;
         if (u < dil.w_ds && v < dil.h_ds) {
             const int64_t pix = (int64_t)v * dil.w_ds + u;
