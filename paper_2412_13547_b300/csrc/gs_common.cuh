@@ -176,33 +176,43 @@ __device__ __forceinline__ float exp2_sfu(float x)
 constexpr float kLog2e = 1.44269504088896340736f;  // log2(e)
 constexpr float kLn2 = 0.693147180559945309417f;    // ln(2) = 1 / log2(e)
 
-// The conic (A, B, C) of a staged record as the coefficients of the base-2
-// exponent: (a, b, c) = log2(e) (-A/2, -B, -C/2), opacity kept, so that
-// power2 = a dx^2 + b dx dy + c dy^2 = log2(e) (-(A dx^2 + C dy^2)/2 - B dx dy)
-// and G = 2^power2.
+constexpr float kLog2AlphaMin = -7.99435343685885793f;  // log2(1/255)
+
+// The conic (A, B, C) and opacity o of a staged record as the terms of the
+// base-2 logarithm of the splat's alpha: (a, b, c) = log2(e) (-A/2, -B, -C/2)
+// and l = log2(o), so that
+//   e2 = a dx^2 + b dx dy + c dy^2 + l = log2(o G),  G = exp(-(A dx^2 + C dy^2)/2 - B dx dy),
+// and the alpha before the clamp is 2^e2. The alpha gates are then comparisons
+// of e2: G <= 1 is e2 <= l, alpha >= 1/255 is e2 >= log2(1/255).
 __device__ __forceinline__ float4 conic_exp2(float4 co)
 {
     return make_float4(__fmul_rn(co.x, -0.5f * kLog2e), __fmul_rn(co.y, -kLog2e), __fmul_rn(co.z, -0.5f * kLog2e),
-                       co.w);
+                       __log2f(co.w));
 }
 
-// The base-2 exponent of a splat at pixel offset (dx, dy), in two parts: the
-// terms of dx alone (a dx^2 and b dx, shared by the pixels of one column) and
-// the rest per pixel. Every kernel evaluates it this way, rounding pinned with
-// intrinsics, so the forward and the backward replay take the same gate
-// decisions.
+// e2 at pixel offset (dx, dy), in two parts: the terms of dx alone (a dx^2 + l
+// and b dx, shared by the pixels of one column) and the rest per pixel. Every
+// kernel evaluates it this way, rounding pinned with intrinsics, so the forward
+// and the backward replay take the same gate decisions.
 struct SplatRow {
     float adx2, bdx;
 };
 
-__device__ __forceinline__ SplatRow splat_row(float dx, float a, float b)
+__device__ __forceinline__ SplatRow splat_row(float dx, float4 s)
 {
-    return SplatRow{__fmul_rn(a, __fmul_rn(dx, dx)), __fmul_rn(b, dx)};
+    return SplatRow{__fadd_rn(__fmul_rn(s.x, __fmul_rn(dx, dx)), s.w), __fmul_rn(s.y, dx)};
 }
 
 __device__ __forceinline__ float splat_power(SplatRow r, float dy, float c)
 {
     return __fmaf_rn(r.bdx, dy, __fmaf_rn(c, __fmul_rn(dy, dy), r.adx2));
+}
+
+// The gate of one pixel on e2 (above): the splat's Gaussian factor at most 1 and
+// alpha at least 1/255.
+__device__ __forceinline__ bool splat_gate(float e2, float l)
+{
+    return !(e2 > l) && !(e2 < kLog2AlphaMin);
 }
 
 // ---------------------------------------------------------------------------

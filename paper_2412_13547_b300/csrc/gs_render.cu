@@ -296,25 +296,25 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     const float2 p = s_p[j];
                     const float4 co = s_co[j];
                     const float dx = __fsub_rn(xr, p.x);
-                    const SplatRow row = splat_row(dx, co.x, co.y);
+                    const SplatRow row = splat_row(dx, co);
                     // the gates of all this thread's pixels first, free of branches so that
                     // their dependency chains interleave; then the blends, in pixel order
-                    float alpha[PPT];
+                    float e2[PPT];
                     bool use[PPT];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         const float dy = __fsub_rn(yr[k], p.y);
-                        const float power = splat_power(row, dy, co.z);
-                        alpha[k] = fminf(kAlphaMax, __fmul_rn(co.w, exp2_sfu(power)));
-                        use[k] = !done[k] && !(power > 0.0f) && !(alpha[k] < kAlphaMin);
+                        e2[k] = splat_power(row, dy, co.z);
+                        use[k] = !done[k] && splat_gate(e2[k], co.w);
                     }
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (!use[k]) continue;
-                        const float Tn = T[k] * (1.0f - alpha[k]);
+                        const float alpha = fminf(kAlphaMax, exp2_sfu(e2[k]));
+                        const float Tn = T[k] * (1.0f - alpha);
                         if (Tn < kTStop) { done[k] = true; --n_live; continue; }
                         const float4 c = s_rgb[j];
-                        const float w = alpha[k] * T[k];
+                        const float w = alpha * T[k];
                         C0[k] = fmaf(c.x, w, C0[k]);
                         C1[k] = fmaf(c.y, w, C1[k]);
                         C2[k] = fmaf(c.z, w, C2[k]);
@@ -500,7 +500,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 s_p[i] = p;
                 s_mask[i] = warp_mask<TILE, PPT>(p, co, dil.d);
                 s_co[i] = conic_exp2(co);
-                s_rgb[i] = rgb;
+                s_rgb[i] = make_float4(rgb.x, rgb.y, rgb.z, co.w > 0.0f ? __frcp_rn(co.w) : 0.0f);  // w: 1/o
                 s_id[i] = g;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) s_acc[i][k] = 0.0f;
@@ -526,7 +526,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     s_p[slot] = p;
                     s_mask[slot] = warp_mask<TILE, PPT>(p, co, dil.d);
                     s_co[slot] = conic_exp2(co);
-                    s_rgb[slot] = rgb;
+                    s_rgb[slot] = make_float4(rgb.x, rgb.y, rgb.z, co.w > 0.0f ? __frcp_rn(co.w) : 0.0f);  // w: 1/o
                     s_id[slot] = g;
                     s_rel[slot] = rel;
 #pragma unroll
@@ -559,30 +559,29 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 float r[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) r[k] = 0.0f;
-                // dL/dpower summed over the thread's pixels, and times dy and dy^2: the conic and
-                // centre gradients are those three sums times per-entry factors of dx
+                // dL/dpower summed over the thread's pixels, and times dy and dy^2: the conic,
+                // centre and opacity gradients are those three sums times per-entry factors
                 float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
                 bool contrib = false;
                 const float2 p = s_p[j];
                 const float4 co = s_co[j];
                 const float4 c = s_rgb[j];
                 const float dx = __fsub_rn(xr, p.x);
-                const SplatRow row = splat_row(dx, co.x, co.y);
+                const SplatRow row = splat_row(dx, co);
                 // gates of all this thread's pixels first (branch-free), then the replay
-                float dyk[PPT], Gk[PPT], ark[PPT];
+                float dyk[PPT], e2[PPT];
                 bool use[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     dyk[k] = __fsub_rn(yr[k], p.y);
-                    const float power = splat_power(row, dyk[k], co.z);
-                    Gk[k] = exp2_sfu(power);
-                    ark[k] = __fmul_rn(co.w, Gk[k]);  // alpha before the 0.99 clamp, as in the forward
-                    use[k] = pos < n_last[k] && !(power > 0.0f) && !(fminf(kAlphaMax, ark[k]) < kAlphaMin);
+                    e2[k] = splat_power(row, dyk[k], co.z);
+                    use[k] = pos < n_last[k] && splat_gate(e2[k], co.w);
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (!use[k]) continue;
-                    const float dy = dyk[k], G = Gk[k], a_raw = ark[k];
+                    const float dy = dyk[k];
+                    const float a_raw = exp2_sfu(e2[k]);  // alpha before the 0.99 clamp, as in the forward
                     const float alpha = fminf(kAlphaMax, a_raw);
                     contrib = true;
                     // one SFU reciprocal serves both divisions by (1 - alpha) >= 0.01 (a few
@@ -600,13 +599,14 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     T[k] = Ti;
                     if (a_raw < kAlphaMax) {
                         const float dpower = a_raw * dalpha;
-                        r[5] = fmaf(G, dalpha, r[5]);
                         const float t = dpower * dy;
                         q0 += dpower;
                         q1 += t;
                         q2 = fmaf(t, dy, q2);
                     }
                 }
+                // dalpha/do = G = alpha / o: the opacity gradient is the dL/dpower sum over o
+                r[5] = q0 * c.w;
                 // dpower/dA = -dx^2/2, dpower/dB = -dx dy, dpower/dC = -dy^2/2. With the staged
                 // (a, b, c): A dx + B dy = -(2a dx + b dy) ln 2 and C dy + B dx = -(2c dy + b dx) ln 2;
                 // the -ln 2 is applied after the warp sum
