@@ -34,14 +34,23 @@ __device__ __forceinline__ void warp_stage(const uint32_t* __restrict__ src, int
     const uint32_t* base = src + (int64_t)g0 * W;
     if (rows == 32 && (W % 4 == 0 || ((reinterpret_cast<uintptr_t>(base) & 15) == 0))) {
         const uint4* b4 = reinterpret_cast<const uint4*>(base);
-#pragma unroll(FEW ? 4 : 8 * W)
-        for (int q = lane; q < 8 * W; q += 32) {
-            uint4 v = __ldg(b4 + q);
-            int w0 = 4 * q;
+        constexpr int KN = (8 * W + 31) / 32;  // vectors per lane, the last one partial when W % 4 != 0
+        auto put = [&](int q) {
+            const uint4 v = __ldg(b4 + q);
+            const int w0 = 4 * q;
             dst[((w0 + 0) / W) * S + (w0 + 0) % W] = v.x;
             dst[((w0 + 1) / W) * S + (w0 + 1) % W] = v.y;
             dst[((w0 + 2) / W) * S + (w0 + 2) % W] = v.z;
             dst[((w0 + 3) / W) * S + (w0 + 3) % W] = v.w;
+        };
+        if constexpr (FEW) {
+#pragma unroll 4
+            for (int k = 0; k < KN; ++k)
+                if (lane + 32 * k < 8 * W) put(lane + 32 * k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KN; ++k)
+                if (lane + 32 * k < 8 * W) put(lane + 32 * k);
         }
     } else {
         for (int w = lane; w < rows * W; w += 32) dst[(w / W) * S + w % W] = __ldg(base + w);
