@@ -243,7 +243,8 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     step.counts.zero_()
     for i in range(n_count):
         ox, oy = offsets[warmup + steps + i]
-        timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
+        # event slot 0, as in the warm-up: the stage times were read above
+        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
     torch.cuda.synchronize()
     counts = step.counts.cpu().numpy() / n_count  # per step
     iters_per_s = steps * 1000.0 / total_ms
