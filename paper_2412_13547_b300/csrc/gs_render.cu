@@ -119,7 +119,7 @@ __device__ __forceinline__ int cta_rank(bool flag, int* s_w, int* total)
 }
 
 // Pixels of a CTA: each warp owns a compact 8-column block of 4*PPT rows and
-// each lane one column and PPT consecutive rows of it. Several pixels per
+// each lane one column and PPT rows of it (WarpBlock). Several pixels per
 // thread share one shared-memory read of each staged record and, in the
 // backward, one warp reduction per list entry.
 template <int TILE, int PPT>
