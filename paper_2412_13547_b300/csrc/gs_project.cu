@@ -712,6 +712,59 @@ __device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const f
     return true;
 }
 
+// Adam over a full, dense warp's rows of means, log-scales, quaternions and
+// logits with all their loads issued together (one round trip to memory for
+// the four tensors): lanes below 24 take one 16-byte vector of each 3-float
+// tensor's 96 floats, every lane its own quaternion and logit.
+__device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g, const float* s_gms, float4 gq,
+                                                float glogit, float bc1, float bc2, int lane)
+{
+    const bool act = lane < 24;
+    const int64_t b3 = (int64_t)g0 * 3;
+    float4 p[2], m[2], v[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (!act) continue;
+        p[t] = reinterpret_cast<const float4*>(a.p[t] + b3)[lane];
+        m[t] = reinterpret_cast<const float4*>(a.m[t] + b3)[lane];
+        v[t] = reinterpret_cast<const float4*>(a.v[t] + b3)[lane];
+    }
+    float4 pq = reinterpret_cast<const float4*>(a.p[2])[g];
+    float4 mq = reinterpret_cast<const float4*>(a.m[2])[g];
+    float4 vq = reinterpret_cast<const float4*>(a.v[2])[g];
+    float po = a.p[3][g], mo = a.m[3][g], vo = a.v[3][g];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (!act) continue;
+        float* pp = &p[t].x;
+        float* mm = &m[t].x;
+        float* vv = &v[t].x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int e = 4 * lane + c;
+            const float gr = s_gms[(e / 3) * 7 + 3 * t + e % 3];
+            adam_step(pp[c], gr, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
+            if (a.gout[t]) a.gout[t][b3 + e] = gr;
+        }
+        reinterpret_cast<float4*>(a.p[t] + b3)[lane] = p[t];
+        reinterpret_cast<float4*>(a.m[t] + b3)[lane] = m[t];
+        reinterpret_cast<float4*>(a.v[t] + b3)[lane] = v[t];
+    }
+    adam_step(pq.x, gq.x, mq.x, vq.x, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+    adam_step(pq.y, gq.y, mq.y, vq.y, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+    adam_step(pq.z, gq.z, mq.z, vq.z, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+    adam_step(pq.w, gq.w, mq.w, vq.w, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+    reinterpret_cast<float4*>(a.p[2])[g] = pq;
+    reinterpret_cast<float4*>(a.m[2])[g] = mq;
+    reinterpret_cast<float4*>(a.v[2])[g] = vq;
+    adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, bc1, bc2, a.lr[3]);
+    a.p[3][g] = po;
+    a.m[3][g] = mo;
+    a.v[3][g] = vo;
+    if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
+    if (a.gout[3]) a.gout[3][g] = glogit;
+}
+
 // One warp per 32 Gaussians: stage the parameters, project and differentiate
 // them in every view of the batch (gradients summed over views), then one
 // Adam step for the warp's rows. MULTI false is the one-view form, which
@@ -809,9 +862,20 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
     const unsigned vis = __ballot_sync(0xffffffffu, a.sparse && valid && visible_any(b, g));
     // coalesced Adam over the warp's rows of means, log-scales and SH
     const float bc1 = a.bias ? a.bias[0] : a.inv_bc1, bc2 = a.bias ? a.bias[1] : a.inv_bc2;
-    adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
-    adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
+    uintptr_t al = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        al |= reinterpret_cast<uintptr_t>(a.p[t]) | reinterpret_cast<uintptr_t>(a.m[t]) |
+              reinterpret_cast<uintptr_t>(a.v[t]);
+    const bool grouped = rows == 32 && !a.sparse && (al & 15) == 0;
+    if (grouped) {
+        adam_small_rows(a, g0, g, s_gms, gq, glogit, bc1, bc2, lane);
+    } else {
+        adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
+        adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
+    }
     adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
+    if (grouped) return;
     // quaternions (16-byte rows) and opacity logits, one row per lane
     if (valid) {
         if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
