@@ -5,7 +5,7 @@ integer radius/rect/tile counts exact except where the oracle flags a decision
 within rounding distance of its threshold), binning (bit-exact: the oracle's
 binning of the GPU's own FP32 rects and depth bits), blending (image within
 1e-4 abs), backward (gradients within 1e-3 of the per-tensor maximum), and
-the full step. Tolerances follow the spec bar: images 1e-4 max abs,
+the full step. Tolerances: images 1e-4 max abs,
 gradients 1e-3 relative, keys/sort order/ranges bit-exact.
 """
 import math
