@@ -130,6 +130,31 @@ KERNEL_OF_STAGE = {"project": "k_project", "render_fwd": "k_render_fwd", "render
                    "project_bwd_adam": "k_project_bwd_adam"}
 
 
+def barrier():
+    """Barrier across the ranks of a multi-GPU run (replicas); a no-op on one GPU."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(values, device):
+    """Each value's maximum over the ranks: the slowest replica sets the job's step time."""
+    import torch
+    import torch.distributed as dist
+    vals = [float(v) for v in values]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(world, ms_per_step):
+    """Whole-job iterations per second: each of the world's replicas takes one step per
+    ms_per_step (the max over ranks)."""
+    return world * 1000.0 / ms_per_step
+
+
 def setup(args, device):
     import torch
     from paper_2412_13547_b300 import build_native, raster as R, scenes
@@ -226,6 +251,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     ctx = clocks if clocks is not None else _Null()
     with ctx:
         torch.cuda.synchronize()
+        barrier()
         start.record()
         for i in range(steps):
             ox, oy = offsets[warmup + i]
@@ -233,6 +259,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
+        barrier()
     total_ms = start.elapsed_time(end)
     stage = timed.stage_ms(steps) if want_stage else None
     ks = k_hist.cpu().numpy()
@@ -346,6 +373,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
     for i in range(total):
         if i == warmup:
             torch.cuda.synchronize()
+            barrier()
             start.record()
         b = i % 2
         if i + 1 < total:
@@ -357,6 +385,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     end.record()
     torch.cuda.synchronize()
+    barrier()
     ms = start.elapsed_time(end)
     return dict(value=steps * 1000.0 / ms, unit=UNIT, h2d_bytes_per_step=int(target_np.nbytes),
                 d2h_bytes_per_step=4, ms_per_step=ms / steps)
@@ -682,14 +711,8 @@ def main():
     e2e = e2e_measure(args, params, cam, target, 2, args.steps, args.warmup, device, rast, snapshot)
 
     # max over ranks of the step time (replicas: every rank runs the whole workload)
-    ms = head["ms_per_step"]
-    e2e_ms = e2e["ms_per_step"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-    value = world * 1000.0 / ms
+    ms, e2e_ms = max_over_ranks([head["ms_per_step"], e2e["ms_per_step"]], device)
+    value = job_throughput(world, ms)
 
     sh_bytes = 48 * 4
     roof = stage_roofline(head, params.n, sh_bytes, pk, R.gs_grid(cam, R.Dilation(2, 1, 0))[0] *
@@ -737,7 +760,7 @@ def main():
         "blends_contributing_per_s": round(head["blends_contributing_per_s"], 1),
         "variants": variants, "stage_ms": stage_tables,
         "roofline": roofline, "cpu_baseline": cpu,
-        "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT,
+        "e2e": {"value": round(job_throughput(world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
         "gpu_launches": launches * args.steps,
         "clocks": clocks.summary(),
