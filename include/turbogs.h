@@ -206,7 +206,8 @@ int32_t gs_tile_order(const uint32_t* ranges, int32_t num_tiles, uint32_t* order
  * Per pixel, walking its tile's list: alpha = min(0.99, opacity * G); entries
  * with alpha < 1/255 (or a positive exponent) are skipped; the walk stops
  * before an entry that would take the transmittance below 1e-4; finally
- * C += T * bg.
+ * C += T * bg. Both gates are decided in FP32 on log2(opacity * G), in the
+ * same arithmetic as gs_render_bwd's replay.
  * Inputs (device): splats, sorted_ids, ranges (from gs_bin_sort). bg: host
  *   float[3].
  * Each blend tile walks its binning tile's list (the same list when
