@@ -79,3 +79,51 @@ def ssim(x: np.ndarray, y: np.ndarray, data_range: float = 1.0, mode: str = "val
     if x.ndim != 3 or x.shape != y.shape:
         raise ValueError("ssim: H x W or H x W x C images of the same shape")
     return float(np.mean([ssim_map(x[..., c], y[..., c], data_range, mode).mean() for c in range(x.shape[2])]))
+
+
+def _filter_adjoint(m: np.ndarray, w: np.ndarray, shape, mode: str) -> np.ndarray:
+    """Adjoint of ``_filter``: spreads each output pixel's value back over its
+    window (a full convolution with the symmetric window, cropped in the
+    'same' mode to undo the zero padding)."""
+    k = len(w)
+    cols = np.apply_along_axis(lambda v: np.convolve(v, w, mode="full"), 0, m)
+    full = np.apply_along_axis(lambda v: np.convolve(v, w, mode="full"), 1, cols)
+    if mode == "same":
+        pad = k // 2
+        full = full[pad:pad + shape[0], pad:pad + shape[1]]
+    return full
+
+
+def ssim_grad(x: np.ndarray, y: np.ndarray, data_range: float = 1.0, mode: str = "valid") -> np.ndarray:
+    """Gradient of the mean SSIM of two single-channel images with respect to x.
+
+    With the window sums m_x = g * x, E_xx = g * x^2, E_xy = g * (x y) of each
+    pixel p, SSIM_p = A1 A2 / (B1 B2), A1 = 2 m_x m_y + C1,
+    A2 = 2 (E_xy - m_x m_y) + C2, B1 = m_x^2 + m_y^2 + C1,
+    B2 = E_xx - m_x^2 + E_yy - m_y^2 + C2. Its partial derivatives in
+    (m_x, E_xx, E_xy) are spread back over each window (the adjoint of the
+    window sum) and chained through dE_xx/dx = 2x, dE_xy/dx = y. The D-SSIM
+    loss (1 - SSIM) / 2 has minus half this gradient."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    w = gaussian_window()
+    c1 = (K1 * data_range) ** 2
+    c2 = (K2 * data_range) ** 2
+    mx = _filter(x, w, mode)
+    my = _filter(y, w, mode)
+    exx = _filter(x * x, w, mode)
+    eyy = _filter(y * y, w, mode)
+    exy = _filter(x * y, w, mode)
+    a1 = 2.0 * mx * my + c1
+    a2 = 2.0 * (exy - mx * my) + c2
+    b1 = mx * mx + my * my + c1
+    b2 = exx - mx * mx + eyy - my * my + c2
+    s = a1 * a2 / (b1 * b2)
+    npix = s.size
+    d_mx = (2.0 * my * a2 - 2.0 * my * a1) / (b1 * b2) - s * (2.0 * mx / b1 - 2.0 * mx / b2)
+    d_exx = -s / b2
+    d_exy = 2.0 * a1 / (b1 * b2)
+    g_m = _filter_adjoint(d_mx / npix, w, x.shape, mode)
+    g_xx = _filter_adjoint(d_exx / npix, w, x.shape, mode)
+    g_xy = _filter_adjoint(d_exy / npix, w, x.shape, mode)
+    return g_m + 2.0 * x * g_xx + y * g_xy

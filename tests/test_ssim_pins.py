@@ -101,3 +101,24 @@ def test_channels_are_averaged():
 def test_rejects_images_smaller_than_the_window():
     with pytest.raises(ValueError):
         S.ssim_map(np.zeros((10, 40)), np.zeros((10, 40)))
+
+
+@pytest.mark.parametrize("mode", ["valid", "same"])
+def test_gradient_matches_central_differences(mode):
+    rng = np.random.default_rng(4)
+    x = rng.random((15, 14))
+    y = np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1)
+    g = S.ssim_grad(x, y, mode=mode)
+    h = 1e-6
+    for (i, j) in ((0, 0), (3, 7), (7, 6), (14, 13), (10, 2)):
+        xp, xm = x.copy(), x.copy()
+        xp[i, j] += h
+        xm[i, j] -= h
+        fd = (S.ssim_map(xp, y, mode=mode).mean() - S.ssim_map(xm, y, mode=mode).mean()) / (2 * h)
+        assert g[i, j] == pytest.approx(fd, rel=1e-6, abs=1e-10), (i, j)
+
+
+def test_gradient_vanishes_at_identity():
+    # SSIM is at its maximum 1 when x = y
+    x = np.random.default_rng(5).random((16, 16))
+    np.testing.assert_allclose(S.ssim_grad(x, x), 0.0, atol=1e-12)
