@@ -37,8 +37,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd iters/sec and Gaussian-pixel blends/sec at 4K, dilated vs full FP32, % HBM roof"
 UNIT = "iters/s"
-SM_COUNT = 148
 FP32_LANES_PER_SM = 128
+SM_COUNT = [0]  # read from the device (torch.cuda.get_device_properties) before any roofline
+
+
+def sm_count():
+    if not SM_COUNT[0]:
+        import torch
+        SM_COUNT[0] = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    return SM_COUNT[0]
 
 
 def peaks():
@@ -233,8 +240,9 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         p = params
         p.sh_store = p.sh
     else:
-        p = GaussianParams(params.means, params.log_scales, params.quats, params.opacity_logits, params.sh,
-                           params.sh.to(sh_dtype).contiguous())
+        # the precision form: the SH kept only in BF16/FP16 (Adam rounds its update stochastically)
+        lowp = params.sh.to(sh_dtype).contiguous()
+        p = GaussianParams(params.means, params.log_scales, params.quats, params.opacity_logits, lowp, lowp)
     max_px = max(R.gs_grid(cam, R.Dilation(d, ox, oy))[0] * R.gs_grid(cam, R.Dilation(d, ox, oy))[1]
                  for ox in range(d) for oy in range(d))
     step = TrainStep(p, rast, AdamConfig(), max_pixels=max_px)
@@ -301,7 +309,7 @@ class _Null:
 def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     """Algorithmic bytes (HBM-bound stages) or FLOPs (blend stages) per launch."""
     hbm = pk["hbm_gbs"]
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    alu_peak = sm_count() * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s, FMA = 2
     k = res["pairs_mean"]
     params_b = n * (4 * (3 + 3 + 4 + 1) + sh_bytes)
     rows = {}
@@ -321,7 +329,7 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     rows["render_bwd"] = ("alu", 12.0 * res["replayed_per_step"] + 41.0 * res["blended_per_step"])
     # projection backward + densification statistics + Adam, fused: parameters, moments and the
     # 2D record read, parameters and moments written, statistics read-modify-written
-    rows["project_bwd_adam"] = ("hbm", 3 * params_b + n * 48 + 3 * n * 59 * 4 + n * (24 + 4))
+    rows["project_bwd_adam"] = ("hbm", 2 * params_b + 4 * n * 59 * 4 + n * 48 + n * (24 + 4))
     out = {}
     for s, (bound, work) in rows.items():
         ms = res["stage_ms"][s]
@@ -334,6 +342,37 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
             out[s] = dict(bound="alu", achieved=ach, peak=alu_peak, unit="TFLOP/s", frac=ach / alu_peak, ms=ms,
                           algorithmic=work)
     return out
+
+
+def memory_report(res, step, params, cam, device):
+    """Device memory of the headline step (recompute-in-backward): the peak
+    allocated while it ran, the per-pixel state the backward replays from
+    (final transmittance and last index, 8 B per rendered pixel), and what a
+    backward that stored the blend state instead would hold: alpha and the
+    transmittance (8 B) of every blended (pixel, entry), a lower bound."""
+    import torch
+    from paper_2412_13547_b300 import raster as R
+    w, h, _, _ = R.gs_grid(cam, R.Dilation(2, 0, 0))
+    n = params.n
+    resident = sum(t.numel() * t.element_size() for t in params.tensors()) + \
+        sum(t.numel() * t.element_size() for t in step.m + step.v)
+    return {"peak_allocated_bytes": int(torch.cuda.max_memory_allocated(device)),
+            "params_and_moments_bytes": int(resident),
+            "replay_state_bytes": int(8 * w * h),
+            "stored_blend_state_bytes": int(8 * res["blended_per_step"]),
+            "note": "d=2 headline step; stored state = 8 B (alpha, T) per blended (pixel, entry), "
+                    f"{res['blended_per_step']:.3e} per step; replay state = T_final + last per pixel, "
+                    f"{n} Gaussians"}
+
+
+def step_hbm(roof, ms_per_step, pk):
+    """The step-level HBM roofline: the algorithmic bytes of every HBM-bound
+    stage of one step over the whole step's time, against the measured copy
+    bandwidth (the blend stages are ALU-bound and add their few bytes here)."""
+    total = sum(r["algorithmic"] for r in roof.values() if r["bound"] == "hbm")
+    ach = total / (ms_per_step * 1e-3) / 1e9
+    return {"bytes": total, "achieved": round(ach, 3), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / pk["hbm_gbs"], 4)}
 
 
 def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, snapshot):
@@ -504,7 +543,7 @@ def run_fit(args, device):
             runs[form] = dict(history=[{k: (round(v, 4) if isinstance(v, float) else v) for k, v in hh.items()}
                                        for hh in hist],
                               rounds=len(fit.rounds), final_psnr=hist[-1]["psnr"], gpu_seconds=hist[-1]["seconds"],
-                              n_final=hist[-1]["n"])
+                              n_final=hist[-1]["n"], overflow_steps=fit.overflow_steps)
             del fit
             torch.cuda.empty_cache()
     # equal PSNR: the lower of the two final held-out PSNRs (as recorded in the histories)
@@ -697,15 +736,23 @@ def main():
 
     pk = peaks()
     clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(device)
     head, head_step = measure_variant(args, params, cam, target_dev, 2, torch.float32, args.steps, args.warmup,
                                       device, rast, snapshot, clocks=clocks)
+    memory = memory_report(head, head_step, params, cam, device)
     variants = {"dilated_d2_fp32": {k: v for k, v in head.items() if k != "stage_ms"}}
     stage_tables = {"dilated_d2_fp32": head["stage_ms"]}
     if not args.no_variants:
         vsteps = max(3, args.steps // 2)
         for name, d, dt in (("full_d1_fp32", 1, torch.float32), ("dilated_d2_bf16", 2, torch.bfloat16),
-                            ("dilated_d4_fp32", 4, torch.float32)):
+                            ("dilated_d2_fp16", 2, torch.float16), ("dilated_d4_fp32", 4, torch.float32)):
             r, _ = measure_variant(args, params, cam, target_dev, d, dt, vsteps, 3, device, rast, snapshot)
+            sh_b = 48 * (4 if dt == torch.float32 else 2)
+            npx = R.gs_grid(cam, R.Dilation(d, 0, 0))[0] * R.gs_grid(cam, R.Dilation(d, 0, 0))[1]
+            vroof = stage_roofline(r, params.n, sh_b, pk, npx)
+            r["step_hbm"] = step_hbm(vroof, r["ms_per_step"], pk)
+            r["fused_pass_hbm_frac"] = round(vroof["project_bwd_adam"]["frac"], 4)
             stage_tables[name] = r.pop("stage_ms")
             variants[name] = r
     e2e = e2e_measure(args, params, cam, target, 2, args.steps, args.warmup, device, rast, snapshot)
@@ -731,10 +778,12 @@ def main():
             traffic = None
     roofline = {"bound": dr["bound"], "achieved": round(dr["achieved"], 3), "peak": dr["peak"], "unit": dr["unit"],
                 "frac": round(dr["frac"], 4), "traffic": traffic, "kernel": KERNEL_OF_STAGE[dom],
-                "peak_source": pk["src"] if dr["bound"] == "hbm" else "derived: 148 SM x 128 FP32 lanes x 2 x "
+                "peak_source": pk["src"] if dr["bound"] == "hbm" else f"derived: {sm_count()} SM x 128 FP32 lanes x 2 x "
                 f"{pk['sm_max_mhz']:.0f} MHz",
                 "stages": {s: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                            for s, r in roof.items()}}
+
+    step_roof = step_hbm(roof, head["ms_per_step"], pk)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -759,7 +808,9 @@ def main():
         "blends_per_s": round(head["blends_evaluated_per_s"], 1),
         "blends_contributing_per_s": round(head["blends_contributing_per_s"], 1),
         "variants": variants, "stage_ms": stage_tables,
-        "roofline": roofline, "cpu_baseline": cpu,
+        "roofline": roofline, "step_hbm_frac": step_roof["frac"], "step_hbm": step_roof,
+        "sm_count": sm_count(), "memory": memory,
+        "cpu_baseline": cpu,
         "e2e": {"value": round(job_throughput(world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
         "gpu_launches": launches * args.steps,

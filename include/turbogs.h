@@ -157,6 +157,12 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  *   scatter then writes every id straight into its slot: first into per-row
  *   lists (one entry per tile row of the rect), then each row list into its
  *   tiles, both levels stable. tiles_x, tiles_y <= 4096.
+ * Output form: the 64-bit (tile << 32 | depth bits) keys are implied, not
+ *   written. The sorted key of entry j of tile t's range is t << 32 | the
+ *   float32 bits of splats[sorted_ids[j]][9], so (sorted_ids, ranges) is the
+ *   whole result of sorting the (key, value) pairs: the same list, position
+ *   for position, as the key sort of the tile-based rasterizer (Sec. 3) on
+ *   the downsampled tile grid (Sec. 3.1).
  * Errors: GS_ERR_ARG for bad sizes, null pointers or a short workspace. */
 size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, int32_t tiles_y);
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
@@ -179,11 +185,17 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
  * the required size in gs_last_error(); for example n = 256K Gaussians with
  * 1.5M pairs on a 1920x1080 grid fits. The call allocates nothing and calls no
  * allocating routine.
- * The first call on each device looks up the array's device address (with
- * that device current) and keeps it; make that first call before any stream
- * capture. All calls share the one array and it keeps the last call's
- * contents: calls that may overlap on the GPU (different streams, or
- * different host threads on one device) race on it, so serialise them. */
+ * Every call looks up the array's device address in the calling thread's
+ * current CUDA context, so the call is valid in any context (a plugin's own
+ * context, or a new one after cudaDeviceReset). With lazy module loading (the
+ * CUDA default since 12.2) the array is reserved when the library's module is
+ * first used on a device, which can fail with out-of-memory in a process
+ * whose device memory is already spoken for: make one call at start-up (it
+ * also loads the module, so make it before any stream capture), or set
+ * CUDA_MODULE_LOADING=EAGER to reserve the array when the library loads.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that may overlap on the GPU (different streams, or different host threads
+ * on one device) race on it, so serialise them. */
 #define GS_BIN_SORT_STATIC_SCRATCH_BYTES (32u << 20)
 int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
                            const float* splats, int32_t tiles_x, int32_t tiles_y, int64_t capacity,
@@ -287,11 +299,26 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * rounding (the two kernels may contract the shared gradient arithmetic into
  * FMAs differently); the Adam update itself is the same pinned arithmetic.
  * adam->param[0..4] are the FP32 parameters (means, log_scales, quats,
- * opacity_logits, sh), updated in place; m, v their moments; lr per tensor.
- * sh_store (device) is the SH storage the forward projection read: adam->param[4]
- * itself (sh_dtype FP32) or its BF16/FP16 copy, which is then refreshed from the
- * updated FP32 values when adam->sh_shadow points at it. With adam->sparse != 0
- * Gaussians with tiles_touched == 0 are left untouched (no moment decay).
+ * opacity_logits, sh), updated in place; m, v their moments (FP32, also for
+ * the SH); lr per tensor. sh_store (device) is the SH storage the forward
+ * projection read. Three forms of SH storage:
+ *   - FP32: sh_store is adam->param[4] (or param[4] is NULL: the same array).
+ *   - low precision only (the precision form: SH and colours stored in
+ *     BF16/FP16, blend and accumulation in FP32): adam->param[4] = NULL and
+ *     sh_dtype BF16 or FP16. sh_store is the parameter itself, updated in place:
+ *     the update is computed in FP32 from the stored value and rounded
+ *     stochastically to sh_dtype (the neighbour away from zero with probability
+ *     equal to the value's position between the two neighbours, from 16 bits
+ *     of the PCG hash of Jarzynski & Olano 2020 applied to base + e, e = g *
+ *     3 (sh_degree+1)^2 + j the element index, base = hash(hash(sr_seed) xor t),
+ *     t the Adam step: *adam->step_dev when given, else adam->step). No FP32
+ *     copy of the SH exists, so the pass moves 2 instead of 4 bytes per SH
+ *     value in each direction. adam->sh_shadow must be NULL.
+ *   - FP32 master with a low-precision copy: adam->param[4] FP32 and sh_store
+ *     its BF16/FP16 copy, refreshed (round to nearest) from the updated FP32
+ *     values when adam->sh_shadow points at it.
+ * With adam->sparse != 0 Gaussians with tiles_touched == 0 are left untouched
+ * (no moment decay).
  * grads_out (nullable host array of 5 device pointers, each nullable) receives
  * the gradients as gs_project_bwd would write them. pos_acc/col_acc/count:
  * as in gs_project_bwd. bias_dev (nullable device pointer to two floats
@@ -310,6 +337,8 @@ typedef struct {
     void* sh_shadow;
     int32_t sh_shadow_dtype;
     const float* bias_dev;
+    const int32_t* step_dev;   /* nullable device int32: t of the rounding stream */
+    uint32_t sr_seed;          /* seed of the stochastic rounding (low-precision SH) */
 } GsAdamParams;
 int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
                             const GsCamera* cam, const GsDilation* dil,
@@ -341,7 +370,11 @@ int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* g
  * with row_mask (device, one byte per row, shared by all tensors) non-null,
  * rows whose byte is 0 are left untouched ("sparse" Adam over visible
  * Gaussians). shadow (nullable) receives the updated parameter converted to
- * shadow_dtype (e.g. the BF16 SH storage the projection reads).
+ * shadow_dtype (e.g. the BF16 SH storage the projection reads). With param
+ * NULL and shadow non-null of BF16/FP16 type, shadow is the parameter itself
+ * (no FP32 copy): the update is computed in FP32 from the stored value and
+ * rounded stochastically, element e of the tensor drawing its 16 random bits
+ * as gs_project_bwd_adam does (seed sr_seed, t = step).
  * The GsAdamTensor array is read on the host; all its pointers are device. */
 #define GS_ADAM_MAX_TENSORS 8
 typedef struct {
@@ -354,7 +387,7 @@ typedef struct {
     int32_t row_width;
     int32_t shadow_dtype;
     float lr;
-    float pad_;
+    uint32_t sr_seed;
 } GsAdamTensor;
 int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float beta2,
                 float eps, int32_t step, const uint8_t* row_mask, gs_stream_t stream);

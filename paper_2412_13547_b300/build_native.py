@@ -32,15 +32,35 @@ def _newest_input() -> float:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every .cu file to an object (in parallel, one nvcc each) and
+    link them into the shared library; skipped when the library is newer than
+    every source."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + FLAGS + ["-shared", "-o", tmp] + sources()
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True, cwd=CSRC)
-    os.replace(tmp, LIB)
+    tag = ".tmp%d" % os.getpid()
+    objs, procs = [], []
+    for src in sources():
+        obj = os.path.join(CSRC, os.path.basename(src)[:-3] + tag + ".o")
+        cmd = [nvcc] + ARCH + FLAGS + ["-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((subprocess.Popen(cmd, cwd=CSRC), cmd))
+        objs.append(obj)
+    try:
+        for pr, cmd in procs:
+            if pr.wait() != 0:
+                raise subprocess.CalledProcessError(pr.returncode, cmd)
+        tmp = LIB + tag
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True, cwd=CSRC)
+        os.replace(tmp, LIB)
+    finally:
+        for pr, _ in procs:
+            if pr.poll() is None:
+                pr.kill()
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

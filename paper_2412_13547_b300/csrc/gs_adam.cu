@@ -20,6 +20,8 @@ struct AdamTensorDev {
     int32_t shadow_dtype;
     float lr;
     int32_t vec4;  // all pointers 16-byte aligned and numel % 4 == 0
+    int32_t lowp;  // the parameter is `shadow` itself (BF16/FP16), rounded stochastically
+    uint32_t sr;   // stream of the stochastic rounding (sr_base of the seed and the step)
 };
 
 struct AdamArgs {
@@ -43,6 +45,19 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a)
     const AdamTensorDev& T = a.t[blockIdx.y];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T.lowp) {
+        // parameter kept only in 16 bits: FP32 update of the stored value, stochastic rounding
+        uint16_t* P = reinterpret_cast<uint16_t*>(T.shadow);
+        for (int64_t e = tid; e < T.numel; e += stride) {
+            if (a.row_mask && !a.row_mask[e / T.row_width]) continue;
+            float p = load_sh_elem(P, e, T.shadow_dtype), m = T.m[e], v = T.v[e];
+            adam_elem(p, T.g[e], m, v, a, T.lr);
+            P[e] = sr_round(p, sr_bits16(T.sr, (uint32_t)e), T.shadow_dtype);
+            T.m[e] = m;
+            T.v[e] = v;
+        }
+        return;
+    }
     if (T.vec4) {
         const int64_t n4 = T.numel / 4;
         for (int64_t i = tid; i < n4; i += stride) {
@@ -105,14 +120,19 @@ int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float b
     int64_t max_work = 0;
     for (int i = 0; i < count; ++i) {
         const GsAdamTensor& t = tensors[i];
-        if (t.numel < 0 || t.row_width < 1 || (t.numel > 0 && (!t.param || !t.grad || !t.m || !t.v)) ||
-            (t.shadow && (t.shadow_dtype < GS_DTYPE_F32 || t.shadow_dtype > GS_DTYPE_F16))) {
-            gs_host::set_error("gs_adam: bad tensor entry");
+        const bool lowp = !t.param && t.shadow != nullptr;
+        if (t.numel < 0 || t.row_width < 1 ||
+            (t.numel > 0 && ((!t.param && !lowp) || !t.grad || !t.m || !t.v)) ||
+            (t.shadow && (t.shadow_dtype < GS_DTYPE_F32 || t.shadow_dtype > GS_DTYPE_F16)) ||
+            (lowp && t.shadow_dtype == GS_DTYPE_F32)) {
+            gs_host::set_error("gs_adam: bad tensor entry (a parameter kept only in `shadow` must be BF16/FP16)");
             return GS_ERR_ARG;
         }
         AdamTensorDev& d = a.t[i];
         d.p = t.param; d.g = t.grad; d.m = t.m; d.v = t.v; d.shadow = t.shadow;
         d.numel = t.numel; d.row_width = t.row_width; d.shadow_dtype = t.shadow_dtype; d.lr = t.lr;
+        d.lowp = lowp ? 1 : 0;
+        d.sr = sr_base(t.sr_seed, (uint32_t)step);
         uintptr_t al = reinterpret_cast<uintptr_t>(t.param) | reinterpret_cast<uintptr_t>(t.grad) |
                        reinterpret_cast<uintptr_t>(t.m) | reinterpret_cast<uintptr_t>(t.v);
         d.vec4 = ((al & 15) == 0) && (t.numel % 4 == 0);

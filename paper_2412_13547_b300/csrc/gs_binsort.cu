@@ -14,7 +14,6 @@
 // caller's capacity.
 #include <algorithm>
 #include <cstdio>
-#include <mutex>
 
 #include "gs_common.cuh"
 
@@ -961,14 +960,6 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     return gs_host::check_launch("gs_bin_sort");
 }
 
-// Device address of g_bin_sort_scratch, looked up once per device with that
-// device current.
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-void* g_static_ptr[kMaxDevices] = {};
-}  // namespace
-
 int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
                            int32_t tiles_x, int32_t tiles_y, int64_t capacity, uint32_t* sorted_ids,
                            uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
@@ -987,28 +978,18 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
         gs_host::set_error(msg);
         return GS_ERR_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        gs_host::set_error(e != cudaSuccess ? cudaGetErrorString(e) : "gs_bin_sort_static: device index too large");
-        return GS_ERR_CUDA;
-    }
+    // The array's device address in the calling thread's current context, looked up on every
+    // call: an address kept from an earlier call could belong to another context (a plugin's own
+    // context, or one destroyed by cudaDeviceReset). Once the module is loaded this is a
+    // host-side table lookup that allocates nothing.
     void* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_static_mutex);
-        if (g_static_ptr[dev] == nullptr) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_bin_sort_scratch);
-            if (e != cudaSuccess || p == nullptr) {
-                char msg[256];
-                std::snprintf(msg, sizeof(msg), "gs_bin_sort_static: cudaGetSymbolAddress failed: %s",
-                              cudaGetErrorString(e));
-                gs_host::set_error(msg);
-                return GS_ERR_CUDA;
-            }
-            g_static_ptr[dev] = p;
-        }
-        scratch = g_static_ptr[dev];
+    const cudaError_t e = cudaGetSymbolAddress(&scratch, g_bin_sort_scratch);
+    if (e != cudaSuccess || scratch == nullptr) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg), "gs_bin_sort_static: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+        gs_host::set_error(msg);
+        return GS_ERR_CUDA;
     }
     return gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, scratch,
                        (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES, capacity, sorted_ids, ranges, num_pairs, stream);

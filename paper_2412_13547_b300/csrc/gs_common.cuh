@@ -341,6 +341,65 @@ __device__ __forceinline__ void store4_as(void* dst, int dtype, int64_t e, float
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of FP32 values to BF16/FP16 storage (for parameters kept
+// only in the low-precision type: an update smaller than half a step of that
+// type still moves the stored value, by a whole step with the matching
+// probability, so the expected stored value follows the FP32 update).
+// ---------------------------------------------------------------------------
+
+// Counter-based generator: the PCG hash of Jarzynski and Olano ("Hash
+// Functions for GPU Rendering", JCGT 9(3), 2020): one step of the 32-bit LCG
+// of PCG, then PCG's RXS-M-XS output permutation.
+__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v)
+{
+    const uint32_t state = v * 747796405u + 2891336453u;
+    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+// Stream of one optimizer step; element e draws pcg_hash(base + e) >> 16.
+__host__ __device__ __forceinline__ uint32_t sr_base(uint32_t seed, uint32_t step)
+{
+    return pcg_hash(pcg_hash(seed) ^ step);
+}
+
+__device__ __forceinline__ uint32_t sr_bits16(uint32_t base, uint32_t e)
+{
+    return pcg_hash(base + e) >> 16;
+}
+
+// x rounded to the BF16 neighbour away from zero when the 16 random bits r are
+// below the FP32 bits it drops (its position between the two neighbours, in
+// units of 2^-16 of a BF16 step), else toward zero. Non-finite: nearest.
+__device__ __forceinline__ uint16_t sr_bf16(float x, uint32_t r)
+{
+    const uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000u) == 0x7f800000u) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return (uint16_t)((b >> 16) + ((b & 0xffffu) > r ? 1u : 0u));
+}
+
+// The same rule for FP16: the neighbour toward zero lo, the step to the next
+// magnitude, and x's position between them in units of 2^-16 of that step
+// (exact: |x| - |lo| is a difference within one binade and the step a power of
+// two). The largest finite magnitude saturates; non-finite: nearest.
+__device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r)
+{
+    if (!isfinite(x)) return __half_as_ushort(__float2half_rn(x));
+    const uint16_t lb = __half_as_ushort(__float2half_rz(x));
+    if ((lb & 0x7fffu) >= 0x7bffu) return lb;
+    const float lo = fabsf(__half2float(__ushort_as_half(lb)));
+    const float hi = fabsf(__half2float(__ushort_as_half((uint16_t)(lb + 1u))));
+    const float frac = __fdiv_rn(__fsub_rn(fabsf(x), lo), __fsub_rn(hi, lo));
+    const uint32_t pos = (uint32_t)__float2uint_rz(__fmul_rn(frac, 65536.0f));
+    return (uint16_t)(lb + (pos > r ? 1u : 0u));
+}
+
+__device__ __forceinline__ uint16_t sr_round(float x, uint32_t r, int dtype)
+{
+    return dtype == GS_DTYPE_BF16 ? sr_bf16(x, r) : sr_f16(x, r);
+}
+
 // SH storage conversions
 __device__ __forceinline__ float load_sh_elem(const void* base, int64_t idx, int dtype)
 {

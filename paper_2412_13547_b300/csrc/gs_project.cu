@@ -537,6 +537,10 @@ struct AdamDev {
     void* shadow;
     int shadow_dtype;
     float* gout[5];
+    int lowp;            // SH kept only in sh_store (BF16/FP16), rounded stochastically
+    uint32_t sr_seed;
+    int step;            // t of the rounding stream when step_dev is null
+    const int* step_dev;
 };
 
 template <int DEG, int DT>
@@ -634,6 +638,94 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
         M[e] = m;
         V[e] = v;
         if (shadow) store_as(shadow, shadow_dtype, base + e, p);
+    }
+}
+
+// Adam over the warp's segment of the SH kept only in 16 bits (BF16/FP16 sh_store,
+// no FP32 copy): the update is computed in FP32 from the stored value and rounded
+// stochastically (element e of the tensor draws sr_bits16(sr, e)). A full, dense
+// warp moves groups of 8 values (one 16-byte vector of the parameter, two of
+// each moment), two groups in flight per lane; otherwise one element at a time.
+template <int W, int GSTRIDE, int DT>
+__device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int rows, const float* s_grad,
+                                                  unsigned vis, float bc1, float bc2, int lane, void* store,
+                                                  uint32_t sr)
+{
+    if constexpr (DT != GS_DTYPE_F32) {
+        const int64_t base = (int64_t)g0 * W;
+        uint16_t* P = reinterpret_cast<uint16_t*>(store) + base;
+        float* M = a.m[4] + base;
+        float* V = a.v[4] + base;
+        float* gout = a.gout[4];
+        const uintptr_t al = reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) |
+                             reinterpret_cast<uintptr_t>(V);
+        auto tofloat = [](uint16_t h) {
+            if constexpr (DT == GS_DTYPE_BF16) return __bfloat162float(__ushort_as_bfloat16(h));
+            else return __half2float(__ushort_as_half(h));
+        };
+        if (rows == 32 && !a.sparse && (al & 15) == 0) {
+            constexpr int Q = 4 * W;            // groups of 8 values in the segment (32 W values)
+            constexpr int KN = (Q + 31) / 32;   // groups per lane, the last one partial when Q % 32 != 0
+            constexpr int B = KN < 2 ? KN : 2;  // groups loaded before any is stored
+            uint4* P8 = reinterpret_cast<uint4*>(P);
+            float4* M4 = reinterpret_cast<float4*>(M);
+            float4* V4 = reinterpret_cast<float4*>(V);
+#pragma unroll
+            for (int k0 = 0; k0 < KN; k0 += B) {
+                uint4 p[B];
+                float4 m[2 * B], v[2 * B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int q = lane + 32 * (k0 + u);
+                    if (k0 + u < KN && q < Q) {
+                        p[u] = P8[q];
+                        m[2 * u] = M4[2 * q];
+                        m[2 * u + 1] = M4[2 * q + 1];
+                        v[2 * u] = V4[2 * q];
+                        v[2 * u + 1] = V4[2 * q + 1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int q = lane + 32 * (k0 + u);
+                    if (k0 + u >= KN || q >= Q) continue;
+                    uint32_t* pw = &p[u].x;
+                    float* mm = &m[2 * u].x;
+                    float* vv = &v[2 * u].x;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int e = 8 * q + c;
+                        const float g = s_grad[(e / W) * GSTRIDE + e % W];
+                        const uint16_t h = (c & 1) ? (uint16_t)(pw[c >> 1] >> 16) : (uint16_t)(pw[c >> 1] & 0xffffu);
+                        float x = tofloat(h);
+                        // m[2u] and m[2u+1] are consecutive in the array of float4s
+                        float& mc = (c < 4) ? mm[c] : (&m[2 * u + 1].x)[c - 4];
+                        float& vc = (c < 4) ? vv[c] : (&v[2 * u + 1].x)[c - 4];
+                        adam_step(x, g, mc, vc, a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
+                        const uint32_t hn = sr_round(x, sr_bits16(sr, (uint32_t)(base + e)), DT);
+                        pw[c >> 1] = (c & 1) ? ((pw[c >> 1] & 0xffffu) | (hn << 16)) : ((pw[c >> 1] & 0xffff0000u) | hn);
+                        if (gout) gout[base + e] = g;
+                    }
+                    P8[q] = p[u];
+                    M4[2 * q] = m[2 * u];
+                    M4[2 * q + 1] = m[2 * u + 1];
+                    V4[2 * q] = v[2 * u];
+                    V4[2 * q + 1] = v[2 * u + 1];
+                }
+            }
+            return;
+        }
+        for (int e = lane; e < rows * W; e += 32) {
+            const int row = e / W, col = e % W;
+            const float g = s_grad[row * GSTRIDE + col];
+            if (gout) gout[base + e] = g;
+            if (a.sparse && !((vis >> row) & 1u)) continue;
+            float x = tofloat(P[e]), m = M[e], v = V[e];
+            adam_step(x, g, m, v, a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
+            P[e] = sr_round(x, sr_bits16(sr, (uint32_t)(base + e)), DT);
+            M[e] = m;
+            V[e] = v;
+        }
     }
 }
 
@@ -773,7 +865,7 @@ __device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g,
 // lane in the Adam step, 5 beat 4 and 6 (spills) on this streaming pass
 template <int DEG, int DT, bool MULTI>
 __global__ void __launch_bounds__(kThreads, MULTI ? 4 : 5)
-k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_constant__ Batch b, AdamDev a,
+k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b, AdamDev a,
                    float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
 {
     using L = ShLayout<DEG, DT>;
@@ -874,7 +966,13 @@ k_project_bwd_adam(int n, const void* __restrict__ sh_store, const __grid_consta
         adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
         adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
     }
-    adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
+    if (a.lowp) {
+        // the SH parameters are sh_store itself: each warp writes only the rows it staged
+        const uint32_t sr = sr_base(a.sr_seed, a.step_dev ? (uint32_t)*a.step_dev : (uint32_t)a.step);
+        adam_segment_lowp<F::KW, F::GS, DT>(a, g0, rows, s_gsh, vis, bc1, bc2, lane, const_cast<void*>(sh_store), sr);
+    } else {
+        adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
+    }
     if (grouped) return;
     // quaternions (16-byte rows) and opacity logits, one row per lane
     if (valid) {
@@ -1101,7 +1199,7 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
     if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
     if (n > 0) {
         for (int t = 0; t < 5; ++t)
-            if (!adam->param[t] || !adam->m[t] || !adam->v[t]) {
+            if ((!adam->param[t] && t < 4) || !adam->m[t] || !adam->v[t]) {
                 gs_host::set_error("gs_project_bwd_adam: null parameter or moment pointer");
                 return GS_ERR_ARG;
             }
@@ -1130,6 +1228,12 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
         gs_host::set_error("gs_project_bwd_adam: need step >= 1, 0 <= beta < 1, eps >= 0, a valid shadow dtype");
         return GS_ERR_ARG;
     }
+    // no FP32 SH parameter: the SH is sh_store itself (stochastic rounding when it is BF16/FP16)
+    const bool lowp = adam->param[4] == nullptr && sh_dtype != GS_DTYPE_F32;
+    if (lowp && adam->sh_shadow) {
+        gs_host::set_error("gs_project_bwd_adam: SH kept only in sh_store (param[4] NULL) takes no sh_shadow");
+        return GS_ERR_ARG;
+    }
     if (n == 0) return GS_OK;
     AdamDev a{};
     for (int t = 0; t < 5; ++t) {
@@ -1149,6 +1253,11 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
     a.sparse = adam->sparse;
     a.shadow = adam->sh_shadow;
     a.shadow_dtype = adam->sh_shadow_dtype;
+    if (!a.p[4] && !lowp) a.p[4] = static_cast<float*>(const_cast<void*>(sh_store));
+    a.lowp = lowp ? 1 : 0;
+    a.sr_seed = adam->sr_seed;
+    a.step = adam->step;
+    a.step_dev = adam->step_dev;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, b, a, pos_acc, col_acc, count, st);
 }

@@ -107,8 +107,8 @@ class Fit:
         self.train_cams, self.train_targets = list(train_cams), list(train_targets)
         self.eval_cams, self.eval_targets = list(eval_cams), list(eval_targets)
         p = GaussianParams.from_arrays(init, self.dev, self.cfg.sh_dtype)
-        self.state = GaussianState(p, [torch.zeros_like(t) for t in p.tensors()],
-                                   [torch.zeros_like(t) for t in p.tensors()],
+        self.state = GaussianState(p, [torch.zeros_like(t, dtype=torch.float32) for t in p.tensors()],
+                                   [torch.zeros_like(t, dtype=torch.float32) for t in p.tensors()],
                                    torch.zeros(p.n, device=self.dev), torch.zeros(p.n, device=self.dev),
                                    torch.zeros(p.n, dtype=torch.int32, device=self.dev))
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=self.dev)
@@ -118,6 +118,7 @@ class Fit:
         self.history = []
         self.rounds = []
         self.headroom = 1.3
+        self.overflow_steps = 0  # steps in which a view overflowed its pair buffers
 
     def _dils(self, cam):
         c = self.cfg
@@ -169,14 +170,16 @@ class Fit:
             self.step.run(k, table=t)
             ev1.record()
             ev1.synchronize()
+            seconds += ev0.elapsed_time(ev1) / 1000.0
+            loss = float(self.step.loss.sum().item()) / V
             if self.step.overflowed():
-                # a view had more pairs than the buffers hold (its lists were left empty, so it added
-                # no gradient to that update): measure them again with more headroom and retake the step
+                # a view had more pairs than its buffers hold: its lists were left empty, so it
+                # added no gradient to this update (the step itself counts, time and views). The
+                # pairs are measured again with more headroom for the following steps.
+                self.overflow_steps += 1
                 self.headroom *= 1.5
                 self._build()
-                continue
-            seconds += ev0.elapsed_time(ev1) / 1000.0
-            self.budget.record(views, float(self.step.loss.sum().item()) / V)
+            self.budget.record(views, loss)
             views += V
             k += 1
         torch.cuda.synchronize()

@@ -24,8 +24,14 @@ def _dev(x, device, dtype=torch.float32):
 class GaussianParams:
     """Device tensors of the Gaussians (Sec. 3): means, log-scales, quaternions
     (w,x,y,z), opacity logits and SH coefficients (n x K x 3). ``sh_store`` is the
-    tensor the projection reads: ``sh`` itself, or a BF16/FP16 copy kept in sync
-    by Adam (mixed-precision storage; blending and accumulation stay FP32)."""
+    tensor the projection reads. Three forms of SH storage:
+
+    * FP32: ``sh`` is ``sh_store``;
+    * low precision (the precision form): ``sh`` is ``sh_store``, a BF16/FP16
+      tensor and the only copy of the SH; Adam updates it in FP32 arithmetic
+      and rounds stochastically (blending and accumulation stay FP32);
+    * FP32 master: ``sh`` FP32 and ``sh_store`` its BF16/FP16 copy, refreshed
+      by Adam after every update."""
     means: torch.Tensor
     log_scales: torch.Tensor
     quats: torch.Tensor
@@ -38,11 +44,22 @@ class GaussianParams:
         return int(self.means.shape[0])
 
     @classmethod
-    def from_arrays(cls, arrays: dict, device="cuda", sh_dtype=torch.float32):
+    def from_arrays(cls, arrays: dict, device="cuda", sh_dtype=torch.float32, master: bool = False):
+        """sh_dtype BF16/FP16 keeps the SH only in that type (rounded to nearest
+        once here), or with master=True as a copy of an FP32 master."""
         p = {k: _dev(arrays[k], device) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
         p["opacity_logits"] = p["opacity_logits"].reshape(-1)
-        store = p["sh"] if sh_dtype == torch.float32 else p["sh"].to(sh_dtype).contiguous()
+        if sh_dtype == torch.float32:
+            return cls(sh_store=p["sh"], **p)
+        store = p["sh"].to(sh_dtype).contiguous()
+        if not master:
+            p["sh"] = store
         return cls(sh_store=store, **p)
+
+    @property
+    def sh_lowp(self) -> bool:
+        """The SH exists only in BF16/FP16 (no FP32 master)."""
+        return self.sh.dtype != torch.float32
 
     def tensors(self):
         return [self.means, self.log_scales, self.quats, self.opacity_logits, self.sh]
@@ -156,7 +173,9 @@ def image_buffers(h_ds: int, w_ds: int, device="cuda"):
 
 class _RasterizeFn(torch.autograd.Function):
     """Differentiable dilated render of one view. Only (t_final, last) and the
-    binned lists are kept for backward; the per-pixel blend state is replayed."""
+    binned lists are kept for backward; the per-pixel blend state is replayed.
+    The parameter tensors go through save_for_backward, so autograd rejects a
+    backward after they were changed in place (e.g. by an optimizer step)."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, cam, dil, bg, cap_hint):
@@ -170,15 +189,17 @@ class _RasterizeFn(torch.autograd.Function):
         cap_hint[0] = max(cap_hint[0], rast.capacity)
         img, t_final, last = image_buffers(h_ds, w_ds, means.device)
         rast.render(cam, dil, bg, img, t_final, last)
-        ctx.rast, ctx.cam, ctx.dil, ctx.bg, ctx.p = rast, cam, dil, bg, p
-        ctx.save_for_backward(t_final, last)
+        ctx.rast, ctx.cam, ctx.dil, ctx.bg = rast, cam, dil, bg
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, t_final, last)
         ctx.mark_non_differentiable(t_final, last)
         return img, t_final, last
 
     @staticmethod
     def backward(ctx, dl_dimg, _g_t, _g_last):
-        t_final, last = ctx.saved_tensors
-        rast, p = ctx.rast, ctx.p
+        means, log_scales, quats, opacity_logits, sh, t_final, last = ctx.saved_tensors
+        p = GaussianParams(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                           opacity_logits.contiguous(), sh.contiguous(), sh.contiguous())
+        rast = ctx.rast
         rast.render_bwd(ctx.cam, ctx.dil, ctx.bg, t_final, last, dl_dimg.contiguous())
         g = [torch.empty_like(t) for t in (p.means, p.log_scales, p.quats, p.opacity_logits)]
         d_sh = torch.empty(p.sh.shape, dtype=torch.float32, device=p.sh.device)
@@ -220,10 +241,11 @@ class TrainStep:
 
     def __init__(self, params: GaussianParams, rast: Rasterizer, adam: AdamConfig = AdamConfig(),
                  max_pixels: int = 1, bg=(0.0, 0.0, 0.0), densify: bool = True, fused: bool = True,
-                 sparse: bool = False):
+                 sparse: bool = False, sr_seed: int = 0x2412):
         dev = params.means.device
         self.p, self.rast, self.adam, self.bg = params, rast, adam, tuple(bg)
         self.fused, self.sparse = bool(fused), bool(sparse)
+        self.sr_seed = int(sr_seed)  # stream of the stochastic rounding of low-precision SH
         self.grads = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -267,13 +289,15 @@ class TrainStep:
         if self.fused:
             R.gs_project_bwd_adam(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,
                                   p.sh_store, cam, dil, rast.tiles_touched, rast.grad2d, sparse=self.sparse,
-                                  sh_shadow=shadow, pos_acc=stats[0], col_acc=stats[1], count=stats[2])
+                                  sh_shadow=shadow, pos_acc=stats[0], col_acc=stats[1], count=stats[2],
+                                  sr_seed=self.sr_seed)
             return
         R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, rast.tiles_touched,
                          rast.grad2d, g[0], g[1], g[2], g[3], g[4], *stats)
         entries = []
         for i, t in enumerate(p.tensors()):
-            e = dict(param=t, grad=g[i], m=self.m[i], v=self.v[i], lr=lrs[i], row_width=max(1, t[0].numel()))
+            e = dict(param=t, grad=g[i], m=self.m[i], v=self.v[i], lr=lrs[i], row_width=max(1, t[0].numel()),
+                     sr_seed=self.sr_seed)
             if i == 4 and shadow is not None:
                 e["shadow"] = shadow
             entries.append(e)
@@ -314,7 +338,7 @@ class BatchTrainStep:
                  bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
                  pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
                  capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0,
-                 state=None, bwd_pixels_per_thread: int = 0):
+                 state=None, bwd_pixels_per_thread: int = 0, sr_seed: int = 0x2412):
         """cams/targets: the views of the batch (any later batch given to
         run(table=views_table(...)) must have no larger images). state: optional
         dict of m, v (lists), pos_acc, col_acc, count and step_dev to continue
@@ -329,6 +353,7 @@ class BatchTrainStep:
         self.bwd_ppt = int(bwd_pixels_per_thread)  # 0: the library's default for the backward
         self.bin_shift = int(bin_shift)
         self.longest_first = bool(longest_first)
+        self.sr_seed = int(sr_seed)  # stream of the stochastic rounding of low-precision SH
         n, V = params.n, self.V
         self.targets = [t.contiguous() for t in targets]
         for c, t in zip(self.cams, self.targets):
@@ -472,7 +497,8 @@ class BatchTrainStep:
         R.gs_project_bwd_adam_batch(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, 1, p.sh_store,
                                     self.table(phase) if table is None else table, sparse=self.sparse,
                                     sh_shadow=shadow, pos_acc=stats[0],
-                                    col_acc=stats[1], count=stats[2], bias_dev=self.bias_dev)
+                                    col_acc=stats[1], count=stats[2], bias_dev=self.bias_dev,
+                                    step_dev=self.step_dev, sr_seed=self.sr_seed)
 
     def run(self, phase: int, counts: bool = False, table=None):
         self.render_pass(phase, counts, table)

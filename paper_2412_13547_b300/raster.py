@@ -55,14 +55,15 @@ class GsAdamTensor(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("shadow", ctypes.c_void_p), ("numel", ctypes.c_int64),
                 ("row_width", ctypes.c_int32), ("shadow_dtype", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("pad_", ctypes.c_float)]
+                ("sr_seed", ctypes.c_uint32)]
 
 
 class GsAdamParams(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p * 5), ("m", ctypes.c_void_p * 5), ("v", ctypes.c_void_p * 5),
                 ("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("step", ctypes.c_int32), ("sparse", ctypes.c_int32),
-                ("sh_shadow", ctypes.c_void_p), ("sh_shadow_dtype", ctypes.c_int32), ("bias_dev", ctypes.c_void_p)]
+                ("sh_shadow", ctypes.c_void_p), ("sh_shadow_dtype", ctypes.c_int32), ("bias_dev", ctypes.c_void_p),
+                ("step_dev", ctypes.c_void_p), ("sr_seed", ctypes.c_uint32)]
 
 
 _VIEW_BUFFERS = ("splats", "radii", "rects", "tiles_touched", "sorted_ids", "ranges", "img", "t_final", "last",
@@ -356,19 +357,32 @@ def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilat
                                  _stream(stream)), "gs_project_bwd")
 
 
-def _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev):
+def _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev, step_dev=None,
+                 sr_seed=0):
+    """The GsAdamParams of a fused optimizer call. A BF16/FP16 params[4] is the
+    SH kept only in that type (param[4] NULL: the call's sh_store, updated with
+    stochastic rounding)."""
     a = GsAdamParams()
     for t in range(5):
-        for arr, src in ((a.param, params), (a.m, m), (a.v, v)):
-            if src[t].dtype != torch.float32 or not src[t].is_contiguous() or not src[t].is_cuda:
-                raise ValueError("parameters and moments must be contiguous FP32 CUDA tensors")
-            arr[t] = src[t].data_ptr()
+        for k, (arr, src) in enumerate(((a.param, params), (a.m, m), (a.v, v))):
+            lowp = k == 0 and t == 4 and src[t].dtype in (torch.bfloat16, torch.float16)
+            if (src[t].dtype != torch.float32 and not lowp) or not src[t].is_contiguous() or not src[t].is_cuda:
+                raise ValueError("parameters and moments must be contiguous FP32 CUDA tensors "
+                                 "(the SH parameter may be BF16/FP16: then it is the SH storage itself)")
+            arr[t] = None if lowp else src[t].data_ptr()
         a.lr[t] = float(lrs[t])
     a.beta1, a.beta2, a.eps, a.step, a.sparse = float(beta1), float(beta2), float(eps), int(step), int(bool(sparse))
     a.sh_shadow = sh_shadow.data_ptr() if sh_shadow is not None else None
     a.sh_shadow_dtype = _SH_DTYPE[sh_shadow.dtype] if sh_shadow is not None else GS_DTYPE_F32
     a.bias_dev = _ptr(bias_dev).value if bias_dev is not None else None
+    a.step_dev = _ptr(step_dev).value if step_dev is not None else None
+    a.sr_seed = int(sr_seed) & 0xFFFFFFFF
     return a
+
+
+def _lowp_sh(params, sh_store):
+    if params[4].dtype != torch.float32 and params[4].data_ptr() != sh_store.data_ptr():
+        raise ValueError("a BF16/FP16 SH parameter must be the sh_store tensor itself")
 
 
 def _grads_out(grads_out):
@@ -379,13 +393,17 @@ def _grads_out(grads_out):
 
 def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, cam, dil: Dilation, tiles_touched,
                         grad2d, sparse=False, sh_shadow=None, pos_acc=None, col_acc=None, count=None,
-                        grads_out=None, bias_dev=None, stream=None):
-    """params, m, v: lists of the 5 FP32 tensors (means, log_scales, quats,
-    opacity_logits, sh), updated in place; lrs: 5 learning rates. bias_dev
-    (optional device float[2] from gs_adam_advance) replaces step."""
+                        grads_out=None, bias_dev=None, step_dev=None, sr_seed=0, stream=None):
+    """params, m, v: lists of the 5 tensors (means, log_scales, quats,
+    opacity_logits, sh), updated in place; all FP32 except that the SH may be
+    kept only in BF16/FP16 (params[4] is then sh_store, rounded stochastically
+    with seed sr_seed). lrs: 5 learning rates. bias_dev (optional device
+    float[2] from gs_adam_advance) replaces step; step_dev (optional device
+    int32) gives the step of the rounding stream."""
     n = params[0].shape[0]
     deg = sh_degree_of(params[4])
-    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev)
+    _lowp_sh(params, sh_store)
+    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev, step_dev, sr_seed)
     _check(load().gs_project_bwd_adam(n, deg, _SH_DTYPE[sh_store.dtype], _ptr(sh_store), ctypes.byref(camera(cam)),
                                       ctypes.byref(dil.c()), _ptr(tiles_touched), _ptr(grad2d), ctypes.byref(a),
                                       _ptr(pos_acc), _ptr(col_acc), _ptr(count), _grads_out(grads_out),
@@ -448,10 +466,11 @@ def gs_render_bwd_batch(n, views, bg, tile_order=None, zero_grad2d=True, pixels_
 
 def gs_project_bwd_adam_batch(params, m, v, lrs, beta1, beta2, eps, step, sh_store, views, sparse=False,
                               sh_shadow=None, pos_acc=None, col_acc=None, count=None, grads_out=None, bias_dev=None,
-                              stream=None):
+                              step_dev=None, sr_seed=0, stream=None):
     t = _table(views)
     n = params[0].shape[0]
-    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev)
+    _lowp_sh(params, sh_store)
+    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, sparse, sh_shadow, bias_dev, step_dev, sr_seed)
     _check(load().gs_project_bwd_adam_batch(n, sh_degree_of(params[4]), _SH_DTYPE[sh_store.dtype], _ptr(sh_store),
                                             t.arr, t.n, ctypes.byref(a), _ptr(pos_acc), _ptr(col_acc), _ptr(count),
                                             _grads_out(grads_out), _stream(stream)), "gs_project_bwd_adam_batch")
@@ -464,7 +483,9 @@ def gs_densify_stats(n, tiles_touched, grad2d, pos_acc, col_acc, count, stream=N
 
 def gs_adam(entries, beta1, beta2, eps, step, row_mask=None, stream=None):
     """entries: list of dicts with param, grad, m, v (float32 CUDA tensors), lr,
-    and optional shadow (bf16/fp16/fp32 tensor of the same shape) and row_width."""
+    and optional shadow (bf16/fp16/fp32 tensor of the same shape), row_width
+    and sr_seed. A BF16/FP16 param is kept only in that type (no shadow): its
+    update is rounded stochastically with seed sr_seed."""
     arr = (GsAdamTensor * max(1, len(entries)))()
     for i, e in enumerate(entries):
         p = e["param"]
@@ -472,6 +493,20 @@ def gs_adam(entries, beta1, beta2, eps, step, row_mask=None, stream=None):
             if e[k].shape != p.shape or e[k].dtype != torch.float32:
                 raise ValueError(f"adam entry {i}: {k} must match param (float32)")
         sh = e.get("shadow")
+        arr[i].sr_seed = int(e.get("sr_seed", 0)) & 0xFFFFFFFF
+        if p.dtype in (torch.bfloat16, torch.float16):
+            if sh is not None:
+                raise ValueError(f"adam entry {i}: a BF16/FP16 parameter takes no shadow")
+            arr[i].param = None
+            arr[i].grad = e["grad"].data_ptr()
+            arr[i].m = e["m"].data_ptr()
+            arr[i].v = e["v"].data_ptr()
+            arr[i].shadow = p.data_ptr()
+            arr[i].numel = p.numel()
+            arr[i].row_width = int(e.get("row_width", p[0].numel() if p.dim() > 1 and p.shape[0] > 0 else 1))
+            arr[i].shadow_dtype = _SH_DTYPE[p.dtype]
+            arr[i].lr = float(e["lr"])
+            continue
         arr[i].param = p.data_ptr()
         arr[i].grad = e["grad"].data_ptr()
         arr[i].m = e["m"].data_ptr()

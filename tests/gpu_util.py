@@ -19,13 +19,13 @@ def params_f64(p32):
     return {k: np.asarray(v, np.float64) for k, v in p32.items()}
 
 
-def gpu_params(p32, sh_dtype=torch.float32):
-    return GaussianParams.from_arrays(p32, DEV, sh_dtype)
+def gpu_params(p32, sh_dtype=torch.float32, master=False):
+    return GaussianParams.from_arrays(p32, DEV, sh_dtype, master=master)
 
 
-def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capacity=None, ppt=0):
+def run_forward(p32, cam, dil, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32, capacity=None, ppt=0, master=False):
     """GPU project + bin + blend. Returns numpy outputs and the rasterizer."""
-    p = gpu_params(p32, sh_dtype)
+    p = gpu_params(p32, sh_dtype, master)
     w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
     btx, bty = R.gs_bin_grid(cam, dil)
     rast = Rasterizer(p.n, capacity=capacity or 1 << 16, device=DEV, max_grid=(btx, bty), pixels_per_thread=ppt)
@@ -104,3 +104,32 @@ def flagged_tiles(orc_proj, gpu_out, tiles_x):
 def tile_pixel_mask(tile_flags, w_ds, h_ds, tiles_x, tile=16):
     ys, xs = np.mgrid[0:h_ds, 0:w_ds]
     return tile_flags[(ys // tile) * tiles_x + xs // tile]
+
+
+# element-wise error reports of the gradient comparisons, written out at the end of
+# the session when GS_PARITY_REPORT names a file (see conftest.py)
+REPORT = {}
+
+
+def grad_report(key, a, b):
+    """max |a - b| / max |b| (the asserted per-tensor figure) beside percentiles
+    of the element-wise relative error |a - b| / (|b| + 1e-3 max |b|) (the floor
+    keeps elements near zero from dividing by nothing); recorded under key."""
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    scale = float(np.abs(b).max()) if b.size else 0.0
+    mr = max_rel(a, b)
+    if scale > 0:
+        el = np.abs(a - b) / (np.abs(b) + 1e-3 * scale)
+        pct = {f"p{q}": float(np.percentile(el, q)) for q in (50, 90, 99, 99.9)}
+    else:
+        pct = {f"p{q}": 0.0 for q in (50, 90, 99, 99.9)}
+    REPORT[report_key(key)] = dict(max_rel=mr, **pct, n=int(b.size))
+    return mr
+
+
+def report_key(key):
+    """key prefixed with the running test's id."""
+    import os
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    return f"{test}:{key}"

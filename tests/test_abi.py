@@ -45,6 +45,31 @@ def test_python_constants_match_the_header():
     assert ctypes.sizeof(R.GsDilation) == 6 * 4
 
 
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the C layout of the header:
+    a C program built with gcc against include/turbogs.h prints every field's
+    offset and each struct's size."""
+    structs = {"GsCamera": R.GsCamera, "GsDilation": R.GsDilation, "GsAdamTensor": R.GsAdamTensor,
+               "GsAdamParams": R.GsAdamParams, "GsRowTensor": R.GsRowTensor, "GsView": R.GsView}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "turbogs.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                    text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(got[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
 def test_host_only_calls():
     assert R.gs_version() >= 100
     cam = type("C", (), dict(R=[[1, 0, 0], [0, 1, 0], [0, 0, 1]], T=[0, 0, 0], fx=100.0, fy=100.0, cx=63.5,

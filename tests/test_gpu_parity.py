@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import lowp
 from oracle import oracle as orc
 from paper_2412_13547_b300 import raster as R
 from paper_2412_13547_b300 import scenes
@@ -155,9 +156,12 @@ def test_binning_equal_depths_keep_index_order():
 # Blend forward / backward on the same lists
 # ---------------------------------------------------------------------------
 
-def render_case(p32, cam, dil, bg=(0.1, 0.2, 0.3)):
-    out, rast, p, bufs = U.run_forward(p32, cam, dil, bg)
-    o = orc.project(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil))
+def render_case(p32, cam, dil, bg=(0.1, 0.2, 0.3), sh_dtype=torch.float32):
+    out, rast, p, bufs = U.run_forward(p32, cam, dil, bg, sh_dtype=sh_dtype)
+    p64 = U.params_f64(p32)
+    # the oracle sees exactly the stored (rounded) coefficients
+    p64["sh"] = p.sh_store.float().cpu().numpy().astype(np.float64)
+    o = orc.project(p64, orc.as_camera(cam), orc.as_dilation(dil))
     # Gaussians the two sides cull differently get no exact comparison: their tiles are excluded
     cull_diff = (o["tiles_touched"] > 0) != (out["tiles_touched"] > 0)
     of = orc.render_fwd(o, out["sorted_ids"], out["ranges"], orc.as_camera(cam), orc.as_dilation(dil), bg)
@@ -171,6 +175,43 @@ def render_case(p32, cam, dil, bg=(0.1, 0.2, 0.3)):
     return out, rast, p, bufs, o, of, excl
 
 
+def check_counts_outside(out, rast, o, cam, dil, excl, bg=(0.1, 0.2, 0.3)):
+    """Blend counts (entries evaluated, entries blended, replayed list prefix).
+    Over the tiles with no excluded pixel they must equal the oracle's exactly:
+    the GPU renders again with the other tiles' lists emptied, the oracle
+    blends only the kept tiles (same lists). Over the whole image they may
+    differ only at excluded pixels, each by at most its tile's list length."""
+    w_ds, h_ds, tx, ty = out["grid"]
+    ys, xs = np.nonzero(excl)
+    tile_of_px = (ys // dil.tile) * tx + xs // dil.tile
+    bad = np.zeros(tx * ty, bool)
+    bad[tile_of_px] = True
+    lens = (out["ranges"][:, 1].astype(np.int64) - out["ranges"][:, 0].astype(np.int64))[:tx * ty]
+    slack = int(lens[tile_of_px].sum())
+    of_all = orc.render_fwd(o, out["sorted_ids"], out["ranges"], orc.as_camera(cam), orc.as_dilation(dil), bg)
+    for i in (0, 1):
+        ref = of_all["n_eval"] if i == 0 else of_all["n_blend"]
+        assert abs(int(out["counts"][i]) - ref) <= slack, (i, int(out["counts"][i]), ref, slack)
+    keep_tiles = np.nonzero(~bad)[0].astype(np.int32)
+    print(f"counts: {keep_tiles.size} of {tx * ty} tiles without an excluded pixel; whole-image slack {slack}")
+    if keep_tiles.size == 0:
+        return
+    ranges = rast.ranges.clone()
+    ranges[:tx * ty][torch.tensor(bad, device=U.DEV)] = 0
+    img, tf, last = image_buffers(h_ds, w_ds, U.DEV)
+    counts = torch.zeros(3, dtype=torch.int64, device=U.DEV)
+    R.gs_render_fwd(rast.n, rast.splats, rast.sorted_ids, ranges, cam, dil, bg, img, tf, last, counts)
+    torch.cuda.synchronize()
+    c = counts.cpu().numpy()
+    # the oracle's ranges are indexed like its tile_ids
+    of = orc.render_fwd(o, out["sorted_ids"], out["ranges"][keep_tiles], orc.as_camera(cam), orc.as_dilation(dil),
+                        bg, tile_ids=keep_tiles)
+    kp = ~U.tile_pixel_mask(bad, w_ds, h_ds, tx, dil.tile)
+    assert c[0] == of["n_eval"], (c[0], of["n_eval"])
+    assert c[1] == of["n_blend"], (c[1], of["n_blend"])
+    assert c[2] == int(of["last"][kp].astype(np.int64).sum())
+
+
 @pytest.mark.parametrize("dil", DILATIONS, ids=_dil_id)
 def test_render_fwd_parity(dil):
     p32, cam, _ = scene_small()
@@ -182,11 +223,9 @@ def test_render_fwd_parity(dil):
     assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
     assert np.abs(out["t_final"] - of["t_final"])[keep].max() < 1e-5
     np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
-    assert out["counts"][0] == of["n_eval"] or excl.any()
-    assert out["counts"][1] == of["n_blend"] or excl.any()
     # the backward's replay work: the sum of the pixels' last positions in their tile lists
     assert out["counts"][2] == int(out["last"].astype(np.int64).sum())
-    assert out["counts"][2] == int(of["last"].astype(np.int64).sum()) or excl.any()
+    check_counts_outside(out, rast, o, cam, dil, excl)
 
 
 def scene_needles(n=1500, w=203, h=157, index=17):
@@ -217,20 +256,28 @@ def test_render_fwd_parity_needles(dil):
     assert out["counts"][1] > 0
     assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
     np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
-    assert out["counts"][1] == of["n_blend"] or excl.any()
+    check_counts_outside(out, rast, o, cam, dil, excl)
     out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil)
     gg = U.split_grad2d(g2d)
     for k in ("dxy", "dconic", "dopacity", "drgb"):
-        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
+        assert U.grad_report(k, gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
 
 
-def test_render_fwd_parity_sh3_ragged():
+@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_render_fwd_parity_sh3_ragged(sh_dtype):
+    """SH degree 3 on ragged image sizes, with the SH stored in FP32, BF16 or
+    FP16 (the oracle is given the stored coefficients): image within 1e-4,
+    last index exact, and the 2D gradients within 1e-3."""
     p32, cam, _ = scene_sh3(131, 97)
     for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1), R.Dilation(3, 0, 2, tile=8)]:
-        out, rast, p, bufs, o, of, excl = render_case(p32, cam, dil)
+        out, rast, p, bufs, o, of, excl = render_case(p32, cam, dil, sh_dtype=sh_dtype)
         keep = ~excl
         assert np.abs(out["img"] - of["img"])[keep].max() < IMG_TOL
         np.testing.assert_array_equal(out["last"][keep], of["last"][keep])
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 1, 0), sh_dtype=sh_dtype)
+    gg = U.split_grad2d(g2d)
+    for k in ("dxy", "dconic", "dopacity", "drgb"):
+        assert U.grad_report(k, gg[k], og[k]) < GRAD_TOL, k
 
 
 @pytest.mark.parametrize("tile,ppts", [(8, (1, 2)), (16, (1, 2, 4)), (32, (2, 4))])
@@ -332,8 +379,8 @@ def test_backward_order_by_last(shift):
     assert sorted(order.cpu().numpy().tolist()) == list(range(total))
 
 
-def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3)):
-    out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg)
+def backward_case(p32, cam, dil, seed=0, bg=(0.1, 0.2, 0.3), sh_dtype=torch.float32):
+    out, rast, p, (img, t_final, last), o, of, excl = render_case(p32, cam, dil, bg, sh_dtype)
     rng = np.random.default_rng(seed)
     dl = rng.standard_normal(out["img"].shape) * 1e-3
     dl[excl] = 0.0
@@ -352,7 +399,7 @@ def test_render_bwd_parity(dil):
     out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil)
     gg = U.split_grad2d(g2d)
     for k in ("dxy", "dconic", "dopacity", "drgb"):
-        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
+        assert U.grad_report(k, gg[k], og[k]) < GRAD_TOL, (k, U.max_rel(gg[k], og[k]))
     assert np.all(g2d[:, 9:] == 0.0)
 
 
@@ -361,10 +408,10 @@ def test_render_bwd_parity_sh3():
     out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 0, 1))
     gg = U.split_grad2d(g2d)
     for k in ("dxy", "dconic", "dopacity", "drgb"):
-        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, k
+        assert U.grad_report(k, gg[k], og[k]) < GRAD_TOL, k
 
 
-@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_project_bwd_parity(sh_dtype):
     p32, cam, _ = scene_sh3()
     dil = R.Dilation(2, 1, 0)
@@ -373,7 +420,7 @@ def test_project_bwd_parity(sh_dtype):
     g2d[flagged] = 0.0
     rast.grad2d.copy_(torch.tensor(g2d, device=U.DEV))
     pp = U.gpu_params(p32, sh_dtype)
-    grads = [torch.empty_like(t) for t in pp.tensors()]
+    grads = [torch.empty_like(t, dtype=torch.float32) for t in pp.tensors()]
     R.gs_project_bwd(pp.means, pp.log_scales, pp.quats, pp.opacity_logits, pp.sh_store, cam, dil, rast.tiles_touched,
                      rast.grad2d, *grads)
     torch.cuda.synchronize()
@@ -381,7 +428,7 @@ def test_project_bwd_parity(sh_dtype):
     p64["sh"] = pp.sh_store.float().cpu().numpy().astype(np.float64)
     ref = orc.project_bwd(p64, orc.as_camera(cam), orc.as_dilation(dil), U.split_grad2d(g2d))
     for name, g in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads):
-        assert U.max_rel(g.cpu().numpy(), ref[name]) < GRAD_TOL, (name, U.max_rel(g.cpu().numpy(), ref[name]))
+        assert U.grad_report(name, g.cpu().numpy(), ref[name]) < GRAD_TOL, (name, U.max_rel(g.cpu().numpy(), ref[name]))
 
 
 # ---------------------------------------------------------------------------
@@ -414,7 +461,7 @@ def test_densify_stats_parity():
         R.gs_densify_stats(n, rast.tiles_touched, rast.grad2d, pos, col, cnt)
     # fused path of the projection backward gives the same accumulation
     pos2, col2, cnt2 = torch.zeros_like(pos), torch.zeros_like(col), torch.zeros_like(cnt)
-    grads = [torch.empty_like(t) for t in p.tensors()]
+    grads = [torch.empty_like(t, dtype=torch.float32) for t in p.tensors()]
     R.gs_project_bwd(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, R.Dilation(2, 1, 1),
                      rast.tiles_touched, rast.grad2d, *grads, pos2, col2, cnt2)
     torch.cuda.synchronize()
@@ -477,32 +524,73 @@ def test_full_step_parity(dil):
     assert abs(loss.item() - ref["loss"]) < 1e-5
     img = step.img[:3 * w_ds * h_ds].view(h_ds, w_ds, 3).cpu().numpy()
     diff = np.abs(img - ref["fwd"]["img"]).max(-1)
-    assert (diff > IMG_TOL).mean() < 1e-3
+    # excluded: pixels whose FP64 gate values lie within the oracle's margin of a threshold, and
+    # the tiles of Gaussians whose radius or rect differs between the FP32 and FP64 projections
+    # (their lists may differ); every other pixel within 1e-4
+    proj = ref["proj"]
+    gpu = dict(rects=rast.rects.cpu().numpy(), radii=rast.radii.cpu().numpy(),
+               ranges=rast.ranges[:tx * ty].cpu().numpy())
+    bad_tiles, _ = U.flagged_tiles(proj, gpu, tx)
+    # and the tiles whose lists differ (two depths whose FP32 order differs from the FP64 one)
+    ids = rast.sorted_ids[:rast.num_pairs()].cpu().numpy().view(np.uint32)
+    granges = gpu["ranges"].view(np.uint32)
+    for t in range(tx * ty):
+        a = ids[granges[t, 0]:granges[t, 1]]
+        b = ref["vals"][ref["ranges"][t, 0]:ref["ranges"][t, 1]]
+        if a.shape != b.shape or (a != b).any():
+            bad_tiles[t] = True
+    excl = ref["fwd"]["ambiguous"] | U.tile_pixel_mask(bad_tiles, w_ds, h_ds, tx, dil.tile)
+    print(f"full step: {excl.mean():.4%} of pixels excluded ({bad_tiles.sum()} of {tx * ty} tiles)")
+    assert excl.mean() < 0.1
+    assert diff[~excl].max() < IMG_TOL
     assert rast.num_pairs() == len(ref["vals"])
     for name, g in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), step.grads):
-        assert U.max_rel(g.cpu().numpy(), ref["grads"][name]) < GRAD_TOL, name
+        assert U.grad_report(name, g.cpu().numpy(), ref["grads"][name]) < GRAD_TOL, name
     # Adam moved every visible Gaussian's parameters
     moved = (p.means != before[0]).any(1).cpu().numpy()
     assert moved[ref["proj"]["tiles_touched"] > 0].mean() > 0.5
 
 
-@pytest.mark.parametrize("sh_dtype,sparse", [(torch.float32, False), (torch.bfloat16, False), (torch.float32, True)])
-def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
+def lowp_spacing(v, dtype):
+    """The step of the 16-bit type at the values v (float64), away from zero."""
+    lo, hi, _ = lowp.neighbours(np.asarray(v, np.float32), "bf16" if dtype == torch.bfloat16 else "f16")
+    return np.abs(hi - lo)
+
+
+def assert_lowp_close(a, b, dtype, min_exact=0.999):
+    """Two low-precision results of the same update computed with different FP32
+    rounding: equal, or (where the FP32 values straddle a rounding decision)
+    one step of the type apart."""
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    assert (a == b).mean() >= min_exact, (a == b).mean()
+    assert (np.abs(a - b) <= lowp_spacing(b, dtype) * (1 + 1e-12)).all()
+
+
+@pytest.mark.parametrize("sh_dtype,sparse,master", [(torch.float32, False, False), (torch.bfloat16, False, True),
+                                                    (torch.bfloat16, False, False), (torch.float16, False, False),
+                                                    (torch.float16, True, False), (torch.float32, True, False)],
+                         ids=["fp32", "bf16-master", "bf16", "fp16", "fp16-sparse", "fp32-sparse"])
+def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse, master):
     """gs_project_bwd_adam equals gs_project_bwd followed by gs_adam (parameters,
-    moments, BF16 shadow, gradients, densification statistics) when both are
+    moments, SH storage, gradients, densification statistics) when both are
     given the same 2D gradients, three steps in a row: up to FP32 rounding of the
-    gradient arithmetic, which the two kernels may contract differently."""
+    gradient arithmetic, which the two kernels may contract differently. SH kept
+    only in BF16/FP16 draws the same stochastic-rounding bits in both paths: equal
+    but where that FP32 rounding straddles a rounding decision."""
     p32, cam, tgt = scene_sh3()
     dil = R.Dilation(2, 1, 0)
-    out, rast, p, (img, tf, last) = U.run_forward(p32, cam, dil, sh_dtype=sh_dtype)
+    out, rast, p, (img, tf, last) = U.run_forward(p32, cam, dil, sh_dtype=sh_dtype, master=master)
     dl = torch.tensor(np.random.default_rng(2).standard_normal(img.shape) * 1e-3, dtype=torch.float32, device=U.DEV)
     rast.render_bwd(cam, dil, (0.0, 0.0, 0.0), tf, last, dl)
     lrs = [1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3]
+    seed = 77
+    lowp_mode = sh_dtype != torch.float32 and not master
     sets = []
     for _ in range(2):
         ps = [t.clone() for t in p.tensors()]
-        sets.append(dict(p=ps, m=[torch.zeros_like(t) for t in ps], v=[torch.zeros_like(t) for t in ps],
-                         shadow=p.sh_store.clone() if sh_dtype != torch.float32 else None,
+        sets.append(dict(p=ps, m=[torch.zeros_like(t, dtype=torch.float32) for t in ps],
+                         v=[torch.zeros_like(t, dtype=torch.float32) for t in ps],
+                         shadow=p.sh_store.clone() if master else None,
                          stats=[torch.zeros(p.n, device=U.DEV), torch.zeros(p.n, device=U.DEV),
                                 torch.zeros(p.n, dtype=torch.int32, device=U.DEV)]))
     mask = (rast.tiles_touched > 0).to(torch.uint8) if sparse else None
@@ -510,30 +598,115 @@ def test_fused_project_bwd_adam_matches_unfused(sh_dtype, sparse):
         # unfused: gradients, then the multi-tensor Adam
         a = sets[0]
         store = a["shadow"] if a["shadow"] is not None else a["p"][4]
-        g = [torch.empty_like(t) for t in a["p"]]
+        g = [torch.empty_like(t, dtype=torch.float32) for t in a["p"]]
         R.gs_project_bwd(*a["p"][:4], store, cam, dil, rast.tiles_touched, rast.grad2d, *g, *a["stats"])
-        ent = [dict(param=a["p"][i], grad=g[i], m=a["m"][i], v=a["v"][i], lr=lrs[i]) for i in range(5)]
+        ent = [dict(param=a["p"][i], grad=g[i], m=a["m"][i], v=a["v"][i], lr=lrs[i], sr_seed=seed) for i in range(5)]
         if a["shadow"] is not None:
             ent[4]["shadow"] = a["shadow"]
         R.gs_adam(ent, 0.9, 0.999, 1e-15, step, row_mask=mask)
         # fused
         b = sets[1]
         storeb = b["shadow"] if b["shadow"] is not None else b["p"][4]
-        gout = [torch.full_like(t, 7.0) for t in b["p"]]
+        gout = [torch.full_like(t, 7.0, dtype=torch.float32) for t in b["p"]]
         R.gs_project_bwd_adam(b["p"], b["m"], b["v"], lrs, 0.9, 0.999, 1e-15, step, storeb, cam, dil,
                               rast.tiles_touched, rast.grad2d, sparse=sparse, sh_shadow=b["shadow"],
-                              pos_acc=b["stats"][0], col_acc=b["stats"][1], count=b["stats"][2], grads_out=gout)
+                              pos_acc=b["stats"][0], col_acc=b["stats"][1], count=b["stats"][2], grads_out=gout,
+                              sr_seed=seed)
         torch.cuda.synchronize()
         for x, y in zip(gout, g):
             assert U.max_rel(x.cpu().numpy(), y.cpu().numpy()) < 1e-6
     for key, rtol in (("p", 1e-6), ("m", 1e-5), ("v", 1e-5), ("stats", 1e-6)):
-        for x, y in zip(sets[0][key], sets[1][key]):
+        for i, (x, y) in enumerate(zip(sets[0][key], sets[1][key])):
             a, b = x.float().cpu().numpy(), y.float().cpu().numpy()
+            if key == "p" and i == 4 and lowp_mode:
+                assert_lowp_close(b, a, sh_dtype)
+                # and the SH moved (the rounding is not stuck at the stored values)
+                assert (a != p.sh_store.float().cpu().numpy()).mean() > 0.05
+                continue
             assert U.max_rel(a, b) < rtol, key
     if sets[0]["shadow"] is not None:
         a, b = sets[0]["shadow"].float().cpu().numpy(), sets[1]["shadow"].float().cpu().numpy()
         # BF16 copies of parameters equal to FP32 rounding: equal or one BF16 step apart
         assert (np.abs(a - b) <= np.abs(b) * 2.0 ** -7 + 1e-30).all()
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_adam_lowp_parity(dtype):
+    """gs_adam on a parameter kept only in BF16/FP16 against the oracle (FP64
+    Adam from the stored values, rounded to FP32, then stochastically with the
+    same hash stream), three steps, each from the GPU's state. The FP32 update
+    of the kernel (SFU square root and division) and the oracle's differ by a
+    few FP32 ulps, which flips a rounding decision only when the random bits
+    fall between the two: equal elsewhere, one step of the type apart there."""
+    from oracle import lowp as L
+    name = "bf16" if dtype == torch.bfloat16 else "f16"
+    rng = np.random.default_rng(8)
+    shape = (1001, 16, 3)
+    p = torch.tensor(rng.standard_normal(shape) * 0.3, dtype=torch.float32).to(dtype).to(U.DEV)
+    m = torch.tensor(rng.standard_normal(shape) * 1e-2, dtype=torch.float32, device=U.DEV)
+    v = torch.tensor(rng.uniform(1e-5, 1e-4, shape), dtype=torch.float32, device=U.DEV)
+    lr, seed = 1e-3, 12345
+    moved = 0.0
+    for step in (1, 2, 3):
+        g = (rng.standard_normal(shape) * 1e-2).astype(np.float32)
+        st = p.float().cpu().numpy().astype(np.float64)
+        mm = m.cpu().numpy().astype(np.float64)
+        vv = v.cpu().numpy().astype(np.float64)
+        ref = L.adam_lowp(st, g, mm, vv, lr, 0.9, 0.999, 1e-15, step, name, seed)
+        R.gs_adam([dict(param=p, grad=torch.tensor(g, device=U.DEV), m=m, v=v, lr=lr, sr_seed=seed, row_width=48)],
+                  0.9, 0.999, 1e-15, step)
+        torch.cuda.synchronize()
+        out = p.float().cpu().numpy().astype(np.float64)
+        assert_lowp_close(out, ref, dtype)
+        np.testing.assert_allclose(m.cpu().numpy(), mm, rtol=1e-5, atol=1e-9)
+        np.testing.assert_allclose(v.cpu().numpy(), vv, rtol=1e-5, atol=1e-12)
+        moved = max(moved, float((out != st).mean()))
+    assert moved > 0.3
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_fused_lowp_against_oracle(dtype):
+    """The fused optimizer pass with the SH kept only in BF16/FP16, against
+    the oracle: projection backward from the stored coefficients (gradients
+    within 1e-3) and the low-precision Adam step of oracle/lowp.py (same hash
+    stream; equal but where the kernel's FP32 update and the oracle's straddle
+    a rounding decision, then one step apart). Moments start from a seeded
+    state of the gradients' scale, so the update is smooth in the gradient."""
+    name = "bf16" if dtype == torch.bfloat16 else "f16"
+    p32, cam, _ = scene_sh3()
+    dil = R.Dilation(2, 1, 0)
+    out, rast, p, o, og, g2d, excl = backward_case(p32, cam, dil, sh_dtype=dtype)
+    flagged = (o["flags"] & orc.FLAG_AMBIGUOUS) != 0
+    rows = np.nonzero((out["tiles_touched"] > 0) & ~flagged)[0]
+    p64 = U.params_f64(p32)
+    p64["sh"] = p.sh_store.float().cpu().numpy().astype(np.float64)
+    ref = orc.project_bwd({k: v[rows] for k, v in p64.items()}, orc.as_camera(cam), orc.as_dilation(dil),
+                          {k: v[rows] for k, v in og.items()})
+    lrs = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3]
+    seed, step = 99, 4
+    rng = np.random.default_rng(3)
+    m0, v0 = [], []
+    for nm, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), p.tensors()):
+        sc = float(np.sqrt(np.mean(ref[nm] ** 2))) or 1.0
+        m0.append(rng.normal(0.0, sc, tuple(t.shape)).astype(np.float32))
+        v0.append((sc * sc * rng.uniform(0.5, 2.0, tuple(t.shape))).astype(np.float32))
+    m = [torch.tensor(x, device=U.DEV) for x in m0]
+    v = [torch.tensor(x, device=U.DEV) for x in v0]
+    stored = p64["sh"].copy()
+    gout = [torch.zeros(tuple(t.shape), dtype=torch.float32, device=U.DEV) for t in p.tensors()]
+    R.gs_project_bwd_adam(p.tensors(), m, v, lrs, 0.9, 0.999, 1e-15, step, p.sh_store, cam, dil,
+                          rast.tiles_touched, rast.grad2d, grads_out=gout, sr_seed=seed)
+    torch.cuda.synchronize()
+    for i, nm in enumerate(("means", "log_scales", "quats", "opacity_logits", "sh")):
+        assert U.grad_report(nm, gout[i].cpu().numpy()[rows], ref[nm]) < GRAD_TOL, nm
+    g_full = np.zeros_like(stored)
+    g_full[rows] = ref["sh"]
+    mm, vv = m0[4].astype(np.float64), v0[4].astype(np.float64)
+    want = lowp.adam_lowp(stored, g_full, mm, vv, lrs[4], 0.9, 0.999, 1e-15, step, name, seed)
+    got = p.sh_store.float().cpu().numpy().astype(np.float64)
+    assert_lowp_close(got[rows], want[rows], dtype, min_exact=0.99)
+    assert (got[rows] != stored[rows]).mean() > 0.3
+    np.testing.assert_allclose(m[4].cpu().numpy()[rows], mm[rows], rtol=1e-3, atol=1e-3 * np.abs(mm).max())
 
 
 # ---------------------------------------------------------------------------
@@ -657,7 +830,7 @@ def test_autograd_matches_oracle_gradient():
                         wts.cpu().numpy().astype(np.float64))
     ref = orc.project_bwd(U.params_f64(p32), orc.as_camera(cam), orc.as_dilation(dil), og)
     for name, t in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), ts):
-        assert U.max_rel(t.grad.cpu().numpy(), ref[name]) < GRAD_TOL, name
+        assert U.grad_report(name, t.grad.cpu().numpy(), ref[name]) < GRAD_TOL, name
 
 
 def test_autograd_finite_differences_hd_64_params():
@@ -755,7 +928,61 @@ def test_uhd_sampled_tiles_parity(d, ox, oy):
     og = orc.render_bwd(o, sv, sr, orc.as_camera(cam), orc.as_dilation(dil), dl.astype(np.float32), tile_ids=tiles)
     gg = U.split_grad2d(rast.grad2d.cpu().numpy())
     for k in ("dxy", "dconic", "dopacity", "drgb"):
-        assert U.max_rel(gg[k], og[k]) < GRAD_TOL, k
+        assert U.grad_report(k, gg[k], og[k]) < GRAD_TOL, k
+    check_fused_pass_against_oracle(p, p32, cam, dil, rast, o, og, seed=d)
+
+
+def check_fused_pass_against_oracle(p, p32, cam, dil, rast, o, og, seed, step=10):
+    """gs_project_bwd_adam at full size, in the bench's launch configuration,
+    against the oracle's projection backward (of the oracle's own 2D gradients),
+    densification statistics and Adam, on the Gaussians the sampled tiles
+    touch (every other row has a zero 2D gradient). The moments start from a
+    seeded state of the gradients' scale, so the update is smooth in the
+    gradient (a first step from zero moments moves by lr * sign(g), which a
+    gradient near zero may flip)."""
+    names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    lrs = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3]
+    b1, b2, eps = 0.9, 0.999, 1e-15
+    ocam, odil = orc.as_camera(cam), orc.as_dilation(dil)
+    g2d = rast.grad2d.cpu().numpy()
+    flagged = (o["flags"] & orc.FLAG_AMBIGUOUS) != 0
+    rows = np.nonzero((np.abs(g2d).sum(1) > 0) & ~flagged & (o["tiles_touched"] > 0))[0]
+    assert rows.size > 100
+    p64 = U.params_f64(p32)
+    sub = {k: v[rows] for k, v in p64.items()}
+    og_sub = {k: v[rows] for k, v in og.items()}
+    ref = orc.project_bwd(sub, ocam, odil, og_sub)
+    rng = np.random.default_rng(seed)
+    m0, v0 = [], []
+    for name, t in zip(names, p.tensors()):
+        sc = float(np.sqrt(np.mean(ref[name] ** 2))) or 1.0
+        m0.append(rng.normal(0.0, sc, tuple(t.shape)).astype(np.float32))
+        v0.append((sc * sc * rng.uniform(0.5, 2.0, tuple(t.shape))).astype(np.float32))
+    m = [torch.tensor(x, device=U.DEV) for x in m0]
+    v = [torch.tensor(x, device=U.DEV) for x in v0]
+    before = [t.detach().cpu().numpy().copy() for t in p.tensors()]
+    gout = [torch.zeros_like(t) for t in p.tensors()]
+    pos, col = torch.zeros(p.n, device=U.DEV), torch.zeros(p.n, device=U.DEV)
+    cnt = torch.zeros(p.n, dtype=torch.int32, device=U.DEV)
+    R.gs_project_bwd_adam(p.tensors(), m, v, lrs, b1, b2, eps, step, p.sh_store, cam, dil, rast.tiles_touched,
+                          rast.grad2d, pos_acc=pos, col_acc=col, count=cnt, grads_out=gout)
+    torch.cuda.synchronize()
+    rp, rc, rn = np.zeros(rows.size), np.zeros(rows.size), np.zeros(rows.size, np.int32)
+    orc.densify_stats(o["tiles_touched"][rows], og_sub, rp, rc, rn)
+    assert U.grad_report("pos_acc", pos.cpu().numpy()[rows], rp) < GRAD_TOL
+    assert U.grad_report("col_acc", col.cpu().numpy()[rows], rc) < GRAD_TOL
+    np.testing.assert_array_equal(cnt.cpu().numpy()[rows], rn)
+    for i, name in enumerate(names):
+        g = gout[i].cpu().numpy()[rows]
+        assert U.grad_report(name, g, ref[name]) < GRAD_TOL, name
+        pr, mr, vr = (before[i][rows].astype(np.float64), m0[i][rows].astype(np.float64),
+                      v0[i][rows].astype(np.float64))
+        orc.adam(pr, ref[name], mr, vr, lrs[i], b1, b2, eps, step)
+        dp = p.tensors()[i].detach().cpu().numpy()[rows].astype(np.float64) - before[i][rows]
+        dr = pr - before[i][rows]
+        ulp = np.abs(before[i][rows]).astype(np.float64) * 2.0 ** -22
+        assert (np.abs(dp - dr) <= GRAD_TOL * np.abs(dr).max() + ulp).all(), name
+        assert U.grad_report(name + "_m", m[i].cpu().numpy()[rows], mr) < GRAD_TOL, name
 
 
 @pytest.mark.parametrize("d,ox,oy,shift", [(2, 1, 0, 2), (4, 3, 1, 1)])
