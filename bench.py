@@ -434,17 +434,19 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
 # Batched views
 # ---------------------------------------------------------------------------
 
-def run_batch(args, device):
+def measure_batch(args, device, d, steps, warmup):
+    """The batched form (A11): 8 views per step of mixed resolution around a
+    2M-Gaussian scene with a heavy-tailed tile load; launch shape picked by the
+    autotuner, per-stage eager times of one pass over the offset phases, then
+    the step replayed from CUDA graphs and timed with CUDA events. Returns a
+    dict (no printing)."""
     import torch
-    from paper_2412_13547_b300 import build_native, raster as R, scenes
+    from paper_2412_13547_b300 import raster as R, scenes
     from paper_2412_13547_b300.pipeline import GaussianParams, BatchTrainStep, autotune_batch
 
-    if not os.path.exists(R.LIB_PATH):
-        build_native.build()
     scene, cams, targets = scenes.workload_batch(min(args.n, 2_000_000))
     tg = [torch.tensor(t, device=device) for t in targets]
     params = GaussianParams.from_arrays(scene.as_dict(), device)
-    d = args.d
     (tile, ppt, shift), table = autotune_batch(params, cams, tg, d=d, iters=2)
     st = BatchTrainStep(params, cams, tg, d=d, tile=tile, pixels_per_thread=ppt, bin_shift=shift)
     # per-stage device times from one eager pass of every phase (events between the calls)
@@ -470,38 +472,138 @@ def run_batch(args, device):
         for k, name in enumerate(("project_batch", "bin_sort_all_views", "blend_fwd_loss_bwd", "project_bwd_adam")):
             stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1]) / st.phases
     st.capture()
-    for _ in range(max(args.warmup, st.phases)):
+    for _ in range(max(warmup, st.phases)):
         st.step()
     torch.cuda.synchronize()
-    steps = max(args.steps, st.phases)
-    clocks = ClockSampler(torch.cuda.current_device())
+    steps = max(steps, st.phases)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with clocks:
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(steps):
-            st.step()
-        e1.record()
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        st.step()
+    e1.record()
+    torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     if st.overflowed():
         raise RuntimeError("pair capacity exceeded during the batch run")
+    out = {"steps_per_s": round(1000.0 / ms, 3), "views_per_s": round(8000.0 / ms, 2), "ms_per_step": round(ms, 4),
+           "steps": steps, "d": d, "tile": tile, "pixels_per_thread": ppt, "bin_tile": tile << shift,
+           "autotune_ms": {f"tile{k[0]}_ppt{k[1]}_bin{k[0] << k[2]}": round(v, 3) for k, v in table.items()},
+           "stage_ms_eager": {k: round(v, 3) for k, v in stage.items()},
+           "pairs_per_view": st.num_pairs.tolist(), "n_gaussians": params.n,
+           "resolutions": [[c.width, c.height] for c in cams],
+           "gpu_launches_per_step": st.launches_per_step()}
+    del st, params, tg
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args, device):
+    import torch
+    from paper_2412_13547_b300 import build_native, raster as R
+
+    if not os.path.exists(R.LIB_PATH):
+        build_native.build()
+    clocks = ClockSampler(torch.cuda.current_device())
+    with clocks:
+        r = measure_batch(args, device, args.d, args.steps, args.warmup)
     line = {
-        "metric": "batched fwd+bwd steps/sec (8 views per step)", "value": round(1000.0 / ms, 3),
-        "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "metric": "batched fwd+bwd steps/sec (8 views per step)", "value": r["steps_per_s"],
+        "unit": "steps/s", "n_gpus": 1, "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "views_per_s": round(8000.0 / ms, 2),
-        "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": d,
-                   "offset": "rotating, view i at phase k takes offset k+i", "tile": tile, "pixels_per_thread": ppt,
-                   "bwd_pixels_per_thread": "library default (4 at tile 16 from 4096 tiles, else 2)", "bin_tile": tile << shift,
-                   "resolutions": [[c.width, c.height] for c in cams], "n_gaussians": params.n,
+        "views_per_s": r["views_per_s"],
+        "config": {"workload": "batch-8-views-mixed-res-2M-gaussians-packed-ball", "d": r["d"],
+                   "offset": "rotating, view i at phase k takes offset k+i", "tile": r["tile"],
+                   "pixels_per_thread": r["pixels_per_thread"],
+                   "bwd_pixels_per_thread": "library default (4 at tile 16 from 4096 tiles, else 2)",
+                   "bin_tile": r["bin_tile"], "resolutions": r["resolutions"], "n_gaussians": r["n_gaussians"],
                    "graph": "one CUDA graph per offset phase, replayed", "l2": "inputs larger than L2"},
-        "autotune_ms": {f"tile{k[0]}_ppt{k[1]}_bin{k[0] << k[2]}": round(v, 3) for k, v in table.items()},
-        "stage_ms_eager": {k: round(v, 3) for k, v in stage.items()},
-        "pairs_per_view": st.num_pairs.tolist(),
-        "gpu_launches": st.launches_per_step() * steps,
+        "autotune_ms": r["autotune_ms"], "stage_ms_eager": r["stage_ms_eager"], "pairs_per_view": r["pairs_per_view"],
+        "gpu_launches": r["gpu_launches_per_step"] * r["steps"],
         "clocks": clocks.summary(),
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Stage times and device memory against resolution and dilation
+# ---------------------------------------------------------------------------
+
+SWEEP_RESOLUTIONS = ((1920, 1080), (2560, 1440), (3840, 2160))
+
+
+def run_sweep(args, device):
+    """The breakdown of Sec. 3.1's profile (the pair generation, the pair sort and
+    the blend against image resolution) for this implementation: per-stage
+    CUDA-event times of the full step, the pair count and the peak device memory
+    at 1920x1080, 2560x1440 and 3840x2160 and d = 1, 2, 4, on the 3M-Gaussian
+    scene seen from the same pose (same field of view)."""
+    import torch
+    from paper_2412_13547_b300 import build_native, raster as R, scenes
+    from paper_2412_13547_b300.pipeline import AdamConfig, GaussianParams, Rasterizer, TrainStep
+
+    if not os.path.exists(R.LIB_PATH):
+        build_native.build()
+    scene, _, _ = scenes.workload_uhd(args.n)
+    params = GaussianParams.from_arrays(scene.as_dict(), device)
+    snapshot = [t.clone() for t in params.tensors()]
+    resident = sum(t.numel() * t.element_size() for t in params.tensors())
+    rows = []
+    steps, warm = max(4, min(args.steps, 20)), 3
+    clocks = ClockSampler(torch.cuda.current_device())
+    with clocks:
+        for (w, h) in SWEEP_RESOLUTIONS:
+            cam = scenes.look_at(scenes.orbit_eye(2.6, 30.0, 20.0), width=w, height=h)
+            target = torch.tensor(scenes.target_image(w, h, 2), device=device)
+            for d in (1, 2, 4):
+                for t, s0 in zip(params.tensors(), snapshot):
+                    t.copy_(s0)
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+                torch.cuda.reset_peak_memory_stats(device)
+                dils = [R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d))
+                        for ox in range(d) for oy in range(d)]
+                rast = Rasterizer(params.n, capacity=1 << 20, device=device,
+                                  max_grid=R.gs_bin_grid(cam, R.Dilation(d, 0, 0, tile=TILE[0],
+                                                                           bin_shift=bin_shift_for(d))))
+                kmax = 0
+                for dil in dils:
+                    rast.project(params, cam, dil)
+                    rast.bin_checked(cam, dil)
+                    kmax = max(kmax, rast.num_pairs())
+                rast.ensure_capacity(int(kmax * 1.2) + 4096)
+                w0, h0, _, _ = R.gs_grid(cam, dils[0])
+                step = TrainStep(params, rast, AdamConfig(), max_pixels=w0 * h0)
+                timed = TimedStep(step, steps)
+                for i in range(warm):
+                    timed.run(0, cam, dils[i % len(dils)], target)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for i in range(steps):
+                    timed.run(i, cam, dils[i % len(dils)], target)
+                e1.record()
+                torch.cuda.synchronize()
+                if rast.num_pairs() > rast.capacity:
+                    raise RuntimeError("pair capacity exceeded in the sweep")
+                ms = e0.elapsed_time(e1) / steps
+                peak = int(torch.cuda.max_memory_allocated(device))
+                stage = {k: round(v, 4) for k, v in timed.stage_ms(steps).items()}
+                rows.append(dict(resolution=[w, h], d=d, ms_per_step=round(ms, 4), iters_per_s=round(1000.0 / ms, 2),
+                                 stage_ms=stage, pairs=int(kmax), bin_tile=TILE[0] << bin_shift_for(d),
+                                 peak_allocated_bytes=peak, above_params_bytes=peak - int(resident),
+                                 step_buffers_bytes=int(sum(b.numel() * b.element_size() for b in (
+                                     rast.splats, rast.radii, rast.rects, rast.tiles_touched, rast.grad2d,
+                                     rast.sorted_ids, rast.workspace, step.img, step.t_final, step.last, step.dl)) +
+                                     sum(t.numel() * t.element_size() for t in step.m + step.v + step.grads))))
+                del step, timed, rast
+    line = {"metric": "stage times and device memory vs resolution and dilation (fwd+bwd step)",
+            "value": None, "unit": "ms", "n_gpus": 1, "steps": steps, "warmup": warm, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"uhd-scene-{params.n}-gaussians-sh3 at 3 resolutions x d in (1, 2, 4)",
+                       "tile": TILE[0], "offset": "rotating", "camera": "radius 2.6, 60 deg field of view"},
+            "rows": rows, "params_bytes": int(resident), "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -513,7 +615,7 @@ def run_batch(args, device):
 def run_fit(args, device):
     import torch
     from paper_2412_13547_b300 import build_native, raster as R, scenes
-    from paper_2412_13547_b300.fit import Fit, FitConfig, psnr, render_views, time_to_psnr
+    from paper_2412_13547_b300.fit import Fit, FitConfig, loglog_fit, psnr, render_views, time_to_psnr
     from paper_2412_13547_b300.pipeline import GaussianParams
 
     if not os.path.exists(R.LIB_PATH):
@@ -540,10 +642,17 @@ def run_fit(args, device):
                                       for k, v in a.__dict__.items()})
             fit = Fit(cfg, init, train, train_t, held, held_t)
             hist = fit.run()
+            b = fit.budget
+            slope, icpt, r2 = loglog_fit(b.steps, b.ema)
+            sub = max(1, len(b.steps) // 60)
             runs[form] = dict(history=[{k: (round(v, 4) if isinstance(v, float) else v) for k, v in hh.items()}
                                        for hh in hist],
                               rounds=len(fit.rounds), final_psnr=hist[-1]["psnr"], gpu_seconds=hist[-1]["seconds"],
-                              n_final=hist[-1]["n"], overflow_steps=fit.overflow_steps)
+                              n_final=hist[-1]["n"], overflow_steps=fit.overflow_steps,
+                              budget_rounds=[{k: (round(v, 5) if isinstance(v, float) else v) for k, v in r.items()}
+                                             for r in fit.rounds],
+                              loss_loglog={"slope": slope, "intercept": icpt, "r2": r2,
+                                           "steps": b.steps[::sub], "ema": [round(x, 6) for x in b.ema[::sub]]})
             del fit
             torch.cuda.empty_cache()
     # equal PSNR: the lower of the two final held-out PSNRs (as recorded in the histories)
@@ -665,10 +774,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=3_000_000)
-    ap.add_argument("--workload", default="uhd", choices=["uhd", "hd", "batch", "fit"],
+    ap.add_argument("--workload", default="uhd", choices=["uhd", "hd", "batch", "fit", "sweep"],
                     help="uhd: 3840x2160, 3M Gaussians (the measured workload); hd: 1920x1080, 1M (profiling); "
                          "batch: 8 mixed-resolution views per step of a 2M-Gaussian scene; "
-                         "fit: time to equal PSNR of the plain and the dilated+BF16+batched forms")
+                         "fit: time to equal PSNR of the plain and the dilated+BF16+batched forms; "
+                         "sweep: stage times and memory at 1080p/1440p/4K x d in (1, 2, 4)")
     ap.add_argument("--fit-views", type=int, default=20000, help="views trained per form (fit workload)")
     ap.add_argument("--fit-res", default="3840x2160")
     ap.add_argument("--fit-gt", type=int, default=2_000_000)
@@ -684,9 +794,12 @@ def main():
     ap.add_argument("--oracle-tiles", type=int, default=16)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="leave the 8-view batched variant out of the default run")
     ap.add_argument("--stages-json", default="")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile side of the lattice image")
+    ap.add_argument("--sh-dtype", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="SH storage of the measured form (profiling; the headline is FP32)")
     ap.add_argument("--bin-shift", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="bin with tiles of tile << bin-shift, blend per tile (-1: about 128 hr px)")
     args = ap.parse_args()
@@ -705,10 +818,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    if args.workload in ("batch", "fit"):
+    if args.workload in ("batch", "fit", "sweep"):
         if world > 1:
             raise SystemExit(f"--workload {args.workload} runs on one GPU")
-        return run_batch(args, device) if args.workload == "batch" else run_fit(args, device)
+        return {"batch": run_batch, "fit": run_fit, "sweep": run_sweep}[args.workload](args, device)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
@@ -738,7 +851,8 @@ def main():
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(device)
-    head, head_step = measure_variant(args, params, cam, target_dev, 2, torch.float32, args.steps, args.warmup,
+    head_dtype = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.sh_dtype]
+    head, head_step = measure_variant(args, params, cam, target_dev, 2, head_dtype, args.steps, args.warmup,
                                       device, rast, snapshot, clocks=clocks)
     memory = memory_report(head, head_step, params, cam, device)
     variants = {"dilated_d2_fp32": {k: v for k, v in head.items() if k != "stage_ms"}}
@@ -755,13 +869,16 @@ def main():
             r["fused_pass_hbm_frac"] = round(vroof["project_bwd_adam"]["frac"], 4)
             stage_tables[name] = r.pop("stage_ms")
             variants[name] = r
+    if not args.no_variants and not args.no_batch and world == 1:
+        # the batched form (8 mixed-resolution views per step, CUDA graphs, autotuned launch shape)
+        variants["batch_8views_d2"] = measure_batch(args, device, 2, max(8, args.steps // 4), 4)
     e2e = e2e_measure(args, params, cam, target, 2, args.steps, args.warmup, device, rast, snapshot)
 
     # max over ranks of the step time (replicas: every rank runs the whole workload)
     ms, e2e_ms = max_over_ranks([head["ms_per_step"], e2e["ms_per_step"]], device)
     value = job_throughput(world, ms)
 
-    sh_bytes = 48 * 4
+    sh_bytes = 48 * (4 if args.sh_dtype == "fp32" else 2)
     roof = stage_roofline(head, params.n, sh_bytes, pk, R.gs_grid(cam, R.Dilation(2, 1, 0))[0] *
                           R.gs_grid(cam, R.Dilation(2, 1, 0))[1])
     dom = max(KERNEL_OF_STAGE, key=lambda s: roof[s]["ms"])

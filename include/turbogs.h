@@ -118,7 +118,11 @@ int32_t gs_bin_grid(const GsCamera* cam, const GsDilation* dil, int32_t* bin_til
  * Outputs (device): splats (n x 16, layout above), radii (n, 0 = culled),
  *   rects (n x 4: x0, y0, x1, y1 inclusive binning tile indices, the blend
  *   tile rectangle shifted right by bin_shift; culled: 0, 0, -1, -1),
- *   tiles_touched (n: binning tiles in the rect; > 0 = visible).
+ *   tiles_touched (n: binning tiles in the rect; > 0 = visible),
+ *   depth_keys (nullable, n uint32: the depth sort key of gs_bin_sort, the
+ *   float32 bits of the depth t_z of a visible Gaussian, at most 0xfffffffe,
+ *   and 0xffffffff for a culled one; given to gs_bin_sort, it saves its
+ *   pass over the splat records).
  *   A Gaussian is culled (radius 0, empty rect) when its blend tile rectangle
  *   is empty, whatever bin_shift.
  * Errors: GS_ERR_ARG for n < 0, a null pointer with n > 0, sh_degree outside
@@ -129,7 +133,7 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
                    const float* opacity_logits, const void* sh,
                    const GsCamera* cam, const GsDilation* dil,
                    float* splats, int32_t* radii, int32_t* rects, int32_t* tiles_touched,
-                   gs_stream_t stream);
+                   uint32_t* depth_keys, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_bin_sort -- the tile-Gaussian pairs of the tile-based rasterizer (Sec. 3,
@@ -138,8 +142,10 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * float32 bits of the depth, value = Gaussian index), sorted ascending by
  * (key, value), and per-tile [start, end) ranges into the sorted values.
  * Inputs (device): rects, tiles_touched (from gs_project for the same
- *   dilation), splats (depth = [9]); tiles_x, tiles_y: the binning grid
- *   (gs_bin_grid). Rects outside the grid are ignored.
+ *   dilation), splats (depth = [9]); depth_keys (nullable: gs_project's keys
+ *   for the same call, used instead of reading the depths from splats);
+ *   tiles_x, tiles_y: the binning grid (gs_bin_grid). Rects outside the grid
+ *   are ignored.
  * Outputs (device): sorted_ids (capacity entries; the first num_pairs hold the
  *   Gaussian ids tile by tile, front to back), ranges (tiles_x*tiles_y x 2,
  *   uint32 start/end; (0, 0) for a tile no Gaussian touches), num_pairs (one
@@ -166,7 +172,7 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * Errors: GS_ERR_ARG for bad sizes, null pointers or a short workspace. */
 size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, int32_t tiles_y);
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
-                    const float* splats, int32_t tiles_x, int32_t tiles_y,
+                    const float* splats, const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y,
                     void* workspace, size_t workspace_bytes, int64_t capacity,
                     uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
                     gs_stream_t stream);
@@ -198,7 +204,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
  * on one device) race on it, so serialise them. */
 #define GS_BIN_SORT_STATIC_SCRATCH_BYTES (32u << 20)
 int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched,
-                           const float* splats, int32_t tiles_x, int32_t tiles_y, int64_t capacity,
+                           const float* splats, const uint32_t* depth_keys, int32_t tiles_x,
+                           int32_t tiles_y, int64_t capacity,
                            uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
                            gs_stream_t stream);
 
@@ -258,6 +265,39 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
                    const float* target, float* dl_dimg, float* loss, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_ssim -- SSIM, the structural-similarity index (Wang et al. 2004) the
+ * paper reports beside PSNR (Sec. 4, metrics), of the rendered lattice image
+ * against the hr target sampled at the same pixels (as gs_loss_l1 samples it).
+ * Per channel and lattice pixel p, with the 11 x 11 Gaussian window (sigma
+ * 1.5, weights summing to 1) sums m_x, m_y, E_xx, E_yy, E_xy around p:
+ *   SSIM_p = (2 m_x m_y + C1)(2 (E_xy - m_x m_y) + C2)
+ *            / ((m_x^2 + m_y^2 + C1)(E_xx - m_x^2 + E_yy - m_y^2 + C2)),
+ * C1 = 0.01^2, C2 = 0.03^2 (values in [0, 1]). mode 0 ("valid"): the mean over
+ * the pixels whose window lies inside the lattice image (at least 11 x 11);
+ * mode 1 ("same"): the mean over all pixels, zeros outside the image (the
+ * form 3DGS fitting trains with). Channels are averaged.
+ * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3).
+ * Outputs (device): *ssim_out (one float, overwritten); d_img (nullable,
+ *   h_ds x w_ds x 3): d (mean SSIM) / d img, overwritten.
+ * workspace: gs_ssim_workspace_size(cam, dil) bytes, 256-byte aligned (9
+ *   floats per lattice pixel and two accumulators; no init needed).
+ * Errors: GS_ERR_ARG for a bad camera/dilation/mode, null pointers, a short or
+ *   misaligned workspace, or a lattice under 11 x 11 in mode 0. */
+size_t gs_ssim_workspace_size(const GsCamera* cam, const GsDilation* dil);
+int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, int32_t mode,
+                float* ssim_out, float* d_img, void* workspace, size_t workspace_bytes, gs_stream_t stream);
+
+/* gs_loss_l1_dssim -- the photometric loss of 3DGS fitting, which the paper's
+ * method builds on (the paper's own loss is the L1 of gs_loss_l1):
+ *   L = (1 - lambda) L1 + lambda (1 - SSIM),  0 <= lambda <= 1,
+ * L1 as in gs_loss_l1 and SSIM as in gs_ssim (mode as there), over the lattice
+ * pixels. Outputs (device): dl_dimg (h_ds x w_ds x 3, overwritten) = dL/dimg,
+ * *loss (overwritten). workspace as gs_ssim. */
+int32_t gs_loss_l1_dssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target,
+                         float lambda, int32_t mode, float* dl_dimg, float* loss, void* workspace,
+                         size_t workspace_bytes, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * gs_render_bwd -- backward of gs_render_fwd. The per-pixel blend state is not
  * stored: each pixel replays its list back to front from t_final and last,
  * recovering T_i = T_{i+1} / (1 - alpha_i), and the per-Gaussian gradients of
@@ -309,9 +349,10 @@ int32_t gs_project_bwd(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  *     the update is computed in FP32 from the stored value and rounded
  *     stochastically to sh_dtype (the neighbour away from zero with probability
  *     equal to the value's position between the two neighbours, from 16 bits
- *     of the PCG hash of Jarzynski & Olano 2020 applied to base + e, e = g *
- *     3 (sh_degree+1)^2 + j the element index, base = hash(hash(sr_seed) xor t),
- *     t the Adam step: *adam->step_dev when given, else adam->step). No FP32
+ *     of the PCG hash of Jarzynski & Olano 2020: elements 2k and 2k + 1 take
+ *     the low and high halves of hash(base + k), e = g * 3 (sh_degree+1)^2 + j
+ *     the element index, base = hash(hash(sr_seed) xor t), t the Adam step:
+ *     *adam->step_dev when given, else adam->step). No FP32
  *     copy of the SH exists, so the pass moves 2 instead of 4 bytes per SH
  *     value in each direction. adam->sh_shadow must be NULL.
  *   - FP32 master with a low-precision copy: adam->param[4] FP32 and sh_store
@@ -416,6 +457,7 @@ typedef struct {
     float* dl_dimg;            /* h_ds x w_ds x 3                              */
     float* grad2d;             /* n x 12                                       */
     float* loss;               /* one float                                    */
+    uint32_t* depth_keys;      /* n, nullable (gs_project's depth_keys)         */
 } GsView;
 
 /* gs_project for every view of the table (one launch). */

@@ -111,3 +111,59 @@ def prune_keep(opacity_logits, logit_min, log_scales=None, log_scale_max=None):
     if log_scales is not None and log_scale_max is not None:
         keep &= np.asarray(log_scales, np.float32).max(1) <= np.float32(log_scale_max)
     return np.nonzero(keep)[0].astype(np.int64)
+
+
+def algorithm1(records, calls, n_init, m_final, start, end, window=200, history=5, warmup=100, lam=0.5,
+               ema_alpha=0.1, alpha_clip=(0.1, 2.0), rate_up=0.05, rate_down=-0.05, grow=1.1, shrink=0.9,
+               m_cap=1.5, m_floor=0.5):
+    """Algorithm 1 (the convergence-aware budget of Sec. 3.2) replayed from a
+    complete record, in the algorithm's own order.
+
+    records: (step, loss) pairs in step order; calls: the steps at which the
+    budget is asked for (each call sees the records up to and including it).
+    Per call, following the algorithm's lines:
+      * the losses of the first ``warmup`` steps are not recorded (Sec. 3.2),
+        and with fewer than three recorded the exponent is 1 (the
+        algorithm's default);
+      * otherwise the recorded losses are smoothed, ema_t = ema_alpha * loss_t
+        + (1 - ema_alpha) * ema_{t-1} (starting at the first loss), and
+        log(ema) is fitted against log(step) by least squares (numpy.polyfit,
+        degree 1) over all of them: alpha_history = -slope; alpha_base is the
+        mean of the last ``history`` such fits (Eq. 6's text);
+      * rate = -slope of the same fit over the last ``window`` points;
+      * the final count M grows x``grow`` (at most m_cap M) when
+        rate > rate_up and shrinks x``shrink`` (at least m_floor M) when
+        rate < rate_down;
+      * Eq. 6: epsilon = alpha_recent - alpha_history in slope terms, that is
+        alpha_base - rate with both as decay exponents, and
+        alpha = alpha_base + lam * tanh(epsilon), clipped to alpha_clip;
+      * Eq. 7: B(t) = N + (t^alpha - 1) / (100^alpha - 1) (M - N), with
+        t = 1 + 99 (step - start) / (end - start) clamped to [1, 100].
+    Returns, per call, a dict of alpha, alpha_base, rate, M and B."""
+    out = []
+    fits = []
+    m_adapt = float(m_final)
+    recs = [(int(s), float(l)) for s, l in records if int(s) > warmup]
+    for c in calls:
+        seen = [(s, l) for s, l in recs if s <= c]
+        alpha, a_base, rate = 1.0, None, 0.0
+        if len(seen) > 2:
+            steps = np.array([s for s, _ in seen], np.float64)
+            ema = np.empty(len(seen))
+            for i, (_, l) in enumerate(seen):
+                ema[i] = l if i == 0 else ema_alpha * l + (1.0 - ema_alpha) * ema[i - 1]
+            x, y = np.log(steps), np.log(np.maximum(ema, 1e-30))
+            fits.append(-np.polyfit(x, y, 1)[0])
+            a_base = float(np.mean(fits[-history:]))
+            k = min(window, len(seen))
+            rate = float(-np.polyfit(x[-k:], y[-k:], 1)[0])
+            if rate > rate_up:
+                m_adapt = min(m_adapt * grow, m_final * m_cap)
+            elif rate < rate_down:
+                m_adapt = max(m_adapt * shrink, m_final * m_floor)
+            eps = a_base - rate
+            alpha = float(np.clip(a_base + lam * np.tanh(eps), *alpha_clip))
+        t = 100.0 if end <= start else 1.0 + 99.0 * min(1.0, max(0.0, (c - start) / float(end - start)))
+        b = float(budget(t, n_init, m_adapt, alpha))
+        out.append(dict(alpha=alpha, alpha_base=a_base, rate=rate, M=m_adapt, B=b))
+    return out

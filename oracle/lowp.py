@@ -18,8 +18,9 @@ expectation. Definitions used here, one per step:
   above |x| with x's sign (rounding toward zero), and hi, the next magnitude;
 * the position of x between them, in units of 2^-16 of the step hi - lo:
   pos = floor(65536 (|x| - |lo|) / (|hi| - |lo|));
-* the random bits: r = pcg(base + e) >> 16 for element e, with
-  base = pcg(pcg(seed) xor t) for the optimizer step t, where pcg is the
+* the random bits: elements 2k and 2k + 1 take the low and the high 16 bits
+  of pcg(base + k), with base = pcg(pcg(seed) xor t) for the optimizer
+  step t, where pcg is the
   PCG hash of Jarzynski and Olano ("Hash Functions for GPU Rendering",
   JCGT 9(3), 2020): one step of PCG's 32-bit LCG followed by PCG's RXS-M-XS
   output permutation (O'Neill 2014);
@@ -53,7 +54,8 @@ def sr_bits16(seed: int, step: int, e):
     """The 16 random bits of elements e (uint32 counters) at optimizer step t."""
     base = pcg_hash(pcg_hash(np.uint64(seed & _M32)) ^ np.uint64(step & _M32))
     e = np.asarray(e, dtype=np.uint64)
-    return pcg_hash((base + e) & np.uint64(_M32)) >> np.uint64(16)
+    h = pcg_hash((base + (e >> np.uint64(1))) & np.uint64(_M32))
+    return np.where((e & np.uint64(1)) == 1, h >> np.uint64(16), h & np.uint64(0xFFFF))
 
 
 def _lo_bits(x32: np.ndarray, dtype: str) -> np.ndarray:

@@ -111,6 +111,7 @@ bool make_batch(const GsView* views, int nviews, gs::Batch* out)
         v.dl = in.dl_dimg;
         v.grad2d = reinterpret_cast<float4*>(in.grad2d);
         v.loss = in.loss;
+        v.keys = in.depth_keys;
         v.tile_begin = tiles;
         tiles += v.dil.tiles_x * v.dil.tiles_y;
     }

@@ -93,8 +93,10 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d
     __syncthreads();
     int64_t begin, end;
     block_segment(sort_count(d_num, cap), gridDim.x, blockIdx.x, begin, end);
-    // begin is a multiple of 4 items (16 bytes); vector loads for the body
-    int64_t body_end = begin + ((end - begin) & ~int64_t(3));
+    // begin is a multiple of 4 items: 16-byte vector loads for the body when the key array
+    // is 16-byte aligned (a caller's key array need only be 4-byte aligned)
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+    int64_t body_end = vec ? begin + ((end - begin) & ~int64_t(3)) : begin;
     const uint4* k4 = reinterpret_cast<const uint4*>(keys);
     for (int64_t i = begin / 4 + threadIdx.x; i < body_end / 4; i += kSortThreads) {
         uint4 v = k4[i];
@@ -179,12 +181,19 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
             k[j] = ok ? keys_in[idx] : 0u;
             v[j] = ok ? (vals_in != nullptr ? vals_in[idx] : (uint32_t)idx) : 0u;
         }
-        // stable rank within the warp: rounds in order, lanes in order
+        // stable rank within the warp: rounds in order, lanes in order. The lanes holding the
+        // same digit come from one ballot per digit bit (the digit has at most 8 bits).
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
             const bool ok = wbase + j * 32 + lane < end;
             const uint32_t dg = ok ? ((k[j] >> shift) & mask) : 0xffffffffu;
-            uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t bit = (dg >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
             uint32_t pre = __popc(peers & lt_mask);
             int leader = __ffs(peers) - 1;
             uint32_t basec = ok ? s_warp[warp][dg] : 0u;
@@ -236,10 +245,13 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
 struct SortBufs {
     uint32_t *keys0, *vals0, *keys1, *vals1;
     bool iota_vals;  // vals0 holds 0, 1, 2, ... on entry: the first pass makes them instead of reading them
+    uint32_t* keys2;  // with an even pass count the result keys land here instead of keys0 (which is
+                      // then only read, e.g. a caller's array); null: keys0
 };
 
 // Sorts (keys0, vals0) by bits [0, bits) of the keys; the result lands in
-// buffer set (passes % 2 == 0 ? 0 : 1). Returns the number of passes.
+// buffer set (passes % 2 == 0 ? 0 : 1), its keys in keys2 when given. Returns
+// the number of passes.
 int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, uint32_t* hist, uint32_t* totals,
                cudaStream_t st)
 {
@@ -247,6 +259,7 @@ int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, u
     if (passes < 1) passes = 1;
     int per = (bits + passes - 1) / passes;
     int shift = 0;
+    uint32_t* k0 = b.keys2 ? b.keys2 : b.keys0;
     uint32_t *ki = b.keys0, *vi = b.vals0, *ko = b.keys1, *vo = b.vals1;
     for (int p = 0; p < passes; ++p) {
         int nb = (bits - shift) < per ? (bits - shift) : per;
@@ -255,9 +268,10 @@ int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, u
         k_radix_scan<<<kRadixBins, kSortThreads, 0, st>>>(hist, G, totals);
         const uint32_t* vin = (p == 0 && b.iota_vals) ? nullptr : vi;
         k_radix_downsweep<<<G, kSortThreads, 0, st>>>(ki, vin, ko, vo, d_num, cap, shift, mask, hist, totals);
-        uint32_t* t;
-        t = ki; ki = ko; ko = t;
-        t = vi; vi = vo; vo = t;
+        // the next pass reads what this one wrote and writes the other set (set 0's keys in k0)
+        uint32_t* t = vi; vi = vo; vo = t;
+        ki = ko;
+        ko = (ko == b.keys1) ? k0 : b.keys1;
         shift += nb;
     }
     return passes;
@@ -281,19 +295,14 @@ __device__ __forceinline__ bool rect_in_grid(int4 r, int TX, int TY)
 constexpr int kKeyThreads = 256;
 constexpr int kKeysPerThread = 4;
 
-// One pass over the Gaussians: the depth sort key of each (the float bits of
-// the view depth, which order like the value since depth > z_near > 0 for a
-// visible Gaussian; all ones for a culled one), and K, the number of
-// (Gaussian, tile) pairs: the rect areas of the visible Gaussians (equal to
-// their tiles_touched), accumulated into *total (zeroed by the caller).
-// Counting from the rects the scatters use keeps every row list within K
-// slots. Each thread takes kKeysPerThread Gaussians a block apart, loads first.
+// One pass over the Gaussians when the caller gives no depth keys: the depth
+// sort key of each (the float bits of the view depth, which order like the
+// value since depth > z_near > 0 for a visible Gaussian; all ones for a culled
+// one). Each thread takes kKeysPerThread Gaussians a block apart, loads first.
 __global__ void __launch_bounds__(kKeyThreads)
-k_keys_and_pairs(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
-                 const int4* __restrict__ rects, int TX, int TY, uint32_t* __restrict__ keys,
-                 unsigned long long* __restrict__ total)
+k_depth_keys(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
+             uint32_t* __restrict__ keys)
 {
-    __shared__ unsigned long long s_sum[kKeyThreads / 32];
     const int64_t g0 = (int64_t)blockIdx.x * (kKeyThreads * kKeysPerThread) + threadIdx.x;
     int tt[kKeysPerThread];
 #pragma unroll
@@ -301,30 +310,12 @@ k_keys_and_pairs(int n, const float4* __restrict__ splats, const int* __restrict
         const int64_t g = g0 + j * kKeyThreads;
         tt[j] = g < n ? tiles_touched[g] : 0;
     }
-    unsigned long long s = 0;
 #pragma unroll
     for (int j = 0; j < kKeysPerThread; ++j) {
         const int64_t g = g0 + j * kKeyThreads;
         if (g >= n) break;
-        uint32_t key = 0xffffffffu;
-        if (tt[j] > 0) {
-            // all ones marks a culled Gaussian: a visible one never takes it (even with bad input)
-            key = min(__float_as_uint(splats[4 * g + 2].y), 0xfffffffeu);
-            const int4 r = rects[g];
-            if (rect_in_grid(r, TX, TY))
-                s += (unsigned long long)(r.z - r.x + 1) * (unsigned long long)(r.w - r.y + 1);
-        }
-        keys[g] = key;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long b = 0;
-#pragma unroll
-        for (int w = 0; w < kKeyThreads / 32; ++w) b += s_sum[w];
-        if (b) atomicAdd(total, b);
+        // all ones marks a culled Gaussian: a visible one never takes it (even with bad input)
+        keys[g] = tt[j] > 0 ? min(__float_as_uint(splats[4 * g + 2].y), 0xfffffffeu) : 0xffffffffu;
     }
 }
 
@@ -465,22 +456,26 @@ __device__ __forceinline__ uint32_t lvl1_id(const uint32_t* perm, const uint32_t
 }
 
 // Level 1a: per level-1 warp (chunk of kRowChunk depth-ordered Gaussians), the
-// number of its Gaussians whose rect spans each tile row -> M1[chunk][row].
-// The rects of four rounds are fetched together.
+// number of its Gaussians whose rect spans each tile row -> M1[chunk][row],
+// and K, the number of (Gaussian, tile) pairs: the rect areas of the visible
+// Gaussians inside the grid, summed into *d_K (zeroed by the caller; complete
+// when this kernel ends, and checked against the capacity by every later
+// one). Counting from the rects the scatters use keeps every row list within
+// K slots. The rects of four rounds are fetched together.
 __global__ void __launch_bounds__(kLvlThreads)
 k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
-           const int4* __restrict__ rects, int TX, int TY, const int64_t* __restrict__ d_K, int64_t cap,
-           uint32_t* __restrict__ M1)
+           const int4* __restrict__ rects, int TX, int TY, int64_t* __restrict__ d_K, uint32_t* __restrict__ M1)
 {
     extern __shared__ int s_lvl[];
     constexpr int U = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * kLvlWarps + warp;
-    if (c >= C1 || overflow(d_K, cap)) return;
+    if (c >= C1) return;
     int* d = s_lvl + warp * (TY + 1);
     for (int i = lane; i <= TY; i += 32) d[i] = 0;
     __syncwarp();
     const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    unsigned long long area = 0;
     for (int kb = k0 + lane; kb < k1; kb += 32 * U) {
         uint32_t g[U];
         bool vis[U];
@@ -494,8 +489,12 @@ k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __r
             if (!vis[j] || !rect_in_grid(r[j], TX, TY)) continue;
             atomicAdd(&d[r[j].y], 1);
             atomicAdd(&d[r[j].w + 1], -1);
+            area += (unsigned long long)(r[j].z - r[j].x + 1) * (unsigned long long)(r[j].w - r[j].y + 1);
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) area += __shfl_down_sync(0xffffffffu, area, o);
+    if (lane == 0 && area) atomicAdd(reinterpret_cast<unsigned long long*>(d_K), area);
     __syncwarp();
     warp_inclusive_scan_smem(d, TY, lane);
     for (int ty = lane; ty < TY; ty += 32) M1[(int64_t)c * TY + ty] = (uint32_t)d[ty];
@@ -876,8 +875,9 @@ size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, 
 }
 
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
-                    int32_t tiles_x, int32_t tiles_y, void* workspace, size_t workspace_bytes, int64_t capacity,
-                    uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
+                    const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y, void* workspace,
+                    size_t workspace_bytes, int64_t capacity, uint32_t* sorted_ids, uint32_t* ranges,
+                    int64_t* num_pairs, gs_stream_t stream)
 {
     using namespace gs;
     if (n < 0 || capacity < 0 || capacity > 0x7fffffffLL || tiles_x <= 0 || tiles_y <= 0 ||
@@ -885,7 +885,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         gs_host::set_error("gs_bin_sort: bad sizes (n >= 0, 0 <= capacity < 2^31, 0 < tiles_x, tiles_y <= 4096)");
         return GS_ERR_ARG;
     }
-    if (!ranges || !num_pairs || (n > 0 && (!rects || !tiles_touched || !splats || !workspace)) ||
+    if (!ranges || !num_pairs || (n > 0 && (!rects || !tiles_touched || (!splats && !depth_keys) || !workspace)) ||
         (capacity > 0 && !sorted_ids)) {
         gs_host::set_error("gs_bin_sort: null pointer");
         return GS_ERR_ARG;
@@ -906,12 +906,16 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         return gs_host::check_launch("gs_bin_sort");
     }
     const int4* rc = reinterpret_cast<const int4*>(rects);
-    // K, and the depth order of the Gaussians: a stable LSD radix sort of (depth bits, id)
-    k_keys_and_pairs<<<(n + kKeyThreads * kKeysPerThread - 1) / (kKeyThreads * kKeysPerThread), kKeyThreads, 0,
-                       st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched, rc, TX, TY, w.dkeys0,
-                             reinterpret_cast<unsigned long long*>(num_pairs));
-    radix_sort(SortBufs{w.dkeys0, w.perm0, w.dkeys1, w.perm1, true}, nullptr, n, 32, sort_blocks(n), w.hist,
-               w.totals, st);  // 4 passes: the sorted keys and the order are back in dkeys0, perm0
+    // the depth order of the Gaussians: a stable LSD radix sort of (depth bits, id), from the
+    // projection's keys or from a pass over the splat records
+    const uint32_t* keys_in = depth_keys;
+    if (!keys_in) {
+        k_depth_keys<<<(n + kKeyThreads * kKeysPerThread - 1) / (kKeyThreads * kKeysPerThread), kKeyThreads, 0,
+                       st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched, w.dkeys0);
+        keys_in = w.dkeys0;
+    }
+    radix_sort(SortBufs{const_cast<uint32_t*>(keys_in), w.perm0, w.dkeys1, w.perm1, true, w.dkeys0}, nullptr, n,
+               32, sort_blocks(n), w.hist, w.totals, st);  // 4 passes: the sorted keys and the order in dkeys0, perm0
     // level 1: rows
     const int C1 = lvl1_warps(n);
     const int lvl1_blocks = (C1 + kLvlWarps - 1) / kLvlWarps;
@@ -920,8 +924,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     }
-    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs,
-                                                        capacity, w.M1);
+    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs, w.M1);
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
     const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb1, kScanGridY));
     k_col_segsum<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
@@ -961,8 +964,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
 }
 
 int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
-                           int32_t tiles_x, int32_t tiles_y, int64_t capacity, uint32_t* sorted_ids,
-                           uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
+                           const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y, int64_t capacity,
+                           uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
 {
     if (n < 0 || capacity < 0 || tiles_x <= 0 || tiles_y <= 0) {
         gs_host::set_error("gs_bin_sort_static: bad sizes (n >= 0, capacity >= 0, tiles > 0)");
@@ -991,7 +994,7 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
         gs_host::set_error(msg);
         return GS_ERR_CUDA;
     }
-    return gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, scratch,
+    return gs_bin_sort(n, rects, tiles_touched, splats, depth_keys, tiles_x, tiles_y, scratch,
                        (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES, capacity, sorted_ids, ranges, num_pairs, stream);
 }
 

@@ -64,6 +64,7 @@ struct ViewDev {
     float* dl;
     float4* grad2d;
     float* loss;
+    uint32_t* keys;  // depth sort keys (nullable)
     int tile_begin;  // first global tile id of this view in the batch
 };
 
@@ -358,7 +359,8 @@ __host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v)
     return (word >> 22u) ^ word;
 }
 
-// Stream of one optimizer step; element e draws pcg_hash(base + e) >> 16.
+// Stream of one optimizer step. Elements 2k and 2k + 1 draw the low and the
+// high 16 bits of pcg_hash(base + k).
 __host__ __device__ __forceinline__ uint32_t sr_base(uint32_t seed, uint32_t step)
 {
     return pcg_hash(pcg_hash(seed) ^ step);
@@ -366,7 +368,8 @@ __host__ __device__ __forceinline__ uint32_t sr_base(uint32_t seed, uint32_t ste
 
 __device__ __forceinline__ uint32_t sr_bits16(uint32_t base, uint32_t e)
 {
-    return pcg_hash(base + e) >> 16;
+    const uint32_t h = pcg_hash(base + (e >> 1));
+    return (e & 1u) ? (h >> 16) : (h & 0xffffu);
 }
 
 // x rounded to the BF16 neighbour away from zero when the 16 random bits r are
@@ -379,11 +382,13 @@ __device__ __forceinline__ uint16_t sr_bf16(float x, uint32_t r)
     return (uint16_t)((b >> 16) + ((b & 0xffffu) > r ? 1u : 0u));
 }
 
-// The same rule for FP16: the neighbour toward zero lo, the step to the next
-// magnitude, and x's position between them in units of 2^-16 of that step
-// (exact: |x| - |lo| is a difference within one binade and the step a power of
-// two). The largest finite magnitude saturates; non-finite: nearest.
-__device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r)
+// The same rule for FP16, in general form: the neighbour toward zero lo, the
+// step to the next magnitude, and x's position between them in units of 2^-16
+// of that step (exact: |x| - |lo| is a difference within one binade and the
+// step a power of two). The largest finite magnitude saturates; non-finite:
+// nearest. Out of line: only values outside FP16's normal range come here, and
+// inlined into the unrolled optimizer loops it would crowd the instruction cache.
+__device__ __noinline__ uint16_t sr_f16_general(float x, uint32_t r)
 {
     if (!isfinite(x)) return __half_as_ushort(__float2half_rn(x));
     const uint16_t lb = __half_as_ushort(__float2half_rz(x));
@@ -393,6 +398,21 @@ __device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r)
     const float frac = __fdiv_rn(__fsub_rn(fabsf(x), lo), __fsub_rn(hi, lo));
     const uint32_t pos = (uint32_t)__float2uint_rz(__fmul_rn(frac, 65536.0f));
     return (uint16_t)(lb + (pos > r ? 1u : 0u));
+}
+
+__device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    if (ex - 113u <= 29u) {
+        // FP16's normal range (2^-14 <= |x| < 2^16), in integer arithmetic: the FP16 pattern
+        // toward zero keeps the top 10 of x's 23 mantissa bits, and the 13 it drops are x's
+        // position in units of 2^-13 of the step (<< 3: units of 2^-16)
+        const uint32_t h = ((b >> 16) & 0x8000u) | ((ex - 112u) << 10) | ((b >> 13) & 0x3ffu);
+        const uint32_t pos = (b & 0x1fffu) << 3;
+        return (uint16_t)(h + ((pos > r && (h & 0x7fffu) != 0x7bffu) ? 1u : 0u));
+    }
+    return sr_f16_general(x, r);
 }
 
 __device__ __forceinline__ uint16_t sr_round(float x, uint32_t r, int dtype)

@@ -336,6 +336,7 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
             V.radii[g] = 0;
             V.rects[g] = make_int4(0, 0, -1, -1);
             V.tiles[g] = 0;
+            if (V.keys) V.keys[g] = 0xffffffffu;
             continue;
         }
         out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
@@ -346,6 +347,9 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
         V.radii[g] = P.radius;
         V.rects[g] = P.rect;
         V.tiles[g] = P.tiles;
+        // the depth sort key: the float bits order like the positive depth; all ones is kept
+        // for the culled
+        if (V.keys) V.keys[g] = min(__float_as_uint(P.tz), 0xfffffffeu);
     }
 }
 
@@ -644,8 +648,9 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
 // Adam over the warp's segment of the SH kept only in 16 bits (BF16/FP16 sh_store,
 // no FP32 copy): the update is computed in FP32 from the stored value and rounded
 // stochastically (element e of the tensor draws sr_bits16(sr, e)). A full, dense
-// warp moves groups of 8 values (one 16-byte vector of the parameter, two of
-// each moment), two groups in flight per lane; otherwise one element at a time.
+// warp moves units of 4 values like adam_segment (an 8-byte vector of the
+// parameter, a 16-byte one of each moment: every warp access is contiguous), 4
+// units in flight per lane; otherwise one element at a time.
 template <int W, int GSTRIDE, int DT>
 __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int rows, const float* s_grad,
                                                   unsigned vis, float bc1, float bc2, int lane, void* store,
@@ -657,60 +662,63 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
         float* M = a.m[4] + base;
         float* V = a.v[4] + base;
         float* gout = a.gout[4];
-        const uintptr_t al = reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) |
-                             reinterpret_cast<uintptr_t>(V);
-        auto tofloat = [](uint16_t h) {
-            if constexpr (DT == GS_DTYPE_BF16) return __bfloat162float(__ushort_as_bfloat16(h));
-            else return __half2float(__ushort_as_half(h));
+        auto tofloat = [](uint32_t h) {
+            if constexpr (DT == GS_DTYPE_BF16) {
+                return __uint_as_float(h << 16);
+            } else {
+                // FP16 -> FP32 in integer arithmetic for normal values (exponent rebased by
+                // 127 - 15), the conversion instruction for zeros, subnormals and non-finite
+                const uint32_t ex = h & 0x7c00u;
+                if (ex != 0u && ex != 0x7c00u)
+                    return __uint_as_float(((h & 0x8000u) << 16) | (((h & 0x7fffu) << 13) + 0x38000000u));
+                return __half2float(__ushort_as_half((uint16_t)h));
+            }
         };
-        if (rows == 32 && !a.sparse && (al & 15) == 0) {
-            constexpr int Q = 4 * W;            // groups of 8 values in the segment (32 W values)
-            constexpr int KN = (Q + 31) / 32;   // groups per lane, the last one partial when Q % 32 != 0
-            constexpr int B = KN < 2 ? KN : 2;  // groups loaded before any is stored
-            uint4* P8 = reinterpret_cast<uint4*>(P);
+        const uintptr_t al = reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(V);
+        if (rows == 32 && !a.sparse && (al & 15) == 0 && (reinterpret_cast<uintptr_t>(P) & 7) == 0) {
+            constexpr int Q = 8 * W;            // units of 4 values in the segment (32 W values)
+            constexpr int KN = (Q + 31) / 32;   // units per lane, the last one partial when Q % 32 != 0
+            constexpr int B = KN < 4 ? KN : 4;  // units loaded before any is stored
+            uint2* P2 = reinterpret_cast<uint2*>(P);
             float4* M4 = reinterpret_cast<float4*>(M);
             float4* V4 = reinterpret_cast<float4*>(V);
 #pragma unroll
             for (int k0 = 0; k0 < KN; k0 += B) {
-                uint4 p[B];
-                float4 m[2 * B], v[2 * B];
+                uint2 p[B];
+                float4 m[B], v[B];
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     const int q = lane + 32 * (k0 + u);
                     if (k0 + u < KN && q < Q) {
-                        p[u] = P8[q];
-                        m[2 * u] = M4[2 * q];
-                        m[2 * u + 1] = M4[2 * q + 1];
-                        v[2 * u] = V4[2 * q];
-                        v[2 * u + 1] = V4[2 * q + 1];
+                        p[u] = P2[q];
+                        m[u] = M4[q];
+                        v[u] = V4[q];
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     const int q = lane + 32 * (k0 + u);
                     if (k0 + u >= KN || q >= Q) continue;
-                    uint32_t* pw = &p[u].x;
-                    float* mm = &m[2 * u].x;
-                    float* vv = &v[2 * u].x;
+                    float x[4] = {tofloat(p[u].x & 0xffffu), tofloat(p[u].x >> 16), tofloat(p[u].y & 0xffffu),
+                                  tofloat(p[u].y >> 16)};
+                    float* mm = &m[u].x;
+                    float* vv = &v[u].x;
+                    // the random bits of the unit's 4 elements: two hashes (base + 4q is even)
+                    const uint32_t k2 = (uint32_t)((base + 4 * q) >> 1);
+                    const uint32_t r01 = pcg_hash(sr + k2), r23 = pcg_hash(sr + k2 + 1u);
+                    const uint32_t rb[4] = {r01 & 0xffffu, r01 >> 16, r23 & 0xffffu, r23 >> 16};
+                    uint32_t h[4];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int e = 8 * q + c;
+                    for (int c = 0; c < 4; ++c) {
+                        const int e = 4 * q + c;
                         const float g = s_grad[(e / W) * GSTRIDE + e % W];
-                        const uint16_t h = (c & 1) ? (uint16_t)(pw[c >> 1] >> 16) : (uint16_t)(pw[c >> 1] & 0xffffu);
-                        float x = tofloat(h);
-                        // m[2u] and m[2u+1] are consecutive in the array of float4s
-                        float& mc = (c < 4) ? mm[c] : (&m[2 * u + 1].x)[c - 4];
-                        float& vc = (c < 4) ? vv[c] : (&v[2 * u + 1].x)[c - 4];
-                        adam_step(x, g, mc, vc, a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
-                        const uint32_t hn = sr_round(x, sr_bits16(sr, (uint32_t)(base + e)), DT);
-                        pw[c >> 1] = (c & 1) ? ((pw[c >> 1] & 0xffffu) | (hn << 16)) : ((pw[c >> 1] & 0xffff0000u) | hn);
+                        adam_step(x[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
+                        h[c] = sr_round(x[c], rb[c], DT);
                         if (gout) gout[base + e] = g;
                     }
-                    P8[q] = p[u];
-                    M4[2 * q] = m[2 * u];
-                    M4[2 * q + 1] = m[2 * u + 1];
-                    V4[2 * q] = v[2 * u];
-                    V4[2 * q + 1] = v[2 * u + 1];
+                    P2[q] = make_uint2(__byte_perm(h[0], h[1], 0x5410), __byte_perm(h[2], h[3], 0x5410));
+                    M4[q] = m[u];
+                    V4[q] = v[u];
                 }
             }
             return;
@@ -1104,7 +1112,7 @@ extern "C" {
 int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* means, const float* log_scales,
                    const float* quats, const float* opacity_logits, const void* sh, const GsCamera* cam,
                    const GsDilation* dil, float* splats, int32_t* radii, int32_t* rects, int32_t* tiles_touched,
-                   gs_stream_t stream)
+                   uint32_t* depth_keys, gs_stream_t stream)
 {
     if (!cam || !dil) { gs_host::set_error("gs_project: camera or dilation is null"); return GS_ERR_ARG; }
     GsView v{};
@@ -1114,6 +1122,7 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype, const float* 
     v.radii = radii;
     v.rects = rects;
     v.tiles_touched = tiles_touched;
+    v.depth_keys = depth_keys;
     return gs_project_batch(n, sh_degree, sh_dtype, means, log_scales, quats, opacity_logits, sh, &v, 1, stream);
 }
 

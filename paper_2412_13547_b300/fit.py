@@ -159,7 +159,9 @@ class Fit:
                 n_old = self.state.n
                 k_seen = int(self.step.num_pairs.max().item())
                 self.state, info = densify_and_prune(self.state, total, c.densify, self.rng)
-                self.rounds.append(dict(views=views, **info))
+                b = self.budget
+                self.rounds.append(dict(views=views, budget=total, alpha=b.alpha, alpha_base=b.alpha_base,
+                                        rate=b.rate, m_adaptive=b.m_adaptive, **info))
                 # pairs grow about like the Gaussians; an overflow below re-measures them
                 cap = int(max(k_seen, 1) * max(1.0, self.state.n / max(1, n_old)) * self.headroom) + 4096
                 self._build(max(cap, self.step.capacity[0]))
@@ -186,6 +188,23 @@ class Fit:
         self.history.append(dict(views=views, seconds=seconds, psnr=psnr(self.state.params, self.eval_cams,
                                                                         self.eval_targets), n=self.state.n))
         return self.history
+
+
+def loglog_fit(steps, ema, skip_frac: float = 0.1):
+    """Fig. 3's check on a fit's smoothed loss: least-squares line of
+    log(EMA loss) against log(step) after the first skip_frac of the steps
+    (the initial stage). Returns (slope, intercept, R^2)."""
+    x = np.log(np.asarray(steps, np.float64))
+    y = np.log(np.maximum(np.asarray(ema, np.float64), 1e-30))
+    k = int(len(x) * skip_frac)
+    x, y = x[k:], y[k:]
+    if len(x) < 3:
+        return 0.0, 0.0, 0.0
+    A = np.c_[x, np.ones_like(x)]
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = y - A @ coef
+    r2 = 1.0 - float(res @ res) / max(float(((y - y.mean()) ** 2).sum()), 1e-300)
+    return float(coef[0]), float(coef[1]), r2
 
 
 def time_to_psnr(history, target_db: float):

@@ -80,6 +80,7 @@ class Rasterizer:
         self.radii = torch.zeros(self.n, dtype=torch.int32, device=self.device)
         self.rects = torch.zeros(self.n, 4, dtype=torch.int32, device=self.device)
         self.tiles_touched = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        self.depth_keys = torch.zeros(self.n, dtype=torch.int32, device=self.device)
         self.grad2d = torch.zeros(self.n, R.GRAD2D_FLOATS, device=self.device)
         self.num_pairs_dev = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.capacity = 0
@@ -122,7 +123,7 @@ class Rasterizer:
     # -- stages ---------------------------------------------------------------
     def project(self, p: GaussianParams, cam, dil: Dilation):
         R.gs_project(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, self.splats,
-                     self.radii, self.rects, self.tiles_touched)
+                     self.radii, self.rects, self.tiles_touched, depth_keys=self.depth_keys)
 
     def bin(self, cam, dil: Dilation):
         w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
@@ -131,7 +132,7 @@ class Rasterizer:
             self.ensure_grid(btx, bty)
         self.ensure_tiles(tx * ty)
         R.gs_bin_sort(self.n, self.rects, self.tiles_touched, self.splats, btx, bty, self.workspace, self.capacity,
-                      self.sorted_ids, self.ranges, self.num_pairs_dev)
+                      self.sorted_ids, self.ranges, self.num_pairs_dev, depth_keys=self.depth_keys)
         if self.longest_first:
             if dil.bin_shift:
                 R.gs_tile_order_batch([R.View(cam, dil, ranges=self.ranges)], self.tile_order)
@@ -241,11 +242,15 @@ class TrainStep:
 
     def __init__(self, params: GaussianParams, rast: Rasterizer, adam: AdamConfig = AdamConfig(),
                  max_pixels: int = 1, bg=(0.0, 0.0, 0.0), densify: bool = True, fused: bool = True,
-                 sparse: bool = False, sr_seed: int = 0x2412):
+                 sparse: bool = False, sr_seed: int = 0x2412, dssim_lambda: float = 0.0):
+        """dssim_lambda > 0 trains with (1 - lambda) L1 + lambda (1 - SSIM)
+        (the 3DGS loss; the paper's is the plain L1, lambda = 0)."""
         dev = params.means.device
         self.p, self.rast, self.adam, self.bg = params, rast, adam, tuple(bg)
         self.fused, self.sparse = bool(fused), bool(sparse)
         self.sr_seed = int(sr_seed)  # stream of the stochastic rounding of low-precision SH
+        self.dssim_lambda = float(dssim_lambda)
+        self.ssim_ws = None
         self.grads = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.m = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
         self.v = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -272,11 +277,21 @@ class TrainStep:
         last = self.last[:P].view(h_ds, w_ds)
         dl = self.dl[:3 * P].view(h_ds, w_ds, 3)
         rast.render(cam, dil, self.bg, img, t_final, last, self.counts if counts else None)
-        R.gs_loss_l1(cam, dil, img, target, dl, self.loss)
+        self.loss_and_grad(cam, dil, img, target, dl)
         rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
         self.step_count += 1
         self.optimize(cam, dil)
         return self.loss
+
+    def loss_and_grad(self, cam, dil: Dilation, img, target, dl):
+        """The photometric loss into self.loss and dL/dimg into dl."""
+        if self.dssim_lambda <= 0.0:
+            R.gs_loss_l1(cam, dil, img, target, dl, self.loss)
+            return
+        need = R.gs_ssim_workspace_size(cam, dil)
+        if self.ssim_ws is None or self.ssim_ws.numel() < need:
+            self.ssim_ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+        R.gs_loss_l1_dssim(cam, dil, img, target, self.dssim_lambda, dl, self.loss, self.ssim_ws)
 
     def optimize(self, cam, dil: Dilation):
         """Projection backward + densification statistics + Adam. The fused
@@ -311,9 +326,10 @@ class TrainStep:
         return 1 + BIN_SORT_KERNELS + 3 * int(self.rast.longest_first) + 1 + 2 + 1 + (1 if self.fused else 2)
 
 
-# kernels in one gs_bin_sort call: depth keys with the pair count, a 4-pass radix sort
-# of the depths (3 kernels a pass), 6 + 2 for the row level, 7 for the tile level
-BIN_SORT_KERNELS = 1 + 4 * 3 + 6 + 2 + 7
+# kernels in one gs_bin_sort call given the projection's depth keys: a 4-pass radix sort
+# of the depths (3 kernels a pass), 6 + 2 for the row level (the row histogram also sums
+# the pair count), 7 for the tile level
+BIN_SORT_KERNELS = 4 * 3 + 6 + 2 + 7
 
 
 # ---------------------------------------------------------------------------
@@ -338,7 +354,7 @@ class BatchTrainStep:
                  bg=(0.0, 0.0, 0.0), densify: bool = True, sparse: bool = False, tile: int = 16,
                  pixels_per_thread: int = 0, center_mode: int = 0, longest_first: bool = True,
                  capacity=None, headroom: float = 1.15, optimize: bool = True, bin_shift: int = 0,
-                 state=None, bwd_pixels_per_thread: int = 0, sr_seed: int = 0x2412):
+                 state=None, bwd_pixels_per_thread: int = 0, sr_seed: int = 0x2412, dssim_lambda: float = 0.0):
         """cams/targets: the views of the batch (any later batch given to
         run(table=views_table(...)) must have no larger images). state: optional
         dict of m, v (lists), pos_acc, col_acc, count and step_dev to continue
@@ -354,6 +370,7 @@ class BatchTrainStep:
         self.bin_shift = int(bin_shift)
         self.longest_first = bool(longest_first)
         self.sr_seed = int(sr_seed)  # stream of the stochastic rounding of low-precision SH
+        self.dssim_lambda = float(dssim_lambda)  # > 0: (1 - lambda) L1 + lambda (1 - SSIM) per view
         n, V = params.n, self.V
         self.targets = [t.contiguous() for t in targets]
         for c, t in zip(self.cams, self.targets):
@@ -363,6 +380,8 @@ class BatchTrainStep:
         self.radii = torch.zeros(V, n, dtype=torch.int32, device=dev)
         self.rects = torch.zeros(V, n, 4, dtype=torch.int32, device=dev)
         self.tiles_touched = torch.zeros(V, n, dtype=torch.int32, device=dev)
+        # rows padded to 16 bytes (the binning reads the keys with 16-byte vectors when aligned)
+        self.depth_keys = torch.zeros(V, (n + 3) // 4 * 4, dtype=torch.int32, device=dev)[:, :n]
         self.grad2d = torch.zeros(V, n, R.GRAD2D_FLOATS, device=dev)
         self.loss = torch.zeros(V, device=dev)
         self.num_pairs = torch.zeros(V, dtype=torch.int64, device=dev)
@@ -397,6 +416,10 @@ class BatchTrainStep:
         self.workspaces = [torch.empty(R.gs_bin_sort_workspace_size(n, c, g[0], g[1]), dtype=torch.uint8, device=dev)
                            for c, g in zip(self.capacity, self.bgrid0)]
         self.bin_streams = [torch.cuda.Stream(device=dev) for _ in range(V)]
+        self.ssim_ws = None
+        if self.dssim_lambda > 0.0:
+            need = max(R.gs_ssim_workspace_size(c, self._dil(0, 0)) for c in self.cams)
+            self.ssim_ws = torch.empty(need, dtype=torch.uint8, device=dev)
 
     @property
     def phases(self) -> int:
@@ -434,7 +457,8 @@ class BatchTrainStep:
                 dil = self._dil(key[0], i)
                 w_ds, h_ds, tx, ty = R.gs_grid(c, dil)
                 v = R.View(c, dil, splats=self.splats[i], radii=self.radii[i], rects=self.rects[i],
-                           tiles_touched=self.tiles_touched[i], grad2d=self.grad2d[i])
+                           tiles_touched=self.tiles_touched[i], grad2d=self.grad2d[i],
+                           depth_keys=self.depth_keys[i])
                 if not project_only:
                     P = w_ds * h_ds
                     v.sorted_ids, v.ranges = self.sorted_ids[i], self.ranges[i]
@@ -466,7 +490,7 @@ class BatchTrainStep:
             with torch.cuda.stream(s):
                 R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty,
                               self.workspaces[i], self.capacity[i], self.sorted_ids[i], self.ranges[i],
-                              self.num_pairs[i:i + 1])
+                              self.num_pairs[i:i + 1], depth_keys=self.depth_keys[i])
         for s in self.bin_streams[:len(t.views)]:
             main.wait_stream(s)
 
@@ -481,7 +505,12 @@ class BatchTrainStep:
             order = self.order
         R.gs_render_fwd_batch(self.p.n, t, self.bg, tile_order=order, counts=self.counts if counts else None,
                               pixels_per_thread=self.ppt)
-        R.gs_loss_l1_batch(t)
+        if self.dssim_lambda > 0.0:
+            # the views share one workspace: their loss calls run in order on this stream
+            for v in t.views:
+                R.gs_loss_l1_dssim(v.cam, v.dil, v.img, v.target, self.dssim_lambda, v.dl_dimg, v.loss, self.ssim_ws)
+        else:
+            R.gs_loss_l1_batch(t)
         if self.longest_first:
             R.gs_tile_order_by_last_batch(t, self.bwd_order)
             order = self.bwd_order

@@ -30,7 +30,7 @@ SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_bin_grid", "gs_project"
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
            "gs_tile_order_batch", "gs_tile_order_by_last_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
            "gs_project_bwd_adam_batch", "gs_densify_workspace_size", "gs_densify_select", "gs_prune_select",
-           "gs_gather_rows", "gs_densify_grow")
+           "gs_gather_rows", "gs_densify_grow", "gs_ssim_workspace_size", "gs_ssim", "gs_loss_l1_dssim")
 
 GS_MAX_ROW_TENSORS = 24
 GS_ROW_COPY, GS_ROW_MEANS, GS_ROW_LOG_SCALES, GS_ROW_QUATS, GS_ROW_STATE, GS_ROW_ZERO = range(6)
@@ -67,7 +67,7 @@ class GsAdamParams(ctypes.Structure):
 
 
 _VIEW_BUFFERS = ("splats", "radii", "rects", "tiles_touched", "sorted_ids", "ranges", "img", "t_final", "last",
-                 "target", "dl_dimg", "grad2d", "loss")
+                 "target", "dl_dimg", "grad2d", "loss", "depth_keys")
 
 
 class GsRowTensor(ctypes.Structure):
@@ -113,6 +113,7 @@ class View:
     dl_dimg: torch.Tensor | None = None
     grad2d: torch.Tensor | None = None
     loss: torch.Tensor | None = None
+    depth_keys: torch.Tensor | None = None
 
 
 class ViewTable:
@@ -169,11 +170,11 @@ def load():
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_grid.argtypes = [cam_p, dil_p, P, P, P, P]
     lib.gs_bin_grid.argtypes = [cam_p, dil_p, P, P]
-    lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P]
+    lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P]
     lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32, i32]
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
-    lib.gs_bin_sort.argtypes = [i32, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
-    lib.gs_bin_sort_static.argtypes = [i32, P, P, P, i32, i32, i64, P, P, P, P]
+    lib.gs_bin_sort.argtypes = [i32, P, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
+    lib.gs_bin_sort_static.argtypes = [i32, P, P, P, P, i32, i32, i64, P, P, P, P]
     lib.gs_tile_order.argtypes = [P, i32, P, P]
     lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P, P]
     lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
@@ -200,8 +201,13 @@ def load():
     rows_p = ctypes.POINTER(GsRowTensor)
     lib.gs_gather_rows.argtypes = [i32, P, rows_p, i32, P]
     lib.gs_densify_grow.argtypes = [i32, i32, P, P, f32, rows_p, i32, P]
+    lib.gs_ssim_workspace_size.argtypes = [cam_p, dil_p]
+    lib.gs_ssim_workspace_size.restype = ctypes.c_size_t
+    lib.gs_ssim.argtypes = [cam_p, dil_p, P, P, i32, P, P, P, ctypes.c_size_t, P]
+    lib.gs_loss_l1_dssim.argtypes = [cam_p, dil_p, P, P, f32, i32, P, P, P, ctypes.c_size_t, P]
     for name in SYMBOLS:
-        if name not in ("gs_last_error", "gs_bin_sort_workspace_size", "gs_densify_workspace_size"):
+        if name not in ("gs_last_error", "gs_bin_sort_workspace_size", "gs_densify_workspace_size",
+                        "gs_ssim_workspace_size"):
             getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -274,15 +280,17 @@ def _need_image(dil, cam, img=None, t_final=None, last=None, dl=None):
 
 
 def gs_project(means, log_scales, quats, opacity_logits, sh, cam, dil: Dilation, splats, radii, rects,
-               tiles_touched, stream=None):
+               tiles_touched, stream=None, depth_keys=None):
+    """depth_keys (optional, n uint32/int32): the depth sort keys for gs_bin_sort."""
     n = means.shape[0]
     deg = sh_degree_of(sh)
     for t, w, name in ((splats, SPLAT_FLOATS, "splats"), (radii, 1, "radii"), (rects, 4, "rects"),
-                       (tiles_touched, 1, "tiles_touched")):
+                       (tiles_touched, 1, "tiles_touched"), (depth_keys, 1, "depth_keys")):
         _need(t, n * w, name)
     _check(load().gs_project(n, deg, _SH_DTYPE[sh.dtype], _ptr(means), _ptr(log_scales), _ptr(quats),
                              _ptr(opacity_logits), _ptr(sh), ctypes.byref(camera(cam)), ctypes.byref(dil.c()),
-                             _ptr(splats), _ptr(radii), _ptr(rects), _ptr(tiles_touched), _stream(stream)),
+                             _ptr(splats), _ptr(radii), _ptr(rects), _ptr(tiles_touched), _ptr(depth_keys),
+                             _stream(stream)),
            "gs_project")
 
 
@@ -291,23 +299,27 @@ def gs_bin_sort_workspace_size(n: int, capacity: int, tiles_x: int, tiles_y: int
 
 
 def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, capacity, sorted_ids, ranges,
-                num_pairs, stream=None):
+                num_pairs, stream=None, depth_keys=None):
+    """depth_keys (optional): gs_project's keys of the same call (saves the pass over splats)."""
     _need(ranges, 2 * int(tiles_x) * int(tiles_y), "ranges")
     _need(sorted_ids, int(capacity), "sorted_ids")
-    _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x), int(tiles_y),
-                              _ptr(workspace), workspace.numel() * workspace.element_size(), int(capacity),
-                              _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)), "gs_bin_sort")
+    _need(depth_keys, int(n), "depth_keys")
+    _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), _ptr(depth_keys),
+                              int(tiles_x), int(tiles_y), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              int(capacity), _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)),
+           "gs_bin_sort")
 
 
 BIN_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def gs_bin_sort_static(n, rects, tiles_touched, splats, tiles_x, tiles_y, capacity, sorted_ids, ranges, num_pairs,
-                       stream=None):
+                       stream=None, depth_keys=None):
     """gs_bin_sort without a workspace argument: for callers that cannot allocate device memory."""
-    _check(load().gs_bin_sort_static(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), int(tiles_x),
-                                     int(tiles_y), int(capacity), _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs),
-                                     _stream(stream)), "gs_bin_sort_static")
+    _need(depth_keys, int(n), "depth_keys")
+    _check(load().gs_bin_sort_static(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), _ptr(depth_keys),
+                                     int(tiles_x), int(tiles_y), int(capacity), _ptr(sorted_ids), _ptr(ranges),
+                                     _ptr(num_pairs), _stream(stream)), "gs_bin_sort_static")
 
 
 def _bg(bg):
@@ -333,6 +345,33 @@ def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
     _need(target, 3 * int(cam.width) * int(cam.height), "target")
     _check(load().gs_loss_l1(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
                              _ptr(dl_dimg), _ptr(loss), _stream(stream)), "gs_loss_l1")
+
+
+SSIM_VALID, SSIM_SAME = 0, 1
+
+
+def gs_ssim_workspace_size(cam, dil: Dilation) -> int:
+    return int(load().gs_ssim_workspace_size(ctypes.byref(camera(cam)), ctypes.byref(dil.c())))
+
+
+def gs_ssim(cam, dil: Dilation, img, target, ssim_out, workspace, d_img=None, mode=SSIM_VALID, stream=None):
+    """Mean SSIM of the lattice image against the sampled target into
+    ssim_out (one float); d_img (optional) receives d(mean SSIM)/d img."""
+    _need_image(dil, cam, img=img, dl=d_img)
+    _need(target, 3 * int(cam.width) * int(cam.height), "target")
+    _check(load().gs_ssim(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target), int(mode),
+                          _ptr(ssim_out), _ptr(d_img), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                          _stream(stream)), "gs_ssim")
+
+
+def gs_loss_l1_dssim(cam, dil: Dilation, img, target, lam, dl_dimg, loss, workspace, mode=SSIM_SAME, stream=None):
+    """(1 - lam) L1 + lam (1 - SSIM) of the lattice image and its gradient."""
+    _need_image(dil, cam, img=img, dl=dl_dimg)
+    _need(target, 3 * int(cam.width) * int(cam.height), "target")
+    _check(load().gs_loss_l1_dssim(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
+                                   float(lam), int(mode), _ptr(dl_dimg), _ptr(loss), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)),
+           "gs_loss_l1_dssim")
 
 
 def gs_render_bwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, t_final, last, dl_dimg, grad2d,

@@ -93,11 +93,11 @@ def test_bad_arguments_are_rejected_before_launch():
     dil = R.GsDilation(1, 0, 0, 0, 16)
     P = ctypes.c_void_p
     # n < 0
-    assert lib.gs_project(-1, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    assert lib.gs_project(-1, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_ERR_ARG
     # sh degree 4
-    assert lib.gs_project(0, 4, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    assert lib.gs_project(0, 4, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_ERR_ARG
     # null pointers with n > 0
-    assert lib.gs_project(5, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_ERR_ARG
+    assert lib.gs_project(5, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_ERR_ARG
     assert "null" in lib.gs_last_error().decode()
     # bad dilation
     bad = R.GsDilation(0, 0, 0, 0, 16)
@@ -112,13 +112,13 @@ def test_bad_arguments_are_rejected_before_launch():
                              P(16), None, 4, None, None) == R.GS_ERR_ARG
     assert lib.gs_tile_order(None, -1, None, None) == R.GS_ERR_ARG
     # capacity >= 2^31
-    assert lib.gs_bin_sort(0, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None) == R.GS_ERR_ARG
+    assert lib.gs_bin_sort(0, None, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None) == R.GS_ERR_ARG
     # adam: too many tensors, bad step
     arr = (R.GsAdamTensor * 9)()
     assert lib.gs_adam(arr, 9, 0.9, 0.999, 1e-8, 1, None, None) == R.GS_ERR_ARG
     assert lib.gs_adam(arr, 1, 0.9, 0.999, 1e-8, 0, None, None) == R.GS_ERR_ARG
     # empty inputs are a no-op success
-    assert lib.gs_project(0, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 4, None) == R.GS_OK
+    assert lib.gs_project(0, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_OK
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

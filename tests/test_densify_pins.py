@@ -221,3 +221,86 @@ def test_time_to_psnr_interpolates_between_evaluations():
     assert time_to_psnr(hist, 22.0) == pytest.approx(5.0)
     assert time_to_psnr(hist, 25.0) == pytest.approx(15.0)
     assert time_to_psnr(hist, 27.0) is None
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1: the oracle's replay pinned by hand, then the host schedule
+# against it
+# ---------------------------------------------------------------------------
+
+def _calls(records, every=400):
+    last = records[-1][0]
+    return list(range(every, last + 1, every))
+
+
+def test_algorithm1_oracle_constant_loss():
+    """A flat loss: every fitted slope is 0, so rate = alpha_base = 0, the final
+    count stays, and alpha = clip(0 + 0.5 tanh(0)) = 0.1, the lower clip."""
+    rec = [(s, 0.25) for s in range(1, 2001)]
+    n0, m = 1000.0, 5000.0
+    out = od.algorithm1(rec, [600, 1200], n0, m, start=500, end=1500)
+    for o, c in zip(out, (600, 1200)):
+        assert o["rate"] == pytest.approx(0.0, abs=1e-12) and o["alpha_base"] == pytest.approx(0.0, abs=1e-12)
+        assert o["M"] == m and o["alpha"] == 0.1
+        t = 1 + 99 * (c - 500) / 1000.0
+        assert o["B"] == pytest.approx(n0 + (t ** 0.1 - 1) / (100 ** 0.1 - 1) * (m - n0), rel=1e-12)
+
+
+def test_algorithm1_oracle_default_exponent_before_three_losses():
+    rec = [(s, 1.0 / s) for s in range(1, 103)]  # steps 101 and 102 recorded after the 100 warm-up steps
+    out = od.algorithm1(rec, [102], 100.0, 300.0, start=0, end=200)
+    assert out[0]["alpha"] == 1.0 and out[0]["M"] == 300.0
+    t = 1 + 99 * 102 / 200.0
+    assert out[0]["B"] == pytest.approx(100.0 + (t - 1) / 99.0 * 200.0, rel=1e-12)
+
+
+def test_algorithm1_oracle_exact_power_laws():
+    """Without smoothing (ema_alpha = 1) a loss s^-0.4 fits slope -0.4 over any
+    window: alpha_base = rate = 0.4, epsilon = 0, alpha = 0.4, and the final
+    count grows x1.1 per call up to 1.5 M. A rising loss s^0.2 has rate -0.2:
+    the count shrinks x0.9 per call down to 0.5 M and alpha clips to 0.1."""
+    calls = [400, 800, 1200, 1600, 2000, 2400]
+    fall = [(s, s ** -0.4) for s in range(1, 2401)]
+    out = od.algorithm1(fall, calls, 10.0, 1000.0, start=0, end=2400, ema_alpha=1.0)
+    for k, o in enumerate(out, start=1):
+        assert o["rate"] == pytest.approx(0.4, rel=1e-9) and o["alpha"] == pytest.approx(0.4, rel=1e-9)
+        assert o["M"] == pytest.approx(min(1000.0 * 1.1 ** k, 1500.0), rel=1e-12)
+    rise = [(s, s ** 0.2) for s in range(1, 2401)]
+    out = od.algorithm1(rise, calls, 10.0, 1000.0, start=0, end=2400, ema_alpha=1.0)
+    for k, o in enumerate(out, start=1):
+        assert o["rate"] == pytest.approx(-0.2, rel=1e-9) and o["alpha"] == 0.1
+        assert o["M"] == pytest.approx(max(1000.0 * 0.9 ** k, 500.0), rel=1e-12)
+
+
+@pytest.mark.parametrize("shape", ["power", "flattening", "rising", "noisy"])
+def test_host_schedule_equals_algorithm1_oracle(shape):
+    """budget.AdaptiveBudget (recorded every step, asked at every round) gives
+    the oracle's alpha, final count and budget at every call."""
+    rng = np.random.default_rng(7)
+    steps = np.arange(1, 4001)
+    if shape == "power":
+        loss = 0.5 * steps ** -0.35
+    elif shape == "flattening":
+        loss = 0.5 * steps ** -0.5 + 0.02
+    elif shape == "rising":
+        loss = 0.1 + 1e-5 * steps
+    else:
+        loss = 0.5 * steps ** -0.3 * np.exp(rng.normal(0, 0.05, steps.size))
+    rec = list(zip(steps.tolist(), loss.tolist()))
+    calls = _calls(rec)
+    n0, m, start, end = 50_000, 400_000, 300, 3000
+    want = od.algorithm1(rec, calls, n0, m, start, end)
+    sched = B.AdaptiveBudget(n0, m, start, end)
+    got = []
+    it = iter(rec)
+    for c in calls:
+        for s, l in it:
+            sched.record(s, l)
+            if s == c:
+                break
+        got.append((sched(c), sched.alpha, sched.m_adaptive, sched.rate))
+    for (b, a, mm, r), w in zip(got, want):
+        assert a == pytest.approx(w["alpha"], rel=1e-9, abs=1e-12)
+        assert mm == pytest.approx(w["M"], rel=1e-12)
+        assert r == pytest.approx(w["rate"], rel=1e-9, abs=1e-12)
+        assert b == int(round(w["B"]))

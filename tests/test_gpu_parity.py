@@ -137,6 +137,48 @@ def test_binning_bitexact_both_paths(dil):
     check_binning(out)
 
 
+@pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0), R.Dilation(2, 1, 1, bin_shift=2)],
+                         ids=["d1", "d2shift2"])
+def test_binning_from_projection_keys_is_identical(dil):
+    """gs_project's depth keys (the float bits of a visible Gaussian's depth,
+    all ones for a culled one) given to gs_bin_sort give the same lists, ranges
+    and pair count, bit for bit, as its own pass over the splat records."""
+    p32, cam, _ = scene_clusters()
+    p = U.gpu_params(p32)
+    n = p.n
+    btx, bty = R.gs_bin_grid(cam, dil)
+    splats = torch.zeros(n, R.SPLAT_FLOATS, device=U.DEV)
+    radii = torch.zeros(n, dtype=torch.int32, device=U.DEV)
+    rects = torch.zeros(n, 4, dtype=torch.int32, device=U.DEV)
+    tiles = torch.zeros(n, dtype=torch.int32, device=U.DEV)
+    # a key array that is 4- but not 16-byte aligned (a row of a batch's key matrix can be)
+    keys = torch.full((n + 1,), 7, dtype=torch.int32, device=U.DEV)[1:]
+    R.gs_project(p.means, p.log_scales, p.quats, p.opacity_logits, p.sh_store, cam, dil, splats, radii, rects, tiles,
+                 depth_keys=keys)
+    k = int(tiles.to(torch.int64).sum().item())
+    cap = k + 1000
+    aligned = torch.empty_like(keys)
+    aligned.copy_(keys)
+    res = []
+    for use_keys in (None, keys, aligned):
+        ws = torch.empty(R.gs_bin_sort_workspace_size(n, cap, btx, bty), dtype=torch.uint8, device=U.DEV)
+        ids = torch.full((cap,), -1, dtype=torch.int32, device=U.DEV)
+        rng = torch.full((btx * bty, 2), -1, dtype=torch.int32, device=U.DEV)
+        num = torch.zeros(1, dtype=torch.int64, device=U.DEV)
+        R.gs_bin_sort(n, rects, tiles, splats, btx, bty, ws, cap, ids, rng, num, depth_keys=use_keys)
+        torch.cuda.synchronize()
+        res.append((num.item(), ids[:k].cpu().numpy(), rng.cpu().numpy()))
+    for r in res[1:]:
+        assert r[0] == res[0][0] == k
+        np.testing.assert_array_equal(r[1], res[0][1])
+        np.testing.assert_array_equal(r[2], res[0][2])
+    kb = keys.cpu().numpy().view(np.uint32)
+    vis = tiles.cpu().numpy() > 0
+    depth_bits = splats[:, 9].cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(kb[vis], np.minimum(depth_bits[vis], 0xFFFFFFFE))
+    assert (kb[~vis] == 0xFFFFFFFF).all() and (~vis).any()
+
+
 def test_binning_equal_depths_keep_index_order():
     """Gaussians with identical depth bits: ties ordered by index."""
     n = 64

@@ -35,7 +35,9 @@ def _values(rng, n, dtype):
 
 def test_pcg_hash_is_uniform_over_consecutive_counters():
     h = lowp.pcg_hash(np.arange(1 << 18, dtype=np.uint64))
-    for part in (h >> np.uint64(24), (h >> np.uint64(16)) & np.uint64(0xFF)):
+    # every byte of the output (both 16-bit halves are used)
+    for part in (h >> np.uint64(24), (h >> np.uint64(16)) & np.uint64(0xFF), (h >> np.uint64(8)) & np.uint64(0xFF),
+                 h & np.uint64(0xFF)):
         counts = np.bincount(part.astype(np.int64), minlength=256)
         exp = h.size / 256.0
         chi2 = float(((counts - exp) ** 2 / exp).sum())
