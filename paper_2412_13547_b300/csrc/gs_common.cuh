@@ -388,7 +388,7 @@ __device__ __forceinline__ uint16_t sr_bf16(float x, uint32_t r)
 // step a power of two). The largest finite magnitude saturates; non-finite:
 // nearest. Out of line: only values outside FP16's normal range come here, and
 // inlined into the unrolled optimizer loops it would crowd the instruction cache.
-__device__ __noinline__ uint16_t sr_f16_general(float x, uint32_t r)
+static __device__ __noinline__ uint16_t sr_f16_general(float x, uint32_t r)
 {
     if (!isfinite(x)) return __half_as_ushort(__float2half_rn(x));
     const uint16_t lb = __half_as_ushort(__float2half_rz(x));
