@@ -742,20 +742,29 @@ def run_reference(args):
         return 0
     from oracle import oracle as orc
     orc.build()
-    vals = []
+    vals, walls = [], []
     info = None
     for i in range(args.warmup + args.steps):
         v, info = oracle_sample(args.n, d=2, n_tiles=args.oracle_tiles, seed=i)
         if i >= args.warmup:
             vals.append(v)
+            walls.append(info["sample_wall_s"])
     value = float(statistics.median(vals))
     cores = info["cores"]
     sample = (f"each step: FP64 oracle projects, back-projects and Adam-steps all {args.n} Gaussians and blends "
               f"(fwd+bwd) {args.oracle_tiles} random 16x16 tiles of the d=2 lattice, scaled to all "
               f"{info['tiles_total']} tiles")
+    # ms_per_step is the measured wall time of one such sampled step (what the run's clock sees);
+    # value is the full step's rate estimated from it (the blend part scaled to every tile)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(statistics.median(walls)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "value_basis": {"kind": "estimated full step from a timed sample",
+                            "full_step_ms_estimate": 1000.0 / value,
+                            "blend_tiles_timed": info["tiles"], "blend_tiles_total": info["tiles_total"],
+                            "blend_scale": info["tiles_total"] / float(info["tiles"]),
+                            "timed_in_full": "projection, projection backward, densification statistics and Adam "
+                                             f"of all {args.n} Gaussians"},
             "config": headline_config("uhd", args.n, 3840, 2160, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

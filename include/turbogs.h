@@ -149,7 +149,9 @@ int32_t gs_project(int32_t n, int32_t sh_degree, int32_t sh_dtype,
  * Outputs (device): sorted_ids (capacity entries; the first num_pairs hold the
  *   Gaussian ids tile by tile, front to back), ranges (tiles_x*tiles_y x 2,
  *   uint32 start/end; (0, 0) for a tile no Gaussian touches), num_pairs (one
- *   int64: the pair count K).
+ *   int64: the pair count K), num_pairs_max (nullable, one int64: raised to K
+ *   when K is larger and never lowered by the library, so that a caller can
+ *   check once, after many calls, that none overflowed its capacity).
  * No host synchronisation: K is computed and consumed on the device. When
  *   K > capacity, *num_pairs still receives K, no pair is written beyond
  *   capacity, every range is set empty (the render then sees no Gaussian) and
@@ -175,7 +177,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
                     const float* splats, const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y,
                     void* workspace, size_t workspace_bytes, int64_t capacity,
                     uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
-                    gs_stream_t stream);
+                    int64_t* num_pairs_max, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_bin_sort_static -- gs_bin_sort for callers that cannot allocate device
@@ -207,7 +209,7 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
                            const float* splats, const uint32_t* depth_keys, int32_t tiles_x,
                            int32_t tiles_y, int64_t capacity,
                            uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs,
-                           gs_stream_t stream);
+                           int64_t* num_pairs_max, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_tile_order -- a launch order for the blend kernels: the tile ids sorted

@@ -792,10 +792,13 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
 }
 
 // Ranges from the tile counts and starts; (0, 0) for empty tiles and on overflow.
+// K_max (nullable): a high-water mark of K across calls, raised here.
 __global__ void k_ranges_from_counts(int T, const uint32_t* __restrict__ count, const uint32_t* __restrict__ start,
-                                     const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges)
+                                     const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges,
+                                     int64_t* __restrict__ K_max)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K_max && t == 0) atomicMax(reinterpret_cast<unsigned long long*>(K_max), (unsigned long long)*d_K);
     if (t >= T) return;
     const bool ok = !overflow(d_K, cap) && count[t] > 0;
     ranges[t] = ok ? make_uint2(start[t], start[t] + count[t]) : make_uint2(0u, 0u);
@@ -877,7 +880,7 @@ size_t gs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t tiles_x, 
 int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
                     const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y, void* workspace,
                     size_t workspace_bytes, int64_t capacity, uint32_t* sorted_ids, uint32_t* ranges,
-                    int64_t* num_pairs, gs_stream_t stream)
+                    int64_t* num_pairs, int64_t* num_pairs_max, gs_stream_t stream)
 {
     using namespace gs;
     if (n < 0 || capacity < 0 || capacity > 0x7fffffffLL || tiles_x <= 0 || tiles_y <= 0 ||
@@ -956,7 +959,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     k_col_base<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, w.segoff, TX, num_pairs,
                                            capacity);
     k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
-                                                         reinterpret_cast<uint2*>(ranges));
+                                                         reinterpret_cast<uint2*>(ranges), num_pairs_max);
     if (capacity > 0)
         k_seg_scatter<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
                                                                w.rowlist, w.M2, num_pairs, capacity, sorted_ids);
@@ -965,7 +968,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
 
 int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles_touched, const float* splats,
                            const uint32_t* depth_keys, int32_t tiles_x, int32_t tiles_y, int64_t capacity,
-                           uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs, gs_stream_t stream)
+                           uint32_t* sorted_ids, uint32_t* ranges, int64_t* num_pairs, int64_t* num_pairs_max,
+                           gs_stream_t stream)
 {
     if (n < 0 || capacity < 0 || tiles_x <= 0 || tiles_y <= 0) {
         gs_host::set_error("gs_bin_sort_static: bad sizes (n >= 0, capacity >= 0, tiles > 0)");
@@ -995,7 +999,8 @@ int32_t gs_bin_sort_static(int32_t n, const int32_t* rects, const int32_t* tiles
         return GS_ERR_CUDA;
     }
     return gs_bin_sort(n, rects, tiles_touched, splats, depth_keys, tiles_x, tiles_y, scratch,
-                       (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES, capacity, sorted_ids, ranges, num_pairs, stream);
+                       (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES, capacity, sorted_ids, ranges, num_pairs,
+                       num_pairs_max, stream);
 }
 
 }  // extern "C"

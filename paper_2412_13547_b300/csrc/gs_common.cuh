@@ -382,37 +382,31 @@ __device__ __forceinline__ uint16_t sr_bf16(float x, uint32_t r)
     return (uint16_t)((b >> 16) + ((b & 0xffffu) > r ? 1u : 0u));
 }
 
-// The same rule for FP16, in general form: the neighbour toward zero lo, the
-// step to the next magnitude, and x's position between them in units of 2^-16
-// of that step (exact: |x| - |lo| is a difference within one binade and the
-// step a power of two). The largest finite magnitude saturates; non-finite:
-// nearest. Out of line: only values outside FP16's normal range come here, and
-// inlined into the unrolled optimizer loops it would crowd the instruction cache.
-static __device__ __noinline__ uint16_t sr_f16_general(float x, uint32_t r)
-{
-    if (!isfinite(x)) return __half_as_ushort(__float2half_rn(x));
-    const uint16_t lb = __half_as_ushort(__float2half_rz(x));
-    if ((lb & 0x7fffu) >= 0x7bffu) return lb;
-    const float lo = fabsf(__half2float(__ushort_as_half(lb)));
-    const float hi = fabsf(__half2float(__ushort_as_half((uint16_t)(lb + 1u))));
-    const float frac = __fdiv_rn(__fsub_rn(fabsf(x), lo), __fsub_rn(hi, lo));
-    const uint32_t pos = (uint32_t)__float2uint_rz(__fmul_rn(frac, 65536.0f));
-    return (uint16_t)(lb + (pos > r ? 1u : 0u));
-}
-
+// The same rule for FP16, in integer arithmetic on x's bits. In FP16's normal
+// range the pattern toward zero keeps the top 10 of x's 23 mantissa bits and
+// the 13 it drops are x's position in units of 2^-13 of the step (<< 3: units
+// of 2^-16). Below it (FP16 subnormals and zero, steps of 2^-24) the position
+// comes from |x| 2^24 = m + f (m the subnormal mantissa; the scaling by a power
+// of two and the difference are exact). Magnitudes from 2^16 saturate at the
+// largest finite value, as does rounding up from it; non-finite: nearest.
 __device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r)
 {
     const uint32_t b = __float_as_uint(x);
+    const uint32_t sign = (b >> 16) & 0x8000u;
     const uint32_t ex = (b >> 23) & 0xffu;
     if (ex - 113u <= 29u) {
-        // FP16's normal range (2^-14 <= |x| < 2^16), in integer arithmetic: the FP16 pattern
-        // toward zero keeps the top 10 of x's 23 mantissa bits, and the 13 it drops are x's
-        // position in units of 2^-13 of the step (<< 3: units of 2^-16)
-        const uint32_t h = ((b >> 16) & 0x8000u) | ((ex - 112u) << 10) | ((b >> 13) & 0x3ffu);
+        const uint32_t h = sign | ((ex - 112u) << 10) | ((b >> 13) & 0x3ffu);
         const uint32_t pos = (b & 0x1fffu) << 3;
         return (uint16_t)(h + ((pos > r && (h & 0x7fffu) != 0x7bffu) ? 1u : 0u));
     }
-    return sr_f16_general(x, r);
+    if (ex < 113u) {
+        const float y = __fmul_rn(fabsf(x), 16777216.0f);
+        const uint32_t m = __float2uint_rz(y);
+        const uint32_t pos = __float2uint_rz(__fmul_rn(__fsub_rn(y, (float)m), 65536.0f));
+        return (uint16_t)((sign | m) + (pos > r ? 1u : 0u));
+    }
+    if (ex == 255u) return __half_as_ushort(__float2half_rn(x));
+    return (uint16_t)(sign | 0x7bffu);
 }
 
 __device__ __forceinline__ uint16_t sr_round(float x, uint32_t r, int dtype)

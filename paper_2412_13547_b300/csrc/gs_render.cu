@@ -322,7 +322,9 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                         lj[k] = j;
                         if constexpr (COUNT) ++n_blend;
                     }
-                    if (!__any_sync(0xffffffffu, n_live > 0)) break;
+                    // no vote per entry on whether the warp still has live pixels: done pixels skip
+                    // their gates above, and the chunk loop votes before the next 32 entries
+                    // (a vote per entry cost 5% of the forward on the 4K step)
                 }
                 if constexpr (COUNT) n_eval += (uint32_t)n_live * (uint32_t)(c1 - next_j);
             }

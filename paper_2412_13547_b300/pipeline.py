@@ -385,6 +385,7 @@ class BatchTrainStep:
         self.grad2d = torch.zeros(V, n, R.GRAD2D_FLOATS, device=dev)
         self.loss = torch.zeros(V, device=dev)
         self.num_pairs = torch.zeros(V, dtype=torch.int64, device=dev)
+        self.num_pairs_max = torch.zeros(V, dtype=torch.int64, device=dev)  # high-water marks since the last check
         self.counts = torch.zeros(3, dtype=torch.int64, device=dev)
         # the largest grid of each view over the offsets (offset 0 renders the most pixels)
         self.grid0 = [R.gs_grid(c, self._dil(0, 0)) for c in self.cams]
@@ -490,7 +491,8 @@ class BatchTrainStep:
             with torch.cuda.stream(s):
                 R.gs_bin_sort(self.p.n, self.rects[i], self.tiles_touched[i], self.splats[i], tx, ty,
                               self.workspaces[i], self.capacity[i], self.sorted_ids[i], self.ranges[i],
-                              self.num_pairs[i:i + 1], depth_keys=self.depth_keys[i])
+                              self.num_pairs[i:i + 1], depth_keys=self.depth_keys[i],
+                              num_pairs_max=self.num_pairs_max[i:i + 1])
         for s in self.bin_streams[:len(t.views)]:
             main.wait_stream(s)
 
@@ -557,9 +559,11 @@ class BatchTrainStep:
         return self.loss
 
     def overflowed(self) -> bool:
-        """True when a view had more pairs than its capacity in the last step
-        (its lists were then left empty). Host synchronisation."""
-        k = self.num_pairs.tolist()
+        """True when a view had more pairs than its capacity in any step since
+        the last call (its lists were then left empty): a high-water mark the
+        binning keeps on the device, read and reset here. Host synchronisation."""
+        k = self.num_pairs_max.tolist()
+        self.num_pairs_max.zero_()
         return any(ki > ci for ki, ci in zip(k, self.capacity))
 
     def launches_per_step(self) -> int:

@@ -173,8 +173,8 @@ def load():
     lib.gs_project.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P]
     lib.gs_bin_sort_workspace_size.argtypes = [i32, i64, i32, i32]
     lib.gs_bin_sort_workspace_size.restype = ctypes.c_size_t
-    lib.gs_bin_sort.argtypes = [i32, P, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P]
-    lib.gs_bin_sort_static.argtypes = [i32, P, P, P, P, i32, i32, i64, P, P, P, P]
+    lib.gs_bin_sort.argtypes = [i32, P, P, P, P, i32, i32, P, ctypes.c_size_t, i64, P, P, P, P, P]
+    lib.gs_bin_sort_static.argtypes = [i32, P, P, P, P, i32, i32, i64, P, P, P, P, P]
     lib.gs_tile_order.argtypes = [P, i32, P, P]
     lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P, P]
     lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
@@ -299,14 +299,16 @@ def gs_bin_sort_workspace_size(n: int, capacity: int, tiles_x: int, tiles_y: int
 
 
 def gs_bin_sort(n, rects, tiles_touched, splats, tiles_x, tiles_y, workspace, capacity, sorted_ids, ranges,
-                num_pairs, stream=None, depth_keys=None):
-    """depth_keys (optional): gs_project's keys of the same call (saves the pass over splats)."""
+                num_pairs, stream=None, depth_keys=None, num_pairs_max=None):
+    """depth_keys (optional): gs_project's keys of the same call (saves the pass over splats);
+    num_pairs_max (optional int64[1]): high-water mark of the pair count across calls."""
     _need(ranges, 2 * int(tiles_x) * int(tiles_y), "ranges")
     _need(sorted_ids, int(capacity), "sorted_ids")
     _need(depth_keys, int(n), "depth_keys")
     _check(load().gs_bin_sort(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), _ptr(depth_keys),
                               int(tiles_x), int(tiles_y), _ptr(workspace), workspace.numel() * workspace.element_size(),
-                              int(capacity), _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _stream(stream)),
+                              int(capacity), _ptr(sorted_ids), _ptr(ranges), _ptr(num_pairs), _ptr(num_pairs_max),
+                              _stream(stream)),
            "gs_bin_sort")
 
 
@@ -319,7 +321,7 @@ def gs_bin_sort_static(n, rects, tiles_touched, splats, tiles_x, tiles_y, capaci
     _need(depth_keys, int(n), "depth_keys")
     _check(load().gs_bin_sort_static(int(n), _ptr(rects), _ptr(tiles_touched), _ptr(splats), _ptr(depth_keys),
                                      int(tiles_x), int(tiles_y), int(capacity), _ptr(sorted_ids), _ptr(ranges),
-                                     _ptr(num_pairs), _stream(stream)), "gs_bin_sort_static")
+                                     _ptr(num_pairs), None, _stream(stream)), "gs_bin_sort_static")
 
 
 def _bg(bg):

@@ -112,7 +112,7 @@ def test_bad_arguments_are_rejected_before_launch():
                              P(16), None, 4, None, None) == R.GS_ERR_ARG
     assert lib.gs_tile_order(None, -1, None, None) == R.GS_ERR_ARG
     # capacity >= 2^31
-    assert lib.gs_bin_sort(0, None, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None) == R.GS_ERR_ARG
+    assert lib.gs_bin_sort(0, None, None, None, None, 1, 1, None, 0, 1 << 31, None, P(16), P(16), None, None) == R.GS_ERR_ARG
     # adam: too many tensors, bad step
     arr = (R.GsAdamTensor * 9)()
     assert lib.gs_adam(arr, 9, 0.9, 0.999, 1e-8, 1, None, None) == R.GS_ERR_ARG

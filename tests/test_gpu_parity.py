@@ -706,6 +706,33 @@ def test_adam_lowp_parity(dtype):
     assert moved > 0.3
 
 
+def test_adam_lowp_fp16_range_edges():
+    """FP16 kept parameters across its range: subnormals and zero, both ends of
+    the normal range and the largest finite value (where rounding up
+    saturates), against the oracle's rounding of the same update."""
+    from oracle import lowp as L
+    base = np.array([0.0, 1e-7, 3e-6, 6.0e-5, 6.2e-5, 1e-3, 1.0, 1000.0, 6.0e4, 65504.0])
+    vals = np.concatenate([base, -base])
+    rng = np.random.default_rng(12)
+    x = np.repeat(vals, 64)
+    p = torch.tensor(x, dtype=torch.float32).to(torch.float16).to(U.DEV)
+    g = rng.standard_normal(x.size).astype(np.float32)
+    m = torch.zeros(x.size, device=U.DEV)
+    v = torch.zeros(x.size, device=U.DEV)
+    st = p.float().cpu().numpy().astype(np.float64)
+    mm, vv = np.zeros(x.size), np.zeros(x.size)
+    for lr in (1e-6,):
+        ref = L.adam_lowp(st, g, mm, vv, lr, 0.9, 0.999, 1e-15, 1, "f16", 321)
+        R.gs_adam([dict(param=p, grad=torch.tensor(g, device=U.DEV), m=m, v=v, lr=lr, sr_seed=321)],
+                  0.9, 0.999, 1e-15, 1)
+        torch.cuda.synchronize()
+        out = p.float().cpu().numpy().astype(np.float64)
+        assert np.isfinite(out).all() and np.abs(out).max() <= 65504.0
+        assert_lowp_close(out, ref, torch.float16, min_exact=0.99)
+        # values far below the update's size move by whole steps in both directions
+        assert (out[np.abs(x) < 1e-5] != st[np.abs(x) < 1e-5]).any()
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_fused_lowp_against_oracle(dtype):
     """The fused optimizer pass with the SH kept only in BF16/FP16, against
@@ -840,6 +867,28 @@ def test_capacity_overflow_then_regrow():
     rast.bin(cam, dil)
     torch.cuda.synchronize()
     assert (rast.ranges[: out["ranges"].shape[0]].cpu().numpy().view(np.uint32) == out_ok["ranges"]).all()
+
+
+def test_pair_count_high_water_mark_is_sticky():
+    """num_pairs_max keeps the largest pair count of all calls: an overflowing
+    call followed by a smaller one still shows the overflow."""
+    p32, cam, _ = scene_small()
+    dil = R.Dilation()
+    out, rast, p, bufs = U.run_forward(p32, cam, dil)
+    k = out["k"]
+    tx, ty = R.gs_bin_grid(cam, dil)
+    mx = torch.zeros(1, dtype=torch.int64, device=U.DEV)
+    num = torch.zeros(1, dtype=torch.int64, device=U.DEV)
+    for cap in (k // 2, k + 10):
+        ws = torch.empty(R.gs_bin_sort_workspace_size(p.n, cap, tx, ty), dtype=torch.uint8, device=U.DEV)
+        ids = torch.empty(cap, dtype=torch.int32, device=U.DEV)
+        R.gs_bin_sort(p.n, rast.rects, rast.tiles_touched, rast.splats, tx, ty, ws, cap, ids, rast.ranges, num,
+                      num_pairs_max=mx)
+    # a call on nothing visible: K = 0 does not lower the mark
+    empty = torch.zeros_like(rast.tiles_touched)
+    R.gs_bin_sort(p.n, rast.rects, empty, rast.splats, tx, ty, ws, k + 10, ids, rast.ranges, num, num_pairs_max=mx)
+    torch.cuda.synchronize()
+    assert num.item() == 0 and mx.item() == k
 
 
 def test_deterministic_forward():
