@@ -313,10 +313,11 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     k = res["pairs_mean"]
     params_b = n * (4 * (3 + 3 + 4 + 1) + sh_bytes)
     rows = {}
-    # projection: parameters in, 48-B splat + radius + rect + tile count out
-    rows["project"] = ("hbm", params_b + n * (48 + 4 + 16 + 4))
-    # binning floor: one read and one write of (key, value) per pair plus the per-Gaussian keys/rects
-    rows["bin_sort"] = ("hbm", 24.0 * k + n * (48 + 16 + 4 + 8))
+    # projection: parameters in, 48-B splat + radius + rect + tile count + depth key out
+    rows["project"] = ("hbm", params_b + n * (48 + 4 + 16 + 4 + 4))
+    # binning floor: one read and one write of (key, value) per pair plus the per-Gaussian depth
+    # key, rect and tile count read and the sorted (key, id) written
+    rows["bin_sort"] = ("hbm", 24.0 * k + n * (4 + 16 + 4 + 8))
     # blend forward: 12 FP32 operations per evaluated (pixel, entry) -- the offset, the
     # exponent (7), its scaling for the SFU exp, alpha, the clamp and the gate -- and 7 more
     # per blended one (transmittance, weight, three colour FMAs, the stop test)

@@ -662,17 +662,12 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
         float* M = a.m[4] + base;
         float* V = a.v[4] + base;
         float* gout = a.gout[4];
+        // the stored value as FP32: a shift for BF16, the conversion instruction for FP16 (one
+        // instruction; an integer form with a branch for subnormals measured slower, 0.881 ->
+        // 0.829 ms)
         auto tofloat = [](uint32_t h) {
-            if constexpr (DT == GS_DTYPE_BF16) {
-                return __uint_as_float(h << 16);
-            } else {
-                // FP16 -> FP32 in integer arithmetic for normal values (exponent rebased by
-                // 127 - 15), the conversion instruction for zeros, subnormals and non-finite
-                const uint32_t ex = h & 0x7c00u;
-                if (ex != 0u && ex != 0x7c00u)
-                    return __uint_as_float(((h & 0x8000u) << 16) | (((h & 0x7fffu) << 13) + 0x38000000u));
-                return __half2float(__ushort_as_half((uint16_t)h));
-            }
+            if constexpr (DT == GS_DTYPE_BF16) return __uint_as_float(h << 16);
+            else return __half2float(__ushort_as_half((uint16_t)h));
         };
         const uintptr_t al = reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(V);
         if (rows == 32 && !a.sparse && (al & 15) == 0 && (reinterpret_cast<uintptr_t>(P) & 7) == 0) {
@@ -682,7 +677,10 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
             uint2* P2 = reinterpret_cast<uint2*>(P);
             float4* M4 = reinterpret_cast<float4*>(M);
             float4* V4 = reinterpret_cast<float4*>(V);
-#pragma unroll
+            // the groups of units one after another (not unrolled): the rounding's integer work
+            // would otherwise crowd the instruction cache (BF16 0.744 -> 0.729 ms, FP16
+            // 0.998 -> 0.881 ms on 3M Gaussians)
+#pragma unroll 1
             for (int k0 = 0; k0 < KN; k0 += B) {
                 uint2 p[B];
                 float4 m[B], v[B];
