@@ -924,6 +924,21 @@ def test_autograd_matches_oracle_gradient():
         assert U.grad_report(name, t.grad.cpu().numpy(), ref[name]) < GRAD_TOL, name
 
 
+def test_autograd_rejects_parameters_changed_in_place():
+    """The parameters go through save_for_backward: changing one in place
+    between the forward and the backward (an optimizer step) is an error, not
+    a silent gradient at the changed values."""
+    from paper_2412_13547_b300.pipeline import rasterize
+    p32, cam, _ = scene_sh3(64, 48)
+    p = U.gpu_params(p32)
+    ts = [t.clone().requires_grad_(True) for t in p.tensors()]
+    img, _, _ = rasterize(*ts, cam, R.Dilation(2, 1, 0))
+    with torch.no_grad():
+        ts[0].add_(1e-3)
+    with pytest.raises(RuntimeError, match="inplace"):
+        img.sum().backward()
+
+
 def test_autograd_finite_differences_hd_64_params():
     """1920x1080, 1M Gaussians, d=2: the autograd.Function gradient of a random
     linear loss against FP64 central differences (the oracle's forward with the
