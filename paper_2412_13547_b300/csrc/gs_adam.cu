@@ -42,6 +42,7 @@ __device__ __forceinline__ void store_shadow(void* shadow, int dtype, int64_t e,
 
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a)
 {
+    kernel_prologue();
     const AdamTensorDev& T = a.t[blockIdx.y];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +148,7 @@ int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float b
     int64_t bx = (max_work + 255) / 256;
     if (bx > 148 * 8) bx = 148 * 8;
     dim3 grid((unsigned)bx, (unsigned)count);
-    k_adam<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    gs::launch(k_adam, grid, 256, 0, reinterpret_cast<cudaStream_t>(stream), a);
     return gs_host::check_launch("gs_adam");
 }
 

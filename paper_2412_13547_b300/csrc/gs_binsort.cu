@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kSortThreads)
 k_radix_upsweep(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d_num, int64_t cap, int shift,
                 uint32_t mask, uint32_t* __restrict__ hist)
 {
+    kernel_prologue();
     __shared__ uint32_t s_hist[kSortWarps][kRadixBins];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * kRadixBins; i += kSortThreads) (&s_hist[0][0])[i] = 0u;
@@ -120,6 +121,7 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scan(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ totals)
 {
+    kernel_prologue();
     __shared__ uint32_t s_tmp[kSortWarps + 1];
     uint32_t* row = hist + (int64_t)blockIdx.x * G;
     const int per = (G + kSortThreads - 1) / kSortThreads;
@@ -146,6 +148,7 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
                   const int64_t* __restrict__ d_num, int64_t cap, int shift, uint32_t mask,
                   const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals)
 {
+    kernel_prologue();
     __shared__ uint32_t s_base[kRadixBins];
     __shared__ uint32_t s_warp[kSortWarps][kRadixBins];
     __shared__ uint32_t s_start[kRadixBins];
@@ -264,10 +267,10 @@ int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, u
     for (int p = 0; p < passes; ++p) {
         int nb = (bits - shift) < per ? (bits - shift) : per;
         uint32_t mask = (nb >= 32) ? 0xffffffffu : ((1u << nb) - 1u);
-        k_radix_upsweep<<<G, kSortThreads, 0, st>>>(ki, d_num, cap, shift, mask, hist);
-        k_radix_scan<<<kRadixBins, kSortThreads, 0, st>>>(hist, G, totals);
+        gs::launch(k_radix_upsweep, G, kSortThreads, 0, st, ki, d_num, cap, shift, mask, hist);
+        gs::launch(k_radix_scan, kRadixBins, kSortThreads, 0, st, hist, G, totals);
         const uint32_t* vin = (p == 0 && b.iota_vals) ? nullptr : vi;
-        k_radix_downsweep<<<G, kSortThreads, 0, st>>>(ki, vin, ko, vo, d_num, cap, shift, mask, hist, totals);
+        gs::launch(k_radix_downsweep, G, kSortThreads, 0, st, ki, vin, ko, vo, d_num, cap, shift, mask, hist, totals);
         // the next pass reads what this one wrote and writes the other set (set 0's keys in k0)
         uint32_t* t = vi; vi = vo; vo = t;
         ki = ko;
@@ -303,6 +306,7 @@ __global__ void __launch_bounds__(kKeyThreads)
 k_depth_keys(int n, const float4* __restrict__ splats, const int* __restrict__ tiles_touched,
              uint32_t* __restrict__ keys)
 {
+    kernel_prologue();
     const int64_t g0 = (int64_t)blockIdx.x * (kKeyThreads * kKeysPerThread) + threadIdx.x;
     int tt[kKeysPerThread];
 #pragma unroll
@@ -466,6 +470,7 @@ __global__ void __launch_bounds__(kLvlThreads)
 k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
            const int4* __restrict__ rects, int TX, int TY, int64_t* __restrict__ d_K, uint32_t* __restrict__ M1)
 {
+    kernel_prologue();
     extern __shared__ int s_lvl[];
     constexpr int U = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -526,6 +531,7 @@ k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict
              const uint32_t* __restrict__ active, const uint32_t* __restrict__ rowbase, int col_div,
              const int64_t* __restrict__ d_K, int64_t cap)
 {
+    kernel_prologue();
     const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
     const int act = active_rows(active, col_div, c, R);
@@ -545,6 +551,7 @@ __global__ void k_col_totals(int R, int Cc, uint32_t* __restrict__ SS, uint32_t*
                              const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
                              int64_t cap)
 {
+    kernel_prologue();
     const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
     const int nsb = (active_rows(active, col_div, c, R) + kScanRows - 1) / kScanRows;
@@ -569,6 +576,7 @@ __global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __
                                                      uint32_t* __restrict__ start, int64_t* __restrict__ sum,
                                                      const int64_t* __restrict__ d_K, int64_t cap)
 {
+    kernel_prologue();
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_carry;
     if (overflow(d_K, cap)) return;
@@ -613,6 +621,7 @@ k_col_base(int R, int Cc, uint32_t* __restrict__ M, const uint32_t* __restrict__
            const uint32_t* __restrict__ start, const uint32_t* __restrict__ active,
            const uint32_t* __restrict__ rowbase, int col_div, const int64_t* __restrict__ d_K, int64_t cap)
 {
+    kernel_prologue();
     const int c = blockIdx.x * kColsPerBlock + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
     const int act = active_rows(active, col_div, c, R);
@@ -643,6 +652,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* 
               const int4* __restrict__ rects, int TX, int TY, const uint32_t* __restrict__ M1,
               const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ rowlist)
 {
+    kernel_prologue();
     extern __shared__ int s_lvl[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * kLvlWarps + warp;
@@ -676,6 +686,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* 
 __global__ void k_row_segments(int TY, const uint32_t* __restrict__ rowlen, uint32_t* __restrict__ nseg,
                                const int64_t* __restrict__ d_K, int64_t cap)
 {
+    kernel_prologue();
     const int ty = blockIdx.x * blockDim.x + threadIdx.x;
     if (ty >= TY || overflow(d_K, cap)) return;
     nseg[ty] = (rowlen[ty] + kSegLen - 1) / kSegLen;
@@ -701,6 +712,7 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
            const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS, const uint2* __restrict__ rowlist,
            const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ M2)
 {
+    kernel_prologue();
     extern __shared__ int s_lvl[];
     if (overflow(d_K, cap)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -739,6 +751,7 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
               const uint2* __restrict__ rowlist, const uint32_t* __restrict__ M2,
               const int64_t* __restrict__ d_K, int64_t cap, uint32_t* __restrict__ out)
 {
+    kernel_prologue();
     extern __shared__ int s_lvl[];
     if (overflow(d_K, cap)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -797,6 +810,7 @@ __global__ void k_ranges_from_counts(int T, const uint32_t* __restrict__ count, 
                                      const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges,
                                      int64_t* __restrict__ K_max)
 {
+    kernel_prologue();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (K_max && t == 0) atomicMax(reinterpret_cast<unsigned long long*>(K_max), (unsigned long long)*d_K);
     if (t >= T) return;
@@ -913,8 +927,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     // projection's keys or from a pass over the splat records
     const uint32_t* keys_in = depth_keys;
     if (!keys_in) {
-        k_depth_keys<<<(n + kKeyThreads * kKeysPerThread - 1) / (kKeyThreads * kKeysPerThread), kKeyThreads, 0,
-                       st>>>(n, reinterpret_cast<const float4*>(splats), tiles_touched, w.dkeys0);
+        gs::launch(k_depth_keys, (n + kKeyThreads * kKeysPerThread - 1) / (kKeyThreads * kKeysPerThread), kKeyThreads,
+                   0, st, n, reinterpret_cast<const float4*>(splats), tiles_touched, w.dkeys0);
         keys_in = w.dkeys0;
     }
     radix_sort(SortBufs{const_cast<uint32_t*>(keys_in), w.perm0, w.dkeys1, w.perm1, true, w.dkeys0}, nullptr, n,
@@ -927,19 +941,20 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     }
-    k_row_hist<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs, w.M1);
+    gs::launch(k_row_hist, lvl1_blocks, kLvlThreads, smem1, st, n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs, w.M1);
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
     const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb1, kScanGridY));
-    k_col_segsum<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
-    k_col_totals<<<(TY * 32 + 255) / 256, 256, 0, st>>>(C1, TY, w.SS1, w.rowlen, nullptr, 1, num_pairs, capacity);
-    k_scan_small<<<1, 1024, 0, st>>>(TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
-    k_col_base<<<g1, kLvlThreads, 0, st>>>(C1, TY, w.M1, w.SS1, w.rowstart, nullptr, nullptr, 1, num_pairs,
-                                           capacity);
-    k_row_scatter<<<lvl1_blocks, kLvlThreads, smem1, st>>>(n, C1, w.perm0, w.dkeys0, rc, TX, TY, w.M1,
-                                                           num_pairs, capacity, w.rowlist);
+    gs::launch(k_col_segsum, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
+    gs::launch(k_col_totals, (TY * 32 + 255) / 256, 256, 0, st, C1, TY, w.SS1, w.rowlen, nullptr, 1, num_pairs,
+               capacity);
+    gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
+    gs::launch(k_col_base, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, w.rowstart, nullptr, nullptr, 1, num_pairs,
+               capacity);
+    gs::launch(k_row_scatter, lvl1_blocks, kLvlThreads, smem1, st, n, C1, w.perm0, w.dkeys0, rc, TX, TY, w.M1,
+               num_pairs, capacity, w.rowlist);
     // level 2: tiles within each row
-    k_row_segments<<<(TY + 255) / 256, 256, 0, st>>>(TY, w.rowlen, w.nseg, num_pairs, capacity);
-    k_scan_small<<<1, 1024, 0, st>>>(TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
+    gs::launch(k_row_segments, (TY + 255) / 256, 256, 0, st, TY, w.rowlen, w.nseg, num_pairs, capacity);
+    gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
     const int NSR = lvl2_rows(n);
     const size_t smem2 = (size_t)kLvlWarps * (TX + 1 + 64) * sizeof(int);
     const size_t smem2h = (size_t)(TX + 1) * sizeof(int);
@@ -948,21 +963,21 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     }
     const int lvl2_blocks = 148 * 8;
-    k_seg_hist<<<lvl2_blocks, kLvlThreads, smem2h, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS, w.rowlist,
-                                                        num_pairs, capacity, w.M2);
+    gs::launch(k_seg_hist, lvl2_blocks, kLvlThreads, smem2h, st, TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
+               w.rowlist, num_pairs, capacity, w.M2);
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;
     const dim3 g2((T + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb2, kScanGridY));
-    k_col_segsum<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.nseg, w.segoff, TX, num_pairs, capacity);
-    k_col_totals<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(NSR, T, w.SS2, w.tcount, w.nseg, TX, num_pairs,
-                                                                      capacity);
-    k_scan_small<<<1, 1024, 0, st>>>(T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
-    k_col_base<<<g2, kLvlThreads, 0, st>>>(NSR, T, w.M2, w.SS2, w.tstart, w.nseg, w.segoff, TX, num_pairs,
-                                           capacity);
-    k_ranges_from_counts<<<(T + 255) / 256, 256, 0, st>>>(T, w.tcount, w.tstart, num_pairs, capacity,
-                                                         reinterpret_cast<uint2*>(ranges), num_pairs_max);
+    gs::launch(k_col_segsum, g2, kLvlThreads, 0, st, NSR, T, w.M2, w.SS2, w.nseg, w.segoff, TX, num_pairs, capacity);
+    gs::launch(k_col_totals, (int)(((int64_t)T * 32 + 255) / 256), 256, 0, st, NSR, T, w.SS2, w.tcount, w.nseg, TX,
+               num_pairs, capacity);
+    gs::launch(k_scan_small, 1, 1024, 0, st, T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
+    gs::launch(k_col_base, g2, kLvlThreads, 0, st, NSR, T, w.M2, w.SS2, w.tstart, w.nseg, w.segoff, TX, num_pairs,
+               capacity);
+    gs::launch(k_ranges_from_counts, (T + 255) / 256, 256, 0, st, T, w.tcount, w.tstart, num_pairs, capacity,
+               reinterpret_cast<uint2*>(ranges), num_pairs_max);
     if (capacity > 0)
-        k_seg_scatter<<<lvl2_blocks, kLvlThreads, smem2, st>>>(TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
-                                                               w.rowlist, w.M2, num_pairs, capacity, sorted_ids);
+        gs::launch(k_seg_scatter, lvl2_blocks, kLvlThreads, smem2, st, TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
+                   w.rowlist, w.M2, num_pairs, capacity, sorted_ids);
     return gs_host::check_launch("gs_bin_sort");
 }
 

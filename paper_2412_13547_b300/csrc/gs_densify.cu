@@ -93,6 +93,7 @@ __device__ __forceinline__ int block_rank(bool flag, int* s_warp, int* block_tot
 __global__ void __launch_bounds__(kBlk) k_scan_blocks(int nb, const int* __restrict__ cnt, int* __restrict__ base,
                                                       int* __restrict__ total)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     int run = 0;
     for (int b0 = 0; b0 < nb; b0 += kBlk) {
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_keys(int n, const float* __restrict
                                                   int branch, unsigned* __restrict__ keys, unsigned* __restrict__ hist,
                                                   SelState* __restrict__ st)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     unsigned k = 0u;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_keys(int n, const float* __restrict
 __global__ void __launch_bounds__(kBlk) k_ds_find(int max_new, int phase, const unsigned* __restrict__ hist,
                                                   SelState* __restrict__ st)
 {
+    kernel_prologue();
     __shared__ unsigned s_part[kBlk];
     constexpr int PER = kHistBins / kBlk;  // 64 bins per thread, thread 0 holds the top bins
     if (phase == 0 && st->candidates <= max_new) {
@@ -216,6 +219,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_find(int max_new, int phase, const 
 __global__ void __launch_bounds__(kBlk) k_ds_hist_lo(int n, const unsigned* __restrict__ keys,
                                                      unsigned* __restrict__ hist, const SelState* __restrict__ st)
 {
+    kernel_prologue();
     if (st->all) return;
     const int i = blockIdx.x * kBlk + threadIdx.x;
     if (i >= n) return;
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_hist_lo(int n, const unsigned* __re
 __global__ void __launch_bounds__(kBlk) k_ds_count_eq(int n, const unsigned* __restrict__ keys,
                                                       const SelState* __restrict__ st, int* __restrict__ blk)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     const bool eq = !st->all && i < n && keys[i] == st->thr;
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_rank_eq(int n, const unsigned* __re
                                                      const SelState* __restrict__ st, const int* __restrict__ base_eq,
                                                      int* __restrict__ rank_eq, int* __restrict__ blk)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     const bool eq = !st->all && i < n && keys[i] == st->thr;
@@ -266,6 +272,7 @@ __global__ void __launch_bounds__(kBlk) k_ds_write(int n, const unsigned* __rest
                                                    const int* __restrict__ rank_eq, const SelState* __restrict__ st,
                                                    const int* __restrict__ base, int* __restrict__ out)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     const bool sel = selected_flag(i, n, keys, rank_eq, st);
@@ -291,6 +298,7 @@ __global__ void __launch_bounds__(kBlk) k_keep_count(int n, const float* __restr
                                                      const float* __restrict__ ls, float ls_max,
                                                      int* __restrict__ blk)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     int tot;
@@ -302,6 +310,7 @@ __global__ void __launch_bounds__(kBlk) k_keep_write(int n, const float* __restr
                                                      const float* __restrict__ ls, float ls_max,
                                                      const int* __restrict__ base, int* __restrict__ out)
 {
+    kernel_prologue();
     __shared__ int s_warp[33];
     const int i = blockIdx.x * kBlk + threadIdx.x;
     const bool k = keep_flag(i, n, logits, logit_min, ls, ls_max);
@@ -321,6 +330,7 @@ __global__ void k_rows(int n_out, int n_old, const int* __restrict__ index, cons
                        const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, int words, int zero_new,
                        int zero_all)
 {
+    kernel_prologue();
     const int64_t total = (int64_t)n_out * words;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -359,6 +369,7 @@ struct SplitArgs {
 __global__ void k_split(int n_old, int m, const int* __restrict__ selected, const float* __restrict__ noise,
                         float log_split, SplitArgs a)
 {
+    kernel_prologue();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     const int g = selected[j];
@@ -443,17 +454,17 @@ int32_t gs_densify_select(int32_t n, const float* pos_acc, const float* col_acc,
     const int nb = (n + kBlk - 1) / kBlk;
     cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * kHistBins, st);
     cudaMemsetAsync(w.st, 0, sizeof(SelState), st);
-    k_ds_keys<<<nb, kBlk, 0, st>>>(n, pos_acc, col_acc, count, tau_pos, tau_color, color_branch, w.keys, w.hist,
-                                   w.st);
-    k_ds_find<<<1, kBlk, 0, st>>>(max_new, 0, w.hist, w.st);
+    gs::launch(k_ds_keys, nb, kBlk, 0, st, n, pos_acc, col_acc, count, tau_pos, tau_color, color_branch, w.keys,
+               w.hist, w.st);
+    gs::launch(k_ds_find, 1, kBlk, 0, st, max_new, 0, w.hist, w.st);
     cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * kHistBins, st);
-    k_ds_hist_lo<<<nb, kBlk, 0, st>>>(n, w.keys, w.hist, w.st);
-    k_ds_find<<<1, kBlk, 0, st>>>(max_new, 1, w.hist, w.st);
-    k_ds_count_eq<<<nb, kBlk, 0, st>>>(n, w.keys, w.st, w.blk);
-    k_scan_blocks<<<1, kBlk, 0, st>>>(nb, w.blk, w.blk_base, nullptr);
-    k_ds_rank_eq<<<nb, kBlk, 0, st>>>(n, w.keys, w.st, w.blk_base, w.rank, w.blk);
-    k_scan_blocks<<<1, kBlk, 0, st>>>(nb, w.blk, w.blk_base, num_selected);
-    k_ds_write<<<nb, kBlk, 0, st>>>(n, w.keys, w.rank, w.st, w.blk_base, selected);
+    gs::launch(k_ds_hist_lo, nb, kBlk, 0, st, n, w.keys, w.hist, w.st);
+    gs::launch(k_ds_find, 1, kBlk, 0, st, max_new, 1, w.hist, w.st);
+    gs::launch(k_ds_count_eq, nb, kBlk, 0, st, n, w.keys, w.st, w.blk);
+    gs::launch(k_scan_blocks, 1, kBlk, 0, st, nb, w.blk, w.blk_base, nullptr);
+    gs::launch(k_ds_rank_eq, nb, kBlk, 0, st, n, w.keys, w.st, w.blk_base, w.rank, w.blk);
+    gs::launch(k_scan_blocks, 1, kBlk, 0, st, nb, w.blk, w.blk_base, num_selected);
+    gs::launch(k_ds_write, nb, kBlk, 0, st, n, w.keys, w.rank, w.st, w.blk_base, selected);
     return gs_host::check_launch("gs_densify_select");
 }
 
@@ -477,9 +488,10 @@ int32_t gs_prune_select(int32_t n, const float* opacity_logits, float logit_min,
         return GS_ERR_ARG;
     }
     const int nb = (n + kBlk - 1) / kBlk;
-    k_keep_count<<<nb, kBlk, 0, st>>>(n, opacity_logits, logit_min, log_scales, log_scale_max, w.blk);
-    k_scan_blocks<<<1, kBlk, 0, st>>>(nb, w.blk, w.blk_base, num_keep);
-    k_keep_write<<<nb, kBlk, 0, st>>>(n, opacity_logits, logit_min, log_scales, log_scale_max, w.blk_base, keep);
+    gs::launch(k_keep_count, nb, kBlk, 0, st, n, opacity_logits, logit_min, log_scales, log_scale_max, w.blk);
+    gs::launch(k_scan_blocks, 1, kBlk, 0, st, nb, w.blk, w.blk_base, num_keep);
+    gs::launch(k_keep_write, nb, kBlk, 0, st, n, opacity_logits, logit_min, log_scales, log_scale_max, w.blk_base,
+               keep);
     return gs_host::check_launch("gs_prune_select");
 }
 
@@ -495,9 +507,9 @@ int32_t gs_gather_rows(int32_t n_out, const int32_t* index, const GsRowTensor* t
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int t = 0; t < count; ++t) {
         const int words = tensors[t].row_bytes / 4;
-        k_rows<<<grid_for((int64_t)n_out * words), 256, 0, st>>>(
-            n_out, 0, index, nullptr, static_cast<const uint32_t*>(tensors[t].src),
-            static_cast<uint32_t*>(tensors[t].dst), words, 0, tensors[t].role == GS_ROW_ZERO);
+        gs::launch(k_rows, grid_for((int64_t)n_out * words), 256, 0, st, n_out, 0, index, nullptr,
+                   static_cast<const uint32_t*>(tensors[t].src), static_cast<uint32_t*>(tensors[t].dst), words, 0,
+                   tensors[t].role == GS_ROW_ZERO);
     }
     return gs_host::check_launch("gs_gather_rows");
 }
@@ -549,12 +561,11 @@ int32_t gs_densify_grow(int32_t n_old, int32_t m, const int32_t* selected, const
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int t = 0; t < count; ++t) {
         const int words = tensors[t].row_bytes / 4;
-        k_rows<<<grid_for((int64_t)n_new * words), 256, 0, st>>>(
-            n_new, n_old, nullptr, selected, static_cast<const uint32_t*>(tensors[t].src),
-            static_cast<uint32_t*>(tensors[t].dst), words, tensors[t].role == GS_ROW_STATE,
-            tensors[t].role == GS_ROW_ZERO);
+        gs::launch(k_rows, grid_for((int64_t)n_new * words), 256, 0, st, n_new, n_old, nullptr, selected,
+                   static_cast<const uint32_t*>(tensors[t].src), static_cast<uint32_t*>(tensors[t].dst), words,
+                   tensors[t].role == GS_ROW_STATE, tensors[t].role == GS_ROW_ZERO);
     }
-    if (m > 0) k_split<<<(m + 255) / 256, 256, 0, st>>>(n_old, m, selected, noise, log_split_scale, sa);
+    if (m > 0) gs::launch(k_split, (m + 255) / 256, 256, 0, st, n_old, m, selected, noise, log_split_scale, sa);
     return gs_host::check_launch("gs_densify_grow");
 }
 

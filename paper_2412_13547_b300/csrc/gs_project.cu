@@ -292,6 +292,7 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
           const float4* __restrict__ quats, const float* __restrict__ logits, const void* __restrict__ sh,
           const __grid_constant__ Batch b)
 {
+    kernel_prologue();
     using L = ShLayout<DEG, DT>;
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -471,6 +472,7 @@ k_project_bwd(int n, const float* __restrict__ means, const float* __restrict__ 
               float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pos_acc,
               float* __restrict__ col_acc, int* __restrict__ count)
 {
+    kernel_prologue();
     using L = ShLayout<DEG, DT>;
     constexpr int K = L::K;
     extern __shared__ uint32_t smem[];
@@ -874,6 +876,7 @@ __global__ void __launch_bounds__(kThreads, MULTI ? 4 : 5)
 k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b, AdamDev a,
                    float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
 {
+    kernel_prologue();
     using L = ShLayout<DEG, DT>;
     using F = FusedLayout<DEG, DT>;
     extern __shared__ uint32_t smem[];
@@ -1008,6 +1011,7 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
 // new step, evaluated in double like the host path.
 __global__ void k_adam_advance(int* step, float b1, float b2, float* bias)
 {
+    kernel_prologue();
     const int t = *step + 1;
     *step = t;
     bias[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
@@ -1017,6 +1021,7 @@ __global__ void k_adam_advance(int* step, float b1, float b2, float* bias)
 __global__ void k_densify(int n, const int* __restrict__ tiles_touched, const float4* __restrict__ grad2d,
                           float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
 {
+    kernel_prologue();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n || tiles_touched[g] <= 0) return;
     float4 G0 = grad2d[3 * (int64_t)g], G1 = grad2d[3 * (int64_t)g + 1], G2 = grad2d[3 * (int64_t)g + 2];
@@ -1037,8 +1042,8 @@ int32_t launch_project(int n, const float* means, const float* log_scales, const
     auto kern = b.nviews > 1 ? k_project<DEG, DT, true> : k_project<DEG, DT, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,
-                                         b);
+    gs::launch(kern, blocks, kThreads, smem, st, n, means, log_scales, reinterpret_cast<const float4*>(quats), logits,
+               sh, b);
     return gs_host::check_launch("gs_project");
 }
 
@@ -1053,9 +1058,9 @@ int32_t launch_project_bwd(int n, const float* means, const float* log_scales, c
     auto kern = k_project_bwd<DEG, DT>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    kern<<<blocks, kThreads, smem, st>>>(n, means, log_scales, reinterpret_cast<const float4*>(quats), logits, sh,
-                                         cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
-                                         reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
+    gs::launch(kern, blocks, kThreads, smem, st, n, means, log_scales, reinterpret_cast<const float4*>(quats), logits,
+               sh, cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
+               reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd");
 }
 
@@ -1068,7 +1073,7 @@ int32_t launch_project_bwd_adam(int n, const void* sh_store, const Batch& b, con
     auto kern = b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    kern<<<blocks, kThreads, smem, st>>>(n, sh_store, b, a, pos, col, cnt);
+    gs::launch(kern, blocks, kThreads, smem, st, n, sh_store, b, a, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd_adam");
 }
 
@@ -1275,7 +1280,7 @@ int32_t gs_adam_advance(int32_t* step_dev, float beta1, float beta2, float* bias
         gs_host::set_error("gs_adam_advance: need device step and bias pointers and 0 <= beta < 1");
         return GS_ERR_ARG;
     }
-    gs::k_adam_advance<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(step_dev, beta1, beta2, bias_dev);
+    gs::launch(gs::k_adam_advance, 1, 1, 0, reinterpret_cast<cudaStream_t>(stream), step_dev, beta1, beta2, bias_dev);
     return gs_host::check_launch("gs_adam_advance");
 }
 
@@ -1292,8 +1297,8 @@ int32_t gs_densify_stats(int32_t n, const int32_t* tiles_touched, const float* g
         return GS_ERR_ARG;
     }
     if (n == 0) return GS_OK;
-    gs::k_densify<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        n, tiles_touched, reinterpret_cast<const float4*>(grad2d), pos_acc, col_acc, count);
+    gs::launch(gs::k_densify, (n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream), n, tiles_touched,
+               reinterpret_cast<const float4*>(grad2d), pos_acc, col_acc, count);
     return gs_host::check_launch("gs_densify_stats");
 }
 

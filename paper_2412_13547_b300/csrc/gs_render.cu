@@ -672,6 +672,7 @@ __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (fwd_min_blocks<
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
              unsigned long long* __restrict__ counts)
 {
+    kernel_prologue();
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
     render_fwd_tile<TILE, PPT, FILTER, COUNT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img,
@@ -682,6 +683,7 @@ template <int TILE, int PPT, bool MULTI, bool FILTER>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (bwd_min_blocks<TILE, PPT>()))
 k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg)
 {
+    kernel_prologue();
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
     render_bwd_tile<TILE, PPT, FILTER>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.t_final, V.last,
@@ -690,6 +692,7 @@ k_render_bwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order
 
 __global__ void k_loss_zero(const __grid_constant__ Batch b)
 {
+    kernel_prologue();
     if ((int)threadIdx.x < b.nviews) *b.v[threadIdx.x].loss = 0.0f;
 }
 
@@ -697,6 +700,7 @@ __global__ void k_loss_zero(const __grid_constant__ Batch b)
 // rendered pixels, against the hr target sampled at the view's lattice.
 __global__ void k_loss_l1(const __grid_constant__ Batch b)
 {
+    kernel_prologue();
     const ViewDev& V = b.v[blockIdx.y];
     const Dil& dil = V.dil;
     const int width = V.cam.width;
@@ -819,6 +823,7 @@ __device__ __forceinline__ void order_from_buckets(int T, const uint8_t* s_b, ui
 // the buckets are computed once into dynamic shared memory (T bytes).
 __global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Batch b, uint32_t* __restrict__ order)
 {
+    kernel_prologue();
     extern __shared__ uint8_t s_bkt[];
     const int T = b.total_tiles;
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
@@ -834,6 +839,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const __grid_constant__ Bat
 // written to key[global tile].
 __global__ void __launch_bounds__(256) k_tile_last_max(const __grid_constant__ Batch b, uint32_t* __restrict__ key)
 {
+    kernel_prologue();
     const int gt = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (gt >= b.total_tiles) return;  // uniform over the warp
     const ViewDev& V = b.v[view_of_tile(b, gt)];
@@ -858,6 +864,7 @@ __global__ void __launch_bounds__(256) k_tile_last_max(const __grid_constant__ B
 __global__ void __launch_bounds__(1024) k_tile_order_global(const __grid_constant__ Batch b,
                                                             uint32_t* __restrict__ order)
 {
+    kernel_prologue();
     const int T = b.total_tiles;
     __shared__ uint32_t s_hist[256];
     __shared__ uint32_t s_off[256];
@@ -878,6 +885,7 @@ __global__ void __launch_bounds__(1024) k_tile_order_global(const __grid_constan
 
 __global__ void __launch_bounds__(1024) k_tile_order_keys(int T, uint32_t* __restrict__ order)
 {
+    kernel_prologue();
     extern __shared__ uint8_t s_bkt[];
     for (int t = threadIdx.x; t < T; t += blockDim.x) s_bkt[t] = (uint8_t)order_bucket(order[t]);
     __syncthreads();
@@ -892,9 +900,9 @@ int32_t launch_tile_order(const Batch& b, uint32_t* order, cudaStream_t st, cons
     const int T = b.total_tiles;
     if (T <= kMaxKeyedOrderTiles) {
         if (T > 48 * 1024) cudaFuncSetAttribute(k_tile_order, cudaFuncAttributeMaxDynamicSharedMemorySize, T);
-        k_tile_order<<<1, 1024, (size_t)T, st>>>(b, order);
+        gs::launch(k_tile_order, 1, 1024, (size_t)T, st, b, order);
     } else {
-        k_tile_order_global<<<1, 1024, 0, st>>>(b, order);
+        gs::launch(k_tile_order_global, 1, 1024, 0, st, b, order);
     }
     return gs_host::check_launch(what);
 }
@@ -929,7 +937,7 @@ void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long 
         : (multi ? (filter ? k_render_fwd<TILE, PPT, true, true, false> : k_render_fwd<TILE, PPT, true, false, false>)
                  : (filter ? k_render_fwd<TILE, PPT, false, true, false>
                            : k_render_fwd<TILE, PPT, false, false, false>));
-    kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg, counts);
+    gs::launch(kern, b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st, b, order, bg, counts);
 }
 
 template <int TILE, int PPT>
@@ -938,7 +946,7 @@ void launch_bwd(const Batch& b, const uint32_t* order, float3 bg, cudaStream_t s
     const bool multi = b.nviews > 1, filter = any_shift(b);
     auto kern = multi ? (filter ? k_render_bwd<TILE, PPT, true, true> : k_render_bwd<TILE, PPT, true, false>)
                       : (filter ? k_render_bwd<TILE, PPT, false, true> : k_render_bwd<TILE, PPT, false, false>);
-    kern<<<b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st>>>(b, order, bg);
+    gs::launch(kern, b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st, b, order, bg);
 }
 
 // The instantiated (tile, pixels per thread) pairs.
@@ -1100,9 +1108,9 @@ int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (T > kMaxKeyedOrderTiles)  // more tiles than shared memory holds buckets for: the list-length order
         return launch_tile_order(b, order, st, "gs_tile_order_by_last_batch");
-    k_tile_last_max<<<(int)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(b, order);
+    gs::launch(k_tile_last_max, (int)(((int64_t)T * 32 + 255) / 256), 256, 0, st, b, order);
     if (T > 48 * 1024) cudaFuncSetAttribute(k_tile_order_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, T);
-    k_tile_order_keys<<<1, 1024, (size_t)T, st>>>(T, order);
+    gs::launch(k_tile_order_keys, 1, 1024, (size_t)T, st, T, order);
     return gs_host::check_launch("gs_tile_order_by_last_batch");
 }
 
@@ -1134,11 +1142,11 @@ int32_t gs_loss_l1_batch(const GsView* views, int32_t nviews, gs_stream_t stream
         if (P > pmax) pmax = P;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    k_loss_zero<<<1, 32, 0, st>>>(b);
+    gs::launch(k_loss_zero, 1, 32, 0, st, b);
     int64_t bx = (pmax + 255) / 256;
     const int64_t cap = (148 * 16 + nviews - 1) / nviews;
     if (bx > cap) bx = cap;
-    k_loss_l1<<<dim3((unsigned)bx, (unsigned)nviews), 256, 0, st>>>(b);
+    gs::launch(k_loss_l1, dim3((unsigned)bx, (unsigned)nviews), 256, 0, st, b);
     return gs_host::check_launch("gs_loss_l1");
 }
 

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_fwd(Lattice L, const float* __restrict__ img, const float* __restrict__ target, float* __restrict__ part,
            double* __restrict__ acc)
 {
+    kernel_prologue();
     __shared__ float s_w[kTaps];
     __shared__ float s_x[kIH][kIW], s_y[kIH][kIW];
     __shared__ float s_h[5][kIH][kTW];
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kSsimThreads)
 k_ssim_bwd(Lattice L, const float* __restrict__ img, const float* __restrict__ target,
            const float* __restrict__ part, float ssim_scale, float l1_scale, float* __restrict__ out)
 {
+    kernel_prologue();
     __shared__ float s_w[kTaps];
     __shared__ float s_p[3][kIH][kIW];
     __shared__ float s_h[3][kIH][kTW];
@@ -218,6 +220,7 @@ k_ssim_bwd(Lattice L, const float* __restrict__ img, const float* __restrict__ t
 __global__ void k_ssim_final(const double* __restrict__ acc, Lattice L, float lambda, float* __restrict__ ssim_out,
                              float* __restrict__ loss)
 {
+    kernel_prologue();
     const double s = acc[0] * (double)L.inv_n;
     const double l1 = acc[1] * (double)L.inv_p3;
     if (ssim_out) *ssim_out = (float)s;
@@ -267,14 +270,14 @@ int32_t run_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, c
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
     const dim3 grid((L.w + kTW - 1) / kTW, (L.h + kTH - 1) / kTH);
-    k_ssim_fwd<<<grid, kSsimThreads, 0, st>>>(L, img, target, part, acc);
+    gs::launch(k_ssim_fwd, grid, kSsimThreads, 0, st, L, img, target, part, acc);
     if (grad) {
         // loss form: d/dx [(1 - lambda) L1 + lambda (1 - SSIM)]; metric form: d SSIM / dx
         const float ss = loss_form ? -lambda : 1.0f;
         const float l1 = loss_form ? (1.0f - lambda) * L.inv_p3 : 0.0f;
-        k_ssim_bwd<<<grid, kSsimThreads, 0, st>>>(L, img, target, part, ss, l1, grad);
+        gs::launch(k_ssim_bwd, grid, kSsimThreads, 0, st, L, img, target, part, ss, l1, grad);
     }
-    k_ssim_final<<<1, 1, 0, st>>>(acc, L, lambda, ssim_out, loss);
+    gs::launch(k_ssim_final, 1, 1, 0, st, acc, L, lambda, ssim_out, loss);
     return gs_host::check_launch(loss_form ? "gs_loss_l1_dssim" : "gs_ssim");
 }
 
