@@ -5,9 +5,10 @@
 // The result equals sorting the pairs (tile_id << 32 | depth bits, id) by
 // (key, id): every tile's list of Gaussian ids, front to back. It is built
 // without materialising or sorting pair keys:
-//   1. the Gaussians are sorted by (depth bits, id) with a stable LSD radix
-//      sort of 32-bit keys (N items, 4 passes; culled Gaussians carry the
-//      all-ones key, so the sorted keys also tell which entries are visible);
+//   1. the visible Gaussians are sorted by (depth bits, id) with a stable LSD
+//      radix sort of 32-bit keys (4 passes; culled Gaussians carry the all-ones
+//      key and the first pass drops them, so the later ones sort the visible
+//      ones only and level 1 reads their count from the device);
 //   2. a two-level counting scatter (rows, then tiles within a row) writes each
 //      id straight into its final slot (see the section comment below).
 // The pair count K stays on the device; every kernel checks it against the
@@ -31,6 +32,7 @@ constexpr int kItemsPerThread = 8;
 constexpr int kTileItems = kSortThreads * kItemsPerThread;  // 2048
 constexpr int kRadixBins = 256;
 constexpr int kMaxSortBlocks = 148 * 4;  // one wave of the downsweep (64 registers: 4 CTAs per SM)
+constexpr uint32_t kCulledKey = 0xffffffffu;  // depth key of a culled Gaussian (a visible one never takes it)
 
 __device__ __forceinline__ int64_t sort_count(const int64_t* d_num, int64_t cap)
 {
@@ -85,7 +87,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_upsweep(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d_num, int64_t cap, int shift,
-                uint32_t mask, uint32_t* __restrict__ hist)
+                uint32_t mask, bool drop, uint32_t* __restrict__ hist)
 {
     kernel_prologue();
     __shared__ uint32_t s_hist[kSortWarps][kRadixBins];
@@ -99,15 +101,18 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d
     const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
     int64_t body_end = vec ? begin + ((end - begin) & ~int64_t(3)) : begin;
     const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+    // drop: keys equal to kCulledKey are left out (not counted here, not written by the downsweep)
     for (int64_t i = begin / 4 + threadIdx.x; i < body_end / 4; i += kSortThreads) {
-        uint4 v = k4[i];
-        atomicAdd(&s_hist[warp][(v.x >> shift) & mask], 1u);
-        atomicAdd(&s_hist[warp][(v.y >> shift) & mask], 1u);
-        atomicAdd(&s_hist[warp][(v.z >> shift) & mask], 1u);
-        atomicAdd(&s_hist[warp][(v.w >> shift) & mask], 1u);
+        const uint4 v = k4[i];
+        if (!drop || v.x != kCulledKey) atomicAdd(&s_hist[warp][(v.x >> shift) & mask], 1u);
+        if (!drop || v.y != kCulledKey) atomicAdd(&s_hist[warp][(v.y >> shift) & mask], 1u);
+        if (!drop || v.z != kCulledKey) atomicAdd(&s_hist[warp][(v.z >> shift) & mask], 1u);
+        if (!drop || v.w != kCulledKey) atomicAdd(&s_hist[warp][(v.w >> shift) & mask], 1u);
     }
-    for (int64_t i = body_end + threadIdx.x; i < end; i += kSortThreads)
-        atomicAdd(&s_hist[warp][(keys[i] >> shift) & mask], 1u);
+    for (int64_t i = body_end + threadIdx.x; i < end; i += kSortThreads) {
+        const uint32_t v = keys[i];
+        if (!drop || v != kCulledKey) atomicAdd(&s_hist[warp][(v >> shift) & mask], 1u);
+    }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) {
         uint32_t s = 0;
@@ -145,8 +150,9 @@ k_radix_scan(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ totals)
 __global__ void __launch_bounds__(kSortThreads, 4)
 k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                   uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                  const int64_t* __restrict__ d_num, int64_t cap, int shift, uint32_t mask,
-                  const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals)
+                  const int64_t* __restrict__ d_num, int64_t cap, int shift, uint32_t mask, bool drop,
+                  const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals,
+                  int64_t* __restrict__ kept_out)
 {
     kernel_prologue();
     __shared__ uint32_t s_base[kRadixBins];
@@ -154,6 +160,7 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
     __shared__ uint32_t s_start[kRadixBins];
     __shared__ uint32_t s_count[kRadixBins];
     __shared__ uint32_t s_tmp[kSortWarps + 1];
+    __shared__ uint32_t s_ntile;
     __shared__ uint32_t s_keys[kTileItems];
     __shared__ uint32_t s_vals[kTileItems];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,6 +174,8 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
         uint32_t all;
         uint32_t pre = block_exclusive_scan_256(tot, s_tmp, all);
         s_base[threadIdx.x] = pre + hist[(int64_t)threadIdx.x * G + blockIdx.x];
+        // the number of items kept (all of them unless culled keys are dropped)
+        if (kept_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *kept_out = (int64_t)all;
     }
     __syncthreads();
 
@@ -176,6 +185,7 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
         // per item: its key, value and rank among the warp's items of its digit (the digit
         // is recomputed from the key where needed, to keep the registers for 4 CTAs per SM)
         uint32_t k[kItemsPerThread], v[kItemsPerThread], rk[kItemsPerThread];
+        uint32_t okm = 0u;  // bit j: item j is in range and kept
         const int64_t wbase = tile + warp * (32 * kItemsPerThread);
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
@@ -183,12 +193,14 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
             bool ok = idx < end;
             k[j] = ok ? keys_in[idx] : 0u;
             v[j] = ok ? (vals_in != nullptr ? vals_in[idx] : (uint32_t)idx) : 0u;
+            ok = ok && !(drop && k[j] == kCulledKey);
+            okm |= ok ? (1u << j) : 0u;
         }
         // stable rank within the warp: rounds in order, lanes in order. The lanes holding the
         // same digit come from one ballot per digit bit (the digit has at most 8 bits).
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
-            const bool ok = wbase + j * 32 + lane < end;
+            const bool ok = (okm >> j) & 1u;
             const uint32_t dg = ok ? ((k[j] >> shift) & mask) : 0xffffffffu;
             uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
@@ -220,18 +232,19 @@ k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
             uint32_t all;
             uint32_t st = block_exclusive_scan_256(run, s_tmp, all);
             s_start[d] = st;
+            if (d == 0) s_ntile = all;
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kItemsPerThread; ++j) {
-            if (wbase + j * 32 + lane >= end) continue;
+            if (!((okm >> j) & 1u)) continue;
             const uint32_t dg = (k[j] >> shift) & mask;
             uint32_t lp = s_start[dg] + s_warp[warp][dg] + rk[j];
             s_keys[lp] = k[j];
             s_vals[lp] = v[j];
         }
         __syncthreads();
-        const int n_tile = (int)((end - tile) < kTileItems ? (end - tile) : kTileItems);
+        const int n_tile = (int)s_ntile;  // the tile's kept items
         for (int lp = threadIdx.x; lp < n_tile; lp += kSortThreads) {
             uint32_t key = s_keys[lp];
             uint32_t d = (key >> shift) & mask;
@@ -254,9 +267,12 @@ struct SortBufs {
 
 // Sorts (keys0, vals0) by bits [0, bits) of the keys; the result lands in
 // buffer set (passes % 2 == 0 ? 0 : 1), its keys in keys2 when given. Returns
-// the number of passes.
+// the number of passes. kept (nullable): the first pass drops the items whose
+// key is kCulledKey and writes the number kept here; the later passes and the
+// result cover only those (the dropped ones would all sort last, in index
+// order, so the kept prefix is the same as in the full sort).
 int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, uint32_t* hist, uint32_t* totals,
-               cudaStream_t st)
+               int64_t* kept, cudaStream_t st)
 {
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
@@ -267,10 +283,13 @@ int radix_sort(SortBufs b, const int64_t* d_num, int64_t cap, int bits, int G, u
     for (int p = 0; p < passes; ++p) {
         int nb = (bits - shift) < per ? (bits - shift) : per;
         uint32_t mask = (nb >= 32) ? 0xffffffffu : ((1u << nb) - 1u);
-        gs::launch(k_radix_upsweep, G, kSortThreads, 0, st, ki, d_num, cap, shift, mask, hist);
+        const bool drop = p == 0 && kept != nullptr;
+        const int64_t* cnt = (p > 0 && kept != nullptr) ? kept : d_num;
+        gs::launch(k_radix_upsweep, G, kSortThreads, 0, st, ki, cnt, cap, shift, mask, drop, hist);
         gs::launch(k_radix_scan, kRadixBins, kSortThreads, 0, st, hist, G, totals);
         const uint32_t* vin = (p == 0 && b.iota_vals) ? nullptr : vi;
-        gs::launch(k_radix_downsweep, G, kSortThreads, 0, st, ki, vin, ko, vo, d_num, cap, shift, mask, hist, totals);
+        gs::launch(k_radix_downsweep, G, kSortThreads, 0, st, ki, vin, ko, vo, cnt, cap, shift, mask, drop, hist,
+                   totals, drop ? kept : nullptr);
         // the next pass reads what this one wrote and writes the other set (set 0's keys in k0)
         uint32_t* t = vi; vi = vo; vo = t;
         ki = ko;
@@ -450,12 +469,13 @@ __device__ __forceinline__ void scatter_round(V val, int b0, int nb, uint32_t* c
 }
 
 // Level-1 input of sorted position k: the Gaussian id and whether it is
-// visible (its sorted depth key is not the culled key).
+// visible (its sorted depth key is not the culled key: the sort dropped the
+// culled ones, this keeps the test for the record).
 __device__ __forceinline__ uint32_t lvl1_id(const uint32_t* perm, const uint32_t* skeys, int k, int k1, bool& vis)
 {
     vis = false;
     if (k >= k1) return 0u;
-    vis = skeys[k] != 0xffffffffu;
+    vis = skeys[k] != kCulledKey;
     return perm[k];
 }
 
@@ -467,8 +487,9 @@ __device__ __forceinline__ uint32_t lvl1_id(const uint32_t* perm, const uint32_t
 // one). Counting from the rects the scatters use keeps every row list within
 // K slots. The rects of four rounds are fetched together.
 __global__ void __launch_bounds__(kLvlThreads)
-k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
-           const int4* __restrict__ rects, int TX, int TY, int64_t* __restrict__ d_K, uint32_t* __restrict__ M1)
+k_row_hist(int n, const int64_t* __restrict__ d_nvis, int C1, const uint32_t* __restrict__ perm,
+           const uint32_t* __restrict__ skeys, const int4* __restrict__ rects, int TX, int TY,
+           int64_t* __restrict__ d_K, uint32_t* __restrict__ M1)
 {
     kernel_prologue();
     extern __shared__ int s_lvl[];
@@ -479,7 +500,7 @@ k_row_hist(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __r
     int* d = s_lvl + warp * (TY + 1);
     for (int i = lane; i <= TY; i += 32) d[i] = 0;
     __syncwarp();
-    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, (int)min((int64_t)n, *d_nvis));
     unsigned long long area = 0;
     for (int kb = k0 + lane; kb < k1; kb += 32 * U) {
         uint32_t g[U];
@@ -648,9 +669,10 @@ __device__ __forceinline__ uint32_t pack_x(int4 r) { return (uint32_t)r.x | ((ui
 // depth order, at the slots M1 (now bases) gives it. The ids and rects of the
 // next round are fetched while the current round is written.
 __global__ void __launch_bounds__(kLvlThreads)
-k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
-              const int4* __restrict__ rects, int TX, int TY, const uint32_t* __restrict__ M1,
-              const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ rowlist)
+k_row_scatter(int n, const int64_t* __restrict__ d_nvis, int C1, const uint32_t* __restrict__ perm,
+              const uint32_t* __restrict__ skeys, const int4* __restrict__ rects, int TX, int TY,
+              const uint32_t* __restrict__ M1, const int64_t* __restrict__ d_K, int64_t cap,
+              uint2* __restrict__ rowlist)
 {
     kernel_prologue();
     extern __shared__ int s_lvl[];
@@ -661,7 +683,7 @@ k_row_scatter(int n, int C1, const uint32_t* __restrict__ perm, const uint32_t* 
     uint32_t* scratch = cnt + TY + 1;
     for (int ty = lane; ty < TY; ty += 32) cnt[ty] = M1[(int64_t)c * TY + ty];
     __syncwarp();
-    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, n);
+    const int k0 = c * kRowChunk, k1 = min(k0 + kRowChunk, (int)min((int64_t)n, *d_nvis));
     bool vis_n;
     uint32_t g_n = lvl1_id(perm, skeys, k0 + lane, k1, vis_n);
     int4 r_n = vis_n ? rects[g_n] : make_int4(0, 0, -1, -1);
@@ -827,7 +849,7 @@ struct Ws {
     uint32_t *M1, *SS1, *rowlen, *rowstart;
     uint2* rowlist;
     uint32_t *nseg, *segoff;
-    int64_t *R, *NS;
+    int64_t *R, *NS, *nvis;
     uint32_t *M2, *SS2, *tcount, *tstart;
     size_t bytes;
 };
@@ -871,6 +893,7 @@ Ws carve(void* base, int n, int64_t cap, int tiles_x, int tiles_y)
     w.segoff = (uint32_t*)take(TY * 4);
     w.R = (int64_t*)take(8);
     w.NS = (int64_t*)take(8);
+    w.nvis = (int64_t*)take(8);
     w.M2 = (uint32_t*)take((size_t)lvl2_segments((int64_t)rows_cap, (int)TY) * (size_t)tiles_x * 4);
     w.SS2 = (uint32_t*)take((size_t)((NSR + kScanRows - 1) / kScanRows) * T * 4);
     w.tcount = (uint32_t*)take(T * 4);
@@ -931,8 +954,10 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
                    0, st, n, reinterpret_cast<const float4*>(splats), tiles_touched, w.dkeys0);
         keys_in = w.dkeys0;
     }
+    // (4 passes: the sorted keys and the order in dkeys0, perm0). The culled Gaussians are dropped
+    // by the first pass; the others, *w.nvis of them, are sorted.
     radix_sort(SortBufs{const_cast<uint32_t*>(keys_in), w.perm0, w.dkeys1, w.perm1, true, w.dkeys0}, nullptr, n,
-               32, sort_blocks(n), w.hist, w.totals, st);  // 4 passes: the sorted keys and the order in dkeys0, perm0
+               32, sort_blocks(n), w.hist, w.totals, w.nvis, st);
     // level 1: rows
     const int C1 = lvl1_warps(n);
     const int lvl1_blocks = (C1 + kLvlWarps - 1) / kLvlWarps;
@@ -941,7 +966,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     }
-    gs::launch(k_row_hist, lvl1_blocks, kLvlThreads, smem1, st, n, C1, w.perm0, w.dkeys0, rc, TX, TY, num_pairs, w.M1);
+    gs::launch(k_row_hist, lvl1_blocks, kLvlThreads, smem1, st, n, w.nvis, C1, w.perm0, w.dkeys0, rc, TX, TY,
+               num_pairs, w.M1);
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
     const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb1, kScanGridY));
     gs::launch(k_col_segsum, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
@@ -950,8 +976,8 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
     gs::launch(k_col_base, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, w.rowstart, nullptr, nullptr, 1, num_pairs,
                capacity);
-    gs::launch(k_row_scatter, lvl1_blocks, kLvlThreads, smem1, st, n, C1, w.perm0, w.dkeys0, rc, TX, TY, w.M1,
-               num_pairs, capacity, w.rowlist);
+    gs::launch(k_row_scatter, lvl1_blocks, kLvlThreads, smem1, st, n, w.nvis, C1, w.perm0, w.dkeys0, rc, TX, TY,
+               w.M1, num_pairs, capacity, w.rowlist);
     // level 2: tiles within each row
     gs::launch(k_row_segments, (TY + 255) / 256, 256, 0, st, TY, w.rowlen, w.nseg, num_pairs, capacity);
     gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
