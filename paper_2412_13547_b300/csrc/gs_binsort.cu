@@ -565,16 +565,12 @@ k_col_segsum(int R, int Cc, const uint32_t* __restrict__ M, uint32_t* __restrict
     }
 }
 
-// One warp per column: exclusive scan of the column's segment sums in place
-// (32 segments per step; only the ceil(active / kScanRows) segments that hold
-// active rows), the column total into total[c].
-__global__ void k_col_totals(int R, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
-                             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
-                             int64_t cap)
+// Exclusive scan of column c's segment sums in place by one warp (32 segments
+// per step; only the ceil(active / kScanRows) segments that hold active rows),
+// the column total into total[c].
+__device__ __forceinline__ void col_total_warp(int R, int Cc, int c, uint32_t* SS, uint32_t* total,
+                                               const uint32_t* active, int col_div, int lane)
 {
-    kernel_prologue();
-    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
     const int nsb = (active_rows(active, col_div, c, R) + kScanRows - 1) / kScanRows;
     uint32_t run = 0;
     for (int b0 = 0; b0 < nsb; b0 += 32) {
@@ -592,15 +588,25 @@ __global__ void k_col_totals(int R, int Cc, uint32_t* __restrict__ SS, uint32_t*
     if (lane == 0) total[c] = run;
 }
 
-// Single block: exclusive scan of x[0..len) -> start; the sum -> *sum (nullable).
-__global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __restrict__ x,
-                                                     uint32_t* __restrict__ start, int64_t* __restrict__ sum,
-                                                     const int64_t* __restrict__ d_K, int64_t cap)
+// One warp per column: col_total_warp over all Cc columns.
+__global__ void k_col_totals(int R, int Cc, uint32_t* __restrict__ SS, uint32_t* __restrict__ total,
+                             const uint32_t* __restrict__ active, int col_div, const int64_t* __restrict__ d_K,
+                             int64_t cap)
 {
     kernel_prologue();
+    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (c >= Cc || overflow(d_K, cap)) return;  // uniform over the warp
+    col_total_warp(R, Cc, c, SS, total, active, col_div, lane);
+}
+
+// Exclusive scan of x[0..len) -> start by one block of 1024 threads; the sum ->
+// *sum (nullable). count_ranges (nullable): also ranges[i] = [start, start +
+// x[i]) for x[i] > 0, else (0, 0). Every thread of the block must call it.
+__device__ void block_scan_1024(int len, const uint32_t* __restrict__ x, uint32_t* __restrict__ start,
+                                int64_t* __restrict__ sum, uint2* __restrict__ count_ranges)
+{
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_carry;
-    if (overflow(d_K, cap)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long carry = 0;
     for (int base = 0; base < len; base += 1024) {
@@ -626,13 +632,55 @@ __global__ void __launch_bounds__(1024) k_scan_small(int len, const uint32_t* __
         }
         __syncthreads();
         const unsigned long long excl = carry + s_w[warp] + inc - v;
-        if (i < len) start[i] = (uint32_t)excl;
+        if (i < len) {
+            start[i] = (uint32_t)excl;
+            if (count_ranges)
+                count_ranges[i] = v > 0 ? make_uint2((uint32_t)excl, (uint32_t)(excl + v)) : make_uint2(0u, 0u);
+        }
         if (threadIdx.x == 1023) s_carry = excl + v;
         __syncthreads();
         carry = s_carry;
         __syncthreads();
     }
     if (threadIdx.x == 0 && sum) *sum = (int64_t)carry;
+}
+
+// Level-1 row bookkeeping in one block of 1024 threads, after the column
+// segment sums of M1: per tile row the exclusive scan of its segment sums (in
+// place) and its row-list length, the rows' starts (exclusive scan) and the
+// row-list total *R, then the level-2 segments per row (ceil(rowlen /
+// kSegLen)), their offsets (exclusive scan) and total *NS.
+__global__ void __launch_bounds__(1024)
+k_lvl1_rows(int C1, int TY, uint32_t* __restrict__ SS1, uint32_t* __restrict__ rowlen,
+            uint32_t* __restrict__ rowstart, int64_t* __restrict__ R, uint32_t* __restrict__ nseg,
+            uint32_t* __restrict__ segoff, int64_t* __restrict__ NS, const int64_t* __restrict__ d_K, int64_t cap)
+{
+    kernel_prologue();
+    if (overflow(d_K, cap)) return;  // uniform over the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < TY; c += 32) col_total_warp(C1, TY, c, SS1, rowlen, nullptr, 1, lane);
+    __syncthreads();
+    block_scan_1024(TY, rowlen, rowstart, R, nullptr);
+    for (int ty = threadIdx.x; ty < TY; ty += 1024) nseg[ty] = (rowlen[ty] + kSegLen - 1) / kSegLen;
+    __syncthreads();
+    block_scan_1024(TY, nseg, segoff, NS, nullptr);
+}
+
+// Level-2 tile starts in one block of 1024 threads: the exclusive scan of the
+// tile counts, and the ranges ((0, 0) for empty tiles). On overflow every range
+// is set empty instead. K_max (nullable): a high-water mark of K across calls,
+// raised here.
+__global__ void __launch_bounds__(1024)
+k_tile_starts(int T, const uint32_t* __restrict__ count, uint32_t* __restrict__ start,
+              const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges, int64_t* __restrict__ K_max)
+{
+    kernel_prologue();
+    if (K_max && threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long*>(K_max), (unsigned long long)*d_K);
+    if (overflow(d_K, cap)) {
+        for (int t = threadIdx.x; t < T; t += 1024) ranges[t] = make_uint2(0u, 0u);
+        return;
+    }
+    block_scan_1024(T, count, start, nullptr, ranges);
 }
 
 // M[r][c] <- start[c] + (sum of M[r'][c] for r' < r): the first slot of row r
@@ -702,16 +750,6 @@ k_row_scatter(int n, const int64_t* __restrict__ d_nvis, int C1, const uint32_t*
         }
         scatter_round<uint2>(make_uint2(g, pack_x(r)), y0, nr, cnt, scratch, rowlist, cap, lane);
     }
-}
-
-// Level-2 segments: row ty's list is cut into nseg[ty] = ceil(rowlen / kSegLen) segments.
-__global__ void k_row_segments(int TY, const uint32_t* __restrict__ rowlen, uint32_t* __restrict__ nseg,
-                               const int64_t* __restrict__ d_K, int64_t cap)
-{
-    kernel_prologue();
-    const int ty = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ty >= TY || overflow(d_K, cap)) return;
-    nseg[ty] = (rowlen[ty] + kSegLen - 1) / kSegLen;
 }
 
 // Segment index -> (row, segment within the row): the largest row whose first
@@ -824,20 +862,6 @@ k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint3
         }
         __syncthreads();
     }
-}
-
-// Ranges from the tile counts and starts; (0, 0) for empty tiles and on overflow.
-// K_max (nullable): a high-water mark of K across calls, raised here.
-__global__ void k_ranges_from_counts(int T, const uint32_t* __restrict__ count, const uint32_t* __restrict__ start,
-                                     const int64_t* __restrict__ d_K, int64_t cap, uint2* __restrict__ ranges,
-                                     int64_t* __restrict__ K_max)
-{
-    kernel_prologue();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (K_max && t == 0) atomicMax(reinterpret_cast<unsigned long long*>(K_max), (unsigned long long)*d_K);
-    if (t >= T) return;
-    const bool ok = !overflow(d_K, cap) && count[t] > 0;
-    ranges[t] = ok ? make_uint2(start[t], start[t] + count[t]) : make_uint2(0u, 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -971,16 +995,13 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     const int nsb1 = (C1 + kScanRows - 1) / kScanRows;
     const dim3 g1((TY + kColsPerBlock - 1) / kColsPerBlock, std::min(nsb1, kScanGridY));
     gs::launch(k_col_segsum, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, nullptr, nullptr, 1, num_pairs, capacity);
-    gs::launch(k_col_totals, (TY * 32 + 255) / 256, 256, 0, st, C1, TY, w.SS1, w.rowlen, nullptr, 1, num_pairs,
-               capacity);
-    gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.rowlen, w.rowstart, w.R, num_pairs, capacity);
+    gs::launch(k_lvl1_rows, 1, 1024, 0, st, C1, TY, w.SS1, w.rowlen, w.rowstart, w.R, w.nseg, w.segoff, w.NS,
+               num_pairs, capacity);
     gs::launch(k_col_base, g1, kLvlThreads, 0, st, C1, TY, w.M1, w.SS1, w.rowstart, nullptr, nullptr, 1, num_pairs,
                capacity);
     gs::launch(k_row_scatter, lvl1_blocks, kLvlThreads, smem1, st, n, w.nvis, C1, w.perm0, w.dkeys0, rc, TX, TY,
                w.M1, num_pairs, capacity, w.rowlist);
     // level 2: tiles within each row
-    gs::launch(k_row_segments, (TY + 255) / 256, 256, 0, st, TY, w.rowlen, w.nseg, num_pairs, capacity);
-    gs::launch(k_scan_small, 1, 1024, 0, st, TY, w.nseg, w.segoff, w.NS, num_pairs, capacity);
     const int NSR = lvl2_rows(n);
     const size_t smem2 = (size_t)kLvlWarps * (TX + 1 + 64) * sizeof(int);
     const size_t smem2h = (size_t)(TX + 1) * sizeof(int);
@@ -996,11 +1017,10 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
     gs::launch(k_col_segsum, g2, kLvlThreads, 0, st, NSR, T, w.M2, w.SS2, w.nseg, w.segoff, TX, num_pairs, capacity);
     gs::launch(k_col_totals, (int)(((int64_t)T * 32 + 255) / 256), 256, 0, st, NSR, T, w.SS2, w.tcount, w.nseg, TX,
                num_pairs, capacity);
-    gs::launch(k_scan_small, 1, 1024, 0, st, T, w.tcount, w.tstart, nullptr, num_pairs, capacity);
+    gs::launch(k_tile_starts, 1, 1024, 0, st, T, w.tcount, w.tstart, num_pairs, capacity,
+               reinterpret_cast<uint2*>(ranges), num_pairs_max);
     gs::launch(k_col_base, g2, kLvlThreads, 0, st, NSR, T, w.M2, w.SS2, w.tstart, w.nseg, w.segoff, TX, num_pairs,
                capacity);
-    gs::launch(k_ranges_from_counts, (T + 255) / 256, 256, 0, st, T, w.tcount, w.tstart, num_pairs, capacity,
-               reinterpret_cast<uint2*>(ranges), num_pairs_max);
     if (capacity > 0)
         gs::launch(k_seg_scatter, lvl2_blocks, kLvlThreads, smem2, st, TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
                    w.rowlist, w.M2, num_pairs, capacity, sorted_ids);

@@ -327,9 +327,9 @@ class TrainStep:
 
 
 # kernels in one gs_bin_sort call given the projection's depth keys: a 4-pass radix sort
-# of the depths (3 kernels a pass), 6 + 2 for the row level (the row histogram also sums
-# the pair count), 7 for the tile level
-BIN_SORT_KERNELS = 4 * 3 + 6 + 2 + 7
+# of the depths (3 kernels a pass), 5 for the row level (the row histogram also sums the
+# pair count), 6 for the tile level
+BIN_SORT_KERNELS = 4 * 3 + 5 + 6
 
 
 # ---------------------------------------------------------------------------
