@@ -246,13 +246,17 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     max_px = max(R.gs_grid(cam, R.Dilation(d, ox, oy))[0] * R.gs_grid(cam, R.Dilation(d, ox, oy))[1]
                  for ox in range(d) for oy in range(d))
     step = TrainStep(p, rast, AdamConfig(), max_pixels=max_px)
-    timed = TimedStep(step, steps)
+    # the per-stage table comes from further steps with CUDA events between the stages, after the
+    # timed ones: events between kernels would also cut the programmatic-launch overlap of the
+    # stage boundaries out of the timed steps
+    stage_steps = min(steps, 20) if want_stage else 0
+    timed = TimedStep(step, max(1, stage_steps))
     n_count = d * d  # instrumented steps (every offset once) for the blend counts, after the timed ones
-    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps + n_count)]
+    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps + stage_steps + n_count)]
+    dil_of = lambda i: R.Dilation(d, offsets[i][0], offsets[i][1], tile=TILE[0], bin_shift=bin_shift_for(d))
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
     for i in range(warmup):
-        ox, oy = offsets[i]
-        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev)
+        step(cam, dil_of(i), target_dev)
     torch.cuda.synchronize()
     step.counts.zero_()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -262,24 +266,24 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         barrier()
         start.record()
         for i in range(steps):
-            ox, oy = offsets[warmup + i]
-            timed.run(i, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev)
+            step(cam, dil_of(warmup + i), target_dev)
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
         barrier()
     total_ms = start.elapsed_time(end)
-    stage = timed.stage_ms(steps) if want_stage else None
     ks = k_hist.cpu().numpy()
     if ks.max() > rast.capacity:
         raise RuntimeError(f"pair capacity {rast.capacity} exceeded ({ks.max()}); rerun with more headroom")
+    for i in range(stage_steps):
+        timed.run(i, cam, dil_of(warmup + steps + i), target_dev)
+    torch.cuda.synchronize()
+    stage = timed.stage_ms(stage_steps) if want_stage else None
     # the blend counts (instrumentation the training step does not need) from d*d further
     # steps, one per lattice offset, outside the timed region
     step.counts.zero_()
     for i in range(n_count):
-        ox, oy = offsets[warmup + steps + i]
-        # event slot 0, as in the warm-up: the stage times were read above
-        timed.run(0, cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), target_dev, counts=True)
+        timed.run(0, cam, dil_of(warmup + steps + stage_steps + i), target_dev, counts=True)
     torch.cuda.synchronize()
     counts = step.counts.cpu().numpy() / n_count  # per step
     iters_per_s = steps * 1000.0 / total_ms
@@ -322,7 +326,9 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     # exponent (7), its scaling for the SFU exp, alpha, the clamp and the gate -- and 7 more
     # per blended one (transmittance, weight, three colour FMAs, the stop test)
     rows["render_fwd"] = ("alu", 12.0 * res["evaluated_per_step"] + 7.0 * res["blended_per_step"])
-    rows["loss"] = ("hbm", 36.0 * step_pixels)
+    # L1 loss: the image read, dL/dimg written (12 B each per pixel) and the 8-bit target's lattice
+    # pixel read (3 B)
+    rows["loss"] = ("hbm", 27.0 * step_pixels)
     # blend backward: the same 12 gate operations per replayed (pixel, entry) and 41 per
     # contributing one (the replayed blends: transmittance recovery, the colour, alpha,
     # exponent, conic and centre gradients); the stage's time includes the memset of the
@@ -391,7 +397,7 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
                  for ox in range(d) for oy in range(d))
     step = TrainStep(params, rast, AdamConfig(), max_pixels=max_px)
     host_t = torch.from_numpy(target_np).pin_memory()
-    bufs = [torch.empty(target_np.shape, device=device) for _ in range(2)]
+    bufs = [torch.empty(target_np.shape, dtype=host_t.dtype, device=device) for _ in range(2)]
     loss_host = torch.zeros(steps + warmup, dtype=torch.float32).pin_memory()
     copy_stream = torch.cuda.Stream()
     comp = torch.cuda.current_stream()
@@ -446,7 +452,7 @@ def measure_batch(args, device, d, steps, warmup):
     from paper_2412_13547_b300.pipeline import GaussianParams, BatchTrainStep, autotune_batch
 
     scene, cams, targets = scenes.workload_batch(min(args.n, 2_000_000))
-    tg = [torch.tensor(t, device=device) for t in targets]
+    tg = [torch.tensor(scenes.quantize_u8(t), device=device) for t in targets]
     params = GaussianParams.from_arrays(scene.as_dict(), device)
     (tile, ppt, shift), table = autotune_batch(params, cams, tg, d=d, iters=2)
     st = BatchTrainStep(params, cams, tg, d=d, tile=tile, pixels_per_thread=ppt, bin_shift=shift)
@@ -556,7 +562,7 @@ def run_sweep(args, device):
     with clocks:
         for (w, h) in SWEEP_RESOLUTIONS:
             cam = scenes.look_at(scenes.orbit_eye(2.6, 30.0, 20.0), width=w, height=h)
-            target = torch.tensor(scenes.target_image(w, h, 2), device=device)
+            target = torch.tensor(scenes.quantize_u8(scenes.target_image(w, h, 2)), device=device)
             for d in (1, 2, 4):
                 for t, s0 in zip(params.tensors(), snapshot):
                     t.copy_(s0)
@@ -697,6 +703,7 @@ def oracle_sample(n_arg, d=2, n_tiles=16, seed=0):
     from paper_2412_13547_b300 import scenes
 
     scene, cam, target = scenes.workload_uhd(n_arg)
+    target = scenes.u8_values(scenes.quantize_u8(target))  # the values the GPU arm's 8-bit target holds
     p = {k: np.asarray(v, np.float64) for k, v in scene.as_dict().items()}
     ocam = orc.as_camera(cam)
     dil = orc.Dilation(d, 1, 0)
@@ -733,7 +740,7 @@ def headline_config(workload, n, width, height, world):
                          "hd-1920x1080-1M-gaussians-sh3") + " (dilated d=2, rotating offset)",
             "n_gaussians": n, "resolution": [width, height], "d": 2, "tile": TILE[0],
             "bin_tile": TILE[0] << bin_shift_for(2),
-            "parallelism": "replicas" if world > 1 else "single",
+            "parallelism": "replicas" if world > 1 else "single", "target": "8-bit RGB, read as t/255",
             "l2": "inputs larger than L2 (params 708 MB, pair buffers > 1 GB)"}
 
 
@@ -837,10 +844,12 @@ def main():
         dist.init_process_group("nccl", device_id=device)
 
     scene, cam, target, params = setup(args, device)
-    from paper_2412_13547_b300 import raster as R
+    from paper_2412_13547_b300 import raster as R, scenes
     from paper_2412_13547_b300.pipeline import Rasterizer
 
-    target_dev = torch.tensor(target, device=device)
+    # the target as photographs are stored (8-bit RGB); the loss reads t * (1/255)
+    target8 = scenes.quantize_u8(target)
+    target_dev = torch.tensor(target8, device=device)
     snapshot = [t.clone() for t in params.tensors()]
     # pair capacity: the largest K over the forms measured, plus headroom (no host sync in the step)
     if args.workload != "uhd":
@@ -882,7 +891,7 @@ def main():
     if not args.no_variants and not args.no_batch and world == 1:
         # the batched form (8 mixed-resolution views per step, CUDA graphs, autotuned launch shape)
         variants["batch_8views_d2"] = measure_batch(args, device, 2, max(8, args.steps // 4), 4)
-    e2e = e2e_measure(args, params, cam, target, 2, args.steps, args.warmup, device, rast, snapshot)
+    e2e = e2e_measure(args, params, cam, target8, 2, args.steps, args.warmup, device, rast, snapshot)
 
     # max over ranks of the step time (replicas: every rank runs the whole workload)
     ms, e2e_ms = max_over_ranks([head["ms_per_step"], e2e["ms_per_step"]], device)

@@ -257,14 +257,24 @@ int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids
                       const uint32_t* tile_order, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Targets. A target image (height x width x 3, row-major) is FP32 values in
+ * [0, 1] (GS_TARGET_F32), or 8-bit values t as photographs are stored
+ * (GS_TARGET_U8), which every kernel reads as the FP32 product t * (1/255),
+ * 1/255 rounded to FP32 (0x3B808081): a quarter of the bytes to copy to the
+ * device and to read per step. */
+#define GS_TARGET_F32 0
+#define GS_TARGET_U8 1
+
+/* ---------------------------------------------------------------------------
  * gs_loss_l1 -- L1 photometric loss of the rendered lattice pixels against the
  * hr target sampled at the same pixels (supervision with "corresponding
  * high-resolution pixels", Sec. 3.1): L = mean |img - target| over h_ds*w_ds*3
  * values, dL/dimg = sign(img - target) / (3 * h_ds * w_ds) (sign(0) = 0).
- * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3).
+ * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3, of
+ *   target_dtype, GS_TARGET_F32 or GS_TARGET_U8).
  * Outputs (device): dl_dimg (h_ds x w_ds x 3), loss (one float, overwritten). */
 int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
-                   const float* target, float* dl_dimg, float* loss, gs_stream_t stream);
+                   const void* target, int32_t target_dtype, float* dl_dimg, float* loss, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * gs_ssim -- SSIM, the structural-similarity index (Wang et al. 2004) the
@@ -278,7 +288,8 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
  * the pixels whose window lies inside the lattice image (at least 11 x 11);
  * mode 1 ("same"): the mean over all pixels, zeros outside the image (the
  * form 3DGS fitting trains with). Channels are averaged.
- * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3).
+ * Inputs (device): img (h_ds x w_ds x 3), target (height x width x 3, of
+ *   target_dtype as for gs_loss_l1).
  * Outputs (device): *ssim_out (one float, overwritten); d_img (nullable,
  *   h_ds x w_ds x 3): d (mean SSIM) / d img, overwritten.
  * workspace: gs_ssim_workspace_size(cam, dil) bytes, 256-byte aligned (9
@@ -286,8 +297,9 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
  * Errors: GS_ERR_ARG for a bad camera/dilation/mode, null pointers, a short or
  *   misaligned workspace, or a lattice under 11 x 11 in mode 0. */
 size_t gs_ssim_workspace_size(const GsCamera* cam, const GsDilation* dil);
-int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, int32_t mode,
-                float* ssim_out, float* d_img, void* workspace, size_t workspace_bytes, gs_stream_t stream);
+int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                int32_t target_dtype, int32_t mode, float* ssim_out, float* d_img, void* workspace,
+                size_t workspace_bytes, gs_stream_t stream);
 
 /* gs_loss_l1_dssim -- the photometric loss of 3DGS fitting, which the paper's
  * method builds on (the paper's own loss is the L1 of gs_loss_l1):
@@ -295,8 +307,8 @@ int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, co
  * L1 as in gs_loss_l1 and SSIM as in gs_ssim (mode as there), over the lattice
  * pixels. Outputs (device): dl_dimg (h_ds x w_ds x 3, overwritten) = dL/dimg,
  * *loss (overwritten). workspace as gs_ssim. */
-int32_t gs_loss_l1_dssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target,
-                         float lambda, int32_t mode, float* dl_dimg, float* loss, void* workspace,
+int32_t gs_loss_l1_dssim(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                         int32_t target_dtype, float lambda, int32_t mode, float* dl_dimg, float* loss, void* workspace,
                          size_t workspace_bytes, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -455,11 +467,12 @@ typedef struct {
     float* img;                /* h_ds x w_ds x 3                              */
     float* t_final;            /* h_ds x w_ds                                  */
     uint32_t* last;            /* h_ds x w_ds                                  */
-    const float* target;       /* height x width x 3 (hr)                      */
+    const void* target;        /* height x width x 3 (hr), of target_dtype     */
     float* dl_dimg;            /* h_ds x w_ds x 3                              */
     float* grad2d;             /* n x 12                                       */
     float* loss;               /* one float                                    */
     uint32_t* depth_keys;      /* n, nullable (gs_project's depth_keys)         */
+    int32_t target_dtype;      /* GS_TARGET_F32 or GS_TARGET_U8                */
 } GsView;
 
 /* gs_project for every view of the table (one launch). */

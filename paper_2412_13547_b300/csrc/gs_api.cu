@@ -108,6 +108,11 @@ bool make_batch(const GsView* views, int nviews, gs::Batch* out)
         v.t_final = in.t_final;
         v.last = in.last;
         v.target = in.target;
+        v.target_dtype = in.target_dtype;
+        if (in.target_dtype != GS_TARGET_F32 && in.target_dtype != GS_TARGET_U8) {
+            set_error("view: target_dtype must be GS_TARGET_F32 or GS_TARGET_U8");
+            return false;
+        }
         v.dl = in.dl_dimg;
         v.grad2d = reinterpret_cast<float4*>(in.grad2d);
         v.loss = in.loss;

@@ -1058,9 +1058,9 @@ int32_t launch_project_bwd(int n, const float* means, const float* log_scales, c
     auto kern = k_project_bwd<DEG, DT>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    gs::launch(kern, blocks, kThreads, smem, st, n, means, log_scales, reinterpret_cast<const float4*>(quats), logits,
-               sh, cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
-               reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
+    gs::launch_serial(kern, blocks, kThreads, smem, st, n, means, log_scales, reinterpret_cast<const float4*>(quats),
+                      logits, sh, cam, dil, tiles, reinterpret_cast<const float4*>(grad2d), d_means, d_ls,
+                      reinterpret_cast<float4*>(d_q), d_logits, d_sh, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd");
 }
 
@@ -1073,7 +1073,7 @@ int32_t launch_project_bwd_adam(int n, const void* sh_store, const Batch& b, con
     auto kern = b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    gs::launch(kern, blocks, kThreads, smem, st, n, sh_store, b, a, pos, col, cnt);
+    gs::launch_serial(kern, blocks, kThreads, smem, st, n, sh_store, b, a, pos, col, cnt);
     return gs_host::check_launch("gs_project_bwd_adam");
 }
 

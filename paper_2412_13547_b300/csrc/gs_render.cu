@@ -698,16 +698,15 @@ __global__ void k_loss_zero(const __grid_constant__ Batch b)
 
 // L1 loss of each view (blockIdx.y) and its gradient sign/(3P) w.r.t. the
 // rendered pixels, against the hr target sampled at the view's lattice.
-__global__ void k_loss_l1(const __grid_constant__ Batch b)
+// The L1 terms of the lattice pixels a thread takes (grid-stride), for a
+// target of type TD; returns the thread's sum of |img - target|.
+template <int TD>
+__device__ __forceinline__ float loss_l1_pixels(const ViewDev& V, float inv)
 {
-    kernel_prologue();
-    const ViewDev& V = b.v[blockIdx.y];
     const Dil& dil = V.dil;
     const int width = V.cam.width;
     const int64_t P = (int64_t)dil.w_ds * dil.h_ds;
-    const float inv = (float)(1.0 / (3.0 * (double)P));
     const float* __restrict__ img = V.img;
-    const float* __restrict__ target = V.target;
     float* __restrict__ dl = V.dl;
     float acc = 0.0f;
     for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < P;
@@ -716,11 +715,23 @@ __global__ void k_loss_l1(const __grid_constant__ Batch b)
         const int64_t h = ((int64_t)(dil.d * v + dil.oy) * width + (dil.d * u + dil.ox)) * 3;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const float r = img[3 * pix + ch] - target[h + ch];
+            const float r = img[3 * pix + ch] - target_value<TD>(V.target, h + ch);
             acc += fabsf(r);
             dl[3 * pix + ch] = r > 0.0f ? inv : (r < 0.0f ? -inv : 0.0f);
         }
     }
+    return acc;
+}
+
+__global__ void k_loss_l1(const __grid_constant__ Batch b)
+{
+    kernel_prologue();
+    const ViewDev& V = b.v[blockIdx.y];
+    const Dil& dil = V.dil;
+    const int64_t P = (int64_t)dil.w_ds * dil.h_ds;
+    const float inv = (float)(1.0 / (3.0 * (double)P));
+    float acc = V.target_dtype == GS_TARGET_U8 ? loss_l1_pixels<GS_TARGET_U8>(V, inv)
+                                               : loss_l1_pixels<GS_TARGET_F32>(V, inv);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     __shared__ float s_sum[32];
@@ -1114,13 +1125,14 @@ int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_
     return gs_host::check_launch("gs_tile_order_by_last_batch");
 }
 
-int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, float* dl_dimg,
-                   float* loss, gs_stream_t stream)
+int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                   int32_t target_dtype, float* dl_dimg, float* loss, gs_stream_t stream)
 {
     if (!cam || !dil) { gs_host::set_error("gs_loss_l1: camera or dilation is null"); return GS_ERR_ARG; }
     GsView v = gs::single_view(cam, dil);
     v.img = const_cast<float*>(img);
     v.target = target;
+    v.target_dtype = target_dtype;
     v.dl_dimg = dl_dimg;
     v.loss = loss;
     return gs_loss_l1_batch(&v, 1, stream);

@@ -48,6 +48,7 @@ struct Lattice {
     int d, ox, oy;     // hr pixel of lattice (u, v): (d u + ox, d v + oy)
     int width;         // hr width (target row stride)
     int mode;          // 0 valid, 1 same
+    int target_dtype;  // GS_TARGET_F32 or GS_TARGET_U8
     float inv_n;       // 1 / (3 * pixels averaged)
     float inv_p3;      // 1 / (3 * lattice pixels): the L1 mean
 };
@@ -57,16 +58,17 @@ __device__ __forceinline__ bool counted(const Lattice& L, int u, int v)
     return L.mode == 1 ? true : (u >= kR && u < L.w - kR && v >= kR && v < L.h - kR);
 }
 
-__device__ __forceinline__ float target_at(const Lattice& L, const float* t, int u, int v, int c)
+__device__ __forceinline__ float target_at(const Lattice& L, const void* t, int u, int v, int c)
 {
-    return t[((int64_t)(L.d * v + L.oy) * L.width + (L.d * u + L.ox)) * 3 + c];
+    const int64_t i = ((int64_t)(L.d * v + L.oy) * L.width + (L.d * u + L.ox)) * 3 + c;
+    return L.target_dtype == GS_TARGET_U8 ? target_value<GS_TARGET_U8>(t, i) : target_value<GS_TARGET_F32>(t, i);
 }
 
 // Forward: per channel, the window sums of the CTA's output tile, SSIM and its
 // partials (scaled by the mean's 1/N) into part[pix][c][0..2] (zero for a
 // pixel the mean leaves out); sums of SSIM and |x - y| into acc[0], acc[1].
 __global__ void __launch_bounds__(kSsimThreads)
-k_ssim_fwd(Lattice L, const float* __restrict__ img, const float* __restrict__ target, float* __restrict__ part,
+k_ssim_fwd(Lattice L, const float* __restrict__ img, const void* __restrict__ target, float* __restrict__ part,
            double* __restrict__ acc)
 {
     kernel_prologue();
@@ -161,7 +163,7 @@ k_ssim_fwd(Lattice L, const float* __restrict__ img, const float* __restrict__ t
 // out = ssim_scale * g + l1_scale * sign(x - y) (l1_scale 0: the SSIM gradient
 // alone).
 __global__ void __launch_bounds__(kSsimThreads)
-k_ssim_bwd(Lattice L, const float* __restrict__ img, const float* __restrict__ target,
+k_ssim_bwd(Lattice L, const float* __restrict__ img, const void* __restrict__ target,
            const float* __restrict__ part, float ssim_scale, float l1_scale, float* __restrict__ out)
 {
     kernel_prologue();
@@ -251,9 +253,9 @@ size_t ssim_ws_bytes(const Lattice& L)
     return 256 + (((size_t)L.w * L.h * 9 * sizeof(float) + 255) & ~size_t(255));
 }
 
-int32_t run_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, int32_t mode,
-                 float lambda, bool loss_form, float* ssim_out, float* loss, float* grad, void* workspace,
-                 size_t workspace_bytes, gs_stream_t stream)
+int32_t run_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                 int32_t target_dtype, int32_t mode, float lambda, bool loss_form, float* ssim_out, float* loss,
+                 float* grad, void* workspace, size_t workspace_bytes, gs_stream_t stream)
 {
     Lattice L;
     if (!make_lattice(cam, dil, mode, &L)) return GS_ERR_ARG;
@@ -261,6 +263,11 @@ int32_t run_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, c
         gs_host::set_error("ssim: null image, target or workspace");
         return GS_ERR_ARG;
     }
+    if (target_dtype != GS_TARGET_F32 && target_dtype != GS_TARGET_U8) {
+        gs_host::set_error("ssim: target_dtype must be GS_TARGET_F32 or GS_TARGET_U8");
+        return GS_ERR_ARG;
+    }
+    L.target_dtype = target_dtype;
     if (workspace_bytes < ssim_ws_bytes(L) || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
         gs_host::set_error("ssim: workspace too small or not 256-byte aligned");
         return GS_ERR_ARG;
@@ -293,26 +300,27 @@ size_t gs_ssim_workspace_size(const GsCamera* cam, const GsDilation* dil)
     return gs::ssim_ws_bytes(L);
 }
 
-int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target, int32_t mode,
-                float* ssim_out, float* d_img, void* workspace, size_t workspace_bytes, gs_stream_t stream)
+int32_t gs_ssim(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                int32_t target_dtype, int32_t mode, float* ssim_out, float* d_img, void* workspace,
+                size_t workspace_bytes, gs_stream_t stream)
 {
     if (!ssim_out) {
         gs_host::set_error("gs_ssim: null output");
         return GS_ERR_ARG;
     }
-    return gs::run_ssim(cam, dil, img, target, mode, 0.0f, false, ssim_out, nullptr, d_img, workspace,
+    return gs::run_ssim(cam, dil, img, target, target_dtype, mode, 0.0f, false, ssim_out, nullptr, d_img, workspace,
                         workspace_bytes, stream);
 }
 
-int32_t gs_loss_l1_dssim(const GsCamera* cam, const GsDilation* dil, const float* img, const float* target,
-                         float lambda, int32_t mode, float* dl_dimg, float* loss, void* workspace,
+int32_t gs_loss_l1_dssim(const GsCamera* cam, const GsDilation* dil, const float* img, const void* target,
+                         int32_t target_dtype, float lambda, int32_t mode, float* dl_dimg, float* loss, void* workspace,
                          size_t workspace_bytes, gs_stream_t stream)
 {
     if (!dl_dimg || !loss || !(lambda >= 0.0f && lambda <= 1.0f)) {
         gs_host::set_error("gs_loss_l1_dssim: null output or lambda outside [0, 1]");
         return GS_ERR_ARG;
     }
-    return gs::run_ssim(cam, dil, img, target, mode, lambda, true, nullptr, loss, dl_dimg, workspace,
+    return gs::run_ssim(cam, dil, img, target, target_dtype, mode, lambda, true, nullptr, loss, dl_dimg, workspace,
                         workspace_bytes, stream);
 }
 

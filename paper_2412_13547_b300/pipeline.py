@@ -374,8 +374,8 @@ class BatchTrainStep:
         n, V = params.n, self.V
         self.targets = [t.contiguous() for t in targets]
         for c, t in zip(self.cams, self.targets):
-            if tuple(t.shape) != (c.height, c.width, 3) or t.dtype != torch.float32:
-                raise ValueError("each target must be an FP32 height x width x 3 tensor on the device")
+            if tuple(t.shape) != (c.height, c.width, 3) or t.dtype not in (torch.float32, torch.uint8):
+                raise ValueError("each target must be an FP32 or 8-bit height x width x 3 tensor on the device")
         self.splats = torch.zeros(V, n, R.SPLAT_FLOATS, device=dev)
         self.radii = torch.zeros(V, n, dtype=torch.int32, device=dev)
         self.rects = torch.zeros(V, n, 4, dtype=torch.int32, device=dev)

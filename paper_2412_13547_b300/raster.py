@@ -76,7 +76,21 @@ class GsRowTensor(ctypes.Structure):
 
 
 class GsView(ctypes.Structure):
-    _fields_ = [("cam", GsCamera), ("dil", GsDilation)] + [(k, ctypes.c_void_p) for k in _VIEW_BUFFERS]
+    _fields_ = [("cam", GsCamera), ("dil", GsDilation)] + [(k, ctypes.c_void_p) for k in _VIEW_BUFFERS] + \
+        [("target_dtype", ctypes.c_int32)]
+
+
+TARGET_F32, TARGET_U8 = 0, 1  # GS_TARGET_F32, GS_TARGET_U8
+
+
+def target_dtype(t) -> int:
+    """The C ABI's code for a target image tensor: FP32 values, or 8-bit values
+    the kernels read as t * (1/255)."""
+    if t is None or t.dtype == torch.float32:
+        return TARGET_F32
+    if t.dtype == torch.uint8:
+        return TARGET_U8
+    raise ValueError(f"target: float32 or uint8 expected, got {t.dtype}")
 
 
 @dataclass(frozen=True)
@@ -133,6 +147,7 @@ class ViewTable:
             for k in _VIEW_BUFFERS:
                 t = getattr(v, k)
                 setattr(self.arr[i], k, None if t is None else _ptr(t).value)
+            self.arr[i].target_dtype = target_dtype(v.target)
 
 
 def _table(views) -> ViewTable:
@@ -177,7 +192,7 @@ def load():
     lib.gs_bin_sort_static.argtypes = [i32, P, P, P, P, i32, i32, i64, P, P, P, P, P]
     lib.gs_tile_order.argtypes = [P, i32, P, P]
     lib.gs_render_fwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P, P]
-    lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, P, P, P]
+    lib.gs_loss_l1.argtypes = [cam_p, dil_p, P, P, i32, P, P, P]
     lib.gs_render_bwd.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, i32, P, P]
     lib.gs_project_bwd.argtypes = [i32, i32, i32, P, P, P, P, P, cam_p, dil_p, P, P, P, P, P, P, P, P, P, P, P]
     lib.gs_densify_stats.argtypes = [i32, P, P, P, P, P, P]
@@ -203,8 +218,8 @@ def load():
     lib.gs_densify_grow.argtypes = [i32, i32, P, P, f32, rows_p, i32, P]
     lib.gs_ssim_workspace_size.argtypes = [cam_p, dil_p]
     lib.gs_ssim_workspace_size.restype = ctypes.c_size_t
-    lib.gs_ssim.argtypes = [cam_p, dil_p, P, P, i32, P, P, P, ctypes.c_size_t, P]
-    lib.gs_loss_l1_dssim.argtypes = [cam_p, dil_p, P, P, f32, i32, P, P, P, ctypes.c_size_t, P]
+    lib.gs_ssim.argtypes = [cam_p, dil_p, P, P, i32, i32, P, P, P, ctypes.c_size_t, P]
+    lib.gs_loss_l1_dssim.argtypes = [cam_p, dil_p, P, P, i32, f32, i32, P, P, P, ctypes.c_size_t, P]
     for name in SYMBOLS:
         if name not in ("gs_last_error", "gs_bin_sort_workspace_size", "gs_densify_workspace_size",
                         "gs_ssim_workspace_size"):
@@ -346,7 +361,7 @@ def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
     _need_image(dil, cam, img=img, dl=dl_dimg)
     _need(target, 3 * int(cam.width) * int(cam.height), "target")
     _check(load().gs_loss_l1(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
-                             _ptr(dl_dimg), _ptr(loss), _stream(stream)), "gs_loss_l1")
+                             target_dtype(target), _ptr(dl_dimg), _ptr(loss), _stream(stream)), "gs_loss_l1")
 
 
 SSIM_VALID, SSIM_SAME = 0, 1
@@ -361,8 +376,8 @@ def gs_ssim(cam, dil: Dilation, img, target, ssim_out, workspace, d_img=None, mo
     ssim_out (one float); d_img (optional) receives d(mean SSIM)/d img."""
     _need_image(dil, cam, img=img, dl=d_img)
     _need(target, 3 * int(cam.width) * int(cam.height), "target")
-    _check(load().gs_ssim(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target), int(mode),
-                          _ptr(ssim_out), _ptr(d_img), _ptr(workspace), workspace.numel() * workspace.element_size(),
+    _check(load().gs_ssim(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
+                          target_dtype(target), int(mode), _ptr(ssim_out), _ptr(d_img), _ptr(workspace), workspace.numel() * workspace.element_size(),
                           _stream(stream)), "gs_ssim")
 
 
@@ -371,7 +386,7 @@ def gs_loss_l1_dssim(cam, dil: Dilation, img, target, lam, dl_dimg, loss, worksp
     _need_image(dil, cam, img=img, dl=dl_dimg)
     _need(target, 3 * int(cam.width) * int(cam.height), "target")
     _check(load().gs_loss_l1_dssim(ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(img), _ptr(target),
-                                   float(lam), int(mode), _ptr(dl_dimg), _ptr(loss), _ptr(workspace),
+                                   target_dtype(target), float(lam), int(mode), _ptr(dl_dimg), _ptr(loss), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _stream(stream)),
            "gs_loss_l1_dssim")
 

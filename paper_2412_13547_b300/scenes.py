@@ -187,6 +187,18 @@ def target_image(width: int, height: int, index: int, seed_offset: int = 0) -> n
     return rng.uniform(0.0, 1.0, (height, width, 3)).astype(np.float32)
 
 
+def quantize_u8(img: np.ndarray) -> np.ndarray:
+    """An image in [0, 1] as 8-bit values (round to nearest), the form photographs
+    are stored in and the kernels accept as targets (GS_TARGET_U8)."""
+    return np.clip(np.rint(np.asarray(img, np.float64) * 255.0), 0, 255).astype(np.uint8)
+
+
+def u8_values(img8: np.ndarray) -> np.ndarray:
+    """The FP32 values the kernels read for an 8-bit target: t * (1/255), 1/255
+    rounded to FP32 and the product rounded to FP32."""
+    return np.asarray(img8, np.uint8).astype(np.float32) * np.float32(1.0 / 255.0)
+
+
 # ----------------------------------------------------------------------------
 # Named workloads
 # ----------------------------------------------------------------------------

@@ -38,6 +38,7 @@ def test_python_constants_match_the_header():
     assert int(defs["GS_GRAD2D_FLOATS"]) == R.GRAD2D_FLOATS
     assert int(defs["GS_ADAM_MAX_TENSORS"]) == R.ADAM_MAX_TENSORS
     assert int(defs["GS_MAX_VIEWS"]) == R.MAX_VIEWS
+    assert int(defs["GS_TARGET_F32"]) == R.TARGET_F32 and int(defs["GS_TARGET_U8"]) == R.TARGET_U8
     assert int(defs["GS_MAX_ROW_TENSORS"]) == R.GS_MAX_ROW_TENSORS
     assert shifts["GS_BIN_SORT_STATIC_SCRATCH_BYTES"] == R.BIN_SORT_STATIC_SCRATCH_BYTES
     for role in ("COPY", "MEANS", "LOG_SCALES", "QUATS", "STATE", "ZERO"):
@@ -117,6 +118,12 @@ def test_bad_arguments_are_rejected_before_launch():
     arr = (R.GsAdamTensor * 9)()
     assert lib.gs_adam(arr, 9, 0.9, 0.999, 1e-8, 1, None, None) == R.GS_ERR_ARG
     assert lib.gs_adam(arr, 1, 0.9, 0.999, 1e-8, 0, None, None) == R.GS_ERR_ARG
+    # a target type the kernels do not know
+    assert lib.gs_loss_l1(ctypes.byref(cam), ctypes.byref(dil), P(16), P(16), 7, P(16), P(16), None) == R.GS_ERR_ARG
+    assert "target_dtype" in lib.gs_last_error().decode()
+    ws = P(256)
+    assert lib.gs_ssim(ctypes.byref(cam), ctypes.byref(dil), P(16), P(16), 2, 0, P(16), None, ws, 1 << 30,
+                       None) == R.GS_ERR_ARG
     # empty inputs are a no-op success
     assert lib.gs_project(0, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_OK
 

@@ -492,6 +492,39 @@ def test_loss_l1_parity():
         np.testing.assert_allclose(dl.cpu().numpy(), g, rtol=1e-6, atol=1e-12)
 
 
+def _u8_target(tgt):
+    """An 8-bit target and the FP32 values the kernels read for it (t * (1/255),
+    1/255 rounded to FP32, the product rounded to FP32)."""
+    t8 = np.clip(np.rint(np.asarray(tgt, np.float64) * 255.0), 0, 255).astype(np.uint8)
+    return t8, t8.astype(np.float32) * np.float32(1.0 / 255.0)
+
+
+def test_loss_l1_parity_u8_target():
+    """An 8-bit target: the oracle on the values the header defines, and the
+    FP32 path given those values, agree with the 8-bit path (the gradient bit
+    for bit; the loss up to the order of its atomic sums)."""
+    _, cam, tgt = scene_small()
+    t8, t8f = _u8_target(tgt)
+    assert t8f.dtype == np.float32 and np.abs(t8f - tgt).max() <= 0.5 / 255 + 1e-7
+    for dil in [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0), R.Dilation(3, 2, 1)]:
+        w_ds, h_ds, _, _ = R.gs_grid(cam, dil)
+        img = np.random.default_rng(2).uniform(0, 1, (h_ds, w_ds, 3)).astype(np.float32)
+        img[0, 0] = t8f[dil.oy, dil.ox]  # a zero residual: sign(0) = 0 in both paths
+        t_img = torch.tensor(img, device=U.DEV)
+        outs = []
+        for target in (torch.tensor(t8, device=U.DEV), torch.tensor(t8f, device=U.DEV)):
+            dl = torch.empty_like(t_img)
+            loss = torch.zeros(1, device=U.DEV)
+            R.gs_loss_l1(cam, dil, t_img, target, dl, loss)
+            outs.append((loss.item(), dl.cpu().numpy()))
+        assert abs(outs[0][0] - outs[1][0]) <= 1e-6 * outs[1][0]
+        np.testing.assert_array_equal(outs[0][1], outs[1][1])
+        assert np.all(outs[0][1][0, 0] == 0.0)
+        L, g = orc.loss_l1(img, t8f.astype(np.float64), orc.as_camera(cam), orc.as_dilation(dil))
+        assert abs(outs[0][0] - L) < 1e-6 * max(1.0, L)
+        np.testing.assert_allclose(outs[0][1], g, rtol=1e-6, atol=1e-12)
+
+
 def test_densify_stats_parity():
     p32, cam, _ = scene_small()
     out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 1, 1))

@@ -40,6 +40,35 @@ CASES = [(40, 23, R.Dilation(1, 0, 0)), (131, 97, R.Dilation(1, 0, 0)), (300, 17
          (257, 199, R.Dilation(3, 2, 1))]
 
 
+def test_ssim_u8_target_matches_its_fp32_values():
+    """An 8-bit target gives the SSIM, the gradient and the D-SSIM loss of the
+    FP32 target holding t * (1/255) (the per-pixel results bit for bit, the
+    sums up to the order of their atomic additions), and the oracle's SSIM of it."""
+    w, h, dil = 300, 170, R.Dilation(2, 1, 0)
+    cam = _cam(w, h)
+    w_ds, h_ds, _, _ = R.gs_grid(cam, dil)
+    _, tgt = _images(w, h, 3)
+    img, _ = _images(w_ds, h_ds, 4)
+    t8 = np.clip(np.rint(tgt.astype(np.float64) * 255.0), 0, 255).astype(np.uint8)
+    t8f = t8.astype(np.float32) * np.float32(1.0 / 255.0)
+    ws = torch.empty(R.gs_ssim_workspace_size(cam, dil), dtype=torch.uint8, device=U.DEV)
+    ti = torch.tensor(img, device=U.DEV)
+    res = []
+    for target in (torch.tensor(t8, device=U.DEV), torch.tensor(t8f, device=U.DEV)):
+        out = torch.zeros(1, device=U.DEV)
+        g = torch.zeros((h_ds, w_ds, 3), device=U.DEV)
+        R.gs_ssim(cam, dil, ti, target, out, ws, d_img=g, mode=R.SSIM_SAME)
+        dl = torch.zeros((h_ds, w_ds, 3), device=U.DEV)
+        loss = torch.zeros(1, device=U.DEV)
+        R.gs_loss_l1_dssim(cam, dil, ti, target, 0.2, dl, loss, ws)
+        res.append((out.item(), g.cpu().numpy(), loss.item(), dl.cpu().numpy()))
+    assert abs(res[0][0] - res[1][0]) <= 1e-6 and abs(res[0][2] - res[1][2]) <= 1e-6 * abs(res[1][2])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    np.testing.assert_array_equal(res[0][3], res[1][3])
+    ref = S.ssim(img.astype(np.float64), _lattice(t8f.astype(np.float64), dil, w_ds, h_ds), mode="same")
+    assert abs(res[0][0] - ref) < SSIM_TOL
+
+
 def _lattice(tgt_hr, dil, w_ds, h_ds):
     return tgt_hr[dil.oy::dil.d, dil.ox::dil.d][:h_ds, :w_ds]
 

@@ -3,9 +3,10 @@
 Every kernel is launched through gs::launch, which allows programmatic
 dependent launch: a kernel may be scheduled before its predecessor on the
 stream has finished, so it must wait for it (kernel_prologue) before it
-touches memory. These checks keep that invariant: no kernel launched with the
-triple-chevron syntax, and every __global__ function's first statement is the
-prologue."""
+touches memory (gs::launch_serial, an ordinary launch, is kept for the
+kernels measured slower with it). These checks keep that invariant: no kernel
+launched with the triple-chevron syntax, and every __global__ function's
+first statement is the prologue."""
 import glob
 import os
 import re
