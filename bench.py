@@ -275,6 +275,10 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     ks = k_hist.cpu().numpy()
     if ks.max() > rast.capacity:
         raise RuntimeError(f"pair capacity {rast.capacity} exceeded ({ks.max()}); rerun with more headroom")
+    # the stage steps issue an event around every call: the host queues them behind a sleep
+    # so that its own pace (which varies between machines) leaves no gaps in the events' intervals
+    if stage_steps:
+        torch.cuda._sleep(int(8e6) * stage_steps)  # about 4 ms a step at 2 GHz
     for i in range(stage_steps):
         timed.run(i, cam, dil_of(warmup + steps + i), target_dev)
     torch.cuda.synchronize()
@@ -586,6 +590,8 @@ def run_sweep(args, device):
                 for i in range(warm):
                     timed.run(0, cam, dils[i % len(dils)], target)
                 torch.cuda.synchronize()
+                # queued behind a sleep, so that the host's pace leaves no gaps in the events' intervals
+                torch.cuda._sleep(int(8e6) * steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 for i in range(steps):
