@@ -358,7 +358,7 @@ k_depth_keys(int n, const float4* __restrict__ splats, const int* __restrict__ t
 constexpr int kLvlWarps = 8;              // warps per block of the level kernels
 constexpr int kLvlThreads = kLvlWarps * 32;
 constexpr int kRowChunk = 512;            // Gaussians per level-1 warp
-constexpr int kSegLen = 4096;             // row-list entries per level-2 segment (one CTA of 8 warps)
+constexpr int kSegLen = 2048;             // row-list entries per level-2 segment (one CTA of 8 warps)
 constexpr int kScanRows = 32;             // matrix rows per block of the column scans
 constexpr int kMaxGridSide = 4096;        // tiles_x, tiles_y limit (per-warp shared counters)
 
@@ -805,7 +805,9 @@ k_seg_hist(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t
 // cross-warp exclusive prefix per tile (starting from the segment's first slot
 // in M2) gives every warp its own counters, and the warps write the ids of
 // their sub-range into the row's tile lists, in order.
-__global__ void __launch_bounds__(kLvlThreads)
+// (6 CTAs per SM: 2048-entry segments and the higher occupancy took the 4K binning from 0.325 to
+// 0.321 ms)
+__global__ void __launch_bounds__(kLvlThreads, 6)
 k_seg_scatter(int TX, int TY, const uint32_t* __restrict__ rowstart, const uint32_t* __restrict__ rowlen,
               const uint32_t* __restrict__ segoff, const int64_t* __restrict__ d_NS,
               const uint2* __restrict__ rowlist, const uint32_t* __restrict__ M2,
