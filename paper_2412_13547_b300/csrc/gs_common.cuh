@@ -244,6 +244,54 @@ __device__ __forceinline__ float exp2_sfu(float x)
     return y;
 }
 
+// Two FP32 values in one 64-bit register pair, for the paired FP32
+// instructions of sm_100 and later (add/sub/mul/fma.rn.f32x2): one instruction
+// does the arithmetic of two pixels, each element rounded exactly as the
+// scalar instruction would round it.
+struct f32x2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f32x2 pk(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpk(f32x2 a, float& x, float& y)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+}
+__device__ __forceinline__ float pk_sum(f32x2 a)
+{
+    float x, y;
+    unpk(a, x, y);
+    return x + y;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
 constexpr float kLog2e = 1.44269504088896340736f;  // log2(e)
 constexpr float kLn2 = 0.693147180559945309417f;    // ln(2) = 1 / log2(e)
 

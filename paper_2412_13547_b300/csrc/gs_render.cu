@@ -474,6 +474,22 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
         gS[k] = T[k] * (g0[k] * bg.x + g1[k] * bg.y + g2[k] * bg.z);
         my_max = max(my_max, n_last[k]);
     }
+    // with an even number of pixels a thread replays them in pairs, two pixels per paired FP32
+    // instruction (pair q holds pixels 2q and 2q + 1)
+    constexpr bool PAIRS = (PPT % 2) == 0;
+    constexpr int NP = PAIRS ? PPT / 2 : 1;
+    f32x2 TP[NP], gSP[NP], g0P[NP], g1P[NP], g2P[NP], yrP[NP];
+    if constexpr (PAIRS) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            TP[q] = pk(T[2 * q], T[2 * q + 1]);
+            gSP[q] = pk(gS[2 * q], gS[2 * q + 1]);
+            g0P[q] = pk(g0[2 * q], g0[2 * q + 1]);
+            g1P[q] = pk(g1[2 * q], g1[2 * q + 1]);
+            g2P[q] = pk(g2[2 * q], g2[2 * q + 1]);
+            yrP[q] = pk(yr[2 * q], yr[2 * q + 1]);
+        }
+    }
     const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
@@ -570,6 +586,55 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                 const float4 c = s_rgb[j];
                 const float dx = __fsub_rn(xr, p.x);
                 const SplatRow row = splat_row(dx, co);
+                if constexpr (PAIRS) {
+                    // Pairs of pixels, branch-free: a pixel the entry does not reach (gate, or past
+                    // its last contributor) takes alpha = 0, so that its transmittance is divided
+                    // by 1 exactly and its weight and opacity terms are 0; the exponent is the
+                    // scalar form's, element by element.
+                    const f32x2 pyP = pk(p.y, p.y), czzP = pk(co.z, co.z);
+                    const f32x2 adxP = pk(row.adx2, row.adx2), bdxP = pk(row.bdx, row.bdx);
+                    const f32x2 cxP = pk(c.x, c.x), cyP = pk(c.y, c.y), czP = pk(c.z, c.z), oneP = pk(1.0f, 1.0f);
+                    f32x2 q0P = pk(0.0f, 0.0f), q1P = q0P, q2P = q0P, r6P = q0P, r7P = q0P, r8P = q0P;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const f32x2 dyP = sub2(yrP[q], pyP);
+                        const f32x2 e2P = fma2(bdxP, dyP, fma2(czzP, mul2(dyP, dyP), adxP));
+                        float e0, e1;
+                        unpk(e2P, e0, e1);
+                        const bool u0 = pos < n_last[2 * q] && splat_gate(e0, co.w);
+                        const bool u1 = pos < n_last[2 * q + 1] && splat_gate(e1, co.w);
+                        contrib = contrib || u0 || u1;
+                        const float a0 = exp2_sfu(e0), a1 = exp2_sfu(e1);  // alpha before the clamp
+                        const float al0 = u0 ? fminf(kAlphaMax, a0) : 0.0f;
+                        const float al1 = u1 ? fminf(kAlphaMax, a1) : 0.0f;
+                        // the opacity and conic terms only below the clamp
+                        const f32x2 aP = pk(u0 && a0 < kAlphaMax ? a0 : 0.0f, u1 && a1 < kAlphaMax ? a1 : 0.0f);
+                        const f32x2 alP = pk(al0, al1);
+                        float o0, o1;
+                        unpk(sub2(oneP, alP), o0, o1);
+                        const f32x2 invP = pk(__fdividef(1.0f, o0), __fdividef(1.0f, o1));
+                        const f32x2 TiP = mul2(TP[q], invP);
+                        const f32x2 wP = mul2(alP, TiP);
+                        r6P = fma2(wP, g0P[q], r6P);
+                        r7P = fma2(wP, g1P[q], r7P);
+                        r8P = fma2(wP, g2P[q], r8P);
+                        const f32x2 gcP = fma2(g2P[q], czP, fma2(g1P[q], cyP, mul2(g0P[q], cxP)));
+                        const f32x2 dalP = mul2(invP, sub2(mul2(TP[q], gcP), gSP[q]));
+                        gSP[q] = fma2(wP, gcP, gSP[q]);
+                        TP[q] = TiP;
+                        const f32x2 dpP = mul2(aP, dalP);
+                        const f32x2 tP = mul2(dpP, dyP);
+                        q0P = add2(q0P, dpP);
+                        q1P = add2(q1P, tP);
+                        q2P = fma2(tP, dyP, q2P);
+                    }
+                    q0 = pk_sum(q0P);
+                    q1 = pk_sum(q1P);
+                    q2 = pk_sum(q2P);
+                    r[6] = pk_sum(r6P);
+                    r[7] = pk_sum(r7P);
+                    r[8] = pk_sum(r8P);
+                } else {
                 // gates of all this thread's pixels first (branch-free), then the replay
                 float dyk[PPT], e2[PPT];
                 bool use[PPT];
@@ -606,6 +671,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                         q1 += t;
                         q2 = fmaf(t, dy, q2);
                     }
+                }
                 }
                 // dalpha/do = G = alpha / o: the opacity gradient is the dL/dpower sum over o
                 r[5] = q0 * c.w;
