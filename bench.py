@@ -137,6 +137,14 @@ KERNEL_OF_STAGE = {"project": "k_project", "render_fwd": "k_render_fwd", "render
                    "project_bwd_adam": "k_project_bwd_adam"}
 
 
+def gpu_sleep(cycles: int):
+    """Hold the current stream for about `cycles` SM clocks (torch's spin kernel), so that the host
+    can queue the launches behind it; a no-op where torch does not provide one."""
+    import torch
+    if hasattr(torch.cuda, "_sleep"):
+        torch.cuda._sleep(int(cycles))
+
+
 def barrier():
     """Barrier across the ranks of a multi-GPU run (replicas); a no-op on one GPU."""
     import torch.distributed as dist
@@ -278,7 +286,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     # the stage steps issue an event around every call: the host queues them behind a sleep
     # so that its own pace (which varies between machines) leaves no gaps in the events' intervals
     if stage_steps:
-        torch.cuda._sleep(int(8e6) * stage_steps)  # about 4 ms a step at 2 GHz
+        gpu_sleep(int(8e6) * stage_steps)  # about 4 ms a step at 2 GHz
     for i in range(stage_steps):
         timed.run(i, cam, dil_of(warmup + steps + i), target_dev)
     torch.cuda.synchronize()
@@ -591,7 +599,7 @@ def run_sweep(args, device):
                     timed.run(0, cam, dils[i % len(dils)], target)
                 torch.cuda.synchronize()
                 # queued behind a sleep, so that the host's pace leaves no gaps in the events' intervals
-                torch.cuda._sleep(int(8e6) * steps)
+                gpu_sleep(int(8e6) * steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 for i in range(steps):
