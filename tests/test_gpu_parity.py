@@ -380,6 +380,53 @@ def test_longest_first_order_does_not_change_results():
     assert U.max_rel(outs[1][3], outs[0][3]) < 1e-5
 
 
+@pytest.mark.parametrize("shift", [0, 2])
+def test_forward_reuses_the_backward_order_of_the_same_view(shift):
+    """After a backward, the next forward of the same camera and grid (another lattice
+    offset) launches in that backward's order (no order kernel): results bit-identical to the
+    list-length order; another camera gets the list-length order again."""
+    p32, cam, _ = scene_sh3(200, 150)
+    p = U.gpu_params(p32)
+    d0, d1 = R.Dilation(2, 0, 0, bin_shift=shift), R.Dilation(2, 1, 1, bin_shift=shift)
+    w_ds, h_ds, tx, ty = R.gs_grid(cam, d1)
+    grid = R.gs_bin_grid(cam, R.Dilation(2, 0, 0, bin_shift=0))
+    bg = (0.2, 0.2, 0.2)
+    rast = Rasterizer(p.n, capacity=1 << 17, max_grid=grid)
+    rast.project(p, cam, d0)
+    rast.bin_checked(cam, d0)
+    assert rast.fwd_order_kernels == 1
+    w0, h0, _, _ = R.gs_grid(cam, d0)
+    img, tf, last = image_buffers(h0, w0)
+    rast.render(cam, d0, bg, img, tf, last)
+    dl = torch.tensor(np.random.default_rng(1).standard_normal((h0, w0, 3)) * 1e-3, dtype=torch.float32,
+                      device=U.DEV)
+    rast.render_bwd(cam, d0, bg, tf, last, dl)
+    bwd_order = rast.bwd_order[:tx * ty].clone()
+    rast.project(p, cam, d1)
+    rast.bin_checked(cam, d1)
+    assert rast.fwd_order_kernels == 0
+    np.testing.assert_array_equal(rast.tile_order[:tx * ty].cpu().numpy(), bwd_order.cpu().numpy())
+    outs = []
+    for r in (rast, Rasterizer(p.n, capacity=1 << 17, max_grid=grid)):
+        if r is not rast:
+            r.project(p, cam, d1)
+            r.bin_checked(cam, d1)
+            assert r.fwd_order_kernels == 1
+        img, tf, last = image_buffers(h_ds, w_ds)
+        r.render(cam, d1, bg, img, tf, last)
+        torch.cuda.synchronize()
+        outs.append((img.cpu().numpy(), tf.cpu().numpy(), last.cpu().numpy()))
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    assert sorted(rast.tile_order[:tx * ty].cpu().numpy().tolist()) == list(range(tx * ty))
+    # another camera: the list-length order
+    cam2 = scenes.look_at(scenes.orbit_eye(3.0, 40.0, 15.0), width=200, height=150)
+    rast.render_bwd(cam, d1, bg, tf, last, torch.zeros(h_ds, w_ds, 3, device=U.DEV))
+    rast.project(p, cam2, d1)
+    rast.bin_checked(cam2, d1)
+    assert rast.fwd_order_kernels == 1
+
+
 def _tile_max_last(last, tile, tx, ty):
     h, w = last.shape
     pad = np.zeros((ty * tile, tx * tile), np.int64)
