@@ -423,6 +423,12 @@ class BatchTrainStep:
         self.dl = [torch.empty(g[1], g[0], 3, device=dev) for g in self.grid0]
         self.order = torch.zeros(sum(g[2] * g[3] for g in self.grid0), dtype=torch.int32, device=dev)
         self.bwd_order = torch.zeros_like(self.order)
+        # The forward launches in the previous backward's order when every view keeps its tile grid
+        # over the offset phases (the global tile layout is then the same in every phase) and that
+        # backward ran on this step's own views; otherwise in the list-length order.
+        self.reuse_order = all(len({R.gs_grid(c, self._dil(ph, i))[2:] for ph in range(self.phases)}) == 1
+                               for i, c in enumerate(self.cams))
+        self._bwd_order_ok = False
         # moments, device-side Adam step and densification statistics
         st = state or {}
         self.m = st.get("m") or [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -524,13 +530,17 @@ class BatchTrainStep:
 
     def render_pass(self, phase: int, counts: bool = False, table=None):
         """Everything up to the 2D gradients of every view (no parameter update)."""
+        own = table is None or table is self._tables.get((phase % self.phases, False))
         t = self.table(phase) if table is None else table
         self._project(t)
         self.bin_views(t)
         order = None
         if self.longest_first:
-            R.gs_tile_order_batch(t, self.order)
-            order = self.order
+            if own and self.reuse_order and self._bwd_order_ok:
+                order = self.bwd_order  # the previous backward's (tiles by the list extent they replayed)
+            else:
+                R.gs_tile_order_batch(t, self.order)
+                order = self.order
         R.gs_render_fwd_batch(self.p.n, t, self.bg, tile_order=order, counts=self.counts if counts else None,
                               pixels_per_thread=self.ppt)
         if self.dssim_lambda > 0.0:
@@ -542,6 +552,7 @@ class BatchTrainStep:
         if self.longest_first:
             R.gs_tile_order_by_last_batch(t, self.bwd_order)
             order = self.bwd_order
+            self._bwd_order_ok = own and self.reuse_order
         R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True,
                               pixels_per_thread=self.bwd_ppt)
 
@@ -594,10 +605,12 @@ class BatchTrainStep:
 
     def launches_per_step(self) -> int:
         """Kernels one step launches (memsets not counted): projection, the
-        binning of every view, the tile orders (the forward's, and the
-        backward's from `last`: two kernels), both blend launches, the loss
-        (zeroing + reduction), and the Adam step advance + the fused optimizer."""
-        return 1 + BIN_SORT_KERNELS * self.V + 3 * int(self.longest_first) + 1 + 2 + 1 + \
+        binning of every view, the tile orders (the forward's, none when it
+        reuses the previous backward's, and the backward's from `last`: two
+        kernels), both blend launches, the loss (zeroing + reduction), and the
+        Adam step advance + the fused optimizer."""
+        orders = (2 + (0 if self.reuse_order else 1)) if self.longest_first else 0
+        return 1 + BIN_SORT_KERNELS * self.V + orders + 1 + 2 + 1 + \
             (2 if self.optimize_step else 0)
 
 

@@ -15,7 +15,7 @@ import torch
 from oracle import oracle as orc
 from paper_2412_13547_b300 import raster as R
 from paper_2412_13547_b300 import scenes
-from paper_2412_13547_b300.pipeline import AdamConfig, BatchTrainStep, autotune_batch
+from paper_2412_13547_b300.pipeline import AdamConfig, BatchTrainStep, GaussianParams, autotune_batch
 
 import gpu_util as U
 
@@ -368,6 +368,8 @@ def test_batch_train_step_graph_replay_equals_eager(batch):
     st.capture()  # one eager step per phase, then one graph per phase
     torch.cuda.synchronize()
     assert st.step_dev.item() == st.phases
+    # odd image sizes change a view's tile grid with the offset: the list-length order every step
+    assert not st.reuse_order and not st._bwd_order_ok
     lrs = [st.adam.lr_means, st.adam.lr_log_scales, st.adam.lr_quats, st.adam.lr_opacity, st.adam.lr_sh]
     for ph in range(st.phases):
         snap = [t.clone() for t in _state(st)]
@@ -400,6 +402,35 @@ def test_batch_train_step_graph_replay_equals_eager(batch):
     assert not torch.equal(imgs[0], imgs[1])
     assert st.step_dev.item() == 3 * st.phases
     assert not st.overflowed()
+
+
+def test_batch_forward_in_the_previous_backward_order():
+    """Views whose tile grids do not change with the offset: after the first phase the
+    batched forward launches in the previous backward's order (no order kernel), with
+    results bit-identical to the list-length order."""
+    s = scenes.cluster_scene(20000, index=8, log_scale_mean=-3.6)
+    cams = [scenes.look_at(scenes.orbit_eye(2.6, az, 20.0), width=w, height=h)
+            for (w, h), az in (((256, 128), 20.0), ((192, 160), 140.0), ((320, 192), 260.0))]
+    tg = [torch.tensor(scenes.quantize_u8(scenes.target_image(c.width, c.height, 8, seed_offset=i + 1)), device=DEV)
+          for i, c in enumerate(cams)]
+    p32 = U.params_np(s)
+    p = U.gpu_params(p32)
+    st = BatchTrainStep(p, cams, tg, d=2)
+    assert st.reuse_order
+    st.run(0)
+    assert st._bwd_order_ok
+    snap = [t.clone() for t in p.tensors()]
+    st.run(1)  # its forward launches in the order the phase-0 backward made
+    torch.cuda.synchronize()
+    imgs = [x.clone() for x in st.img]
+    lasts = [x.clone() for x in st.last]
+    ref = BatchTrainStep(GaussianParams(*snap, snap[4]), cams, tg, d=2)
+    assert not ref._bwd_order_ok
+    ref.render_pass(1)  # the list-length order
+    torch.cuda.synchronize()
+    for i in range(len(cams)):
+        assert torch.equal(imgs[i], ref.img[i]), i
+        assert torch.equal(lasts[i], ref.last[i]), i
 
 
 def test_batch_train_step_reduces_loss(batch):
