@@ -107,6 +107,7 @@ class Rasterizer:
             self.ranges = torch.zeros(self.max_tiles, 2, dtype=torch.int32, device=self.device)
             self.tile_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
             self.bwd_order = torch.zeros(self.max_tiles, dtype=torch.int32, device=self.device)
+            self._bwd_order_for = None  # the new buffers hold no order
 
     def ensure_grid(self, tiles_x: int, tiles_y: int):
         """Grow the workspace so that binning grids up to (tiles_x, tiles_y) fit."""
