@@ -131,7 +131,8 @@ def bin_shift_for(d: int) -> int:
         return SHIFT[0]
     return max(0, min(2, 3 - int(math.log2(max(1, d)))))
 
-STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
+# render_fwd includes the L1 loss and the zeroing of the 2D-gradient rows, fused into the blend launch
+STAGES = ("project", "bin_sort", "render_fwd", "render_bwd", "project_bwd_adam")
 # stages that are one kernel launch each (the roofline's candidates for the dominant kernel)
 KERNEL_OF_STAGE = {"project": "k_project", "render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd",
                    "project_bwd_adam": "k_project_bwd_adam"}
@@ -215,14 +216,11 @@ class TimedStep:
         last = st.last[:P].view(h_ds, w_ds)
         dl = st.dl[:3 * P].view(h_ds, w_ds, 3)
         mark("render_fwd", 0)
-        rast.render(cam, dil, st.bg, img, t_final, last, st.counts if counts else None)
+        # the blend, the L1 loss and the zeroing of the 2D-gradient rows in one launch (TrainStep's path)
+        rast.render_l1(cam, dil, st.bg, img, t_final, last, target, dl, st.loss, st.counts if counts else None)
         mark("render_fwd", 1)
-        mark("loss", 0)
-        R.gs_loss_l1(cam, dil, img, target, dl, st.loss)
-        mark("loss", 1)
         mark("render_bwd", 0)
-        # the library zeroes the 2D-gradient rows (one memset) before the blend backward
-        rast.render_bwd(cam, dil, st.bg, t_final, last, dl, zero_grad2d=True)
+        rast.render_bwd(cam, dil, st.bg, t_final, last, dl, zero_grad2d=False)
         mark("render_bwd", 1)
         st.step_count += 1
         mark("project_bwd_adam", 0)
@@ -338,13 +336,9 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     # exponent (7), its scaling for the SFU exp, alpha, the clamp and the gate -- and 7 more
     # per blended one (transmittance, weight, three colour FMAs, the stop test)
     rows["render_fwd"] = ("alu", 12.0 * res["evaluated_per_step"] + 7.0 * res["blended_per_step"])
-    # L1 loss: the image read, dL/dimg written (12 B each per pixel) and the 8-bit target's lattice
-    # pixel read (3 B)
-    rows["loss"] = ("hbm", 27.0 * step_pixels)
     # blend backward: the same 12 gate operations per replayed (pixel, entry) and 41 per
     # contributing one (the replayed blends: transmittance recovery, the colour, alpha,
-    # exponent, conic and centre gradients); the stage's time includes the memset of the
-    # 2D-gradient rows it accumulates into (48 B per Gaussian, about 2% of the stage)
+    # exponent, conic and centre gradients)
     rows["render_bwd"] = ("alu", 12.0 * res["replayed_per_step"] + 41.0 * res["blended_per_step"])
     # projection backward + densification statistics + Adam, fused: parameters, moments and the
     # 2D record read, parameters and moments written, statistics read-modify-written
@@ -360,6 +354,10 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
             ach = work / (ms * 1e-3) / 1e12
             out[s] = dict(bound="alu", achieved=ach, peak=alu_peak, unit="TFLOP/s", frac=ach / alu_peak, ms=ms,
                           algorithmic=work)
+    # HBM bytes the forward's launch moves besides the blend: the L1 loss (dL/dimg written, 12 B a
+    # pixel, and the 8-bit target's lattice pixel read, 3 B; the image is not read back) and the
+    # zeroing of the 2D-gradient rows (48 B per Gaussian); counted in the step's HBM total
+    out["render_fwd"]["fused_hbm_bytes"] = 15.0 * step_pixels + 48.0 * n
     return out
 
 
@@ -388,7 +386,8 @@ def step_hbm(roof, ms_per_step, pk):
     """The step-level HBM roofline: the algorithmic bytes of every HBM-bound
     stage of one step over the whole step's time, against the measured copy
     bandwidth (the blend stages are ALU-bound and add their few bytes here)."""
-    total = sum(r["algorithmic"] for r in roof.values() if r["bound"] == "hbm")
+    total = sum(r["algorithmic"] for r in roof.values() if r["bound"] == "hbm") + \
+        sum(r.get("fused_hbm_bytes", 0.0) for r in roof.values())
     ach = total / (ms_per_step * 1e-3) / 1e9
     return {"bytes": total, "achieved": round(ach, 3), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(ach / pk["hbm_gbs"], 4)}
@@ -479,10 +478,10 @@ def measure_batch(args, device, d, steps, warmup):
         st.bin_views(t)
         R.gs_tile_order_batch(t, st.order)
         ev[2].record()
-        R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt)
-        R.gs_loss_l1_batch(t)
+        R.gs_render_fwd_batch(params.n, t, st.bg, tile_order=st.order, pixels_per_thread=ppt,
+                              flags=R.FWD_L1 | R.FWD_ZERO_GRAD2D)
         R.gs_tile_order_by_last_batch(t, st.bwd_order)
-        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.bwd_order, zero_grad2d=True,
+        R.gs_render_bwd_batch(params.n, t, st.bg, tile_order=st.bwd_order, zero_grad2d=False,
                               pixels_per_thread=st.bwd_ppt)
         ev[3].record()
         st.optimize(ph)

@@ -277,6 +277,25 @@ int32_t gs_loss_l1(const GsCamera* cam, const GsDilation* dil, const float* img,
                    const void* target, int32_t target_dtype, float* dl_dimg, float* loss, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_render_fwd_l1 -- gs_render_fwd and gs_loss_l1 in one launch (plus a
+ * one-thread kernel that zeroes *loss first): each pixel's L1 term and
+ * dL/dimg come from the colour the blend holds in registers, with
+ * gs_loss_l1's arithmetic (dl_dimg bit-identical; *loss equal up to the order
+ * of the float additions). grad2d_zero (nullable, n x 12, 16-byte aligned):
+ * zeroed by the same launch, for a gs_render_bwd with zero_grad2d = 0. The
+ * forward is bound by its arithmetic and leaves DRAM idle, so the loss and the
+ * zeroing cost it little, where as separate passes they would be paid in full.
+ * Other arguments, outputs and errors as gs_render_fwd and gs_loss_l1. */
+#define GS_FWD_L1 1
+#define GS_FWD_ZERO_GRAD2D 2
+int32_t gs_render_fwd_l1(int32_t n, const float* splats, const uint32_t* sorted_ids,
+                         const uint32_t* ranges, const GsCamera* cam, const GsDilation* dil,
+                         const float* bg, float* img, float* t_final, uint32_t* last,
+                         const void* target, int32_t target_dtype, float* dl_dimg, float* loss,
+                         float* grad2d_zero, unsigned long long* counts, int32_t pixels_per_thread,
+                         const uint32_t* tile_order, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * gs_ssim -- SSIM, the structural-similarity index (Wang et al. 2004) the
  * paper reports beside PSNR (Sec. 4, metrics), of the rendered lattice image
  * against the hr target sampled at the same pixels (as gs_loss_l1 samples it).
@@ -504,10 +523,13 @@ int32_t gs_tile_order_by_last_batch(const GsView* views, int32_t nviews, uint32_
  * the blend launches take the tiles of all views from one work queue
  * (tile_order, nullable = view by view). counts as in gs_render_fwd, summed
  * over views. gs_render_bwd_batch zeroes each view's grad2d first when
- * zero_grad2d != 0. */
+ * zero_grad2d != 0. gs_render_fwd_batch's flags (0, or GS_FWD_L1 and/or
+ * GS_FWD_ZERO_GRAD2D, as gs_render_fwd_l1 does for one view): GS_FWD_L1 also
+ * computes every view's L1 loss into its loss and dl_dimg from its target;
+ * GS_FWD_ZERO_GRAD2D zeroes every view's grad2d. */
 int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
                             const uint32_t* tile_order, unsigned long long* counts,
-                            int32_t pixels_per_thread, gs_stream_t stream);
+                            int32_t pixels_per_thread, int32_t flags, gs_stream_t stream);
 int32_t gs_loss_l1_batch(const GsView* views, int32_t nviews, gs_stream_t stream);
 int32_t gs_render_bwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
                             const uint32_t* tile_order, int32_t zero_grad2d,

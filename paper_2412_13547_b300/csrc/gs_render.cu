@@ -187,12 +187,18 @@ constexpr bool kBwdInterleave = true;
 // dropped while staging (what remains is this tile's own list, in order).
 // COUNT: the blend counts are accumulated (instrumentation, compiled out
 // when the caller passes no counts).
+// flags (GS_FWD_*, uniform over the launch): GS_FWD_ZERO_GRAD2D, this tile's
+// slice of the view's n 2D-gradient rows is zeroed (the CTAs of a view cover
+// all its rows; the forward leaves DRAM idle, so the stores cost it nothing);
+// GS_FWD_L1, each pixel's L1 loss term and dL/dimg are computed from the colour
+// in registers (the gs_loss_l1 arithmetic) and the tile's sum added to *loss.
 template <int TILE, int PPT, bool FILTER, bool COUNT>
 __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restrict__ splats,
                                                 const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
                                                 const Dil& dil, float3 bg, float* __restrict__ img,
                                                 float* __restrict__ t_final, uint32_t* __restrict__ last,
-                                                unsigned long long* __restrict__ counts)
+                                                unsigned long long* __restrict__ counts, const ViewDev& V, int n,
+                                                uint32_t flags)
 {
     using Geo = TileGeom<TILE, PPT>;
     constexpr int NT = Geo::THREADS, BATCH = Geo::BATCH;
@@ -213,6 +219,14 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
     const float xr = (float)(dil.d * wb.lx);
 
     if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
+    if (flags & GS_FWD_ZERO_GRAD2D) {
+        // rows [r0, r1) of this tile's share; a row is 3 float4 (16-byte aligned, checked on the host)
+        const int ntiles = dil.tiles_x * dil.tiles_y;
+        const int64_t per = ((int64_t)n + ntiles - 1) / ntiles;
+        const int64_t r0 = min((int64_t)n, (int64_t)tile * per), r1 = min((int64_t)n, r0 + per);
+        float4* g4 = reinterpret_cast<float4*>(V.grad2d);
+        for (int64_t i = 3 * r0 + threadIdx.x; i < 3 * r1; i += NT) g4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     const uint2 rg = ranges[FILTER ? bin_tile_of(dil, tile) : tile];
     float T[PPT], C0[PPT], C1[PPT], C2[PPT], yr[PPT];
     uint32_t last_pos[PPT], last_own[PPT];  // last blended entry: binning-list and own-list position + 1
@@ -338,16 +352,45 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
         }
         own_base += (uint32_t)cnt;
     }
+    const bool l1 = (flags & GS_FWD_L1) != 0;
+    const bool t8 = V.target_dtype == GS_TARGET_U8;
+    const float inv = (float)(1.0 / (3.0 * (double)dil.w_ds * (double)dil.h_ds));
+    float l1_acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int v = ty * TILE + wb.row(k);
         if (u < dil.w_ds && v < dil.h_ds) {
             const int64_t pix = (int64_t)v * dil.w_ds + u;
-            img[3 * pix] = fmaf(T[k], bg.x, C0[k]);
-            img[3 * pix + 1] = fmaf(T[k], bg.y, C1[k]);
-            img[3 * pix + 2] = fmaf(T[k], bg.z, C2[k]);
+            const float col[3] = {fmaf(T[k], bg.x, C0[k]), fmaf(T[k], bg.y, C1[k]), fmaf(T[k], bg.z, C2[k])};
+            img[3 * pix] = col[0];
+            img[3 * pix + 1] = col[1];
+            img[3 * pix + 2] = col[2];
             t_final[pix] = T[k];
             last[pix] = last_pos[k];
+            if (l1) {
+                // the L1 term against the hr target at the lattice pixel (gs_loss_l1's arithmetic)
+                const int64_t h = ((int64_t)(dil.d * v + dil.oy) * V.cam.width + (dil.d * u + dil.ox)) * 3;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float tg = t8 ? target_value<GS_TARGET_U8>(V.target, h + ch)
+                                        : target_value<GS_TARGET_F32>(V.target, h + ch);
+                    const float r = col[ch] - tg;
+                    l1_acc += fabsf(r);
+                    V.dl[3 * pix + ch] = r > 0.0f ? inv : (r < 0.0f ? -inv : 0.0f);
+                }
+            }
+        }
+    }
+    if (l1) {
+        __shared__ float s_l1[NT / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1_acc += __shfl_down_sync(0xffffffffu, l1_acc, o);
+        if ((threadIdx.x & 31) == 0) s_l1[threadIdx.x >> 5] = l1_acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < NT / 32; ++w) t += s_l1[w];
+            atomicAdd(V.loss, t * inv);
         }
     }
     if constexpr (COUNT) {
@@ -736,13 +779,13 @@ constexpr int bwd_min_blocks()
 template <int TILE, int PPT, bool MULTI, bool FILTER, bool COUNT>
 __global__ void __launch_bounds__(TileGeom<TILE, PPT>::THREADS, (fwd_min_blocks<TILE, PPT>()))
 k_render_fwd(const __grid_constant__ Batch b, const uint32_t* __restrict__ order, float3 bg,
-             unsigned long long* __restrict__ counts)
+             unsigned long long* __restrict__ counts, int n, uint32_t flags)
 {
     kernel_prologue();
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const ViewDev& V = b.v[MULTI ? view_of_tile(b, gt) : 0];
     render_fwd_tile<TILE, PPT, FILTER, COUNT>(gt - V.tile_begin, V.splats, V.ids, V.ranges, V.dil, bg, V.img,
-                                              V.t_final, V.last, counts);
+                                              V.t_final, V.last, counts, V, n, flags);
 }
 
 template <int TILE, int PPT, bool MULTI, bool FILTER>
@@ -1005,7 +1048,8 @@ bool any_shift(const Batch& b)
 }
 
 template <int TILE, int PPT>
-void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, cudaStream_t st)
+void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long long* counts, int n, uint32_t flags,
+                cudaStream_t st)
 {
     const bool multi = b.nviews > 1, filter = any_shift(b);
     auto kern = counts != nullptr
@@ -1014,7 +1058,7 @@ void launch_fwd(const Batch& b, const uint32_t* order, float3 bg, unsigned long 
         : (multi ? (filter ? k_render_fwd<TILE, PPT, true, true, false> : k_render_fwd<TILE, PPT, true, false, false>)
                  : (filter ? k_render_fwd<TILE, PPT, false, true, false>
                            : k_render_fwd<TILE, PPT, false, false, false>));
-    gs::launch(kern, b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st, b, order, bg, counts);
+    gs::launch(kern, b.total_tiles, TileGeom<TILE, PPT>::THREADS, 0, st, b, order, bg, counts, n, flags);
 }
 
 template <int TILE, int PPT>
@@ -1064,12 +1108,35 @@ int32_t gs_render_fwd(int32_t n, const float* splats, const uint32_t* sorted_ids
     v.img = img;
     v.t_final = t_final;
     v.last = last;
-    return gs_render_fwd_batch(n, &v, 1, bg, tile_order, counts, pixels_per_thread, stream);
+    return gs_render_fwd_batch(n, &v, 1, bg, tile_order, counts, pixels_per_thread, 0, stream);
+}
+
+int32_t gs_render_fwd_l1(int32_t n, const float* splats, const uint32_t* sorted_ids, const uint32_t* ranges,
+                         const GsCamera* cam, const GsDilation* dil, const float* bg, float* img, float* t_final,
+                         uint32_t* last, const void* target, int32_t target_dtype, float* dl_dimg, float* loss,
+                         float* grad2d_zero, unsigned long long* counts, int32_t pixels_per_thread,
+                         const uint32_t* tile_order, gs_stream_t stream)
+{
+    if (!cam || !dil) { gs_host::set_error("gs_render_fwd_l1: camera or dilation is null"); return GS_ERR_ARG; }
+    GsView v = gs::single_view(cam, dil);
+    v.splats = const_cast<float*>(splats);
+    v.sorted_ids = const_cast<uint32_t*>(sorted_ids);
+    v.ranges = const_cast<uint32_t*>(ranges);
+    v.img = img;
+    v.t_final = t_final;
+    v.last = last;
+    v.target = target;
+    v.target_dtype = target_dtype;
+    v.dl_dimg = dl_dimg;
+    v.loss = loss;
+    v.grad2d = grad2d_zero;
+    const int32_t flags = GS_FWD_L1 | (grad2d_zero ? GS_FWD_ZERO_GRAD2D : 0);
+    return gs_render_fwd_batch(n, &v, 1, bg, tile_order, counts, pixels_per_thread, flags, stream);
 }
 
 int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, const float* bg,
                             const uint32_t* tile_order, unsigned long long* counts, int32_t pixels_per_thread,
-                            gs_stream_t stream)
+                            int32_t flags, gs_stream_t stream)
 {
     using namespace gs;
     if (n < 0) { gs_host::set_error("n must be >= 0"); return GS_ERR_ARG; }
@@ -1083,11 +1150,28 @@ int32_t gs_render_fwd_batch(int32_t n, const GsView* views, int32_t nviews, cons
         }
     }
     if (!bg) { gs_host::set_error("gs_render_fwd: bg is null"); return GS_ERR_ARG; }
+    if ((flags & ~(GS_FWD_L1 | GS_FWD_ZERO_GRAD2D)) != 0) {
+        gs_host::set_error("gs_render_fwd: unknown flags");
+        return GS_ERR_ARG;
+    }
+    for (int i = 0; i < nviews; ++i) {
+        const ViewDev& v = b.v[i];
+        if ((flags & GS_FWD_L1) && (!v.target || !v.dl || !v.loss)) {
+            gs_host::set_error("gs_render_fwd: the fused loss needs target, dl_dimg and loss");
+            return GS_ERR_ARG;
+        }
+        if ((flags & GS_FWD_ZERO_GRAD2D) && n > 0 &&
+            (!v.grad2d || (reinterpret_cast<uintptr_t>(v.grad2d) & 15) != 0)) {
+            gs_host::set_error("gs_render_fwd: zeroing needs a 16-byte aligned grad2d");
+            return GS_ERR_ARG;
+        }
+    }
     const int ppt = resolve_ppt(b.v[0].dil.tile, pixels_per_thread, false, b.total_tiles);
     if (ppt < 0) return GS_ERR_ARG;
     const float3 c = make_float3(bg[0], bg[1], bg[2]);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GS_TILE_SWITCH(b.v[0].dil.tile, ppt, launch_fwd, b, tile_order, c, counts, st);
+    if (flags & GS_FWD_L1) gs::launch(k_loss_zero, 1, 32, 0, st, b);
+    GS_TILE_SWITCH(b.v[0].dil.tile, ppt, launch_fwd, b, tile_order, c, counts, n, (uint32_t)flags, st);
     return gs_host::check_launch("gs_render_fwd");
 }
 

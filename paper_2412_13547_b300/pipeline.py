@@ -169,6 +169,14 @@ class Rasterizer:
         R.gs_render_fwd(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last, counts,
                         pixels_per_thread=self.ppt, tile_order=self.tile_order if self.longest_first else None)
 
+    def render_l1(self, cam, dil: Dilation, bg, img, t_final, last, target, dl_dimg, loss, counts=None,
+                  zero_grad2d: bool = True):
+        """render() and the L1 loss (into loss and dl_dimg) in one launch, which also zeroes
+        the 2D-gradient rows for a render_bwd(..., zero_grad2d=False) when asked."""
+        R.gs_render_fwd_l1(self.n, self.splats, self.sorted_ids, self.ranges, cam, dil, bg, img, t_final, last,
+                           target, dl_dimg, loss, grad2d_zero=self.grad2d if zero_grad2d else None, counts=counts,
+                           pixels_per_thread=self.ppt, tile_order=self.tile_order if self.longest_first else None)
+
     def render_bwd(self, cam, dil: Dilation, bg, t_final, last, dl_dimg, zero_grad2d: bool = True):
         order = None
         if self.longest_first:
@@ -300,9 +308,15 @@ class TrainStep:
         t_final = self.t_final[:P].view(h_ds, w_ds)
         last = self.last[:P].view(h_ds, w_ds)
         dl = self.dl[:3 * P].view(h_ds, w_ds, 3)
-        rast.render(cam, dil, self.bg, img, t_final, last, self.counts if counts else None)
-        self.loss_and_grad(cam, dil, img, target, dl)
-        rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
+        if self.dssim_lambda <= 0.0:
+            # the blend, the L1 loss and the zeroing of the 2D-gradient rows in one launch
+            rast.render_l1(cam, dil, self.bg, img, t_final, last, target, dl, self.loss,
+                           self.counts if counts else None)
+            rast.render_bwd(cam, dil, self.bg, t_final, last, dl, zero_grad2d=False)
+        else:
+            rast.render(cam, dil, self.bg, img, t_final, last, self.counts if counts else None)
+            self.loss_and_grad(cam, dil, img, target, dl)
+            rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
         self.step_count += 1
         self.optimize(cam, dil)
         return self.loss
@@ -346,11 +360,13 @@ class TrainStep:
     def launches_per_step(self) -> int:
         """Kernels the last step launched (memsets not counted): projection, the
         binning, the forward's tile order (none when it reused the previous
-        backward's), blend, loss (zeroing + reduction), the backward's tile order
-        (two kernels), blend backward, and the fused optimizer (or projection
-        backward + Adam)."""
+        backward's), the loss zeroing and the blend with the L1 loss fused into it
+        (with D-SSIM: the blend, then the SSIM loss's three kernels), the
+        backward's tile order (two kernels), blend backward, and the fused
+        optimizer (or projection backward + Adam)."""
         orders = (self.rast.fwd_order_kernels + 2) if self.rast.longest_first else 0
-        return 1 + BIN_SORT_KERNELS + orders + 1 + 2 + 1 + (1 if self.fused else 2)
+        fwd_loss = 2 if self.dssim_lambda <= 0.0 else 1 + 3
+        return 1 + BIN_SORT_KERNELS + orders + fwd_loss + 1 + (1 if self.fused else 2)
 
 
 # kernels in one gs_bin_sort call given the projection's depth keys: a 4-pass radix sort
@@ -542,19 +558,19 @@ class BatchTrainStep:
             else:
                 R.gs_tile_order_batch(t, self.order)
                 order = self.order
+        # with the L1 loss, the loss and the zeroing of every view's 2D-gradient rows run in the blend launch
+        l1 = self.dssim_lambda <= 0.0
         R.gs_render_fwd_batch(self.p.n, t, self.bg, tile_order=order, counts=self.counts if counts else None,
-                              pixels_per_thread=self.ppt)
-        if self.dssim_lambda > 0.0:
+                              pixels_per_thread=self.ppt, flags=(R.FWD_L1 | R.FWD_ZERO_GRAD2D) if l1 else 0)
+        if not l1:
             # the views share one workspace: their loss calls run in order on this stream
             for v in t.views:
                 R.gs_loss_l1_dssim(v.cam, v.dil, v.img, v.target, self.dssim_lambda, v.dl_dimg, v.loss, self.ssim_ws)
-        else:
-            R.gs_loss_l1_batch(t)
         if self.longest_first:
             R.gs_tile_order_by_last_batch(t, self.bwd_order)
             order = self.bwd_order
             self._bwd_order_ok = own and self.reuse_order
-        R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=True,
+        R.gs_render_bwd_batch(self.p.n, t, self.bg, tile_order=order, zero_grad2d=not l1,
                               pixels_per_thread=self.bwd_ppt)
 
     def optimize(self, phase: int, table=None):
@@ -608,10 +624,12 @@ class BatchTrainStep:
         """Kernels one step launches (memsets not counted): projection, the
         binning of every view, the tile orders (the forward's, none when it
         reuses the previous backward's, and the backward's from `last`: two
-        kernels), both blend launches, the loss (zeroing + reduction), and the
-        Adam step advance + the fused optimizer."""
+        kernels), both blend launches, the loss zeroing (the L1 loss runs in
+        the forward launch; D-SSIM adds three kernels a view), and the Adam
+        step advance + the fused optimizer."""
         orders = (2 + (0 if self.reuse_order else 1)) if self.longest_first else 0
-        return 1 + BIN_SORT_KERNELS * self.V + orders + 1 + 2 + 1 + \
+        fwd_loss = 2 if self.dssim_lambda <= 0.0 else 1 + 3 * self.V
+        return 1 + BIN_SORT_KERNELS * self.V + orders + fwd_loss + 1 + \
             (2 if self.optimize_step else 0)
 
 

@@ -28,7 +28,7 @@ MAX_VIEWS = 16
 SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_bin_grid", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
            "gs_bin_sort_static", "gs_tile_order", "gs_render_fwd", "gs_loss_l1", "gs_render_bwd", "gs_project_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
-           "gs_tile_order_batch", "gs_tile_order_by_last_batch", "gs_render_fwd_batch", "gs_loss_l1_batch", "gs_render_bwd_batch",
+           "gs_tile_order_batch", "gs_tile_order_by_last_batch", "gs_render_fwd_batch", "gs_render_fwd_l1", "gs_loss_l1_batch", "gs_render_bwd_batch",
            "gs_project_bwd_adam_batch", "gs_densify_workspace_size", "gs_densify_select", "gs_prune_select",
            "gs_gather_rows", "gs_densify_grow", "gs_ssim_workspace_size", "gs_ssim", "gs_loss_l1_dssim")
 
@@ -204,7 +204,8 @@ def load():
     lib.gs_project_batch.argtypes = [i32, i32, i32, P, P, P, P, P, view_p, i32, P]
     lib.gs_tile_order_batch.argtypes = [view_p, i32, P, P]
     lib.gs_tile_order_by_last_batch.argtypes = [view_p, i32, P, P]
-    lib.gs_render_fwd_batch.argtypes = [i32, view_p, i32, P, P, P, i32, P]
+    lib.gs_render_fwd_batch.argtypes = [i32, view_p, i32, P, P, P, i32, i32, P]
+    lib.gs_render_fwd_l1.argtypes = [i32, P, P, P, cam_p, dil_p, P, P, P, P, P, i32, P, P, P, P, i32, P, P]
     lib.gs_loss_l1_batch.argtypes = [view_p, i32, P]
     lib.gs_render_bwd_batch.argtypes = [i32, view_p, i32, P, P, i32, i32, P]
     lib.gs_project_bwd_adam_batch.argtypes = [i32, i32, i32, P, view_p, i32, ctypes.POINTER(GsAdamParams), P, P, P,
@@ -357,6 +358,23 @@ def gs_render_fwd(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_
                                 int(pixels_per_thread), _ptr(tile_order), _stream(stream)), "gs_render_fwd")
 
 
+FWD_L1, FWD_ZERO_GRAD2D = 1, 2  # GS_FWD_L1, GS_FWD_ZERO_GRAD2D
+
+
+def gs_render_fwd_l1(n, splats, sorted_ids, ranges, cam, dil: Dilation, bg, img, t_final, last, target, dl_dimg,
+                     loss, grad2d_zero=None, counts=None, pixels_per_thread=0, tile_order=None, stream=None):
+    """gs_render_fwd and gs_loss_l1 in one launch; grad2d_zero (optional) is zeroed by it."""
+    _need_image(dil, cam, img, t_final, last, dl=dl_dimg)
+    _need(target, 3 * int(cam.width) * int(cam.height), "target")
+    _need(counts, 3, "counts")
+    _need(grad2d_zero, int(n) * GRAD2D_FLOATS, "grad2d")
+    _check(load().gs_render_fwd_l1(int(n), _ptr(splats), _ptr(sorted_ids), _ptr(ranges), ctypes.byref(camera(cam)),
+                                   ctypes.byref(dil.c()), _bg(bg), _ptr(img), _ptr(t_final), _ptr(last),
+                                   _ptr(target), target_dtype(target), _ptr(dl_dimg), _ptr(loss), _ptr(grad2d_zero),
+                                   _ptr(counts), int(pixels_per_thread), _ptr(tile_order), _stream(stream)),
+           "gs_render_fwd_l1")
+
+
 def gs_loss_l1(cam, dil: Dilation, img, target, dl_dimg, loss, stream=None):
     _need_image(dil, cam, img=img, dl=dl_dimg)
     _need(target, 3 * int(cam.width) * int(cam.height), "target")
@@ -502,11 +520,13 @@ def gs_tile_order_by_last_batch(views, order, stream=None):
            "gs_tile_order_by_last_batch")
 
 
-def gs_render_fwd_batch(n, views, bg, tile_order=None, counts=None, pixels_per_thread=0, stream=None):
+def gs_render_fwd_batch(n, views, bg, tile_order=None, counts=None, pixels_per_thread=0, flags=0, stream=None):
+    """flags: 0, or FWD_L1 (each view's L1 loss and dL/dimg from its target) and/or
+    FWD_ZERO_GRAD2D (each view's grad2d zeroed), fused into the blend launch."""
     t = _table(views)
     _need(counts, 3, "counts")
     _check(load().gs_render_fwd_batch(int(n), t.arr, t.n, _bg(bg), _ptr(tile_order), _ptr(counts),
-                                      int(pixels_per_thread), _stream(stream)), "gs_render_fwd_batch")
+                                      int(pixels_per_thread), int(flags), _stream(stream)), "gs_render_fwd_batch")
 
 
 def gs_loss_l1_batch(views, stream=None):

@@ -118,6 +118,15 @@ def test_bad_arguments_are_rejected_before_launch():
     arr = (R.GsAdamTensor * 9)()
     assert lib.gs_adam(arr, 9, 0.9, 0.999, 1e-8, 1, None, None) == R.GS_ERR_ARG
     assert lib.gs_adam(arr, 1, 0.9, 0.999, 1e-8, 0, None, None) == R.GS_ERR_ARG
+    # unknown forward flags, and the fused loss without its buffers
+    assert lib.gs_render_fwd_batch(0, None, 0, bg, None, None, 0, 0, None) == R.GS_ERR_ARG
+    v = (R.GsView * 1)()
+    v[0].cam, v[0].dil = cam, dil
+    v[0].ranges, v[0].img, v[0].t_final, v[0].last = 16, 16, 16, 16
+    assert lib.gs_render_fwd_batch(0, v, 1, bg, None, None, 0, 4, None) == R.GS_ERR_ARG
+    assert "flags" in lib.gs_last_error().decode()
+    assert lib.gs_render_fwd_batch(0, v, 1, bg, None, None, 0, R.FWD_L1, None) == R.GS_ERR_ARG
+    assert "fused loss" in lib.gs_last_error().decode()
     # a target type the kernels do not know
     assert lib.gs_loss_l1(ctypes.byref(cam), ctypes.byref(dil), P(16), P(16), 7, P(16), P(16), None) == R.GS_ERR_ARG
     assert "target_dtype" in lib.gs_last_error().decode()

@@ -217,6 +217,31 @@ def test_loss_batch_equals_single_views(batch):
         assert abs(b["loss"].item() - loss.item()) < 1e-6 * max(1.0, L)
 
 
+def test_render_fwd_batch_fused_loss_and_zeroing(batch):
+    """flags GS_FWD_L1 | GS_FWD_ZERO_GRAD2D: every view's image, dL/dimg and loss as the
+    separate batched calls give them, and every view's 2D-gradient rows zeroed."""
+    V = Views(*batch)
+    V.project()
+    V.bin()
+    order = V.order()
+    R.gs_render_fwd_batch(V.p.n, V.table(), BG, tile_order=order)
+    R.gs_loss_l1_batch(V.table())
+    torch.cuda.synchronize()
+    ref = [(b["img"].clone(), b["dl_dimg"].clone(), b["loss"].item()) for b in V.bufs]
+    for b in V.bufs:
+        b["img"].fill_(5.0)
+        b["dl_dimg"].fill_(5.0)
+        b["loss"].fill_(5.0)
+        b["grad2d"].fill_(5.0)
+    R.gs_render_fwd_batch(V.p.n, V.table(), BG, tile_order=order, flags=R.FWD_L1 | R.FWD_ZERO_GRAD2D)
+    torch.cuda.synchronize()
+    for b, (img, dl, loss) in zip(V.bufs, ref):
+        assert torch.equal(b["img"], img)
+        assert torch.equal(b["dl_dimg"], dl)
+        assert abs(b["loss"].item() - loss) <= 1e-6 * max(loss, 1e-12)
+        assert int(torch.count_nonzero(b["grad2d"]).item()) == 0
+
+
 def test_render_bwd_batch_equals_single_views(batch):
     V = Views(*batch)
     V.project()

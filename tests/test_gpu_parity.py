@@ -572,6 +572,43 @@ def test_loss_l1_parity_u8_target():
         np.testing.assert_allclose(outs[0][1], g, rtol=1e-6, atol=1e-12)
 
 
+@pytest.mark.parametrize("u8", [False, True], ids=["f32_target", "u8_target"])
+@pytest.mark.parametrize("dil", [R.Dilation(1, 0, 0), R.Dilation(2, 1, 0, bin_shift=2)], ids=["d1", "d2s2"])
+def test_render_fwd_l1_equals_the_separate_calls(dil, u8):
+    """gs_render_fwd_l1 = gs_render_fwd + gs_loss_l1 (image, T, last and dL/dimg bit for bit, the loss
+    up to the order of its sums) and leaves the 2D-gradient rows zeroed."""
+    p32, cam, tgt = scene_sh3(200, 150)
+    p = U.gpu_params(p32)
+    w_ds, h_ds, tx, ty = R.gs_grid(cam, dil)
+    rast = Rasterizer(p.n, capacity=1 << 18, max_grid=R.gs_bin_grid(cam, dil))
+    rast.project(p, cam, dil)
+    rast.bin_checked(cam, dil)
+    target = torch.tensor(scenes.quantize_u8(tgt) if u8 else tgt, device=U.DEV)
+    bg = (0.2, 0.3, 0.1)
+    img, tf, last = image_buffers(h_ds, w_ds)
+    rast.render(cam, dil, bg, img, tf, last)
+    dl = torch.empty_like(img)
+    loss = torch.zeros(1, device=U.DEV)
+    R.gs_loss_l1(cam, dil, img, target, dl, loss)
+    img2, tf2, last2 = image_buffers(h_ds, w_ds)
+    dl2 = torch.full_like(img, 7.0)
+    loss2 = torch.full((1,), 5.0, device=U.DEV)
+    rast.grad2d.fill_(3.0)
+    counts = torch.zeros(3, dtype=torch.int64, device=U.DEV)
+    rast.render_l1(cam, dil, bg, img2, tf2, last2, target, dl2, loss2, counts=counts)
+    torch.cuda.synchronize()
+    for a, b in ((img, img2), (tf, tf2), (last, last2), (dl, dl2)):
+        assert torch.equal(a, b)
+    assert abs(loss.item() - loss2.item()) <= 1e-6 * loss.item()
+    assert int(torch.count_nonzero(rast.grad2d).item()) == 0
+    assert counts[0].item() > 0
+    # without the zeroing the rows are left alone
+    rast.grad2d.fill_(3.0)
+    rast.render_l1(cam, dil, bg, img2, tf2, last2, target, dl2, loss2, zero_grad2d=False)
+    torch.cuda.synchronize()
+    assert bool((rast.grad2d == 3.0).all())
+
+
 def test_densify_stats_parity():
     p32, cam, _ = scene_small()
     out, rast, p, o, og, g2d, excl = backward_case(p32, cam, R.Dilation(2, 1, 1))
