@@ -196,16 +196,21 @@ class TimedStep:
         self.ev = {s: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                        for _ in range(steps)] for s in STAGES}
 
-    def run(self, i, cam, dil, target, counts=False):
-        from paper_2412_13547_b300 import raster as R
+    def run(self, i, cam, dil, target, counts=False, next_view=None):
+        from paper_2412_13547_b300.pipeline import _view_key
         st, p, rast = self.step, self.step.p, self.step.rast
         ev = self.ev
 
         def mark(name, k):
             ev[name][i][k].record()
 
+        # as TrainStep: no projection when the previous optimizer pass projected into this view
+        # (the stage then times an empty interval)
+        st.projected = st._projected_for is None or st._projected_for != _view_key(cam, dil)
         mark("project", 0)
-        rast.project(p, cam, dil)
+        if st.projected:
+            rast.project(p, cam, dil)
+        st._projected_for = None
         mark("project", 1)
         mark("bin_sort", 0)
         w_ds, h_ds, tx, ty = rast.bin(cam, dil)
@@ -224,7 +229,7 @@ class TimedStep:
         mark("render_bwd", 1)
         st.step_count += 1
         mark("project_bwd_adam", 0)
-        st.optimize(cam, dil)
+        st.optimize(cam, dil, next_view)
         mark("project_bwd_adam", 1)
         return st.loss
 
@@ -258,11 +263,14 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     stage_steps = min(steps, 20) if want_stage else 0
     timed = TimedStep(step, max(1, stage_steps))
     n_count = d * d  # instrumented steps (every offset once) for the blend counts, after the timed ones
-    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps + stage_steps + n_count)]
+    offsets = [scenes.rotating_offset(i, d) for i in range(warmup + steps + stage_steps + n_count + 1)]
     dil_of = lambda i: R.Dilation(d, offsets[i][0], offsets[i][1], tile=TILE[0], bin_shift=bin_shift_for(d))
     k_hist = torch.zeros(steps, dtype=torch.int64, device=device)
+    # the optimizer pass of each step also projects into the next step's view (unless
+    # --project-separately): the parameters cross HBM once per step
+    nxt = (lambda i: None) if args.project_separately else (lambda i: (cam, dil_of(i + 1)))
     for i in range(warmup):
-        step(cam, dil_of(i), target_dev)
+        step(cam, dil_of(i), target_dev, next_view=nxt(i))
     torch.cuda.synchronize()
     step.counts.zero_()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -272,7 +280,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
         barrier()
         start.record()
         for i in range(steps):
-            step(cam, dil_of(warmup + i), target_dev)
+            step(cam, dil_of(warmup + i), target_dev, next_view=nxt(warmup + i))
             k_hist[i:i + 1].copy_(rast.num_pairs_dev)
         end.record()
         torch.cuda.synchronize()
@@ -286,14 +294,15 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
     if stage_steps:
         gpu_sleep(int(8e6) * stage_steps)  # about 4 ms a step at 2 GHz
     for i in range(stage_steps):
-        timed.run(i, cam, dil_of(warmup + steps + i), target_dev)
+        timed.run(i, cam, dil_of(warmup + steps + i), target_dev, next_view=nxt(warmup + steps + i))
     torch.cuda.synchronize()
     stage = timed.stage_ms(stage_steps) if want_stage else None
     # the blend counts (instrumentation the training step does not need) from d*d further
     # steps, one per lattice offset, outside the timed region
     step.counts.zero_()
     for i in range(n_count):
-        timed.run(0, cam, dil_of(warmup + steps + stage_steps + i), target_dev, counts=True)
+        j = warmup + steps + stage_steps + i
+        timed.run(0, cam, dil_of(j), target_dev, counts=True, next_view=nxt(j))
     torch.cuda.synchronize()
     counts = step.counts.cpu().numpy() / n_count  # per step
     iters_per_s = steps * 1000.0 / total_ms
@@ -302,7 +311,7 @@ def measure_variant(args, params, cam, target_dev, d, sh_dtype, steps, warmup, d
                blends_contributing_per_s=float(counts[1]) * iters_per_s,
                pairs_mean=float(ks.mean()), loss=float(step.loss.item()), d=d,
                tile=TILE[0], bin_tile=TILE[0] << bin_shift_for(d),
-               sh_dtype=str(sh_dtype).replace("torch.", ""))
+               sh_dtype=str(sh_dtype).replace("torch.", ""), fused_next=not args.project_separately)
     if want_stage:
         res["stage_ms"] = stage
         res["evaluated_per_step"] = float(counts[0])
@@ -328,7 +337,10 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     params_b = n * (4 * (3 + 3 + 4 + 1) + sh_bytes)
     rows = {}
     # projection: parameters in, 48-B splat + radius + rect + tile count + depth key out
-    rows["project"] = ("hbm", params_b + n * (48 + 4 + 16 + 4 + 4))
+    proj_out = n * (48 + 4 + 16 + 4 + 4)
+    fused_next = res.get("fused_next", False)
+    if not fused_next:
+        rows["project"] = ("hbm", params_b + proj_out)
     # binning floor: one read and one write of (key, value) per pair plus the per-Gaussian depth
     # key, rect and tile count read and the sorted (key, id) written
     rows["bin_sort"] = ("hbm", 24.0 * k + n * (4 + 16 + 4 + 8))
@@ -341,8 +353,11 @@ def stage_roofline(res, n, sh_bytes, pk, step_pixels):
     # exponent, conic and centre gradients)
     rows["render_bwd"] = ("alu", 12.0 * res["replayed_per_step"] + 41.0 * res["blended_per_step"])
     # projection backward + densification statistics + Adam, fused: parameters, moments and the
-    # 2D record read, parameters and moments written, statistics read-modify-written
-    rows["project_bwd_adam"] = ("hbm", 2 * params_b + 4 * n * 59 * 4 + n * 48 + n * (24 + 4))
+    # 2D record read, parameters and moments written, statistics read-modify-written; with the
+    # next step's projection in the same pass, its outputs written too (the parameters it
+    # projects are the ones the pass already holds)
+    rows["project_bwd_adam"] = ("hbm", 2 * params_b + 4 * n * 59 * 4 + n * 48 + n * (24 + 4) +
+                                (proj_out if fused_next else 0))
     out = {}
     for s, (bound, work) in rows.items():
         ms = res["stage_ms"][s]
@@ -425,6 +440,8 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
     for b in range(2):
         free[b].record(comp)
     total = warmup + steps
+    offsets = [scenes.rotating_offset(i, d) for i in range(total + 1)]
+    dil_of = lambda i: R.Dilation(d, offsets[i][0], offsets[i][1], tile=TILE[0], bin_shift=bin_shift_for(d))
     issue_copy(0)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(total):
@@ -436,8 +453,8 @@ def e2e_measure(args, params, cam, target_np, d, steps, warmup, device, rast, sn
         if i + 1 < total:
             issue_copy(i + 1)
         comp.wait_event(ready[b])
-        ox, oy = scenes.rotating_offset(i, d)
-        loss = step(cam, R.Dilation(d, ox, oy, tile=TILE[0], bin_shift=bin_shift_for(d)), bufs[b])
+        nxt = None if args.project_separately else (cam, dil_of(i + 1))
+        loss = step(cam, dil_of(i), bufs[b], next_view=nxt)
         free[b].record(comp)
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     end.record()
@@ -594,15 +611,18 @@ def run_sweep(args, device):
                 w0, h0, _, _ = R.gs_grid(cam, dils[0])
                 step = TrainStep(params, rast, AdamConfig(), max_pixels=w0 * h0)
                 timed = TimedStep(step, steps)
+                # each optimizer pass projects into the next step's view, as in the headline step
+                nxt = (lambda i: None) if args.project_separately else \
+                    (lambda i: (cam, dils[(i + 1) % len(dils)]))
                 for i in range(warm):
-                    timed.run(0, cam, dils[i % len(dils)], target)
+                    timed.run(0, cam, dils[i % len(dils)], target, next_view=nxt(i))
                 torch.cuda.synchronize()
                 # queued behind a sleep, so that the host's pace leaves no gaps in the events' intervals
                 gpu_sleep(int(8e6) * steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 for i in range(steps):
-                    timed.run(i, cam, dils[i % len(dils)], target)
+                    timed.run(i, cam, dils[(warm + i) % len(dils)], target, next_view=nxt(warm + i))
                 e1.record()
                 torch.cuda.synchronize()
                 if rast.num_pairs() > rast.capacity:
@@ -826,6 +846,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="leave the 8-view batched variant out of the default run")
     ap.add_argument("--stages-json", default="")
+    ap.add_argument("--project-separately", action="store_true",
+                    help="project each step in its own launch instead of in the previous step's optimizer pass")
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread of the blend kernels (0 = default)")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile side of the lattice image")
     ap.add_argument("--sh-dtype", default="fp32", choices=["fp32", "bf16", "fp16"],
@@ -913,7 +935,7 @@ def main():
     sh_bytes = 48 * (4 if args.sh_dtype == "fp32" else 2)
     roof = stage_roofline(head, params.n, sh_bytes, pk, R.gs_grid(cam, R.Dilation(2, 1, 0))[0] *
                           R.gs_grid(cam, R.Dilation(2, 1, 0))[1])
-    dom = max(KERNEL_OF_STAGE, key=lambda s: roof[s]["ms"])
+    dom = max((s for s in KERNEL_OF_STAGE if s in roof), key=lambda s: roof[s]["ms"])
     dr = roof[dom]
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")

@@ -545,6 +545,28 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
                                   float* pos_acc, float* col_acc, int32_t* count,
                                   float* const* grads_out, gs_stream_t stream);
 
+/* gs_project_bwd_adam_next -- gs_project_bwd_adam (one view, dense Adam:
+ * adam->sparse must be 0) followed, in the same launch, by gs_project of the
+ * updated parameters into the next training step's view: next->cam and
+ * next->dil, outputs into next->splats (16-byte aligned), radii, rects
+ * (16-byte aligned), tiles_touched and depth_keys (nullable), exactly as
+ * gs_project(..., next->cam, next->dil, ...) would write them after this
+ * call: the same formulas on the same stored values, so radii, rects, tile
+ * counts, depth keys, centres, opacities and colours are equal, and the conic
+ * equal up to FP32 rounding (the two kernels may contract its products into
+ * FMAs differently); the parameters equal gs_project_bwd_adam's up to the
+ * same rounding of the gradient arithmetic. The
+ * next step then skips its projection: the parameters cross HBM once per step
+ * instead of twice. next's output buffers may be the ones this call's
+ * tiles_touched lives in (each Gaussian's count is read before it is
+ * rewritten). Errors: as gs_project_bwd_adam, plus GS_ERR_ARG for sparse Adam
+ * or a null or misaligned next buffer. */
+int32_t gs_project_bwd_adam_next(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                 const GsCamera* cam, const GsDilation* dil, const int32_t* tiles_touched,
+                                 const float* grad2d, const GsAdamParams* adam, float* pos_acc,
+                                 float* col_acc, int32_t* count, float* const* grads_out,
+                                 const GsView* next, gs_stream_t stream);
+
 /* ===========================================================================
  * Densification and pruning under a Gaussian budget (Sec. 3.2, Sec. 3.3).
  * Run once per densification interval. The host reads the device counts the

@@ -442,6 +442,14 @@ __device__ __forceinline__ void store_as(void* dst, int dtype, int64_t e, float 
     else reinterpret_cast<float*>(dst)[e] = val;
 }
 
+// The value store_as keeps for val, as FP32 (round to nearest for BF16/FP16).
+__device__ __forceinline__ float stored_value(int dtype, float val)
+{
+    if (dtype == GS_DTYPE_BF16) return __bfloat162float(__float2bfloat16_rn(val));
+    if (dtype == GS_DTYPE_F16) return __half2float(__float2half_rn(val));
+    return val;
+}
+
 // Four consecutive values stored as one vector in the given dtype: 8 bytes for
 // BF16/FP16 at element e (e a multiple of 4 and the array 8-byte aligned), 16
 // bytes for FP32.

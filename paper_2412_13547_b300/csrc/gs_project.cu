@@ -286,6 +286,35 @@ __device__ __forceinline__ void project_one(const Cam& cam, const Dil& dil, cons
 // Projection of every Gaussian into every view of the batch. The warp stages
 // its 32 parameter rows once and loops over the views, so the parameters are
 // read once per batch whatever the number of views.
+// The outputs of one Gaussian's projection into view V: the splat record, radius,
+// binning rect, tile count and depth key (an empty record for a culled one).
+__device__ __forceinline__ void write_projection(const ViewDev& V, int g, const Proj& P)
+{
+    float4* out = V.splats + 4 * (int64_t)g;
+    if (P.culled) {
+        out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
+        out[3] = make_float4(0.f, 0.f, __int_as_float(-1), __int_as_float(-1));
+        V.radii[g] = 0;
+        V.rects[g] = make_int4(0, 0, -1, -1);
+        V.tiles[g] = 0;
+        if (V.keys) V.keys[g] = 0xffffffffu;
+        return;
+    }
+    out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
+    out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
+    out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
+    out[3] = make_float4(__int_as_float(P.frect.x), __int_as_float(P.frect.y), __int_as_float(P.frect.z),
+                         __int_as_float(P.frect.w));
+    V.radii[g] = P.radius;
+    V.rects[g] = P.rect;
+    V.tiles[g] = P.tiles;
+    // the depth sort key: the float bits order like the positive depth; all ones is kept
+    // for the culled
+    if (V.keys) V.keys[g] = min(__float_as_uint(P.tz), 0xfffffffeu);
+}
+
 template <int DEG, int DT, bool MULTI>
 __global__ void __launch_bounds__(kThreads, MULTI ? 1 : 8)
 k_project(int n, const float* __restrict__ means, const float* __restrict__ log_scales,
@@ -328,29 +357,7 @@ k_project(int n, const float* __restrict__ means, const float* __restrict__ log_
             read_sh<DEG, DT>(s_sh, sh, g, lane, c);
             sh_colour<DEG>(V.cam, mean, c, P.dir, P.inv_vlen, P.rgb_raw);
         }
-        float4* out = V.splats + 4 * (int64_t)g;
-        if (P.culled) {
-            out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[2] = make_float4(0.f, P.tz, 0.f, 0.f);
-            out[3] = make_float4(0.f, 0.f, __int_as_float(-1), __int_as_float(-1));
-            V.radii[g] = 0;
-            V.rects[g] = make_int4(0, 0, -1, -1);
-            V.tiles[g] = 0;
-            if (V.keys) V.keys[g] = 0xffffffffu;
-            continue;
-        }
-        out[0] = make_float4(P.px.hi, P.py.hi, P.A, P.B);
-        out[1] = make_float4(P.C, P.opacity, fmaxf(P.rgb_raw[0], 0.0f), fmaxf(P.rgb_raw[1], 0.0f));
-        out[2] = make_float4(fmaxf(P.rgb_raw[2], 0.0f), P.tz, P.px.lo, P.py.lo);
-        out[3] = make_float4(__int_as_float(P.frect.x), __int_as_float(P.frect.y), __int_as_float(P.frect.z),
-                             __int_as_float(P.frect.w));
-        V.radii[g] = P.radius;
-        V.rects[g] = P.rect;
-        V.tiles[g] = P.tiles;
-        // the depth sort key: the float bits order like the positive depth; all ones is kept
-        // for the culled
-        if (V.keys) V.keys[g] = min(__float_as_uint(P.tz), 0xfffffffeu);
+        write_projection(V, g, P);
     }
 }
 
@@ -572,9 +579,12 @@ __device__ __forceinline__ bool visible_any(const Batch& b, int g)
 // gradients read from shared memory rows of stride GSTRIDE at column offset
 // goff. A full, dense warp moves 16-byte vectors with several in flight per
 // lane; otherwise one element at a time. Bit r of vis marks row r visible
-// (sparse Adam updates only those rows).
-template <int W, int GSTRIDE>
-__device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, int rows, const float* s_grad,
+// (sparse Adam updates only those rows). WB: each element's gradient slot in
+// shared memory takes the element's new value as the projection will read it
+// (the shadow's rounding when there is a shadow copy), for a projection of the
+// updated parameters in the same kernel (dense Adam only).
+template <int W, int GSTRIDE, bool WB = false>
+__device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, int rows, float* s_grad,
                                              int goff, unsigned vis, float bc1, float bc2, int lane, void* shadow,
                                              int shadow_dtype)
 {
@@ -621,9 +631,11 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int e = 4 * q + c;
-                    const float g = s_grad[(e / W) * GSTRIDE + goff + e % W];
+                    const int slot = (e / W) * GSTRIDE + goff + e % W;
+                    const float g = s_grad[slot];
                     adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
                     if (a.gout[t]) a.gout[t][base + e] = g;
+                    if constexpr (WB) s_grad[slot] = pp[c];
                 }
                 P4[q] = p[u];
                 M4[q] = m[u];
@@ -631,11 +643,23 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
                 if (shadow) store4_as(shadow, shadow_dtype, base + 4 * q, p[u]);
             }
         }
+        if constexpr (WB) {
+            // the shadow's rounding of the new values, in a pass of its own (a select in the
+            // loop above costs registers the streaming loads need)
+            if (shadow && shadow_dtype != GS_DTYPE_F32) {
+                __syncwarp();
+                for (int e = lane; e < 32 * W; e += 32) {
+                    const int slot = (e / W) * GSTRIDE + goff + e % W;
+                    s_grad[slot] = stored_value(shadow_dtype, s_grad[slot]);
+                }
+            }
+        }
         return;
     }
     for (int e = lane; e < rows * W; e += 32) {
         const int row = e / W, col = e % W;
-        const float g = s_grad[row * GSTRIDE + goff + col];
+        const int slot = row * GSTRIDE + goff + col;
+        const float g = s_grad[slot];
         if (a.gout[t]) a.gout[t][base + e] = g;
         if (a.sparse && !((vis >> row) & 1u)) continue;
         float p = P[e], m = M[e], v = V[e];
@@ -644,6 +668,7 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
         M[e] = m;
         V[e] = v;
         if (shadow) store_as(shadow, shadow_dtype, base + e, p);
+        if constexpr (WB) s_grad[slot] = shadow ? stored_value(shadow_dtype, p) : p;
     }
 }
 
@@ -653,8 +678,8 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
 // warp moves units of 4 values like adam_segment (an 8-byte vector of the
 // parameter, a 16-byte one of each moment: every warp access is contiguous), 4
 // units in flight per lane; otherwise one element at a time.
-template <int W, int GSTRIDE, int DT>
-__device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int rows, const float* s_grad,
+template <int W, int GSTRIDE, int DT, bool WB = false>
+__device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int rows, float* s_grad,
                                                   unsigned vis, float bc1, float bc2, int lane, void* store,
                                                   uint32_t sr)
 {
@@ -711,10 +736,12 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const int e = 4 * q + c;
-                        const float g = s_grad[(e / W) * GSTRIDE + e % W];
+                        const int slot = (e / W) * GSTRIDE + e % W;
+                        const float g = s_grad[slot];
                         adam_step(x[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
                         h[c] = sr_round(x[c], rb[c], DT);
                         if (gout) gout[base + e] = g;
+                        if constexpr (WB) s_grad[slot] = tofloat(h[c]);
                     }
                     P2[q] = make_uint2(__byte_perm(h[0], h[1], 0x5410), __byte_perm(h[2], h[3], 0x5410));
                     M4[q] = m[u];
@@ -725,14 +752,17 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
         }
         for (int e = lane; e < rows * W; e += 32) {
             const int row = e / W, col = e % W;
-            const float g = s_grad[row * GSTRIDE + col];
+            const int slot = row * GSTRIDE + col;
+            const float g = s_grad[slot];
             if (gout) gout[base + e] = g;
             if (a.sparse && !((vis >> row) & 1u)) continue;
             float x = tofloat(P[e]), m = M[e], v = V[e];
             adam_step(x, g, m, v, a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
-            P[e] = sr_round(x, sr_bits16(sr, (uint32_t)(base + e)), DT);
+            const uint16_t hv = sr_round(x, sr_bits16(sr, (uint32_t)(base + e)), DT);
+            P[e] = hv;
             M[e] = m;
             V[e] = v;
+            if constexpr (WB) s_grad[slot] = tofloat(hv);
         }
     }
 }
@@ -816,8 +846,13 @@ __device__ __forceinline__ bool fused_view_grad(const ViewDev& V, int g, const f
 // logits with all their loads issued together (one round trip to memory for
 // the four tensors): lanes below 24 take one 16-byte vector of each 3-float
 // tensor's 96 floats, every lane its own quaternion and logit.
-__device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g, const float* s_gms, float4 gq,
-                                                float glogit, float bc1, float bc2, int lane)
+// The means and log-scales of the warp's 32 rows (16-byte vectors, lanes 0..23)
+// and each lane's quaternion and opacity logit. The new means and log-scales also
+// go to their gradient slots in s_gms, and the lane's new quaternion and logit to
+// q_new and logit_new, for a projection of the updated parameters.
+__device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g, float* s_gms, float4 gq,
+                                                float glogit, float bc1, float bc2, int lane, float4& q_new,
+                                                float& logit_new)
 {
     const bool act = lane < 24;
     const int64_t b3 = (int64_t)g0 * 3;
@@ -842,9 +877,11 @@ __device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g,
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int e = 4 * lane + c;
-            const float gr = s_gms[(e / 3) * 7 + 3 * t + e % 3];
+            const int slot = (e / 3) * 7 + 3 * t + e % 3;
+            const float gr = s_gms[slot];
             adam_step(pp[c], gr, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
             if (a.gout[t]) a.gout[t][b3 + e] = gr;
+            s_gms[slot] = pp[c];
         }
         reinterpret_cast<float4*>(a.p[t] + b3)[lane] = p[t];
         reinterpret_cast<float4*>(a.m[t] + b3)[lane] = m[t];
@@ -863,18 +900,58 @@ __device__ __forceinline__ void adam_small_rows(const AdamDev& a, int g0, int g,
     a.v[3][g] = vo;
     if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
     if (a.gout[3]) a.gout[3][g] = glogit;
+    q_new = pq;
+    logit_new = po;
+}
+
+// The quaternion (16-byte row) and opacity logit of each lane's Gaussian, one
+// row per lane; their new values to q_new and logit_new.
+__device__ __forceinline__ void adam_quat_logit(const AdamDev& a, int g, bool valid, unsigned vis, float4 gq,
+                                                float glogit, float bc1, float bc2, int lane, float4& q_new,
+                                                float& logit_new)
+{
+    if (valid) {
+        if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
+        if (a.gout[3]) a.gout[3][g] = glogit;
+    }
+    if (valid && !(a.sparse && !((vis >> lane) & 1u))) {
+        float4 p = reinterpret_cast<float4*>(a.p[2])[g];
+        float4 m = reinterpret_cast<float4*>(a.m[2])[g];
+        float4 v = reinterpret_cast<float4*>(a.v[2])[g];
+        adam_step(p.x, gq.x, m.x, v.x, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.y, gq.y, m.y, v.y, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.z, gq.z, m.z, v.z, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        adam_step(p.w, gq.w, m.w, v.w, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
+        reinterpret_cast<float4*>(a.p[2])[g] = p;
+        reinterpret_cast<float4*>(a.m[2])[g] = m;
+        reinterpret_cast<float4*>(a.v[2])[g] = v;
+        float po = a.p[3][g], mo = a.m[3][g], vo = a.v[3][g];
+        adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, bc1, bc2, a.lr[3]);
+        a.p[3][g] = po;
+        a.m[3][g] = mo;
+        a.v[3][g] = vo;
+        q_new = p;
+        logit_new = po;
+    }
 }
 
 // One warp per 32 Gaussians: stage the parameters, project and differentiate
 // them in every view of the batch (gradients summed over views), then one
 // Adam step for the warp's rows. MULTI false is the one-view form, which
 // writes the gradients instead of accumulating them.
+// NEXT (one view, dense Adam): the updated parameters, which the Adam step also
+// leaves in the warp's shared-memory gradient slots, are then projected into
+// the next step's view nv (gs_project's formulas on the same stored values;
+// only the conic may round differently, as the two kernels contract its
+// products differently), so the next step reads the parameters from HBM once
+// instead of twice.
 // 5 CTAs per SM (96 registers, no spills): with 4 vectors per array in flight per
 // lane in the Adam step, 5 beat 4 and 6 (spills) on this streaming pass
-template <int DEG, int DT, bool MULTI>
+template <int DEG, int DT, bool MULTI, bool NEXT = false>
 __global__ void __launch_bounds__(kThreads, MULTI ? 4 : 5)
 k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b, AdamDev a,
-                   float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count)
+                   float* __restrict__ pos_acc, float* __restrict__ col_acc, int* __restrict__ count,
+                   const __grid_constant__ ViewDev nv)
 {
     kernel_prologue();
     using L = ShLayout<DEG, DT>;
@@ -969,43 +1046,50 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
         al |= reinterpret_cast<uintptr_t>(a.p[t]) | reinterpret_cast<uintptr_t>(a.m[t]) |
               reinterpret_cast<uintptr_t>(a.v[t]);
     const bool grouped = rows == 32 && !a.sparse && (al & 15) == 0;
+    float4 q_new = make_float4(0.f, 0.f, 0.f, 0.f);
+    float logit_new = 0.0f;
     if (grouped) {
-        adam_small_rows(a, g0, g, s_gms, gq, glogit, bc1, bc2, lane);
+        adam_small_rows(a, g0, g, s_gms, gq, glogit, bc1, bc2, lane, q_new, logit_new);
     } else {
-        adam_segment<3, 7>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
-        adam_segment<3, 7>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
+        adam_segment<3, 7, NEXT>(a, 0, g0, rows, s_gms, 0, vis, bc1, bc2, lane, nullptr, 0);
+        adam_segment<3, 7, NEXT>(a, 1, g0, rows, s_gms, 3, vis, bc1, bc2, lane, nullptr, 0);
     }
     if (a.lowp) {
         // the SH parameters are sh_store itself: each warp writes only the rows it staged
         const uint32_t sr = sr_base(a.sr_seed, a.step_dev ? (uint32_t)*a.step_dev : (uint32_t)a.step);
-        adam_segment_lowp<F::KW, F::GS, DT>(a, g0, rows, s_gsh, vis, bc1, bc2, lane, const_cast<void*>(sh_store), sr);
+        adam_segment_lowp<F::KW, F::GS, DT, NEXT>(a, g0, rows, s_gsh, vis, bc1, bc2, lane,
+                                                  const_cast<void*>(sh_store), sr);
     } else {
-        adam_segment<F::KW, F::GS>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
+        adam_segment<F::KW, F::GS, NEXT>(a, 4, g0, rows, s_gsh, 0, vis, bc1, bc2, lane, a.shadow, a.shadow_dtype);
     }
-    if (grouped) return;
-    // quaternions (16-byte rows) and opacity logits, one row per lane
-    if (valid) {
-        if (a.gout[2]) reinterpret_cast<float4*>(a.gout[2])[g] = gq;
-        if (a.gout[3]) a.gout[3][g] = glogit;
-    }
-    if (valid && !(a.sparse && !((vis >> lane) & 1u))) {
-        float4 p = reinterpret_cast<float4*>(a.p[2])[g];
-        float4 m = reinterpret_cast<float4*>(a.m[2])[g];
-        float4 v = reinterpret_cast<float4*>(a.v[2])[g];
-        adam_step(p.x, gq.x, m.x, v.x, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
-        adam_step(p.y, gq.y, m.y, v.y, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
-        adam_step(p.z, gq.z, m.z, v.z, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
-        adam_step(p.w, gq.w, m.w, v.w, a.b1, a.b2, a.eps, bc1, bc2, a.lr[2]);
-        reinterpret_cast<float4*>(a.p[2])[g] = p;
-        reinterpret_cast<float4*>(a.m[2])[g] = m;
-        reinterpret_cast<float4*>(a.v[2])[g] = v;
-        float po = a.p[3][g], mo = a.m[3][g], vo = a.v[3][g];
-        adam_step(po, glogit, mo, vo, a.b1, a.b2, a.eps, bc1, bc2, a.lr[3]);
-        a.p[3][g] = po;
-        a.m[3][g] = mo;
-        a.v[3][g] = vo;
+    if (!grouped) adam_quat_logit(a, g, valid, vis, gq, glogit, bc1, bc2, lane, q_new, logit_new);
+    if constexpr (NEXT) {
+        // the next step's projection from the updated values in the gradient slots
+        __syncwarp();
+        if (valid) {
+            float mean[3], ls[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                mean[j] = grow[j];
+                ls[j] = grow[3 + j];
+            }
+            // project_one, with the SH coefficients read only for a Gaussian the view keeps
+            // (as in k_project: they are live for its colour alone)
+            Proj P;
+            project_geometry<DEG>(nv.cam, nv.dil, mean, ls, q_new, logit_new, P);
+            if (!P.culled) {
+                float c[16][3];
+#pragma unroll
+                for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) c[k][ch] = gshrow[3 * k + ch];
+                sh_colour<DEG>(nv.cam, mean, c, P.dir, P.inv_vlen, P.rgb_raw);
+            }
+            write_projection(nv, g, P);
+        }
     }
 }
+
 
 // Advances the device-side Adam step and writes the bias corrections of the
 // new step, evaluated in double like the host path.
@@ -1066,14 +1150,16 @@ int32_t launch_project_bwd(int n, const float* means, const float* log_scales, c
 
 template <int DEG, int DT>
 int32_t launch_project_bwd_adam(int n, const void* sh_store, const Batch& b, const AdamDev& a, float* pos, float* col,
-                                int* cnt, cudaStream_t st)
+                                int* cnt, const ViewDev* next, cudaStream_t st)
 {
     using F = FusedLayout<DEG, DT>;
     size_t smem = sizeof(uint32_t) * F::WARP_WORDS * kWarps;
-    auto kern = b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>;
+    auto kern = next ? k_project_bwd_adam<DEG, DT, false, true>
+                     : (b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
-    gs::launch_serial(kern, blocks, kThreads, smem, st, n, sh_store, b, a, pos, col, cnt);
+    const ViewDev nv = next ? *next : ViewDev{};
+    gs::launch_serial(kern, blocks, kThreads, smem, st, n, sh_store, b, a, pos, col, cnt, nv);
     return gs_host::check_launch("gs_project_bwd_adam");
 }
 
@@ -1198,9 +1284,12 @@ int32_t gs_project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, cons
                                      grads_out, stream);
 }
 
-int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
-                                  const GsView* views, int32_t nviews, const GsAdamParams* adam, float* pos_acc,
-                                  float* col_acc, int32_t* count, float* const* grads_out, gs_stream_t stream)
+// The fused pass of gs_project_bwd_adam(_batch), and with next (one view, dense
+// Adam) the next step's projection of the updated parameters.
+static int32_t project_bwd_adam(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                const GsView* views, int32_t nviews, const GsAdamParams* adam, float* pos_acc,
+                                float* col_acc, int32_t* count, float* const* grads_out, const GsView* next,
+                                gs_stream_t stream)
 {
     using namespace gs;
     if (!adam) { gs_host::set_error("gs_project_bwd_adam: adam is null"); return GS_ERR_ARG; }
@@ -1209,6 +1298,22 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
         return GS_ERR_ARG;
     Batch b;
     if (!gs_host::make_batch(views, nviews, &b)) return GS_ERR_ARG;
+    Batch nb{};
+    if (next) {
+        if (nviews != 1 || adam->sparse) {
+            gs_host::set_error("gs_project_bwd_adam: the next view's projection needs one view and dense Adam");
+            return GS_ERR_ARG;
+        }
+        if (!gs_host::make_batch(next, 1, &nb)) return GS_ERR_ARG;
+        const ViewDev& v = nb.v[0];
+        if (n > 0 && (!v.splats || !v.radii || !v.rects || !v.tiles ||
+                      (reinterpret_cast<uintptr_t>(v.splats) & 15) != 0 ||
+                      (reinterpret_cast<uintptr_t>(v.rects) & 15) != 0)) {
+            gs_host::set_error("gs_project_bwd_adam: the next view needs 16-byte aligned splats and rects, radii "
+                               "and tiles_touched");
+            return GS_ERR_ARG;
+        }
+    }
     if (n > 0) {
         for (int t = 0; t < 5; ++t)
             if ((!adam->param[t] && t < 4) || !adam->m[t] || !adam->v[t]) {
@@ -1270,8 +1375,36 @@ int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype
     a.sr_seed = adam->sr_seed;
     a.step = adam->step;
     a.step_dev = adam->step_dev;
+    const ViewDev* nv = next ? &nb.v[0] : nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, b, a, pos_acc, col_acc, count, st);
+    GS_DISPATCH_DEG_DT(sh_degree, sh_dtype, launch_project_bwd_adam, n, sh_store, b, a, pos_acc, col_acc, count, nv,
+                       st);
+}
+
+int32_t gs_project_bwd_adam_batch(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                  const GsView* views, int32_t nviews, const GsAdamParams* adam, float* pos_acc,
+                                  float* col_acc, int32_t* count, float* const* grads_out, gs_stream_t stream)
+{
+    return project_bwd_adam(n, sh_degree, sh_dtype, sh_store, views, nviews, adam, pos_acc, col_acc, count,
+                            grads_out, nullptr, stream);
+}
+
+int32_t gs_project_bwd_adam_next(int32_t n, int32_t sh_degree, int32_t sh_dtype, const void* sh_store,
+                                 const GsCamera* cam, const GsDilation* dil, const int32_t* tiles_touched,
+                                 const float* grad2d, const GsAdamParams* adam, float* pos_acc, float* col_acc,
+                                 int32_t* count, float* const* grads_out, const GsView* next, gs_stream_t stream)
+{
+    if (!cam || !dil || !next) {
+        gs_host::set_error("gs_project_bwd_adam_next: camera, dilation or next view is null");
+        return GS_ERR_ARG;
+    }
+    GsView v{};
+    v.cam = *cam;
+    v.dil = *dil;
+    v.tiles_touched = const_cast<int32_t*>(tiles_touched);
+    v.grad2d = const_cast<float*>(grad2d);
+    return project_bwd_adam(n, sh_degree, sh_dtype, sh_store, &v, 1, adam, pos_acc, col_acc, count, grads_out, next,
+                            stream);
 }
 
 int32_t gs_adam_advance(int32_t* step_dev, float beta1, float beta2, float* bias_dev, gs_stream_t stream)

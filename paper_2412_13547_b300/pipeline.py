@@ -189,6 +189,11 @@ class Rasterizer:
                         self.grad2d, zero_grad2d=zero_grad2d, pixels_per_thread=self.ppt, tile_order=order)
 
 
+def _view_key(cam, dil: Dilation):
+    """A camera and dilation (lattice offset included), compared byte for byte."""
+    return (bytes(R.camera(cam)), bytes(dil.c()))
+
+
 def _order_key(cam, dil: Dilation, tx: int, ty: int):
     """What a launch order depends on: the view's camera and the tile grid (not the lattice offset)."""
     c = R.camera(cam)
@@ -281,6 +286,8 @@ class TrainStep:
         self.p, self.rast, self.adam, self.bg = params, rast, adam, tuple(bg)
         self.fused, self.sparse = bool(fused), bool(sparse)
         self.sr_seed = int(sr_seed)  # stream of the stochastic rounding of low-precision SH
+        self._projected_for = None  # the view the last optimizer pass projected the parameters into
+        self.projected = True  # the last step ran its own projection
         self.dssim_lambda = float(dssim_lambda)
         self.ssim_ws = None
         self.grads = [torch.zeros_like(t, dtype=torch.float32) for t in params.tensors()]
@@ -299,9 +306,17 @@ class TrainStep:
         self.col_acc = torch.zeros(n, device=dev)
         self.vis_count = torch.zeros(n, dtype=torch.int32, device=dev)
 
-    def __call__(self, cam, dil: Dilation, target: torch.Tensor, counts: bool = False):
+    def __call__(self, cam, dil: Dilation, target: torch.Tensor, counts: bool = False, next_view=None):
+        """One training step on (cam, dil, target). next_view (optional): the (camera,
+        dilation) of the next step; the optimizer pass then also projects the updated
+        parameters into it, and the next step on that view skips its projection (the
+        parameters cross HBM once per step). Anything that changes the parameters between
+        the two steps must call forget_projection()."""
         p, rast = self.p, self.rast
-        rast.project(p, cam, dil)
+        self.projected = self._projected_for is None or self._projected_for != _view_key(cam, dil)
+        if self.projected:
+            rast.project(p, cam, dil)
+        self._projected_for = None
         w_ds, h_ds, tx, ty = rast.bin(cam, dil)
         P = w_ds * h_ds
         img = self.img[:3 * P].view(h_ds, w_ds, 3)
@@ -318,8 +333,12 @@ class TrainStep:
             self.loss_and_grad(cam, dil, img, target, dl)
             rast.render_bwd(cam, dil, self.bg, t_final, last, dl)
         self.step_count += 1
-        self.optimize(cam, dil)
+        self.optimize(cam, dil, next_view)
         return self.loss
+
+    def forget_projection(self):
+        """The next step projects again (after the parameters changed outside the step)."""
+        self._projected_for = None
 
     def loss_and_grad(self, cam, dil: Dilation, img, target, dl):
         """The photometric loss into self.loss and dL/dimg into dl."""
@@ -331,7 +350,7 @@ class TrainStep:
             self.ssim_ws = torch.empty(need, dtype=torch.uint8, device=img.device)
         R.gs_loss_l1_dssim(cam, dil, img, target, self.dssim_lambda, dl, self.loss, self.ssim_ws)
 
-    def optimize(self, cam, dil: Dilation):
+    def optimize(self, cam, dil: Dilation, next_view=None):
         """Projection backward + densification statistics + Adam. The fused
         path (default) is one kernel; the unfused path writes the parameter
         gradients to self.grads and runs gs_adam."""
@@ -339,6 +358,15 @@ class TrainStep:
         lrs = [a.lr_means, a.lr_log_scales, a.lr_quats, a.lr_opacity, a.lr_sh]
         shadow = p.sh_store if p.sh_store.data_ptr() != p.sh.data_ptr() else None
         stats = (self.pos_acc, self.col_acc, self.vis_count) if self.densify else (None, None, None)
+        if self.fused and next_view is not None and not self.sparse:
+            ncam, ndil = next_view
+            nv = R.View(ncam, ndil, splats=rast.splats, radii=rast.radii, rects=rast.rects,
+                        tiles_touched=rast.tiles_touched, depth_keys=rast.depth_keys)
+            R.gs_project_bwd_adam_next(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,
+                                       p.sh_store, cam, dil, rast.tiles_touched, rast.grad2d, nv, sh_shadow=shadow,
+                                       pos_acc=stats[0], col_acc=stats[1], count=stats[2], sr_seed=self.sr_seed)
+            self._projected_for = _view_key(ncam, ndil)
+            return
         if self.fused:
             R.gs_project_bwd_adam(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,
                                   p.sh_store, cam, dil, rast.tiles_touched, rast.grad2d, sparse=self.sparse,
@@ -358,7 +386,8 @@ class TrainStep:
         R.gs_adam(entries, a.beta1, a.beta2, a.eps, self.step_count, row_mask=mask)
 
     def launches_per_step(self) -> int:
-        """Kernels the last step launched (memsets not counted): projection, the
+        """Kernels the last step launched (memsets not counted): projection (none
+        when the previous optimizer pass projected into this step's view), the
         binning, the forward's tile order (none when it reused the previous
         backward's), the loss zeroing and the blend with the L1 loss fused into it
         (with D-SSIM: the blend, then the SSIM loss's three kernels), the
@@ -366,7 +395,7 @@ class TrainStep:
         optimizer (or projection backward + Adam)."""
         orders = (self.rast.fwd_order_kernels + 2) if self.rast.longest_first else 0
         fwd_loss = 2 if self.dssim_lambda <= 0.0 else 1 + 3
-        return 1 + BIN_SORT_KERNELS + orders + fwd_loss + 1 + (1 if self.fused else 2)
+        return int(self.projected) + BIN_SORT_KERNELS + orders + fwd_loss + 1 + (1 if self.fused else 2)
 
 
 # kernels in one gs_bin_sort call given the projection's depth keys: a 4-pass radix sort

@@ -30,7 +30,8 @@ SYMBOLS = ("gs_version", "gs_last_error", "gs_grid", "gs_bin_grid", "gs_project"
            "gs_project_bwd_adam", "gs_adam_advance", "gs_densify_stats", "gs_adam", "gs_project_batch",
            "gs_tile_order_batch", "gs_tile_order_by_last_batch", "gs_render_fwd_batch", "gs_render_fwd_l1", "gs_loss_l1_batch", "gs_render_bwd_batch",
            "gs_project_bwd_adam_batch", "gs_densify_workspace_size", "gs_densify_select", "gs_prune_select",
-           "gs_gather_rows", "gs_densify_grow", "gs_ssim_workspace_size", "gs_ssim", "gs_loss_l1_dssim")
+           "gs_gather_rows", "gs_densify_grow", "gs_ssim_workspace_size", "gs_ssim", "gs_loss_l1_dssim",
+           "gs_project_bwd_adam_next")
 
 GS_MAX_ROW_TENSORS = 24
 GS_ROW_COPY, GS_ROW_MEANS, GS_ROW_LOG_SCALES, GS_ROW_QUATS, GS_ROW_STATE, GS_ROW_ZERO = range(6)
@@ -199,6 +200,8 @@ def load():
     lib.gs_project_bwd_adam.argtypes = [i32, i32, i32, P, cam_p, dil_p, P, P, ctypes.POINTER(GsAdamParams), P, P,
                                         P, P, P]
     lib.gs_adam.argtypes = [ctypes.POINTER(GsAdamTensor), i32, f32, f32, f32, i32, P, P]
+    lib.gs_project_bwd_adam_next.argtypes = [i32, i32, i32, P, cam_p, dil_p, P, P, ctypes.POINTER(GsAdamParams),
+                                             P, P, P, P, ctypes.POINTER(GsView), P]
     lib.gs_adam_advance.argtypes = [P, f32, f32, P, P]
     view_p = ctypes.POINTER(GsView)
     lib.gs_project_batch.argtypes = [i32, i32, i32, P, P, P, P, P, view_p, i32, P]
@@ -483,6 +486,24 @@ def gs_project_bwd_adam(params, m, v, lrs, beta1, beta2, eps, step, sh_store, ca
                                       _ptr(pos_acc), _ptr(col_acc), _ptr(count), _grads_out(grads_out),
                                       _stream(stream)),
            "gs_project_bwd_adam")
+
+
+def gs_project_bwd_adam_next(params, m, v, lrs, beta1, beta2, eps, step, sh_store, cam, dil: Dilation,
+                             tiles_touched, grad2d, next_view, sh_shadow=None, pos_acc=None, col_acc=None, count=None,
+                             grads_out=None, bias_dev=None, step_dev=None, sr_seed=0, stream=None):
+    """gs_project_bwd_adam (dense Adam) and, in the same launch, gs_project of the updated
+    parameters into next_view (a View: its cam, dil, splats, radii, rects, tiles_touched and
+    depth_keys)."""
+    n = params[0].shape[0]
+    deg = sh_degree_of(params[4])
+    _lowp_sh(params, sh_store)
+    a = _adam_params(params, m, v, lrs, beta1, beta2, eps, step, False, sh_shadow, bias_dev, step_dev, sr_seed)
+    nv = next_view if isinstance(next_view, ViewTable) else ViewTable([next_view])
+    _check(load().gs_project_bwd_adam_next(n, deg, _SH_DTYPE[sh_store.dtype], _ptr(sh_store),
+                                           ctypes.byref(camera(cam)), ctypes.byref(dil.c()), _ptr(tiles_touched),
+                                           _ptr(grad2d), ctypes.byref(a), _ptr(pos_acc), _ptr(col_acc), _ptr(count),
+                                           _grads_out(grads_out), nv.arr, _stream(stream)),
+           "gs_project_bwd_adam_next")
 
 
 def gs_adam_advance(step_dev, beta1, beta2, bias_dev, stream=None):
