@@ -197,7 +197,6 @@ class TimedStep:
                        for _ in range(steps)] for s in STAGES}
 
     def run(self, i, cam, dil, target, counts=False, next_view=None):
-        from paper_2412_13547_b300.pipeline import _view_key
         st, p, rast = self.step, self.step.p, self.step.rast
         ev = self.ev
 
@@ -206,7 +205,7 @@ class TimedStep:
 
         # as TrainStep: no projection when the previous optimizer pass projected into this view
         # (the stage then times an empty interval)
-        st.projected = st._projected_for is None or st._projected_for != _view_key(cam, dil)
+        st.projected = st._projected_for is None or st._projected_for != st._proj_key(cam, dil)
         mark("project", 0)
         if st.projected:
             rast.project(p, cam, dil)

@@ -313,7 +313,7 @@ class TrainStep:
         parameters cross HBM once per step). Anything that changes the parameters between
         the two steps must call forget_projection()."""
         p, rast = self.p, self.rast
-        self.projected = self._projected_for is None or self._projected_for != _view_key(cam, dil)
+        self.projected = self._projected_for is None or self._projected_for != self._proj_key(cam, dil)
         if self.projected:
             rast.project(p, cam, dil)
         self._projected_for = None
@@ -340,6 +340,15 @@ class TrainStep:
         """The next step projects again (after the parameters changed outside the step)."""
         self._projected_for = None
 
+    def _proj_key(self, cam, dil: Dilation):
+        """What a projection the optimizer pass wrote stands for: the view, and the parameter
+        and output tensors it was made from and into (a densification that reallocates them,
+        or a resized rasterizer, makes the next step project again by itself; an in-place
+        change of the parameters needs forget_projection())."""
+        p, r = self.p, self.rast
+        return _view_key(cam, dil) + (p.n, p.means.data_ptr(), p.sh_store.data_ptr(), r.splats.data_ptr(),
+                                      r.depth_keys.data_ptr())
+
     def loss_and_grad(self, cam, dil: Dilation, img, target, dl):
         """The photometric loss into self.loss and dL/dimg into dl."""
         if self.dssim_lambda <= 0.0:
@@ -365,7 +374,7 @@ class TrainStep:
             R.gs_project_bwd_adam_next(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,
                                        p.sh_store, cam, dil, rast.tiles_touched, rast.grad2d, nv, sh_shadow=shadow,
                                        pos_acc=stats[0], col_acc=stats[1], count=stats[2], sr_seed=self.sr_seed)
-            self._projected_for = _view_key(ncam, ndil)
+            self._projected_for = self._proj_key(ncam, ndil)
             return
         if self.fused:
             R.gs_project_bwd_adam(p.tensors(), self.m, self.v, lrs, a.beta1, a.beta2, a.eps, self.step_count,

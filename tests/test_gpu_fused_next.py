@@ -128,3 +128,25 @@ def test_train_step_with_the_next_view_equals_projecting_each_step():
         assert (diff > 1e-6 * (1.0 + y.abs())).float().mean().item() < 0.01
     assert (runs[0][2] - runs[1][2]).abs().max().item() < 1e-2
     assert runs[0][3] == [True] * 6 and runs[1][3] == [True] + [False] * 5
+
+
+def test_reallocated_parameters_or_another_view_project_again():
+    """The projection an optimizer pass carries to the next step is used only for the view it was
+    made for and the tensors it was made from: another view, or parameters reallocated between
+    the steps (as densification does), make the step project on its own."""
+    p32, cam = _scene(0)
+    tgt = torch.tensor(scenes.quantize_u8(scenes.target_image(cam.width, cam.height, 3)), device=U.DEV)
+    d0, d1 = R.Dilation(2, 0, 0, bin_shift=1), R.Dilation(2, 1, 0, bin_shift=1)
+    p = U.gpu_params(p32)
+    rast = Rasterizer(p.n, capacity=1 << 18, max_grid=R.gs_bin_grid(cam, d0))
+    w, h, _, _ = R.gs_grid(cam, d0)
+    st = TrainStep(p, rast, max_pixels=w * h)
+    st(cam, d0, tgt, next_view=(cam, d1))
+    st(cam, d0, tgt, next_view=(cam, d1))  # not the view the last pass projected into
+    assert st.projected
+    st(cam, d1, tgt, next_view=(cam, d0))  # the carried projection
+    assert not st.projected
+    p.means = p.means.clone()  # reallocated between the steps
+    st(cam, d0, tgt)
+    assert st.projected
+    torch.cuda.synchronize()
