@@ -133,6 +133,30 @@ def test_bad_arguments_are_rejected_before_launch():
     ws = P(256)
     assert lib.gs_ssim(ctypes.byref(cam), ctypes.byref(dil), P(16), P(16), 2, 0, P(16), None, ws, 1 << 30,
                        None) == R.GS_ERR_ARG
+    # the optimizer pass with the next view's projection: the next view is required, the Adam
+    # dense, and its output buffers present and 16-byte aligned
+    adam = R.GsAdamParams()
+    for t in range(5):
+        adam.param[t], adam.m[t], adam.v[t] = 256 * (t + 1), 256 * (t + 6), 256 * (t + 11)
+    adam.beta1, adam.beta2, adam.step = 0.9, 0.999, 1
+    nxt = (R.GsView * 1)()
+    nxt[0].cam, nxt[0].dil = cam, dil
+    nxt[0].splats, nxt[0].radii, nxt[0].rects, nxt[0].tiles_touched = 4096, 4096, 4096, 4096
+
+    def bwd_next(next_view):
+        return lib.gs_project_bwd_adam_next(8, 0, 0, P(4096), ctypes.byref(cam), ctypes.byref(dil), P(4096),
+                                            P(4096), ctypes.byref(adam), None, None, None, None, next_view, None)
+    assert bwd_next(None) == R.GS_ERR_ARG
+    assert "next view is null" in lib.gs_last_error().decode()
+    adam.sparse = 1
+    assert bwd_next(nxt) == R.GS_ERR_ARG
+    assert "dense Adam" in lib.gs_last_error().decode()
+    adam.sparse = 0
+    nxt[0].splats = 4104  # 8-byte aligned only
+    assert bwd_next(nxt) == R.GS_ERR_ARG
+    assert "16-byte aligned" in lib.gs_last_error().decode()
+    nxt[0].splats, nxt[0].radii = 4096, None
+    assert bwd_next(nxt) == R.GS_ERR_ARG
     # empty inputs are a no-op success
     assert lib.gs_project(0, 0, 0, *[None] * 5, ctypes.byref(cam), ctypes.byref(dil), *[None] * 5, None) == R.GS_OK
 
