@@ -38,10 +38,15 @@ __device__ __forceinline__ void warp_stage(const uint32_t* __restrict__ src, int
         auto put = [&](int q) {
             const uint4 v = __ldg(b4 + q);
             const int w0 = 4 * q;
-            dst[((w0 + 0) / W) * S + (w0 + 0) % W] = v.x;
-            dst[((w0 + 1) / W) * S + (w0 + 1) % W] = v.y;
-            dst[((w0 + 2) / W) * S + (w0 + 2) % W] = v.z;
-            dst[((w0 + 3) / W) * S + (w0 + 3) % W] = v.w;
+            if constexpr (W % 4 == 0 && S % 4 == 0) {
+                // 16-byte aligned rows (dst 16-byte aligned): one vector store, conflict-free
+                *reinterpret_cast<uint4*>(dst + (w0 / W) * S + w0 % W) = v;
+            } else {
+                dst[((w0 + 0) / W) * S + (w0 + 0) % W] = v.x;
+                dst[((w0 + 1) / W) * S + (w0 + 1) % W] = v.y;
+                dst[((w0 + 2) / W) * S + (w0 + 2) % W] = v.z;
+                dst[((w0 + 3) / W) * S + (w0 + 3) % W] = v.w;
+            }
         };
         if constexpr (FEW) {
 #pragma unroll 4
@@ -56,6 +61,46 @@ __device__ __forceinline__ void warp_stage(const uint32_t* __restrict__ src, int
         for (int w = lane; w < rows * W; w += 32) dst[(w / W) * S + w % W] = __ldg(base + w);
     }
     __syncwarp();
+}
+
+// A lane's row of 3K floats in shared memory (16-byte aligned, 3K a multiple
+// of 4) to c, and back, as 16-byte vectors: with a row stride that is a
+// multiple of 4 words but not of 32 lanes' worth, 8 lanes' vectors fall on
+// distinct banks, so these are conflict-free where per-float accesses to such
+// rows would conflict.
+template <int K>
+__device__ __forceinline__ void row_load_vec(const float* row, float (&c)[16][3])
+{
+    static_assert((3 * K) % 4 == 0, "whole vectors");
+#pragma unroll
+    for (int i = 0; i < 3 * K / 4; ++i) {
+        const float4 v = reinterpret_cast<const float4*>(row)[i];
+        c[(4 * i + 0) / 3][(4 * i + 0) % 3] = v.x;
+        c[(4 * i + 1) / 3][(4 * i + 1) % 3] = v.y;
+        c[(4 * i + 2) / 3][(4 * i + 2) % 3] = v.z;
+        c[(4 * i + 3) / 3][(4 * i + 3) % 3] = v.w;
+    }
+}
+
+template <int N, bool VEC>
+__device__ __forceinline__ void zero_row(float* row)
+{
+    if constexpr (VEC) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) reinterpret_cast<float4*>(row)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) row[e] = 0.0f;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void row_store_vec(float* row, const float* vals)
+{
+    static_assert(N % 4 == 0, "whole vectors");
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+        reinterpret_cast<float4*>(row)[i] = make_float4(vals[4 * i], vals[4 * i + 1], vals[4 * i + 2], vals[4 * i + 3]);
 }
 
 template <int DEG, int DT>
@@ -75,7 +120,9 @@ __device__ __forceinline__ void read_sh(const uint32_t* s_sh, const void* sh, in
     using L = ShLayout<DEG, DT>;
     if constexpr (L::STAGE) {
         const uint32_t* row = s_sh + lane * STRIDE;
-        if constexpr (DT == GS_DTYPE_F32) {
+        if constexpr (DT == GS_DTYPE_F32 && STRIDE % 4 == 0 && (L::K * 3) % 4 == 0) {
+            row_load_vec<L::K>(reinterpret_cast<const float*>(row), c);
+        } else if constexpr (DT == GS_DTYPE_F32) {
 #pragma unroll
             for (int k = 0; k < L::K; ++k)
 #pragma unroll
@@ -146,7 +193,7 @@ __device__ __forceinline__ void sh_colour(const Cam& cam, const float* mean, con
 // Backward of sh_colour for dL/drgb = grgb (zero where the colour was clamped):
 // dL/dsh_k = Y_k grgb into gsh[3k + ch] (written, or added when ACC), and the
 // mean's gradient through the direction into gm.
-template <int DEG, bool ACC>
+template <int DEG, bool ACC, bool VEC = false>
 __device__ __forceinline__ void sh_colour_bwd(const float* dir, float inv_vlen, const float* rgb_raw,
                                               const float (&c)[16][3], float g0, float g1, float g2, float* gsh,
                                               float* gm)
@@ -160,8 +207,21 @@ __device__ __forceinline__ void sh_colour_bwd(const float* dir, float inv_vlen, 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         wsh[k] = grgb[0] * c[k][0] + grgb[1] * c[k][1] + grgb[2] * c[k][2];
+        if constexpr (!VEC) {
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = ACC ? gsh[3 * k + ch] + Y[k] * grgb[ch] : Y[k] * grgb[ch];
+            for (int ch = 0; ch < 3; ++ch)
+                gsh[3 * k + ch] = ACC ? gsh[3 * k + ch] + Y[k] * grgb[ch] : Y[k] * grgb[ch];
+        }
+    }
+    if constexpr (VEC) {
+        // a 16-byte aligned row of 3K floats (3K a multiple of 4), written as vectors
+        static_assert(!ACC, "the vector form writes");
+        float gv[48];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gv[3 * k + ch] = Y[k] * grgb[ch];
+        row_store_vec<3 * K>(gsh, gv);
     }
     float gdx, gdy, gdz;
     sh_basis_vjp(DEG, dir[0], dir[1], dir[2], wsh, gdx, gdy, gdz);
@@ -556,15 +616,23 @@ struct AdamDev {
     const int* step_dev;
 };
 
-template <int DEG, int DT>
+template <int DEG, int DT, bool MULTI>
 struct FusedLayout {
     using L = ShLayout<DEG, DT>;
     static constexpr int KW = L::K * 3;                   // SH floats per Gaussian
     static constexpr int GS0 = KW % 2 == 0 ? KW + 1 : KW;  // odd stride of the SH gradient rows
+    // VEC (one view, FP32 SH, rows of whole 16-byte vectors): the rows are 16-byte
+    // aligned with an odd number of vectors per row, and every access to them is a
+    // 16-byte vector (the staging, the reads of the staged row, the gradient row's
+    // writes, Adam's reads of the gradients and write-back of the new values, the
+    // next view's projection): conflict-free, where the per-float accesses to the
+    // odd-stride rows of the other forms conflict 4 ways in the vector passes
+    static constexpr bool VEC = !MULTI && DT == GS_DTYPE_F32 && KW % 4 == 0;
     // one region per lane row: first the staged SH coefficients, then (same lane,
     // after it has read them) its SH gradients
-    static constexpr int GS = (L::STAGE && L::S > GS0) ? L::S : GS0;
+    static constexpr int GS = VEC ? ((KW / 4) % 2 == 1 ? KW : KW + 4) : ((L::STAGE && L::S > GS0) ? L::S : GS0);
     static constexpr int WARP_WORDS = 32 * (3 + 3) + 32 * 7 + 32 * GS;
+    static_assert(!VEC || WARP_WORDS % 4 == 0, "16-byte aligned warp regions");
 };
 
 // Visible in at least one view of the batch (the rows sparse Adam updates).
@@ -628,14 +696,27 @@ __device__ __forceinline__ void adam_segment(const AdamDev& a, int t, int g0, in
                 float* pp = &p[u].x;
                 float* mm = &m[u].x;
                 float* vv = &v[u].x;
+                if constexpr (GSTRIDE % 4 == 0 && W % 4 == 0) {
+                    // 16-byte aligned gradient rows (goff 0): the vector's 4 slots as one vector
+                    float4* gslot = reinterpret_cast<float4*>(s_grad + ((4 * q) / W) * GSTRIDE + goff + (4 * q) % W);
+                    const float4 g4 = *gslot;
+                    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int e = 4 * q + c;
-                    const int slot = (e / W) * GSTRIDE + goff + e % W;
-                    const float g = s_grad[slot];
-                    adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
-                    if (a.gout[t]) a.gout[t][base + e] = g;
-                    if constexpr (WB) s_grad[slot] = pp[c];
+                    for (int c = 0; c < 4; ++c) {
+                        adam_step(pp[c], gv[c], mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
+                        if (a.gout[t]) a.gout[t][base + 4 * q + c] = gv[c];
+                    }
+                    if constexpr (WB) *gslot = p[u];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int e = 4 * q + c;
+                        const int slot = (e / W) * GSTRIDE + goff + e % W;
+                        const float g = s_grad[slot];
+                        adam_step(pp[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[t]);
+                        if (a.gout[t]) a.gout[t][base + e] = g;
+                        if constexpr (WB) s_grad[slot] = pp[c];
+                    }
                 }
                 P4[q] = p[u];
                 M4[q] = m[u];
@@ -955,8 +1036,8 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
 {
     kernel_prologue();
     using L = ShLayout<DEG, DT>;
-    using F = FusedLayout<DEG, DT>;
-    extern __shared__ uint32_t smem[];
+    using F = FusedLayout<DEG, DT, MULTI>;
+    extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g0 = (blockIdx.x * kWarps + warp) * 32;
     if (g0 >= n) return;
@@ -1007,15 +1088,14 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
             const float4 G1 = V.grad2d[3 * (int64_t)g + 1], G2 = V.grad2d[3 * (int64_t)g + 2];
             float dir[3], inv_vlen, rgb_raw[3], gm_dir[3];
             sh_colour<DEG>(V.cam, mean, c, dir, inv_vlen, rgb_raw);
-            sh_colour_bwd<DEG, false>(dir, inv_vlen, rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
+            sh_colour_bwd<DEG, false, F::VEC>(dir, inv_vlen, rgb_raw, c, G1.z, G1.w, G2.x, gshrow, gm_dir);
             have_grad = true;
             Proj P;
             project_geometry<DEG>(V.cam, V.dil, mean, ls, q, logit, P);
             if (P.culled) {
                 // only with tiles counted at other parameters than these: no gradient, as in
                 // the unfused backward
-#pragma unroll
-                for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
+                zero_row<F::KW, F::VEC>(gshrow);
             } else {
                 const float4 G0 = V.grad2d[3 * (int64_t)g];
                 densify_one(g, V.tiles, G0, G1, G2, pos_acc, col_acc, count);
@@ -1031,10 +1111,7 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
             }
         }
     }
-    if (!have_grad) {
-#pragma unroll
-        for (int e = 0; e < F::KW; ++e) gshrow[e] = 0.0f;
-    }
+    if (!have_grad) zero_row<F::KW, F::VEC>(gshrow);
     __syncwarp();
     // a Gaussian is visible for sparse Adam when it touches a tile in any view
     const unsigned vis = __ballot_sync(0xffffffffu, a.sparse && valid && visible_any(b, g));
@@ -1079,10 +1156,14 @@ k_project_bwd_adam(int n, const void* sh_store, const __grid_constant__ Batch b,
             project_geometry<DEG>(nv.cam, nv.dil, mean, ls, q_new, logit_new, P);
             if (!P.culled) {
                 float c[16][3];
+                if constexpr (F::VEC) {
+                    row_load_vec<(DEG + 1) * (DEG + 1)>(gshrow, c);
+                } else {
 #pragma unroll
-                for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
+                    for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) c[k][ch] = gshrow[3 * k + ch];
+                        for (int ch = 0; ch < 3; ++ch) c[k][ch] = gshrow[3 * k + ch];
+                }
                 sh_colour<DEG>(nv.cam, mean, c, P.dir, P.inv_vlen, P.rgb_raw);
             }
             write_projection(nv, g, P);
@@ -1152,10 +1233,11 @@ template <int DEG, int DT>
 int32_t launch_project_bwd_adam(int n, const void* sh_store, const Batch& b, const AdamDev& a, float* pos, float* col,
                                 int* cnt, const ViewDev* next, cudaStream_t st)
 {
-    using F = FusedLayout<DEG, DT>;
-    size_t smem = sizeof(uint32_t) * F::WARP_WORDS * kWarps;
+    const bool multi = !next && b.nviews > 1;
+    size_t smem = sizeof(uint32_t) * kWarps *
+                  (multi ? FusedLayout<DEG, DT, true>::WARP_WORDS : FusedLayout<DEG, DT, false>::WARP_WORDS);
     auto kern = next ? k_project_bwd_adam<DEG, DT, false, true>
-                     : (b.nviews > 1 ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>);
+                     : (multi ? k_project_bwd_adam<DEG, DT, true> : k_project_bwd_adam<DEG, DT, false>);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = (n + kThreads - 1) / kThreads;
     const ViewDev nv = next ? *next : ViewDev{};
