@@ -122,6 +122,21 @@ __device__ __forceinline__ void read_sh(const uint32_t* s_sh, const void* sh, in
         const uint32_t* row = s_sh + lane * STRIDE;
         if constexpr (DT == GS_DTYPE_F32 && STRIDE % 4 == 0 && (L::K * 3) % 4 == 0) {
             row_load_vec<L::K>(reinterpret_cast<const float*>(row), c);
+        } else if constexpr (DT != GS_DTYPE_F32 && STRIDE % 4 == 0 && L::W % 4 == 0) {
+            // 16-bit values, 8 to a 16-byte vector
+#pragma unroll
+            for (int i = 0; i < L::W / 4; ++i) {
+                const uint4 wv = reinterpret_cast<const uint4*>(row)[i];
+                const uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const uint16_t hv = (h & 1) ? (uint16_t)(w4[h >> 1] >> 16) : (uint16_t)(w4[h >> 1] & 0xffffu);
+                    float f;
+                    if constexpr (DT == GS_DTYPE_BF16) f = __bfloat162float(__ushort_as_bfloat16(hv));
+                    else f = __half2float(__ushort_as_half(hv));
+                    c[(8 * i + h) / 3][(8 * i + h) % 3] = f;
+                }
+            }
         } else if constexpr (DT == GS_DTYPE_F32) {
 #pragma unroll
             for (int k = 0; k < L::K; ++k)
@@ -621,13 +636,13 @@ struct FusedLayout {
     using L = ShLayout<DEG, DT>;
     static constexpr int KW = L::K * 3;                   // SH floats per Gaussian
     static constexpr int GS0 = KW % 2 == 0 ? KW + 1 : KW;  // odd stride of the SH gradient rows
-    // VEC (one view, FP32 SH, rows of whole 16-byte vectors): the rows are 16-byte
+    // VEC (one view, rows of whole 16-byte vectors both as stored and as FP32 gradients): the rows are 16-byte
     // aligned with an odd number of vectors per row, and every access to them is a
     // 16-byte vector (the staging, the reads of the staged row, the gradient row's
     // writes, Adam's reads of the gradients and write-back of the new values, the
     // next view's projection): conflict-free, where the per-float accesses to the
     // odd-stride rows of the other forms conflict 4 ways in the vector passes
-    static constexpr bool VEC = !MULTI && DT == GS_DTYPE_F32 && KW % 4 == 0;
+    static constexpr bool VEC = !MULTI && KW % 4 == 0 && (DT == GS_DTYPE_F32 || (KW / 2) % 4 == 0);
     // one region per lane row: first the staged SH coefficients, then (same lane,
     // after it has read them) its SH gradients
     static constexpr int GS = VEC ? ((KW / 4) % 2 == 1 ? KW : KW + 4) : ((L::STAGE && L::S > GS0) ? L::S : GS0);
@@ -814,15 +829,29 @@ __device__ __forceinline__ void adam_segment_lowp(const AdamDev& a, int g0, int 
                     const uint32_t r01 = pcg_hash(sr + k2), r23 = pcg_hash(sr + k2 + 1u);
                     const uint32_t rb[4] = {r01 & 0xffffu, r01 >> 16, r23 & 0xffffu, r23 >> 16};
                     uint32_t h[4];
+                    if constexpr (GSTRIDE % 4 == 0 && W % 4 == 0) {
+                        // 16-byte aligned gradient rows: the unit's 4 slots as one vector
+                        float4* gslot = reinterpret_cast<float4*>(s_grad + ((4 * q) / W) * GSTRIDE + (4 * q) % W);
+                        const float4 g4 = *gslot;
+                        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int e = 4 * q + c;
-                        const int slot = (e / W) * GSTRIDE + e % W;
-                        const float g = s_grad[slot];
-                        adam_step(x[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
-                        h[c] = sr_round(x[c], rb[c], DT);
-                        if (gout) gout[base + e] = g;
-                        if constexpr (WB) s_grad[slot] = tofloat(h[c]);
+                        for (int c = 0; c < 4; ++c) {
+                            adam_step(x[c], gv[c], mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
+                            h[c] = sr_round(x[c], rb[c], DT);
+                            if (gout) gout[base + 4 * q + c] = gv[c];
+                        }
+                        if constexpr (WB) *gslot = make_float4(tofloat(h[0]), tofloat(h[1]), tofloat(h[2]), tofloat(h[3]));
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int e = 4 * q + c;
+                            const int slot = (e / W) * GSTRIDE + e % W;
+                            const float g = s_grad[slot];
+                            adam_step(x[c], g, mm[c], vv[c], a.b1, a.b2, a.eps, bc1, bc2, a.lr[4]);
+                            h[c] = sr_round(x[c], rb[c], DT);
+                            if (gout) gout[base + e] = g;
+                            if constexpr (WB) s_grad[slot] = tofloat(h[c]);
+                        }
                     }
                     P2[q] = make_uint2(__byte_perm(h[0], h[1], 0x5410), __byte_perm(h[2], h[3], 0x5410));
                     M4[q] = m[u];
