@@ -942,7 +942,8 @@ def main():
         try:
             tj = json.load(open(tpath))
             ent = tj.get("kernels", {}).get(KERNEL_OF_STAGE[dom])
-            if ent and tj.get("source_hash") == _source_hash() and tj.get("workload") == args.workload:
+            if (ent and ent.get("source_hash") == _source_hash(KERNEL_OF_STAGE[dom])
+                    and tj.get("workload") == args.workload):
                 traffic = ent.get("bytes_per_launch")
         except Exception:
             traffic = None
@@ -1000,7 +1001,7 @@ def main():
 
 def write_traffic(csv_path, workload):
     """Mean DRAM bytes (read + write) per launch of each of our kernels in an
-    ncu CSV log, tagged with the hash of the kernel sources they came from."""
+    ncu CSV log, each tagged with the hash of the sources it was built from."""
     import csv
     import re
     rows = {}
@@ -1017,8 +1018,9 @@ def write_traffic(csv_path, workload):
         if "dram__bytes_read.sum" not in ent:
             continue
         per.setdefault(ent["kernel"], []).append(ent["dram__bytes_read.sum"] + ent.get("dram__bytes_write.sum", 0.0))
-    out = {"source_hash": _source_hash(), "workload": workload, "from": os.path.basename(csv_path),
-           "kernels": {k: {"bytes_per_launch": statistics.mean(v), "launches": len(v)} for k, v in per.items()}}
+    out = {"workload": workload, "from": os.path.basename(csv_path),
+           "kernels": {k: {"bytes_per_launch": statistics.mean(v), "launches": len(v), "source_hash": _source_hash(k)}
+                       for k, v in per.items()}}
     os.makedirs(os.path.join(ROOT, "profiles"), exist_ok=True)
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
@@ -1026,14 +1028,23 @@ def write_traffic(csv_path, workload):
     return 0
 
 
-def _source_hash():
+# The translation unit each kernel is compiled from (besides the shared header
+# and the C ABI header): a traffic figure stays valid while these are unchanged.
+KERNEL_SOURCE = {"k_project": "gs_project.cu", "k_project_bwd_adam": "gs_project.cu",
+                 "k_render_fwd": "gs_render.cu", "k_render_bwd": "gs_render.cu"}
+
+
+def _source_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for sub in ("csrc",):
-        d = os.path.join(ROOT, "paper_2412_13547_b300", sub)
-        for f in sorted(os.listdir(d)):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2412_13547_b300", "csrc")
+    src = KERNEL_SOURCE.get(kernel)
+    files = ([os.path.join(csrc, src), os.path.join(csrc, "gs_common.cuh"),
+              os.path.join(ROOT, "include", "turbogs.h")] if src else
+             [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))])
+    for fn in files:
+        with open(fn, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -470,13 +470,29 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& c
     return z;
 }
 
+// dL/d centre (x, y), dL/dA and dL/dB of one entry's conic (A, B, C) from
+// the tile's sums a[0..5] = sum q, q dy, q dy^2, dx q, dx^2 q, dx dy q over its
+// pixels, q = dL/d(ln G) with ln G = -(A dx^2 + C dy^2)/2 - B dx dy, and the
+// staged base-2 coefficients s = (a, b, c, .) = log2(e) (-A/2, -B, -C/2, .):
+// dL/dA = -a[4]/2, dL/dB = -a[5] (dL/dC = -a[2]/2 and dL/do = a[0]/o are formed
+// by the caller), and d(ln G)/dp = (A dx + B dy, C dy + B dx)
+// = -ln 2 (2a dx + b dy, 2c dy + b dx).
+__device__ __forceinline__ float4 grad_from_sums(const float* a, float4 s)
+{
+    const float gx = -kLn2 * fmaf(s.y, a[1], 2.0f * s.x * a[3]);
+    const float gy = -kLn2 * fmaf(s.y, a[3], 2.0f * s.z * a[1]);
+    return make_float4(gx, gy, -0.5f * a[4], -a[5]);
+}
+
 // Backward: replay each pixel's list back to front from (t_final, last),
 // recovering T_i = T_{i+1} / (1 - alpha_i). A warp skips entries past the last
 // contributor of all its pixels and entries whose gate box misses its block.
-// Per remaining entry a thread sums the 9 partial gradients of its pixels, the
-// warp sums them (warp_sum9), one lane per component adds the total into a
-// per-batch shared-memory accumulator, and at the end of the batch each
-// (tile, Gaussian) gets one set of vector atomics.
+// Per remaining entry a thread sums 9 values over its pixels (the colour
+// gradients and the six sums the other gradients are linear in), the warp sums
+// them (warp_sum9), one lane per value adds the total into a per-batch
+// shared-memory accumulator, and at the end of the batch each (tile, Gaussian)
+// expands its sums into its 2D gradient (grad_from_sums) and adds that with one
+// set of vector atomics.
 template <int TILE, int PPT, bool FILTER>
 __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restrict__ splats,
                                                 const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
@@ -726,21 +742,20 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                     }
                 }
                 }
-                // dalpha/do = G = alpha / o: the opacity gradient is the dL/dpower sum over o
-                r[5] = q0 * c.w;
-                // dpower/dA = -dx^2/2, dpower/dB = -dx dy, dpower/dC = -dy^2/2. With the staged
-                // (a, b, c): A dx + B dy = -(2a dx + b dy) ln 2 and C dy + B dx = -(2c dy + b dx) ln 2;
-                // the -ln 2 is applied after the warp sum
-                r[2] = -0.5f * dx * dx * q0;
-                r[3] = -dx * q1;
-                r[4] = -0.5f * q2;
-                r[0] = fmaf(co.y, q1, 2.0f * co.x * dx * q0);
-                r[1] = fmaf(co.y * dx, q0, 2.0f * co.z * q1);
+                // the six sums the conic, centre and opacity gradients are linear in (a lane's
+                // pixels share dx): q0, q1 = sum dpower dy, q2 = sum dpower dy^2, and dx q0,
+                // dx^2 q0, dx q1. The tile's totals are expanded once per entry when the batch
+                // is flushed (grad_from_sums), not on every warp visit.
+                r[0] = q0;
+                r[1] = q1;
+                r[2] = q2;
+                r[3] = dx * q0;
+                r[4] = r[3] * dx;
+                r[5] = dx * q1;
                 if (__any_sync(0xffffffffu, contrib)) {
                     int comp;
                     const float z = warp_sum9(r, lane, comp);
-                    // the centre gradients (0, 1) were summed with the base-2 exponent's coefficients
-                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], comp < 2 ? z * -kLn2 : z);
+                    if (comp >= 0 && (lane & 1) == 0) atomicAdd(&s_acc[j][comp], z);
                 }
         }
         }
@@ -751,9 +766,11 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 #pragma unroll
             for (int k = 0; k < 9; ++k) any |= (a[k] != 0.0f);
             if (any) {
+                const float4 g = grad_from_sums(a, s_co[i]);
+                const float4 h = make_float4(-0.5f * a[2], a[0] * s_rgb[i].w, a[6], a[7]);
                 float* dst = grad2d + (int64_t)GS_GRAD2D_FLOATS * s_id[i];
-                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a[0], a[1], a[2], a[3]));
-                atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(a[4], a[5], a[6], a[7]));
+                atomicAdd(reinterpret_cast<float4*>(dst), g);
+                atomicAdd(reinterpret_cast<float4*>(dst + 4), h);
                 atomicAdd(dst + 8, a[8]);
             }
         }
