@@ -267,6 +267,13 @@ __device__ __forceinline__ float pk_sum(f32x2 a)
     unpk(a, x, y);
     return x + y;
 }
+// -(x + y) of the two halves, one add with both operands negated.
+__device__ __forceinline__ float pk_sum_neg(f32x2 a)
+{
+    float x, y;
+    unpk(a, x, y);
+    return -x - y;
+}
 __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
 {
     f32x2 r;

@@ -336,8 +336,10 @@ __device__ __forceinline__ void render_fwd_tile(int tile, const float4* __restri
                     for (int k = 0; k < PPT; ++k) {
                         if (!use[k]) continue;
                         const float alpha = fminf(kAlphaMax, exp2_sfu(e2[k]));
-                        const float w = alpha * T[k];
-                        const float Tn = T[k] - w;  // T (1 - alpha) in two operations, w reused
+                        // T (1 - alpha) in two operations with w reused, rounding pinned so that no
+                        // launch shape contracts it differently
+                        const float w = __fmul_rn(alpha, T[k]);
+                        const float Tn = __fsub_rn(T[k], w);
                         if (Tn < kTStop) { done[k] = true; --n_live; continue; }
                         C0[k] = fmaf(c.x, w, C0[k]);
                         C1[k] = fmaf(c.y, w, C1[k]);
@@ -552,7 +554,7 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             TP[q] = pk(T[2 * q], T[2 * q + 1]);
-            gSP[q] = pk(gS[2 * q], gS[2 * q + 1]);
+            gSP[q] = pk(-gS[2 * q], -gS[2 * q + 1]);  // the paired form carries -g.S
             g0P[q] = pk(g0[2 * q], g0[2 * q + 1]);
             g1P[q] = pk(g1[2 * q], g1[2 * q + 1]);
             g2P[q] = pk(g2[2 * q], g2[2 * q + 1]);
@@ -671,36 +673,39 @@ __device__ __forceinline__ void render_bwd_tile(int tile, const float4* __restri
                         const bool u0 = pos < n_last[2 * q] && splat_gate(e0, co.w);
                         const bool u1 = pos < n_last[2 * q + 1] && splat_gate(e1, co.w);
                         const float a0 = exp2_sfu(e0), a1 = exp2_sfu(e1);  // alpha before the clamp
-                        const float al0 = u0 ? fminf(kAlphaMax, a0) : 0.0f;
-                        const float al1 = u1 ? fminf(kAlphaMax, a1) : 0.0f;
-                        // the opacity and conic terms only below the clamp (al < kAlphaMax: al is
-                        // the unclamped alpha of a replayed pixel, or 0)
-                        const f32x2 aP = pk(al0 < kAlphaMax ? al0 : 0.0f, al1 < kAlphaMax ? al1 : 0.0f);
-                        const f32x2 alP = pk(al0, al1);
+                        // with the signs folded in: nal = -alpha (clamped), nw = -w, and gSP = -g.S,
+                        // so that dL/dalpha = T_i g.c - (1 / (1 - alpha)) g.S is one multiply and one
+                        // FMA; the colour and dL/dpower sums come out negated (pk_sum_neg below)
+                        const float nal0 = u0 ? fmaxf(-kAlphaMax, -a0) : 0.0f;
+                        const float nal1 = u1 ? fmaxf(-kAlphaMax, -a1) : 0.0f;
+                        // the opacity and conic terms only below the clamp (nal > -kAlphaMax: -nal
+                        // is the unclamped alpha of a replayed pixel, or 0)
+                        const f32x2 naP = pk(nal0 > -kAlphaMax ? nal0 : 0.0f, nal1 > -kAlphaMax ? nal1 : 0.0f);
+                        const f32x2 nalP = pk(nal0, nal1);
                         float o0, o1;
-                        unpk(sub2(oneP, alP), o0, o1);
+                        unpk(add2(oneP, nalP), o0, o1);
                         const f32x2 invP = pk(__fdividef(1.0f, o0), __fdividef(1.0f, o1));
                         const f32x2 TiP = mul2(TP[q], invP);
-                        const f32x2 wP = mul2(alP, TiP);
-                        r6P = fma2(wP, g0P[q], r6P);
-                        r7P = fma2(wP, g1P[q], r7P);
-                        r8P = fma2(wP, g2P[q], r8P);
+                        const f32x2 nwP = mul2(nalP, TiP);
+                        r6P = fma2(nwP, g0P[q], r6P);
+                        r7P = fma2(nwP, g1P[q], r7P);
+                        r8P = fma2(nwP, g2P[q], r8P);
                         const f32x2 gcP = fma2(g2P[q], czP, fma2(g1P[q], cyP, mul2(g0P[q], cxP)));
-                        const f32x2 dalP = mul2(invP, sub2(mul2(TP[q], gcP), gSP[q]));
-                        gSP[q] = fma2(wP, gcP, gSP[q]);
+                        const f32x2 dalP = fma2(TiP, gcP, mul2(invP, gSP[q]));
+                        gSP[q] = fma2(nwP, gcP, gSP[q]);
                         TP[q] = TiP;
-                        const f32x2 dpP = mul2(aP, dalP);
+                        const f32x2 dpP = mul2(naP, dalP);
                         const f32x2 tP = mul2(dpP, dyP);
                         q0P = add2(q0P, dpP);
                         q1P = add2(q1P, tP);
                         q2P = fma2(tP, dyP, q2P);
                     }
-                    q0 = pk_sum(q0P);
-                    q1 = pk_sum(q1P);
-                    q2 = pk_sum(q2P);
-                    r[6] = pk_sum(r6P);
-                    r[7] = pk_sum(r7P);
-                    r[8] = pk_sum(r8P);
+                    q0 = pk_sum_neg(q0P);
+                    q1 = pk_sum_neg(q1P);
+                    q2 = pk_sum_neg(q2P);
+                    r[6] = pk_sum_neg(r6P);
+                    r[7] = pk_sum_neg(r7P);
+                    r[8] = pk_sum_neg(r8P);
                 } else {
                 // gates of all this thread's pixels first (branch-free), then the replay
                 r[6] = r[7] = r[8] = 0.0f;
