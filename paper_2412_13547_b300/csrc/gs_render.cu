@@ -126,9 +126,10 @@ template <int TILE, int PPT>
 struct TileGeom {
     static constexpr int PIXELS = TILE * TILE;
     static constexpr int THREADS = PIXELS / PPT;
-    // staged list entries per batch: 256, but 192 for the 64-thread CTAs of tile 16 at 4 pixels per
-    // thread (the backward's default), whose staging arrays then leave room for more CTAs per SM
-    static constexpr int BATCH = (TILE == 16 && PPT == 4) ? 192 : (PIXELS < 256 ? PIXELS : 256);
+    // staged list entries per batch: 256, but 176 for the 64-thread CTAs of tile 16 at 4 pixels per
+    // thread (the backward's default), whose staging arrays then leave shared memory for 13 CTAs
+    // per SM
+    static constexpr int BATCH = (TILE == 16 && PPT == 4) ? 176 : (PIXELS < 256 ? PIXELS : 256);
     static constexpr int WROWS = 4 * PPT;        // rows of a warp's block
     static constexpr int WCOLS = TILE / 8;       // warp blocks across the tile
 };
@@ -801,12 +802,13 @@ constexpr int fwd_min_blocks()
 }
 
 // The backward at tile 16 and 4 pixels per thread (64-thread CTAs) is held to
-// 12 CTAs per SM (78 registers, no spills): 5% faster than the 92 registers it
-// takes unbounded; 14 or 16 CTAs gave no gain or spilled.
+// 13 CTAs per SM (69 registers, no spills; 176-entry batches, so that shared
+// memory holds 13): 5% faster than 12 CTAs with 192-entry batches, and 14 CTAs
+// with 160-entry batches gave no more.
 template <int TILE, int PPT>
 constexpr int bwd_min_blocks()
 {
-    return (TILE == 16 && PPT == 4) ? 12 : 1;
+    return (TILE == 16 && PPT == 4) ? 13 : 1;
 }
 
 template <int TILE, int PPT, bool MULTI, bool FILTER, bool COUNT>
