@@ -146,7 +146,8 @@ int32_t gs_adam(const GsAdamTensor* tensors, int32_t count, float beta1, float b
     a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)step)));
     a.row_mask = row_mask;
     int64_t bx = (max_work + 255) / 256;
-    if (bx > 148 * 8) bx = 148 * 8;
+    const int64_t bmax = (int64_t)gs_host::sm_count() * 8;
+    if (bx > bmax) bx = bmax;
     dim3 grid((unsigned)bx, (unsigned)count);
     gs::launch(k_adam, grid, 256, 0, reinterpret_cast<cudaStream_t>(stream), a);
     return gs_host::check_launch("gs_adam");

@@ -16,6 +16,26 @@ void set_error(const char* msg)
     std::snprintf(g_err, sizeof(g_err), "%s", msg);
 }
 
+int sm_count()
+{
+    constexpr int kMaxDevices = 64;
+    static int cached[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 148;
+    }
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 148;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 int32_t check_launch(const char* what)
 {
     cudaError_t e = cudaGetLastError();

@@ -31,7 +31,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItemsPerThread = 8;
 constexpr int kTileItems = kSortThreads * kItemsPerThread;  // 2048
 constexpr int kRadixBins = 256;
-constexpr int kMaxSortBlocks = 148 * 4;  // one wave of the downsweep (64 registers: 4 CTAs per SM)
+constexpr int kSortBlocksPerSM = 4;  // one wave of the downsweep (64 registers: 4 CTAs per SM)
 constexpr uint32_t kCulledKey = 0xffffffffu;  // depth key of a culled Gaussian (a visible one never takes it)
 
 __device__ __forceinline__ int64_t sort_count(const int64_t* d_num, int64_t cap)
@@ -303,7 +303,8 @@ int sort_blocks(int64_t cap)
 {
     int64_t tiles = (cap + kTileItems - 1) / kTileItems;
     if (tiles < 1) tiles = 1;
-    return (int)(tiles < kMaxSortBlocks ? tiles : kMaxSortBlocks);
+    const int64_t wave = (int64_t)gs_host::sm_count() * kSortBlocksPerSM;
+    return (int)(tiles < wave ? tiles : wave);
 }
 
 // ---------------------------------------------------------------------------
@@ -1011,7 +1012,7 @@ int32_t gs_bin_sort(int32_t n, const int32_t* rects, const int32_t* tiles_touche
         cudaFuncSetAttribute(k_seg_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2h);
         cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     }
-    const int lvl2_blocks = 148 * 8;
+    const int lvl2_blocks = gs_host::sm_count() * 8;
     gs::launch(k_seg_hist, lvl2_blocks, kLvlThreads, smem2h, st, TX, TY, w.rowstart, w.rowlen, w.segoff, w.NS,
                w.rowlist, num_pairs, capacity, w.M2);
     const int nsb2 = (NSR + kScanRows - 1) / kScanRows;

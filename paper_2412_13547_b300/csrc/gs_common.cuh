@@ -576,4 +576,7 @@ bool make_dil(const GsCamera* cam, const GsDilation* in, gs::Dil* out);
 // Fills the device view table from the caller's; checks cameras and dilations
 // (one tile size for all views).
 bool make_batch(const GsView* views, int nviews, gs::Batch* out);
+// Streaming multiprocessors of the current device (read once per device; 148
+// if the query fails), for the grids sized to whole waves.
+int sm_count();
 }  // namespace gs_host

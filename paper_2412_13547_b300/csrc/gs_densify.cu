@@ -417,7 +417,8 @@ bool check_rows(const GsRowTensor* t, int count, bool need_src)
 int grid_for(int64_t work)
 {
     int64_t b = (work + 255) / 256;
-    return (int)(b > 148 * 16 ? 148 * 16 : (b < 1 ? 1 : b));
+    const int64_t bmax = (int64_t)gs_host::sm_count() * 16;
+    return (int)(b > bmax ? bmax : (b < 1 ? 1 : b));
 }
 
 }  // namespace

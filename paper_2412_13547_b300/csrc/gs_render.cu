@@ -1341,7 +1341,7 @@ int32_t gs_loss_l1_batch(const GsView* views, int32_t nviews, gs_stream_t stream
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     gs::launch(k_loss_zero, 1, 32, 0, st, b);
     int64_t bx = (pmax + 255) / 256;
-    const int64_t cap = (148 * 16 + nviews - 1) / nviews;
+    const int64_t cap = ((int64_t)gs_host::sm_count() * 16 + nviews - 1) / nviews;
     if (bx > cap) bx = cap;
     gs::launch(k_loss_l1, dim3((unsigned)bx, (unsigned)nviews), 256, 0, st, b);
     return gs_host::check_launch("gs_loss_l1");
